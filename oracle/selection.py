@@ -1,0 +1,61 @@
+"""Fraction-f slice choice and norm estimates (oracle; test infrastructure only).
+
+Methods, "Summing a fraction of the paths": summing a randomly chosen fraction
+f of the paths yields a state of norm ~f and fidelity ~f (Eq. fidelity_1);
+a single path p has fidelity <psi_p|psi_p> (Eq. fidelity_2).  The paper does
+not say how the paths are drawn; the reading used here:
+  n_f = max(1, floor(f * P + 1/2)) (ties round half up), capped at P;
+  the chosen set is the first n_f entries of a Fisher-Yates shuffle of
+  0..P-1 driven by SplitMix64(seed), j = next() mod (i + 1) for i = P-1..1;
+  returned in ascending order.  No rescaling of the partial sums.
+SplitMix64 follows its published definition (Steele, Lea, Flood 2014):
+  x += 0x9E3779B97F4A7C15; z = x;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EB;  return z ^ (z >> 31).
+"""
+from __future__ import annotations
+
+import math
+from typing import List
+
+import numpy as np
+
+_M64 = (1 << 64) - 1
+
+
+class SplitMix64:
+    def __init__(self, seed: int):
+        self.x = seed & _M64
+
+    def next(self) -> int:
+        self.x = (self.x + 0x9E3779B97F4A7C15) & _M64
+        z = self.x
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+        return z ^ (z >> 31)
+
+
+def n_selected(fidelity: float, P: int) -> int:
+    return int(min(P, max(1, math.floor(fidelity * P + 0.5))))
+
+
+def select_slices(P: int, fidelity: float, seed: int) -> List[int]:
+    a = list(range(P))
+    rng = SplitMix64(seed)
+    for i in range(P - 1, 0, -1):
+        j = rng.next() % (i + 1)
+        a[i], a[j] = a[j], a[i]
+    return sorted(a[:n_selected(fidelity, P)])
+
+
+def norm_estimate(amps: np.ndarray, n_qubits: int) -> float:
+    """Estimated <psi~|psi~> from a sample of amplitudes: 2^n * mean |a|^2."""
+    a = np.asarray(amps).reshape(-1)
+    return float((2.0 ** n_qubits) * np.mean(np.abs(a) ** 2))
+
+
+def overlap_fidelity(psi_exact: np.ndarray, psi_partial: np.ndarray) -> float:
+    """|<psi|psi~>|^2 / <psi~|psi~> (Eq. fidelity_1 / fidelity_2)."""
+    a = np.asarray(psi_exact).reshape(-1)
+    b = np.asarray(psi_partial).reshape(-1)
+    return float(abs(np.vdot(a, b)) ** 2 / np.vdot(b, b).real)

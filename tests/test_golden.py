@@ -1,0 +1,47 @@
+"""Checks against values printed in the paper (tests/golden/paper_values.json)."""
+import json
+import os
+
+import numpy as np
+
+from oracle import permute as PM
+from qflex_inputs import c2_problem, cz_counts
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+def test_golden_permutation_moves():
+    g = GOLD["permutation_example"]
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=(3,) * 7)
+    cur = list(g["source"])
+    y = x
+    for kind, gamma, new in g["moves"]:
+        y = PM.apply_move(y, cur, list(new), kind, gamma)
+        cur = list(new)
+    assert "".join(cur) == g["target"]
+    assert np.array_equal(y, PM.permute(x, [g["source"].index(c) for c in g["target"]]))
+
+
+def test_golden_bris70_sizes():
+    g = GOLD["bris70_sizes"]
+    uncut = 2 ** (g["uncut_rank"] * g["K"]) * g["bytes_per_entry"]
+    assert uncut / 1e12 > g["min_terabytes"]
+    assert 2 ** (g["n_cuts"] * g["K"]) == 2 ** 16
+    assert 2 ** (g["cut_rank"] * g["K"]) == 2 ** 28
+
+
+def test_golden_7x7_sizes():
+    g = GOLD["grid7x7_d40_sizes"]
+    p = c2_problem(0, t=g["t"])
+    K = cz_counts(p.circuit)
+    assert int(np.prod([2 ** int(K[e]) for e in p.cut_edges])) == g["n_paths"]
+    assert 2 ** (6 * int(K[0])) == g["region_entries"]
+
+
+def test_golden_frugal_acceptance():
+    g = GOLD["frugal_acceptance"]
+    for nc, acc, batches in g["cases"]:
+        p = 1 - (1 - 1 / g["M"]) ** nc
+        assert abs(p - acc) < 5e-5
+        assert abs(1e6 / p - batches) / batches < 1e-3

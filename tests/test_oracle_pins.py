@@ -1,0 +1,252 @@
+"""Pins of the FP64 oracle against things other than itself (no GPU).
+
+Each pin is chosen so that a plausible mistake in the oracle (dropped term,
+wrong sign or index, transposed operand) fails at least one of them:
+closed forms for the gates, a brute-force Kronecker-product unitary, the
+state-vector definition, unit norm, slice-sum == uncut, per-slice projector
+substitution, the exact shift rule vs finite differences vs the adjoint, and
+the paper's worked permutation example.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import gates as G
+from oracle import gradients as GR
+from oracle import network as NW
+from oracle import permute as PM
+from oracle import selection as SEL
+from oracle import statevector as SV
+from qflex_inputs import (c1_problem, grid_lattice, grid_problem,
+                          random_bitstrings, random_circuit)
+
+
+# ---------------------------------------------------------------- gates
+def test_gate_closed_forms():
+    assert np.allclose(G.SX @ G.SX, G.X)
+    assert np.allclose(G.SY @ G.SY, G.Y)
+    assert np.allclose(G.T @ G.T, np.diag([1, 1j]))
+    assert np.allclose(G.H @ G.H, np.eye(2))
+    for U in (G.H, G.T, G.SX, G.SY, G.CZ):
+        assert np.allclose(U.conj().T @ U, np.eye(U.shape[0]))
+    assert np.allclose(G.rotation("RX", np.pi), -1j * G.X)
+    for kind, P in (("RX", G.X), ("RY", G.Y), ("RZ", G.Z)):
+        for th in (0.3, 2.0, 5.9):
+            assert np.allclose(G.rotation(kind, th), scipy.linalg.expm(-0.5j * th * P))
+
+
+def test_cz_schmidt_split_sums_to_cz():
+    # (-1)^{ab} = sum_k |k><k|_a (x) Z^k_b, lower-index qubit first
+    acc = sum(np.kron(G.cz_half("proj", k), G.cz_half("z", k)) for k in (0, 1))
+    assert np.allclose(acc, G.CZ)
+
+
+# ---------------------------------------------------------------- state vector
+def _kron_unitary(circ):
+    n = circ.n
+    U = np.eye(1 << n, dtype=np.complex128)
+    for g in sorted(circ.gates, key=lambda g: g.cycle):
+        if g.kind == "CZ":
+            d = np.ones(1 << n, dtype=np.complex128)
+            for idx in range(1 << n):
+                if (idx >> (n - 1 - g.q0)) & 1 and (idx >> (n - 1 - g.q1)) & 1:
+                    d[idx] = -1
+            M = np.diag(d)
+        else:
+            ops = [np.eye(2)] * n
+            ops[g.q0] = G.single_qubit_matrix(g.kind, circ.angles, g.param)
+            M = ops[0]
+            for o in ops[1:]:
+                M = np.kron(M, o)
+        U = M @ U
+    return U
+
+
+@pytest.mark.parametrize("rot", [False, True])
+def test_statevector_vs_kronecker_unitary(rot):
+    circ = random_circuit(grid_lattice(2, 3), 10, seed=4, rotations=rot)
+    U = _kron_unitary(circ)
+    psi = SV.final_state(circ).reshape(-1)
+    assert np.allclose(psi, U[:, 0], atol=1e-13)
+
+
+def test_identity_circuit_amplitude():
+    circ = random_circuit(grid_lattice(2, 2), 0, seed=0)   # H then H
+    psi = SV.final_state(circ).reshape(-1)
+    assert abs(psi[0] - 1) < 1e-14 and np.allclose(psi[1:], 0)
+
+
+# ---------------------------------------------------------------- network
+@pytest.mark.parametrize("rows,cols,t,seed", [(2, 2, 8, 0), (2, 3, 12, 1), (3, 3, 16, 2)])
+def test_contraction_matches_statevector(rows, cols, t, seed):
+    p = grid_problem(rows, cols, t, seed, r0=1, c0=1, cuts=False, tile_rows=1, tile_cols=1)
+    bs = random_bitstrings(p.n, 3, seed)
+    a = NW.amplitudes(p, bs)
+    r = SV.amplitudes(p.circuit, bs, p.open_tile)
+    assert np.max(np.abs(a - r)) < 1e-14
+
+
+def test_c1_full_tile_norm_and_statevector():
+    p = c1_problem(0, full_tile=True)
+    bs = random_bitstrings(16, 1, 0)
+    a = NW.amplitudes(p, bs)[0]
+    assert abs(np.sum(np.abs(a) ** 2) - 1.0) < 1e-12
+    psi = SV.final_state(p.circuit).reshape(-1)
+    assert np.max(np.abs(a - psi)) < 1e-14       # tile = all qubits, qubit 0 most significant
+
+
+def test_slice_sum_equals_uncut_and_per_slice_substitution():
+    p = grid_problem(3, 4, 16, 3, r0=2, c0=2, cuts=True, tile_rows=1, tile_cols=2)
+    P = NW.n_slices(p.circuit, p.cut_edges)
+    assert P == 16
+    bs = random_bitstrings(p.n, 2, 5)
+    full = NW.amplitudes(p, bs)
+    ref = SV.amplitudes(p.circuit, bs, p.open_tile)
+    assert np.max(np.abs(full - ref)) < 1e-15
+    for s in (0, 7, 15):
+        vals = NW.slice_values(p.circuit, p.cut_edges, s)
+        got = NW.slice_amplitudes(p, bs[1], s)
+        want = SV.amplitudes(p.circuit, bs[1:], p.open_tile, cut_values=vals)[0]
+        assert np.max(np.abs(got - want)) < 1e-15
+
+
+def test_mixed_radix_first_cut_most_significant():
+    p = grid_problem(3, 4, 16, 3, r0=2, c0=2, cuts=True, tile_rows=1, tile_cols=2)
+    e0, e1 = p.cut_edges
+    assert NW.slice_values(p.circuit, p.cut_edges, 1) == {e0: 0, e1: 1}
+    assert NW.slice_values(p.circuit, p.cut_edges, 4) == {e0: 1, e1: 0}
+
+
+def test_planted_mistakes_fail_a_pin(monkeypatch):
+    """Plant plausible mistakes in the oracle's CZ split; a pin catches each."""
+    p = grid_problem(2, 3, 12, 1, r0=1, c0=1, cuts=True, tile_rows=1, tile_cols=1)
+    bs = random_bitstrings(p.n, 1, 2)
+    ref = SV.amplitudes(p.circuit, bs, p.open_tile)
+    orig = G.cz_half
+    # (a) a dropped sign: Z^k replaced by the identity -> the amplitude changes
+    monkeypatch.setattr(G, "cz_half", lambda role, k: orig("proj", k) if role == "proj" else np.eye(2))
+    assert np.max(np.abs(NW.amplitudes(p, bs) - ref)) > 1e-6
+    # (b) swapped split orientation: the full sum still matches, but a per-slice
+    #     value no longer equals the substituted state vector (which keeps the
+    #     stated orientation)
+    monkeypatch.setattr(G, "cz_half", lambda role, k: orig("z" if role == "proj" else "proj", k))
+    assert np.max(np.abs(NW.amplitudes(p, bs) - ref)) < 1e-14
+    vals = NW.slice_values(p.circuit, p.cut_edges, 1)
+    monkeypatch.setattr(G, "cz_half", orig)
+    want = SV.amplitudes(p.circuit, bs, p.open_tile, cut_values=vals)[0]
+    monkeypatch.setattr(G, "cz_half", lambda role, k: orig("z" if role == "proj" else "proj", k))
+    got = NW.slice_amplitudes(p, bs[0], 1)
+    assert np.max(np.abs(got - want)) > 1e-6
+
+
+# ---------------------------------------------------------------- gradients
+def test_shift_rule_fd_and_adjoint_agree():
+    circ = random_circuit(grid_lattice(2, 3), 12, seed=7, rotations=True)
+    bs = random_bitstrings(circ.n, 1, 3)
+    tile = [4, 5]
+
+    def amp(th):
+        return SV.amplitudes(circ, bs, tile, angles=th)[0]
+
+    params = list(range(circ.n_params))
+    sr = GR.shift_rule(amp, circ.angles, params)
+    fd = GR.finite_difference(amp, circ.angles, params)
+    assert np.max(np.abs(sr - fd)) < 1e-8
+    g = (np.random.default_rng(0).normal(size=4) + 1j * np.random.default_rng(1).normal(size=4))
+    adj = GR.statevector_adjoint(circ, bs, tile, g)
+    assert np.max(np.abs(adj - GR.loss_gradient(sr, g))) < 1e-12
+
+
+def test_network_shift_rule_matches_statevector():
+    p = grid_problem(2, 3, 12, 9, r0=1, c0=1, cuts=True, tile_rows=1, tile_cols=1, rotations=True)
+    bs = random_bitstrings(p.n, 1, 4)
+    params = [0, 5, p.circuit.n_params - 1]
+    tn = GR.shift_rule(lambda th: NW.amplitudes(p, bs, angles=th)[0], p.circuit.angles, params)
+    sv = GR.shift_rule(lambda th: SV.amplitudes(p.circuit, bs, p.open_tile, angles=th)[0],
+                       p.circuit.angles, params)
+    assert np.max(np.abs(tn - sv)) < 1e-14
+
+
+# ---------------------------------------------------------------- permutation
+def _brute_permute(x, perm):
+    out = np.empty([x.shape[p] for p in perm], dtype=x.dtype)
+    for j in itertools.product(*[range(d) for d in out.shape]):
+        i = [0] * x.ndim
+        for a, p in enumerate(perm):
+            i[p] = j[a]
+        out[j] = x[tuple(i)]
+    return out
+
+
+def test_permute_definition_brute_force():
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(2, 3, 4, 2)) + 1j * rng.normal(size=(2, 3, 4, 2))
+    for perm in ([3, 1, 0, 2], [0, 1, 2, 3], [2, 3, 1, 0]):
+        assert np.array_equal(PM.permute(x, perm), _brute_permute(x, perm))
+
+
+def test_paper_worked_permutation_example():
+    """abcdefg -> cfeadgb through L2 (abc|de|fg -> cae|bd|fg), R4 (-> cae|fd|gb),
+    L2 (-> cfe|ad|gb), as worked in Methods, "Cache-efficient index permutations"."""
+    rng = np.random.default_rng(1)
+    order = list("abcdefg")
+    x = rng.normal(size=(2,) * 7) + 1j * rng.normal(size=(2,) * 7)
+    s1, s2, s3 = list("caebdfg"), list("caefdgb"), list("cfeadgb")
+    y = PM.apply_move(x, order, s1, "L", 2)
+    y = PM.apply_move(y, s1, s2, "R", 4)
+    y = PM.apply_move(y, s2, s3, "L", 2)
+    direct = PM.permute(x, [order.index(c) for c in s3])
+    assert np.array_equal(y, direct)
+    with pytest.raises(ValueError):             # an L move may not touch the right group
+        PM.apply_move(x, order, list("abcdegf"), "L", 2)
+    moves = PM.lr_decompose(order, s3, 2, 4)
+    assert [m[:2] for m in moves] == [("L", 2), ("R", 4), ("L", 2)]
+    assert np.array_equal(PM.permute_lr(x, order, s3, 2, 4), direct)
+
+
+def test_lr_decomposition_random_binary_perms():
+    rng = np.random.default_rng(2)
+    n = 12
+    labels = [chr(ord("a") + i) for i in range(n)]
+    x = rng.normal(size=(2,) * n).astype(np.complex128)
+    for _ in range(10):
+        tgt = list(rng.permutation(labels))
+        want = PM.permute(x, [labels.index(c) for c in tgt])
+        assert np.array_equal(PM.permute_lr(x, labels, tgt, 3, 6), want)
+
+
+# ---------------------------------------------------------------- selection
+def test_splitmix64_published_vector():
+    r = SEL.SplitMix64(0)
+    assert [r.next() for _ in range(3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4,
+                                           0x06C45D188009454F]
+
+
+def test_fraction_selection():
+    assert SEL.n_selected(0.01, 65536) == 655
+    assert SEL.n_selected(0.5 / 1024, 1024) == 1          # 0.5 rounds half up
+    assert SEL.n_selected(1e-9, 1024) == 1
+    assert SEL.n_selected(2.0, 16) == 16
+    s = SEL.select_slices(1024, 0.1, 42)
+    assert len(s) == 102 and s == sorted(set(s)) and s == SEL.select_slices(1024, 0.1, 42)
+    assert s != SEL.select_slices(1024, 0.1, 43)
+    # every slice is equally likely: counts over seeds stay near their mean
+    cnt = np.zeros(64)
+    for seed in range(2000):
+        cnt[SEL.select_slices(64, 0.25, seed)] += 1
+    assert cnt.min() > 0.8 * 500 and cnt.max() < 1.2 * 500
+
+
+def test_all_slices_give_unit_norm_and_fraction_norm_is_reported():
+    p = grid_problem(3, 4, 16, 3, r0=2, c0=2, cuts=True, tile_rows=3, tile_cols=4)
+    bs = random_bitstrings(p.n, 1, 0)
+    full = NW.amplitudes(p, bs)[0]                   # tile = all 12 qubits
+    assert abs(np.sum(np.abs(full) ** 2) - 1) < 1e-12
+    part = NW.amplitudes(p, bs, slices=SEL.select_slices(16, 0.25, 1))[0]
+    nrm = float(np.sum(np.abs(part) ** 2))
+    assert 0.0 < nrm < 1.0                           # norm ~ f; value is reported, not gated
+    f = SEL.overlap_fidelity(full, part)
+    assert 0.0 < f <= 1.0 + 1e-12
