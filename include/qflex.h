@@ -1,0 +1,239 @@
+/*
+ * qflex_gb300 -- C ABI of a single-GPU (GB300, sm_103a) engine that contracts
+ * the 2D-grid tensor network of a random quantum circuit into output
+ * amplitudes, after Villalonga et al., "A flexible high-performance simulator
+ * for verifying and benchmarking quantum circuits implemented on real
+ * hardware" (arXiv:1811.09599, "qFlex").
+ *
+ * The calls follow the paper's problem statement: a circuit on a lattice
+ * (Methods, "Revised set of RQCs" and "Overview of the simulator"), a
+ * contraction ordering (Methods, "Remarks on the choice of cuts and
+ * contraction ordering"), a set of cut bonds whose values define independent
+ * paths (Methods, "Cutting indexes"), output bitstrings with an open tile of
+ * qubits whose 2^k amplitudes come out of one contraction (Methods, "Fast
+ * sampling technique"; SI A), and the fraction of paths summed for
+ * fidelity-f amplitudes (Methods, "Summing a fraction of the paths").
+ *
+ * Conventions for every call:
+ *  - Pointers documented "device" must be device memory of the plan's GPU
+ *    (e.g. torch tensor data); "host" pointers are ordinary host memory.  The
+ *    caller owns every input and output buffer.
+ *  - A plan owns one device workspace allocated in qflex_plan_create (the
+ *    paper preallocates scratch space once, Methods "Implementation of the
+ *    simulator"); no call allocates device memory afterwards.
+ *  - Calls that take a stream enqueue work on it and return at once; the
+ *    returned status covers argument checks and launches.  Errors detected on
+ *    the device (a bounded wait that ran out) set a status word that
+ *    qflex_plan_sync / qflex_device_status report.
+ *  - Nothing throws across the ABI; on failure the call returns a nonzero
+ *    qflex_status and qflex_last_error() describes it (thread-local string).
+ *  - Complex numbers are interleaved (re, im): complex64 = 2 x float,
+ *    complex128 = 2 x double.  Tensors are row-major.
+ */
+#ifndef QFLEX_GB300_H
+#define QFLEX_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QFLEX_ABI_VERSION 1
+
+typedef struct qflex_plan_s* qflex_plan;
+
+typedef enum {
+  QFLEX_OK = 0,
+  QFLEX_ERR_ARG = 1,            /* a null pointer, size or index out of range */
+  QFLEX_ERR_CIRCUIT = 2,        /* malformed circuit (gate on a non-edge, bad kind ...) */
+  QFLEX_ERR_PLAN = 3,           /* invalid ordering, or the plan exceeds the memory budget */
+  QFLEX_ERR_OOM = 4,            /* device allocation failed */
+  QFLEX_ERR_CUDA = 5,           /* a CUDA runtime call failed */
+  QFLEX_ERR_DEVICE_TIMEOUT = 6, /* a bounded device-side wait ran out (kernel returned early) */
+  QFLEX_ERR_UNSUPPORTED = 7     /* valid request this build does not handle (e.g. no GPU) */
+} qflex_status;
+
+/* Arithmetic of the complex GEMMs (the cross-slice sum is always FP64). */
+typedef enum {
+  QFLEX_FP32_SIMT = 0,  /* plain FP32, 4 real FMAs per complex MAC on CUDA cores */
+  QFLEX_TF32X3 = 1,     /* tcgen05 kind::tf32, 3-multiply complex trick, operands split
+                           hi+lo, products hi*hi + hi*lo + lo*hi, FP32 accumulate */
+  QFLEX_BF16X3 = 2,     /* same with bf16 hi+lo splits (kind::f16, bf16 inputs) */
+  QFLEX_BF16_PLAIN = 3, /* one bf16 product per part (reported, not gated) */
+  QFLEX_TF32_PLAIN = 4  /* one tf32 product per part (reported, not gated) */
+} qflex_precision;
+
+/* Gate kinds (Methods, "Revised set of RQCs"; rotations R_P(t) = exp(-i t P/2)). */
+enum {
+  QFLEX_GATE_H = 0, QFLEX_GATE_T = 1, QFLEX_GATE_SX = 2, QFLEX_GATE_SY = 3,
+  QFLEX_GATE_CZ = 4, QFLEX_GATE_RX = 5, QFLEX_GATE_RY = 6, QFLEX_GATE_RZ = 7
+};
+
+/* One gate: cycle (time step, gates sorted by it), kind, qubits (q1 = -1 for
+ * one-qubit gates), param = index into the angle vector for RX/RY/RZ, else -1. */
+typedef struct {
+  int32_t cycle, kind, q0, q1, param;
+} qflex_gate;
+
+typedef struct {
+  int32_t n_qubits;
+  const int32_t* edges;      /* host, [n_edges][2] qubit pairs (lattice bonds) */
+  int32_t n_edges;
+  const qflex_gate* gates;   /* host, [n_gates] */
+  int64_t n_gates;
+  int32_t n_params;          /* length of the angle vector */
+} qflex_circuit;
+
+/* Pairwise contraction order: steps[2i] = dst, steps[2i+1] = src; tensor q
+ * starts as qubit q's grid tensor; the result of a step keeps the id dst. */
+typedef struct {
+  const int32_t* steps;      /* host, [n_steps][2] */
+  int32_t n_steps;
+} qflex_ordering;
+
+typedef struct {
+  const qflex_circuit* circuit;
+  const qflex_ordering* ordering; /* NULL: absorb every qubit into qubit 0 in id order */
+  const int32_t* cut_edges;       /* host, indices into circuit->edges; first = most
+                                     significant digit of the slice id */
+  int32_t n_cuts;
+  const int32_t* open_tile;       /* host, qubit ids; amplitude index j has tile qubit t
+                                     as bit (n_open-1-t) */
+  int32_t n_open;
+} qflex_problem;
+
+typedef struct {
+  int64_t n_slices;          /* P = prod over cuts of 2^{K_e} (Methods, "Cutting indexes") */
+  int32_t n_qubits, n_params, n_open, n_steps;
+  int64_t max_tensor_elems;  /* largest intermediate (complex entries) */
+  size_t workspace_bytes;    /* device bytes owned by the plan */
+  int32_t n_tc_steps;        /* steps whose GEMM runs on the tensor cores */
+  int32_t n_persistent_buffers;
+} qflex_plan_info;
+
+/* Work of one qflex_amplitudes call, counted by replaying the schedule on the
+ * host (reuse of slice-independent tensors included). */
+typedef struct {
+  double cmacs;              /* complex multiply-adds of all GEMMs (8 real flops each) */
+  double tc_cmacs;           /* of which on the tensor cores */
+  double tc_mma_flops;       /* real tensor-core flops executed (3M x splits) */
+  double permute_bytes;      /* algorithmic bytes of operand permutations (read + write) */
+  int64_t launches;          /* kernels launched */
+  int64_t steps_executed;
+  double largest_gemm_cmacs; /* M*N*K of the largest GEMM */
+} qflex_cost;
+
+int32_t qflex_abi_version(void);
+const char* qflex_last_error(void);
+
+/* Build a plan: network metadata (grid-tensor layouts, bond dimensions
+ * 2^{K_e}), cut/slice indexing, ordering validation, per-step permutation and
+ * GEMM descriptors, buffer reuse across paths (SI A: tensors independent of
+ * a cut are built once and reused), and one device workspace.
+ * workspace_bytes_max = 0 means no limit.  device < 0 builds a host-only plan
+ * (no device memory, no CUDA calls) whose info/cost calls work and whose
+ * amplitude calls return QFLEX_ERR_UNSUPPORTED; used to check plans on hosts
+ * without a GPU.  Errors: QFLEX_ERR_ARG, QFLEX_ERR_CIRCUIT, QFLEX_ERR_PLAN,
+ * QFLEX_ERR_OOM, QFLEX_ERR_CUDA. */
+qflex_status qflex_plan_create(const qflex_problem* problem, qflex_precision prec,
+                               size_t workspace_bytes_max, int device, qflex_plan* out);
+void qflex_plan_destroy(qflex_plan plan);
+qflex_status qflex_plan_get_info(qflex_plan plan, qflex_plan_info* info);
+
+/* Cost of qflex_amplitudes(plan, ..., n_bs, slice_ids, n_slice_ids, ...).
+ * slice_ids: host, NULL = all slices. */
+qflex_status qflex_plan_cost(qflex_plan plan, int64_t n_bs, const int64_t* slice_ids,
+                             int64_t n_slice_ids, qflex_cost* out);
+
+/* Fraction-f path choice (Methods, "Summing a fraction of the paths"):
+ * n_f = max(1, floor(f P + 1/2)) capped at P, the first n_f entries of a
+ * Fisher-Yates shuffle of 0..P-1 driven by SplitMix64(seed), sorted.
+ * slice_ids: host, capacity >= n_f. */
+qflex_status qflex_select_slices(qflex_plan plan, double fidelity, uint64_t seed,
+                                 int64_t* slice_ids, int64_t capacity, int64_t* n_selected);
+
+/* Amplitudes of n_bs bitstrings, each with the open tile enumerated:
+ *   amps_out[b][j] = sum_{s in slice_ids} amp_s(x_b with tile bits j)
+ * angles:     device, double [n_params] (may be NULL when n_params == 0)
+ * bitstrings: device, uint8 [n_bs][n_qubits], one byte (0/1) per qubit; tile bits ignored
+ * slice_ids:  host, int64 [n_slice_ids] distinct values in [0, P); NULL = all P slices
+ * amps_out:   device, complex128 [n_bs][2^n_open], overwritten
+ * Grid tensors and GEMMs run in the plan's precision; the slice sum is FP64.
+ * Enqueued on `stream` (a cudaStream_t; NULL = legacy default stream). */
+qflex_status qflex_amplitudes(qflex_plan plan, const double* angles, const uint8_t* bitstrings,
+                              int64_t n_bs, const int64_t* slice_ids, int64_t n_slice_ids,
+                              double* amps_out, void* stream);
+
+/* Amplitudes and the gradient of L = Re sum_{b,j} conj(g[b][j]) amps[b][j] with respect to
+ * every angle (the paper has no gradients): environments of each grid tensor by the
+ * reverse pass through the same pairwise contractions, summed over slices, then the
+ * derivative of each grid tensor w.r.t. each rotation angle from prefix/suffix products of
+ * its qubit's gate line.  grad_amps: device complex128 [n_bs][2^n_open] (g);
+ * grad_angles: device double [n_params], overwritten.  Requires the FP32_SIMT or a
+ * tensor-core precision plan; intermediates of each slice are kept (checkpointed). */
+qflex_status qflex_amplitudes_grad(qflex_plan plan, const double* angles,
+                                   const uint8_t* bitstrings, int64_t n_bs,
+                                   const int64_t* slice_ids, int64_t n_slice_ids,
+                                   const double* grad_amps, double* amps_out,
+                                   double* grad_angles, void* stream);
+
+/* Per-kernel-class timing of a plan's launches, for roofline measurement.
+ * Classes: 0 grid tensors, 1 permutation / operand producer, 2 FP32 GEMM,
+ * 3 tensor-core GEMM, 4 slice sum.  mode != 0 is a bit mask of classes
+ * (bit c = class c): it clears the totals and starts recording a CUDA event
+ * pair around every launch of those classes in later qflex_amplitudes calls;
+ * mode = 0 stops recording.  If out != NULL the call synchronizes the
+ * recorded stream and returns the totals so far: launches, summed
+ * event-to-event milliseconds, algorithmic flops (8 per complex MAC for the
+ * GEMMs; `mma_flops` = real tensor-core flops executed) and algorithmic bytes
+ * (permutation: entries read x 8 + operand bytes written). */
+typedef struct {
+  int64_t launches[5];
+  double ms[5];
+  double flops[5];
+  double mma_flops[5];
+  double bytes[5];
+} qflex_profile;
+qflex_status qflex_plan_profile(qflex_plan plan, int32_t mode, qflex_profile* out);
+
+/* Synchronize the plan's last stream and report its device status word
+ * (QFLEX_ERR_DEVICE_TIMEOUT if a bounded wait ran out); the word is cleared. */
+qflex_status qflex_plan_sync(qflex_plan plan);
+
+/* ---------------- standalone hot-path kernels (same kernels the plan runs) ---------------- */
+
+/* Index permutation of a row-major complex64 tensor (Methods, "Cache-efficient index
+ * permutations"): out axis i = in axis perm[i], i.e.
+ *   out[j_0..j_{r-1}] = in[i] with i_{perm[a]} = j_a.
+ * in, out: device, complex64, distinct non-overlapping buffers of prod(dims) entries.
+ * dims, perm: host, [rank], rank <= 32.  Bit-exact (pure data movement).
+ * Power-of-two dims take the shared-memory tiled kernel; others a gather kernel. */
+qflex_status qflex_permute(const void* in, void* out, int32_t rank, const int64_t* dims,
+                           const int32_t* perm, void* stream);
+
+/* Complex GEMM C[m][n] = sum_k A[m][k] * B[n][k] (both operands K-contiguous),
+ * A: device complex64 [M][K], B: device complex64 [N][K], C: device complex64 [M][N].
+ * prec selects the arithmetic as in qflex_precision; tensor-core precisions need
+ * K % 8 == 0 and M >= 128 (other shapes run on the FP32 path).  workspace: device,
+ * at least qflex_cgemm_workspace_size() bytes (split operand planes). */
+qflex_status qflex_cgemm_workspace_size(int32_t prec, int64_t M, int64_t N, int64_t K,
+                                        size_t* bytes);
+qflex_status qflex_cgemm(int32_t prec, int64_t M, int64_t N, int64_t K, const void* A,
+                         const void* B, void* C, void* workspace, size_t workspace_bytes,
+                         void* stream);
+
+/* FP64 reduction sum_i |amps_i|^2 (Methods, "Summing a fraction of the paths": the
+ * norm <psi~|psi~> and fidelity estimates).  amps: device complex128 [n];
+ * out: device double [1], overwritten. */
+qflex_status qflex_norm(const double* amps, int64_t n, double* out, void* stream);
+
+/* Synchronize `device` and read (and clear) the library's device status word
+ * used by the standalone kernels.  *status = QFLEX_OK or QFLEX_ERR_DEVICE_TIMEOUT. */
+qflex_status qflex_device_status(int device, int32_t* status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QFLEX_GB300_H */

@@ -1,0 +1,235 @@
+"""Thin Python binding over the C ABI (argument marshalling only).
+
+Every computation runs in the CUDA library; PyTorch supplies device memory and
+streams.  Names follow include/qflex.h.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import PRECISIONS, check
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _i64_array(values):
+    if values is None:
+        return None, 0
+    arr = np.ascontiguousarray(np.asarray(values, dtype=np.int64).reshape(-1))
+    return arr, int(arr.size)
+
+
+class Plan:
+    """qflex_plan for one problem (circuit, ordering, cuts, open tile).
+
+    `problem` is a qflex_inputs.Problem (or any object with .circuit,
+    .cut_edges, .open_tile, .ordering).  device < 0 builds a host-only plan.
+    """
+
+    def __init__(self, problem, precision: str = "bf16x3", device: int = 0,
+                 workspace_bytes_max: int = 0):
+        self.lib = _lib.load()
+        circ = problem.circuit
+        self.n_qubits = circ.n
+        self.n_params = circ.n_params
+        self.precision = precision
+        self.device = device
+        edges = np.ascontiguousarray(circ.edge_array().reshape(-1), dtype=np.int32)
+        garr = circ.gate_array()
+        gates = (_lib.Gate * max(1, len(garr)))()
+        for i, row in enumerate(garr):
+            gates[i] = _lib.Gate(*[int(v) for v in row])
+        self._keep = [edges, gates]
+        self._circ = _lib.Circuit(circ.n, edges.ctypes.data_as(C.POINTER(C.c_int32)),
+                                  len(circ.edges), gates, len(garr), circ.n_params)
+        ordering = None
+        if problem.ordering is not None:
+            st = np.ascontiguousarray(np.asarray(problem.ordering, dtype=np.int32).reshape(-1))
+            self._keep.append(st)
+            ordering = _lib.Ordering(st.ctypes.data_as(C.POINTER(C.c_int32)), len(problem.ordering))
+            self._ordering = ordering
+        cuts = np.ascontiguousarray(np.asarray(problem.cut_edges, dtype=np.int32).reshape(-1))
+        tile = np.ascontiguousarray(np.asarray(problem.open_tile, dtype=np.int32).reshape(-1))
+        self._keep += [cuts, tile]
+        self.n_open = int(tile.size)
+        self._prob = _lib.Problem(C.pointer(self._circ),
+                                  C.pointer(ordering) if ordering is not None else None,
+                                  cuts.ctypes.data_as(C.POINTER(C.c_int32)), int(cuts.size),
+                                  tile.ctypes.data_as(C.POINTER(C.c_int32)), int(tile.size))
+        handle = C.c_void_p()
+        check(self.lib.qflex_plan_create(C.byref(self._prob), PRECISIONS[precision],
+                                         workspace_bytes_max, device, C.byref(handle)))
+        self.handle = handle
+
+    # ------------------------------------------------------------------ info
+    def info(self) -> dict:
+        inf = _lib.PlanInfo()
+        check(self.lib.qflex_plan_get_info(self.handle, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in inf._fields_}
+
+    @property
+    def n_slices(self) -> int:
+        return self.info()["n_slices"]
+
+    def cost(self, n_bs: int, slice_ids: Optional[Sequence[int]] = None) -> dict:
+        arr, n = _i64_array(slice_ids)
+        c = _lib.Cost()
+        ptr = arr.ctypes.data_as(C.POINTER(C.c_int64)) if arr is not None else None
+        check(self.lib.qflex_plan_cost(self.handle, n_bs, ptr, n, C.byref(c)))
+        return {k: getattr(c, k) for k, _ in c._fields_}
+
+    def select_slices(self, fidelity: float, seed: int) -> np.ndarray:
+        P = self.n_slices
+        out = np.zeros(P, dtype=np.int64)
+        n = C.c_int64()
+        check(self.lib.qflex_select_slices(self.handle, float(fidelity), C.c_uint64(seed),
+                                           out.ctypes.data_as(C.POINTER(C.c_int64)), P, C.byref(n)))
+        return out[: n.value].copy()
+
+    # ------------------------------------------------------------------ compute
+    def amplitudes(self, bitstrings: torch.Tensor, angles: Optional[torch.Tensor] = None,
+                   slice_ids: Optional[Sequence[int]] = None, out: Optional[torch.Tensor] = None,
+                   stream=None) -> torch.Tensor:
+        """complex128 [n_bs, 2^n_open] on the plan's device (qflex_amplitudes)."""
+        dev = torch.device("cuda", self.device)
+        assert bitstrings.dtype == torch.uint8 and bitstrings.is_cuda and bitstrings.is_contiguous()
+        n_bs = bitstrings.shape[0]
+        T = 1 << self.n_open
+        if out is None:
+            out = torch.empty((n_bs, T, 2), dtype=torch.float64, device=dev)
+        if angles is not None:
+            assert angles.dtype == torch.float64 and angles.is_cuda and angles.is_contiguous()
+        arr, n = _i64_array(slice_ids)
+        ptr = arr.ctypes.data_as(C.POINTER(C.c_int64)) if arr is not None else None
+        check(self.lib.qflex_amplitudes(self.handle, C.c_void_p(angles.data_ptr()) if angles is not None else None,
+                                        C.c_void_p(bitstrings.data_ptr()), n_bs, ptr, n,
+                                        C.c_void_p(out.data_ptr()), _stream_handle(stream)))
+        return torch.view_as_complex(out.view(n_bs, T, 2))
+
+    def amplitudes_grad(self, bitstrings, angles, grad_amps, slice_ids=None, stream=None):
+        """(amps, grad_angles) for L = Re sum conj(g) amps (qflex_amplitudes_grad)."""
+        dev = torch.device("cuda", self.device)
+        n_bs = bitstrings.shape[0]
+        T = 1 << self.n_open
+        amps = torch.empty((n_bs, T, 2), dtype=torch.float64, device=dev)
+        grad = torch.empty(max(1, self.n_params), dtype=torch.float64, device=dev)
+        g = torch.view_as_real(grad_amps.to(torch.complex128).contiguous()).contiguous()
+        arr, n = _i64_array(slice_ids)
+        ptr = arr.ctypes.data_as(C.POINTER(C.c_int64)) if arr is not None else None
+        check(self.lib.qflex_amplitudes_grad(self.handle, C.c_void_p(angles.data_ptr()),
+                                             C.c_void_p(bitstrings.data_ptr()), n_bs, ptr, n,
+                                             C.c_void_p(g.data_ptr()), C.c_void_p(amps.data_ptr()),
+                                             C.c_void_p(grad.data_ptr()), _stream_handle(stream)))
+        return torch.view_as_complex(amps.view(n_bs, T, 2)), grad[: self.n_params]
+
+    def profile_start(self, classes=_lib.PROFILE_CLASSES):
+        """Clear the per-class totals and record an event pair around every
+        launch of the named kernel classes."""
+        mask = sum(1 << _lib.PROFILE_CLASSES.index(c) for c in classes)
+        check(self.lib.qflex_plan_profile(self.handle, mask, None))
+
+    def profile_stop(self) -> dict:
+        """Stop recording; per-class launches, ms, flops, mma_flops, bytes."""
+        pr = _lib.Profile()
+        check(self.lib.qflex_plan_profile(self.handle, 0, C.byref(pr)))
+        return {cls: {"launches": pr.launches[i], "ms": pr.ms[i], "flops": pr.flops[i],
+                      "mma_flops": pr.mma_flops[i], "bytes": pr.bytes[i]}
+                for i, cls in enumerate(_lib.PROFILE_CLASSES)}
+
+    def sync(self):
+        check(self.lib.qflex_plan_sync(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.qflex_plan_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class QFlexAmplitudes(torch.autograd.Function):
+    """amps = QFlexAmplitudes.apply(angles, bitstrings, plan, slice_ids) (complex128).
+
+    Backward calls qflex_amplitudes_grad with the upstream cotangent; the
+    gradient convention for real angles and complex outputs is PyTorch's:
+    grad_angles = sum Re(conj(g) d amp / d angle).
+    """
+
+    @staticmethod
+    def forward(ctx, angles, bitstrings, plan, slice_ids=None):
+        ctx.plan = plan
+        ctx.slice_ids = slice_ids
+        ctx.save_for_backward(angles, bitstrings)
+        return plan.amplitudes(bitstrings, angles, slice_ids)
+
+    @staticmethod
+    def backward(ctx, g):
+        angles, bitstrings = ctx.saved_tensors
+        _, grad = ctx.plan.amplitudes_grad(bitstrings, angles, g, ctx.slice_ids)
+        return grad, None, None, None
+
+
+# ---------------------------------------------------------------------- kernels
+def permute(x: torch.Tensor, perm: Sequence[int], stream=None) -> torch.Tensor:
+    """qflex_permute: out axis i = in axis perm[i] (complex64, bit-exact)."""
+    lib = _lib.load()
+    assert x.dtype == torch.complex64 and x.is_cuda and x.is_contiguous()
+    dims = np.asarray(x.shape, dtype=np.int64)
+    p = np.asarray(perm, dtype=np.int32)
+    out = torch.empty([x.shape[i] for i in perm], dtype=x.dtype, device=x.device)
+    check(lib.qflex_permute(C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), x.dim(),
+                            dims.ctypes.data_as(C.POINTER(C.c_int64)),
+                            p.ctypes.data_as(C.POINTER(C.c_int32)), _stream_handle(stream)))
+    return out
+
+
+def cgemm(A: torch.Tensor, B: torch.Tensor, precision: str = "fp32", workspace=None,
+          stream=None) -> torch.Tensor:
+    """qflex_cgemm: C[m][n] = sum_k A[m][k] B[n][k] (complex64)."""
+    lib = _lib.load()
+    assert A.dtype == torch.complex64 and B.dtype == torch.complex64
+    M, K = A.shape
+    N, K2 = B.shape
+    assert K == K2
+    prec = PRECISIONS[precision]
+    need = C.c_size_t()
+    check(lib.qflex_cgemm_workspace_size(prec, M, N, K, C.byref(need)))
+    if workspace is None and need.value:
+        workspace = torch.empty(need.value, dtype=torch.uint8, device=A.device)
+    out = torch.empty((M, N), dtype=torch.complex64, device=A.device)
+    check(lib.qflex_cgemm(prec, M, N, K, C.c_void_p(A.data_ptr()), C.c_void_p(B.data_ptr()),
+                          C.c_void_p(out.data_ptr()),
+                          C.c_void_p(workspace.data_ptr()) if workspace is not None else None,
+                          need.value, _stream_handle(stream)))
+    return out
+
+
+def norm(amps: torch.Tensor, stream=None) -> torch.Tensor:
+    """qflex_norm: FP64 sum |a|^2 of a complex128 tensor (returns a 1-element tensor)."""
+    lib = _lib.load()
+    a = amps.contiguous()
+    assert a.dtype == torch.complex128 and a.is_cuda
+    out = torch.empty(1, dtype=torch.float64, device=a.device)
+    check(lib.qflex_norm(C.c_void_p(a.data_ptr()), a.numel(), C.c_void_p(out.data_ptr()),
+                         _stream_handle(stream)))
+    return out
+
+
+def device_status(device: int = 0) -> int:
+    lib = _lib.load()
+    v = C.c_int32()
+    check(lib.qflex_device_status(device, C.byref(v)))
+    return v.value

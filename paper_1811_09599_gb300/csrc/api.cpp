@@ -1,0 +1,948 @@
+// Host side of the C ABI (include/qflex.h): planner and executor.
+//
+// The planner turns the paper's problem statement into a fixed schedule:
+//  * network metadata (Methods, "Overview of the simulator"): bond exponent
+//    K_e per edge (number of CZs), per-qubit gate lines compiled into ops for
+//    the grid-tensor kernel, grid-tensor layouts [o?][bonds by neighbour id];
+//  * cuts (Methods, "Cutting indexes"): slice id s in mixed radix 2^{K_e} over
+//    the cut list, first cut most significant; a cut bond is removed from the
+//    views of its two grid tensors and contributes value * stride to their
+//    base offsets, so slicing moves no data;
+//  * the pairwise contraction order (Methods, "Remarks on the choice of cuts
+//    and contraction ordering"), each step = operand permutation into matrix
+//    form (Methods, "Implementation of the simulator") + complex GEMM;
+//  * reuse across paths (SI A: A, pB, pC, ppD are built once and B, AB once
+//    per outer-cut value): each step carries the set of cuts its result
+//    depends on and is re-run only when one of them changes; results reused
+//    across slices keep dedicated buffers, the others share memory by
+//    liveness;
+//  * one device workspace allocated at plan time (Methods, "Implementation
+//    of the simulator": scratch preallocated once).
+#include "qflex.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace qflex;
+
+namespace {
+
+thread_local std::string g_err;
+
+qflex_status fail(qflex_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+#define QF_CUDA(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(QFLEX_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+int ilog2(int64_t v) {
+  int b = 0;
+  while ((int64_t(1) << b) < v) ++b;
+  return b;
+}
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// A tensor as seen by a step: memory legs (cut legs removed) with strides.
+struct Ref {
+  bool grid = true;
+  int id = 0;                                  // qubit (grid) or buffer index
+  std::vector<int> legs;
+  std::vector<int64_t> strides;
+  std::vector<std::pair<int, int64_t>> cut_terms;  // (cut index, stride)
+  uint64_t dep = 0;                            // cuts the values depend on
+};
+
+struct Operand {
+  Ref ref;
+  bool direct = false;      // consumed in place by the GEMM (FP32 path, already in matrix form)
+  bool pow2 = true;
+  PermTile tile{};
+  GatherDesc gather{};
+};
+
+struct Step {
+  int dst = 0, src = 0;
+  Operand A, B;
+  int64_t M = 1, N = 1, K = 1;
+  bool tc = false;
+  int bn = 128;
+  int out_buf = -1;
+  uint64_t dep = 0;
+  std::vector<int> out_legs;
+  TcGemmMaps maps{};
+};
+
+struct Buf {
+  int64_t elems = 0;
+  int producer = -1, consumer = -1;
+  bool persistent = false;
+  size_t offset = 0;
+};
+
+}  // namespace
+
+struct qflex_plan_s {
+  int device = -1;
+  qflex_precision prec = QFLEX_FP32_SIMT;
+  int tc_kind = 0, nsplit = 1;
+  int n = 0, E = 0, n_params = 0;
+  std::vector<int> K;                          // per edge
+  std::vector<std::vector<int>> inc;           // per qubit: incident edges by neighbour id
+  std::vector<int> cuts, cut_of_edge, tile, tile_pos;
+  int64_t P = 1;
+  std::vector<int64_t> leg_dim;                // E bond legs then n output legs
+  std::vector<GridQubitMeta> gmeta;
+  std::vector<int2> gops;
+  int64_t grid_elems = 0;
+  int max_bits = 0;
+  std::vector<Ref> grid_ref;
+  std::vector<Step> steps;
+  std::vector<Buf> bufs;
+  Ref final_ref;
+  std::vector<int64_t> final_strides;          // per tile qubit, tile order
+  int64_t max_tensor = 0;
+  size_t grid_bytes = 0, arena_bytes = 0, opA_bytes = 0, opB_bytes = 0, total_bytes = 0;
+  int n_persistent = 0, n_tc = 0;
+  // device
+  char* d_ws = nullptr;
+  float2* d_grid = nullptr;
+  char* d_arena = nullptr;
+  void* d_opA = nullptr;
+  void* d_opB = nullptr;
+  GridQubitMeta* d_gmeta = nullptr;
+  int2* d_gops = nullptr;
+  int32_t* d_status = nullptr;
+  cudaStream_t last_stream = nullptr;
+  // profiling: event pairs around launches
+  bool profiling = false;
+  int32_t prof_mask = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  struct Rec { int cls; size_t e0; double flops, mma, bytes; };
+  std::vector<Rec> recs;
+  qflex_profile prof{};
+};
+
+namespace {
+
+size_t operand_bytes(const qflex_plan_s& p, bool tc, int64_t elems) {
+  if (!tc) return size_t(elems) * 8;
+  return size_t(elems) * 3 * p.nsplit * (p.tc_kind == 0 ? 4 : 2);
+}
+
+// Permutation descriptors taking `r` to the row-major order `target`.
+bool make_operand(const Ref& r, const std::vector<int>& target, const std::vector<int64_t>& leg_dim,
+                  Operand* op) {
+  op->ref = r;
+  std::vector<int64_t> dims, strides;
+  for (int l : target) {
+    auto it = std::find(r.legs.begin(), r.legs.end(), l);
+    if (it == r.legs.end()) return false;
+    dims.push_back(leg_dim[l]);
+    strides.push_back(r.strides[it - r.legs.begin()]);
+  }
+  op->pow2 = true;
+  for (int64_t d : dims) op->pow2 = op->pow2 && is_pow2(d);
+  if (op->pow2) {
+    std::vector<int64_t> w;
+    for (int a = int(dims.size()) - 1; a >= 0; --a)
+      for (int b = 0; b < ilog2(dims[a]); ++b) w.push_back(strides[a] << b);
+    if (!build_perm_tile(int(w.size()), w.data(), &op->tile)) return false;
+  } else {
+    if (dims.size() > size_t(kGatherMaxRank)) return false;
+    GatherDesc& g = op->gather;
+    g.rank = int(dims.size());
+    g.total = 1;
+    for (size_t a = 0; a < dims.size(); ++a) {
+      g.dims[a] = dims[a];
+      g.in_strides[a] = strides[a];
+      g.total *= dims[a];
+    }
+  }
+  return true;
+}
+
+int64_t leg_product(const std::vector<int>& legs, const std::vector<int64_t>& dim) {
+  int64_t v = 1;
+  for (int l : legs) v *= dim[l];
+  return v;
+}
+
+qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
+  const qflex_circuit* c = pr->circuit;
+  if (!c) return fail(QFLEX_ERR_ARG, "problem->circuit is NULL");
+  if (c->n_qubits <= 0 || c->n_qubits > 4096) return fail(QFLEX_ERR_CIRCUIT, "n_qubits out of range");
+  if (c->n_edges < 0 || (c->n_edges > 0 && !c->edges)) return fail(QFLEX_ERR_CIRCUIT, "bad edge list");
+  if (c->n_gates < 0 || (c->n_gates > 0 && !c->gates)) return fail(QFLEX_ERR_CIRCUIT, "bad gate list");
+  if (c->n_params < 0) return fail(QFLEX_ERR_CIRCUIT, "n_params < 0");
+  const int n = c->n_qubits, E = c->n_edges;
+  p.n = n;
+  p.E = E;
+  p.n_params = c->n_params;
+  // edges and adjacency
+  std::vector<std::pair<int, int>> ed(E);
+  for (int e = 0; e < E; ++e) {
+    int a = c->edges[2 * e], b = c->edges[2 * e + 1];
+    if (a < 0 || b < 0 || a >= n || b >= n || a == b)
+      return fail(QFLEX_ERR_CIRCUIT, "edge " + std::to_string(e) + " is not a pair of distinct qubits");
+    ed[e] = {std::min(a, b), std::max(a, b)};
+  }
+  {
+    auto s = ed;
+    std::sort(s.begin(), s.end());
+    if (std::adjacent_find(s.begin(), s.end()) != s.end()) return fail(QFLEX_ERR_CIRCUIT, "duplicate edge");
+  }
+  auto edge_of = [&](int a, int b) -> int {
+    const std::pair<int, int> key{std::min(a, b), std::max(a, b)};
+    for (int e = 0; e < E; ++e)
+      if (ed[e] == key) return e;
+    return -1;
+  };
+  p.inc.assign(n, {});
+  for (int e = 0; e < E; ++e) {
+    p.inc[ed[e].first].push_back(e);
+    p.inc[ed[e].second].push_back(e);
+  }
+  for (int q = 0; q < n; ++q)
+    std::sort(p.inc[q].begin(), p.inc[q].end(), [&](int x, int y) {
+      const int ox = ed[x].first == q ? ed[x].second : ed[x].first;
+      const int oy = ed[y].first == q ? ed[y].second : ed[y].first;
+      return ox < oy;
+    });
+  // gates: validate, count CZs per edge, per-qubit lines in time order
+  std::vector<int64_t> order(size_t(c->n_gates));
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int64_t x, int64_t y) { return c->gates[x].cycle < c->gates[y].cycle; });
+  p.K.assign(E, 0);
+  std::vector<std::vector<std::pair<int64_t, int>>> line(n);   // (gate index, edge or -1)
+  for (int64_t gi : order) {
+    const qflex_gate& g = c->gates[gi];
+    if (g.kind < 0 || g.kind > 7) return fail(QFLEX_ERR_CIRCUIT, "unknown gate kind");
+    if (g.q0 < 0 || g.q0 >= n) return fail(QFLEX_ERR_CIRCUIT, "gate qubit out of range");
+    if (g.kind == QFLEX_GATE_CZ) {
+      if (g.q1 < 0 || g.q1 >= n || g.q1 == g.q0) return fail(QFLEX_ERR_CIRCUIT, "bad CZ qubits");
+      const int e = edge_of(g.q0, g.q1);
+      if (e < 0) return fail(QFLEX_ERR_CIRCUIT, "CZ on a pair that is not a lattice edge");
+      ++p.K[e];
+      line[g.q0].push_back({gi, e});
+      line[g.q1].push_back({gi, e});
+    } else {
+      if (g.kind >= QFLEX_GATE_RX && (g.param < 0 || g.param >= c->n_params))
+        return fail(QFLEX_ERR_CIRCUIT, "rotation gate angle index out of range");
+      line[g.q0].push_back({gi, -1});
+    }
+  }
+  for (int e = 0; e < E; ++e)
+    if (p.K[e] > 20) return fail(QFLEX_ERR_PLAN, "bond with more than 20 CZs");
+  // legs
+  p.leg_dim.assign(E + n, 2);
+  for (int e = 0; e < E; ++e) p.leg_dim[e] = int64_t(1) << p.K[e];
+  // cuts and tile
+  p.cut_of_edge.assign(E, -1);
+  if (pr->n_cuts < 0 || (pr->n_cuts > 0 && !pr->cut_edges)) return fail(QFLEX_ERR_ARG, "bad cut list");
+  if (pr->n_cuts > 64) return fail(QFLEX_ERR_PLAN, "more than 64 cuts");
+  p.P = 1;
+  for (int i = 0; i < pr->n_cuts; ++i) {
+    const int e = pr->cut_edges[i];
+    if (e < 0 || e >= E || p.cut_of_edge[e] >= 0) return fail(QFLEX_ERR_ARG, "bad or repeated cut edge");
+    p.cut_of_edge[e] = i;
+    p.cuts.push_back(e);
+    if (p.P > (int64_t(1) << 50) >> p.K[e]) return fail(QFLEX_ERR_PLAN, "too many slices");
+    p.P <<= p.K[e];
+  }
+  p.tile_pos.assign(n, -1);
+  if (pr->n_open < 0 || pr->n_open > 30 || (pr->n_open > 0 && !pr->open_tile))
+    return fail(QFLEX_ERR_ARG, "bad open tile");
+  for (int t = 0; t < pr->n_open; ++t) {
+    const int q = pr->open_tile[t];
+    if (q < 0 || q >= n || p.tile_pos[q] >= 0) return fail(QFLEX_ERR_ARG, "bad or repeated tile qubit");
+    p.tile_pos[q] = t;
+    p.tile.push_back(q);
+  }
+  // grid tensors: [o if tile][bond legs by neighbour id], bits per bond leg,
+  // first CZ in time = most significant bit of the leg
+  p.gmeta.resize(n);
+  p.grid_ref.resize(n);
+  int64_t off = 0;
+  for (int q = 0; q < n; ++q) {
+    std::vector<int> low(E, 0);
+    int bits = 0;
+    for (int j = int(p.inc[q].size()) - 1; j >= 0; --j) {
+      low[p.inc[q][j]] = bits;
+      bits += p.K[p.inc[q][j]];
+    }
+    if (bits > 30) return fail(QFLEX_ERR_PLAN, "grid tensor with more than 2^30 entries");
+    GridQubitMeta& m = p.gmeta[q];
+    m.offset = off;
+    m.n_bits = bits;
+    m.op_begin = int(p.gops.size());
+    m.tile = p.tile_pos[q] >= 0;
+    m.qubit = q;
+    std::vector<int> seen(E, 0);
+    for (auto& [gi, e] : line[q]) {
+      const qflex_gate& g = c->gates[gi];
+      if (e < 0) {
+        p.gops.push_back(make_int2(g.kind, g.kind >= QFLEX_GATE_RX ? g.param : -1));
+      } else {
+        const int other = g.q0 == q ? g.q1 : g.q0;
+        const int bitpos = low[e] + p.K[e] - 1 - seen[e]++;
+        p.gops.push_back(make_int2((q < other ? kOpCzProj : kOpCzZ) | (bitpos << 8), -1));
+      }
+    }
+    m.op_count = int(p.gops.size()) - m.op_begin;
+    p.max_bits = std::max(p.max_bits, bits);
+    const int64_t entries = int64_t(1) << bits;
+    // full memory legs and strides
+    std::vector<int> legs;
+    if (m.tile) legs.push_back(E + q);
+    for (int e : p.inc[q]) legs.push_back(e);
+    std::vector<int64_t> strides(legs.size());
+    int64_t st = 1;
+    for (int a = int(legs.size()) - 1; a >= 0; --a) {
+      strides[a] = st;
+      st *= p.leg_dim[legs[a]];
+    }
+    Ref& r = p.grid_ref[q];
+    r.grid = true;
+    r.id = q;
+    for (size_t a = 0; a < legs.size(); ++a) {
+      const int l = legs[a];
+      if (l < E && p.cut_of_edge[l] >= 0) {
+        r.cut_terms.push_back({p.cut_of_edge[l], strides[a]});
+        r.dep |= uint64_t(1) << p.cut_of_edge[l];
+      } else {
+        r.legs.push_back(l);
+        r.strides.push_back(strides[a]);
+      }
+    }
+    off += entries * (m.tile ? 2 : 1);
+  }
+  p.grid_elems = off;
+  // ordering
+  std::vector<int32_t> def;
+  const int32_t* steps = nullptr;
+  int ns = 0;
+  if (pr->ordering) {
+    if (pr->ordering->n_steps < 0 || (pr->ordering->n_steps > 0 && !pr->ordering->steps))
+      return fail(QFLEX_ERR_ARG, "bad ordering");
+    steps = pr->ordering->steps;
+    ns = pr->ordering->n_steps;
+  } else {
+    for (int q = 1; q < n; ++q) {
+      def.push_back(0);
+      def.push_back(q);
+    }
+    steps = def.data();
+    ns = n - 1;
+  }
+  std::vector<Ref> live(n);
+  std::vector<char> alive(n, 1);
+  for (int q = 0; q < n; ++q) live[q] = p.grid_ref[q];
+  const bool tc_prec = p.prec != QFLEX_FP32_SIMT;
+  for (int i = 0; i < ns; ++i) {
+    const int dst = steps[2 * i], src = steps[2 * i + 1];
+    if (dst < 0 || src < 0 || dst >= n || src >= n || dst == src || !alive[dst] || !alive[src])
+      return fail(QFLEX_ERR_PLAN, "ordering step " + std::to_string(i) + " names a dead or invalid tensor");
+    Step s;
+    s.dst = dst;
+    s.src = src;
+    const Ref& ra = live[dst];
+    const Ref& rb = live[src];
+    std::vector<int> shared, ml, nl;
+    for (int l : ra.legs)
+      (std::find(rb.legs.begin(), rb.legs.end(), l) != rb.legs.end() ? shared : ml).push_back(l);
+    for (int l : rb.legs)
+      if (std::find(shared.begin(), shared.end(), l) == shared.end()) nl.push_back(l);
+    s.M = leg_product(ml, p.leg_dim);
+    s.N = leg_product(nl, p.leg_dim);
+    s.K = leg_product(shared, p.leg_dim);
+    if (s.M * s.N > (int64_t(1) << 34) || s.M * s.K > (int64_t(1) << 34) || s.N * s.K > (int64_t(1) << 34))
+      return fail(QFLEX_ERR_PLAN, "intermediate tensor larger than 2^34 entries at step " + std::to_string(i));
+    s.tc = tc_prec && s.M >= 128 && s.N >= 32 && s.K >= 32 && s.K % 8 == 0 &&
+           double(s.M) * s.N * s.K >= double(1 << 22);
+    s.bn = s.N >= 128 ? 128 : 64;
+    s.out_legs = ml;
+    s.out_legs.insert(s.out_legs.end(), nl.begin(), nl.end());
+    std::vector<int> ta = ml, tb = nl;
+    ta.insert(ta.end(), shared.begin(), shared.end());
+    tb.insert(tb.end(), shared.begin(), shared.end());
+    if (!make_operand(ra, ta, p.leg_dim, &s.A) || !make_operand(rb, tb, p.leg_dim, &s.B))
+      return fail(QFLEX_ERR_PLAN, "operand layout not supported at step " + std::to_string(i));
+    s.A.direct = !s.tc && !ra.grid && ra.legs == ta;
+    s.B.direct = !s.tc && !rb.grid && rb.legs == tb;
+    s.dep = ra.dep | rb.dep;
+    if (!ra.grid) p.bufs[ra.id].consumer = i;
+    if (!rb.grid) p.bufs[rb.id].consumer = i;
+    Buf b;
+    b.elems = s.M * s.N;
+    b.producer = i;
+    s.out_buf = int(p.bufs.size());
+    p.bufs.push_back(b);
+    p.max_tensor = std::max(p.max_tensor, b.elems);
+    Ref out;
+    out.grid = false;
+    out.id = s.out_buf;
+    out.legs = s.out_legs;
+    out.strides.resize(out.legs.size());
+    int64_t st = 1;
+    for (int a = int(out.legs.size()) - 1; a >= 0; --a) {
+      out.strides[a] = st;
+      st *= p.leg_dim[out.legs[a]];
+    }
+    out.dep = s.dep;
+    live[dst] = out;
+    alive[src] = 0;
+    if (s.tc) ++p.n_tc;
+    p.steps.push_back(std::move(s));
+  }
+  int left = -1, count = 0;
+  for (int q = 0; q < n; ++q)
+    if (alive[q]) {
+      left = q;
+      ++count;
+    }
+  if (count != 1) return fail(QFLEX_ERR_PLAN, "ordering does not contract the network into one tensor");
+  p.final_ref = live[left];
+  {
+    std::vector<int> want;
+    for (int q : p.tile) want.push_back(E + q);
+    std::vector<int> got = p.final_ref.legs;
+    std::sort(want.begin(), want.end());
+    std::sort(got.begin(), got.end());
+    if (want != got) return fail(QFLEX_ERR_PLAN, "final tensor legs are not the open tile");
+    if (!p.final_ref.cut_terms.empty()) return fail(QFLEX_ERR_PLAN, "final tensor still has cut legs");
+    for (int q : p.tile) {
+      auto it = std::find(p.final_ref.legs.begin(), p.final_ref.legs.end(), E + q);
+      p.final_strides.push_back(p.final_ref.strides[it - p.final_ref.legs.begin()]);
+    }
+  }
+  const uint64_t all_cuts = p.cuts.size() >= 64 ? ~uint64_t(0) : ((uint64_t(1) << p.cuts.size()) - 1);
+  if (!p.final_ref.grid) p.bufs[p.final_ref.id].consumer = ns;   // read by the slice sum
+  // buffers: reused across slices -> dedicated; others share by liveness
+  for (Buf& b : p.bufs) {
+    const uint64_t cdep = b.consumer >= ns ? all_cuts : p.steps[b.consumer].dep;
+    b.persistent = p.steps[b.producer].dep != cdep;
+  }
+  size_t arena = 0;
+  for (Buf& b : p.bufs)
+    if (b.persistent) {
+      b.offset = arena;
+      arena += align256(size_t(b.elems) * 8);
+      ++p.n_persistent;
+    }
+  struct Live { size_t off, size; int end; };
+  std::vector<Live> used;
+  for (Buf& b : p.bufs) {
+    if (b.persistent) continue;
+    used.erase(std::remove_if(used.begin(), used.end(), [&](const Live& l) { return l.end < b.producer; }),
+               used.end());
+    std::sort(used.begin(), used.end(), [](const Live& x, const Live& y) { return x.off < y.off; });
+    const size_t need = align256(size_t(b.elems) * 8);
+    size_t cur = arena;   // transient region starts after the persistent ones
+    for (const Live& l : used) {
+      if (l.off >= cur + need) break;
+      cur = std::max(cur, l.off + l.size);
+    }
+    b.offset = cur;
+    used.push_back({cur, need, b.consumer});
+    p.arena_bytes = std::max(p.arena_bytes, cur + need);
+  }
+  p.arena_bytes = std::max(p.arena_bytes, arena);
+  for (const Step& s : p.steps) {
+    if (!s.A.direct) p.opA_bytes = std::max(p.opA_bytes, operand_bytes(p, s.tc, s.M * s.K));
+    if (!s.B.direct) p.opB_bytes = std::max(p.opB_bytes, operand_bytes(p, s.tc, s.N * s.K));
+  }
+  p.grid_bytes = align256(size_t(p.grid_elems) * 8);
+  p.total_bytes = p.grid_bytes + align256(p.arena_bytes) + align256(p.opA_bytes) + align256(p.opB_bytes) +
+                  align256(sizeof(GridQubitMeta) * n) + align256(sizeof(int2) * std::max<size_t>(1, p.gops.size())) +
+                  256;
+  return QFLEX_OK;
+}
+
+qflex_status allocate(qflex_plan_s& p) {
+  QF_CUDA(cudaSetDevice(p.device));
+  if (cudaMalloc(&p.d_ws, p.total_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p.d_ws = nullptr;
+    return fail(QFLEX_ERR_OOM, "workspace allocation of " + std::to_string(p.total_bytes) + " bytes failed");
+  }
+  char* c = p.d_ws;
+  p.d_grid = reinterpret_cast<float2*>(c);
+  c += p.grid_bytes;
+  p.d_arena = c;
+  c += align256(p.arena_bytes);
+  p.d_opA = c;
+  c += align256(p.opA_bytes);
+  p.d_opB = c;
+  c += align256(p.opB_bytes);
+  p.d_gmeta = reinterpret_cast<GridQubitMeta*>(c);
+  c += align256(sizeof(GridQubitMeta) * p.n);
+  p.d_gops = reinterpret_cast<int2*>(c);
+  c += align256(sizeof(int2) * std::max<size_t>(1, p.gops.size()));
+  p.d_status = reinterpret_cast<int32_t*>(c);
+  QF_CUDA(cudaMemcpy(p.d_gmeta, p.gmeta.data(), sizeof(GridQubitMeta) * p.n, cudaMemcpyHostToDevice));
+  if (!p.gops.empty())
+    QF_CUDA(cudaMemcpy(p.d_gops, p.gops.data(), sizeof(int2) * p.gops.size(), cudaMemcpyHostToDevice));
+  QF_CUDA(cudaMemset(p.d_status, 0, sizeof(int32_t)));
+  for (Step& s : p.steps) {
+    if (!s.tc) continue;
+    if (!tc_encode_maps(p.tc_kind, p.nsplit, s.bn, p.d_opA, s.M, p.d_opB, s.N, s.K, &s.maps))
+      return fail(QFLEX_ERR_CUDA, "tensor map encoding failed (driver entry point missing?)");
+  }
+  return QFLEX_OK;
+}
+
+const float2* ref_ptr(const qflex_plan_s& p, const Ref& r) {
+  if (r.grid) return p.d_grid + p.gmeta[r.id].offset;
+  return reinterpret_cast<const float2*>(p.d_arena + p.bufs[r.id].offset);
+}
+
+int64_t ref_base(const Ref& r, const std::vector<int64_t>& vals) {
+  int64_t b = 0;
+  for (auto& [ci, st] : r.cut_terms) b += vals[ci] * st;
+  return b;
+}
+
+cudaError_t produce(const qflex_plan_s& p, const Operand& op, bool tc, int64_t rows, int64_t cols,
+                    const std::vector<int64_t>& vals, void* out, cudaStream_t s) {
+  const int fmt = tc ? (p.tc_kind == 0 ? kFmtTF32 : kFmtBF16) : kFmtC64;
+  const float2* in = ref_ptr(p, op.ref);
+  const int64_t base = ref_base(op.ref, vals);
+  if (op.pow2) return launch_permute_tiled(in, base, op.tile, fmt, p.nsplit, out, rows * cols, s);
+  return launch_permute_gather(in, base, op.gather, fmt, p.nsplit, out, rows * cols, s);
+}
+
+// Launch `fn` on `s`, bracketed by an event pair when the plan is profiling.
+template <class F>
+cudaError_t timed(qflex_plan_s& p, int cls, double flops, double mma, double bytes, cudaStream_t s, F&& fn) {
+  if (!p.profiling || !((p.prof_mask >> cls) & 1)) return fn();
+  while (p.ev_pool.size() < p.ev_used + 2) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    p.ev_pool.push_back(e);
+  }
+  const size_t i = p.ev_used;
+  p.ev_used += 2;
+  cudaError_t r = cudaEventRecord(p.ev_pool[i], s);
+  if (r != cudaSuccess) return r;
+  if ((r = fn()) != cudaSuccess) return r;
+  p.recs.push_back({cls, i, flops, mma, bytes});
+  return cudaEventRecord(p.ev_pool[i + 1], s);
+}
+
+cudaError_t run_step(qflex_plan_s& p, const Step& st, const std::vector<int64_t>& vals,
+                     cudaStream_t s) {
+  cudaError_t e;
+  const double out_per = st.tc ? 3.0 * p.nsplit * (p.tc_kind == 0 ? 4 : 2) : 8.0;
+  const float2* A = nullptr;
+  const float2* B = nullptr;
+  if (st.A.direct) {
+    A = ref_ptr(p, st.A.ref);
+  } else {
+    if ((e = timed(p, 1, 0, 0, double(st.M) * st.K * (8.0 + out_per), s,
+                   [&] { return produce(p, st.A, st.tc, st.M, st.K, vals, p.d_opA, s); })) != cudaSuccess)
+      return e;
+    A = static_cast<const float2*>(p.d_opA);
+  }
+  if (st.B.direct) {
+    B = ref_ptr(p, st.B.ref);
+  } else {
+    if ((e = timed(p, 1, 0, 0, double(st.N) * st.K * (8.0 + out_per), s,
+                   [&] { return produce(p, st.B, st.tc, st.N, st.K, vals, p.d_opB, s); })) != cudaSuccess)
+      return e;
+    B = static_cast<const float2*>(p.d_opB);
+  }
+  float2* C = reinterpret_cast<float2*>(p.d_arena + p.bufs[st.out_buf].offset);
+  const double mnk = double(st.M) * double(st.N) * double(st.K);
+  const double mma = st.tc ? mnk * 3.0 * (p.nsplit == 2 ? 3.0 : 1.0) * 2.0 : 0.0;
+  const double gbytes = 8.0 * (double(st.M) * st.K + double(st.N) * st.K + double(st.M) * st.N);
+  if (st.tc)
+    return timed(p, 3, 8.0 * mnk, mma, gbytes, s, [&] {
+      return launch_cgemm_tc(p.tc_kind, p.nsplit, st.bn, st.maps, st.M, st.N, st.K, C, p.d_status, s);
+    });
+  return timed(p, 2, 8.0 * mnk, 0, gbytes, s, [&] { return launch_cgemm_simt(st.M, st.N, st.K, A, B, C, s); });
+}
+
+void decode_slice(const qflex_plan_s& p, int64_t s, std::vector<int64_t>& vals) {
+  vals.assign(p.cuts.size(), 0);
+  for (int i = int(p.cuts.size()) - 1; i >= 0; --i) {
+    const int64_t r = int64_t(1) << p.K[p.cuts[i]];
+    vals[i] = s % r;
+    s /= r;
+  }
+}
+
+// Walk the schedule of one call; `f(step index or -1 for slice sum, vals)`.
+template <class F>
+qflex_status walk(const qflex_plan_s& p, int64_t n_bs, const int64_t* ids, int64_t n_ids, F&& f) {
+  std::vector<int64_t> vals, prev;
+  for (int64_t b = 0; b < n_bs; ++b) {
+    if (qflex_status st = f(-2, b, vals)) return st;   // grid tensors for bitstring b
+    bool first = true;
+    const int64_t cnt = ids ? n_ids : p.P;
+    for (int64_t k = 0; k < cnt; ++k) {
+      const int64_t s = ids ? ids[k] : k;
+      decode_slice(p, s, vals);
+      uint64_t changed = 0;
+      for (size_t c = 0; c < vals.size(); ++c)
+        if (first || vals[c] != prev[c]) changed |= uint64_t(1) << c;
+      for (size_t i = 0; i < p.steps.size(); ++i)
+        if (first || (p.steps[i].dep & changed))
+          if (qflex_status st = f(int(i), b, vals)) return st;
+      if (qflex_status st = f(-1, b, vals)) return st;   // slice sum
+      prev = vals;
+      first = false;
+    }
+  }
+  return QFLEX_OK;
+}
+
+qflex_status check_slices(const qflex_plan_s& p, const int64_t* ids, int64_t n_ids) {
+  if (!ids) return QFLEX_OK;
+  if (n_ids < 0) return fail(QFLEX_ERR_ARG, "n_slice_ids < 0");
+  for (int64_t k = 0; k < n_ids; ++k)
+    if (ids[k] < 0 || ids[k] >= p.P) return fail(QFLEX_ERR_ARG, "slice id out of range");
+  return QFLEX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t qflex_abi_version(void) { return QFLEX_ABI_VERSION; }
+
+const char* qflex_last_error(void) { return g_err.c_str(); }
+
+qflex_status qflex_plan_create(const qflex_problem* problem, qflex_precision prec, size_t ws_max, int device,
+                               qflex_plan* out) {
+  if (!problem || !out) return fail(QFLEX_ERR_ARG, "null problem or output");
+  *out = nullptr;
+  if (prec < QFLEX_FP32_SIMT || prec > QFLEX_TF32_PLAIN) return fail(QFLEX_ERR_ARG, "unknown precision");
+  auto p = std::make_unique<qflex_plan_s>();
+  p->prec = prec;
+  p->device = device;
+  p->tc_kind = (prec == QFLEX_TF32X3 || prec == QFLEX_TF32_PLAIN) ? 0 : 1;
+  p->nsplit = (prec == QFLEX_TF32X3 || prec == QFLEX_BF16X3) ? 2 : 1;
+  if (qflex_status st = build_plan(problem, *p)) return st;
+  if (ws_max > 0 && p->total_bytes > ws_max)
+    return fail(QFLEX_ERR_PLAN, "plan needs " + std::to_string(p->total_bytes) + " bytes, budget " +
+                                    std::to_string(ws_max));
+  if (device >= 0) {
+    if (prec != QFLEX_FP32_SIMT && !tc_available())
+      return fail(QFLEX_ERR_UNSUPPORTED, "tensor-map encoder unavailable in this driver");
+    if (qflex_status st = allocate(*p)) {
+      if (p->d_ws) cudaFree(p->d_ws);
+      return st;
+    }
+  }
+  *out = p.release();
+  return QFLEX_OK;
+}
+
+void qflex_plan_destroy(qflex_plan plan) {
+  if (!plan) return;
+  if (plan->d_ws) {
+    cudaSetDevice(plan->device);
+    cudaFree(plan->d_ws);
+  }
+  for (cudaEvent_t e : plan->ev_pool) cudaEventDestroy(e);
+  delete plan;
+}
+
+qflex_status qflex_plan_get_info(qflex_plan p, qflex_plan_info* info) {
+  if (!p || !info) return fail(QFLEX_ERR_ARG, "null argument");
+  info->n_slices = p->P;
+  info->n_qubits = p->n;
+  info->n_params = p->n_params;
+  info->n_open = int(p->tile.size());
+  info->n_steps = int(p->steps.size());
+  info->max_tensor_elems = p->max_tensor;
+  info->workspace_bytes = p->total_bytes;
+  info->n_tc_steps = p->n_tc;
+  info->n_persistent_buffers = p->n_persistent;
+  return QFLEX_OK;
+}
+
+qflex_status qflex_plan_cost(qflex_plan p, int64_t n_bs, const int64_t* ids, int64_t n_ids, qflex_cost* out) {
+  if (!p || !out || n_bs < 0) return fail(QFLEX_ERR_ARG, "bad argument");
+  if (qflex_status st = check_slices(*p, ids, n_ids)) return st;
+  qflex_cost c{};
+  const double prods = p->nsplit == 2 ? 3.0 : 1.0;
+  qflex_status st = walk(*p, n_bs, ids, n_ids, [&](int i, int64_t, const std::vector<int64_t>&) {
+    if (i < 0) {
+      ++c.launches;
+      return QFLEX_OK;
+    }
+    const Step& s = p->steps[i];
+    const double mnk = double(s.M) * double(s.N) * double(s.K);
+    c.cmacs += mnk;
+    c.largest_gemm_cmacs = std::max(c.largest_gemm_cmacs, mnk);
+    if (s.tc) {
+      c.tc_cmacs += mnk;
+      c.tc_mma_flops += mnk * 3.0 * prods * 2.0;
+    }
+    if (!s.A.direct) c.permute_bytes += 16.0 * double(s.M) * double(s.K);
+    if (!s.B.direct) c.permute_bytes += 16.0 * double(s.N) * double(s.K);
+    c.launches += 1 + !s.A.direct + !s.B.direct;
+    ++c.steps_executed;
+    return QFLEX_OK;
+  });
+  if (st) return st;
+  *out = c;
+  return QFLEX_OK;
+}
+
+qflex_status qflex_select_slices(qflex_plan p, double f, uint64_t seed, int64_t* ids, int64_t cap, int64_t* n_sel) {
+  if (!p || !ids || !n_sel || !(f > 0.0)) return fail(QFLEX_ERR_ARG, "bad argument");
+  if (p->P > (int64_t(1) << 32)) return fail(QFLEX_ERR_UNSUPPORTED, "too many slices to shuffle");
+  int64_t nf = int64_t(std::floor(f * double(p->P) + 0.5));
+  nf = std::max<int64_t>(1, std::min<int64_t>(p->P, nf));
+  if (cap < nf) return fail(QFLEX_ERR_ARG, "slice_ids capacity too small");
+  std::vector<int64_t> a(size_t(p->P));
+  std::iota(a.begin(), a.end(), 0);
+  uint64_t x = seed;
+  auto next = [&]() {   // SplitMix64 (Steele, Lea, Flood 2014)
+    x += 0x9E3779B97F4A7C15ull;
+    uint64_t z = x;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  for (int64_t i = p->P - 1; i > 0; --i) {
+    const int64_t j = int64_t(next() % uint64_t(i + 1));
+    std::swap(a[i], a[j]);
+  }
+  std::sort(a.begin(), a.begin() + nf);
+  std::copy(a.begin(), a.begin() + nf, ids);
+  *n_sel = nf;
+  return QFLEX_OK;
+}
+
+qflex_status qflex_amplitudes(qflex_plan p, const double* angles, const uint8_t* bits, int64_t n_bs,
+                              const int64_t* ids, int64_t n_ids, double* amps, void* stream) {
+  if (!p) return fail(QFLEX_ERR_ARG, "null plan");
+  if (p->device < 0) return fail(QFLEX_ERR_UNSUPPORTED, "host-only plan");
+  if (n_bs < 0 || (n_bs > 0 && (!bits || !amps))) return fail(QFLEX_ERR_ARG, "bad bitstrings/output");
+  if (p->n_params > 0 && !angles) return fail(QFLEX_ERR_ARG, "angles required");
+  if (qflex_status st = check_slices(*p, ids, n_ids)) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  QF_CUDA(cudaSetDevice(p->device));
+  p->last_stream = s;
+  const int64_t T = int64_t(1) << p->tile.size();
+  QF_CUDA(cudaMemsetAsync(amps, 0, size_t(n_bs) * T * 2 * sizeof(double), s));
+  return walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) -> qflex_status {
+    cudaError_t e;
+    if (i == -2) {
+      e = timed(*p, 0, 0, 0, 8.0 * p->grid_elems, s, [&] {
+        return launch_gridtensor(p->d_gmeta, p->n, p->max_bits, p->d_gops, angles, bits + b * p->n, p->d_grid, s);
+      });
+    } else if (i == -1) {
+      const float2* src = ref_ptr(*p, p->final_ref) + ref_base(p->final_ref, vals);
+      e = timed(*p, 4, 0, 0, 40.0 * T, s, [&] {
+        return launch_slicesum(src, p->final_strides.data(), int(p->tile.size()), amps + b * T * 2, s);
+      });
+    } else {
+      e = run_step(*p, p->steps[i], vals, s);
+    }
+    if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
+    return QFLEX_OK;
+  });
+}
+
+qflex_status qflex_amplitudes_grad(qflex_plan, const double*, const uint8_t*, int64_t, const int64_t*, int64_t,
+                                   const double*, double*, double*, void*) {
+  return fail(QFLEX_ERR_UNSUPPORTED, "gradients are not built yet");
+}
+
+qflex_status qflex_plan_profile(qflex_plan p, int32_t mode, qflex_profile* out) {
+  if (!p) return fail(QFLEX_ERR_ARG, "null plan");
+  if (p->device < 0) return fail(QFLEX_ERR_UNSUPPORTED, "host-only plan");
+  QF_CUDA(cudaSetDevice(p->device));
+  auto drain = [&]() -> qflex_status {
+    if (p->recs.empty()) return QFLEX_OK;
+    QF_CUDA(cudaEventSynchronize(p->ev_pool[p->recs.back().e0 + 1]));
+    for (const auto& r : p->recs) {
+      float ms = 0.f;
+      QF_CUDA(cudaEventElapsedTime(&ms, p->ev_pool[r.e0], p->ev_pool[r.e0 + 1]));
+      p->prof.launches[r.cls] += 1;
+      p->prof.ms[r.cls] += ms;
+      p->prof.flops[r.cls] += r.flops;
+      p->prof.mma_flops[r.cls] += r.mma;
+      p->prof.bytes[r.cls] += r.bytes;
+    }
+    p->recs.clear();
+    p->ev_used = 0;
+    return QFLEX_OK;
+  };
+  if (mode < 0 || mode > 31) return fail(QFLEX_ERR_ARG, "mode must be a class mask in [0, 31]");
+  if (mode != 0) {
+    if (qflex_status st = drain()) return st;
+    p->prof = qflex_profile{};
+    p->profiling = true;
+    p->prof_mask = mode;
+  } else {
+    p->profiling = false;
+  }
+  if (out) {
+    if (qflex_status st = drain()) return st;
+    *out = p->prof;
+  }
+  return QFLEX_OK;
+}
+
+qflex_status qflex_plan_sync(qflex_plan p) {
+  if (!p) return fail(QFLEX_ERR_ARG, "null plan");
+  if (p->device < 0) return QFLEX_OK;
+  QF_CUDA(cudaSetDevice(p->device));
+  QF_CUDA(cudaStreamSynchronize(p->last_stream));
+  int32_t w = 0;
+  QF_CUDA(cudaMemcpy(&w, p->d_status, sizeof(w), cudaMemcpyDeviceToHost));
+  if (w) {
+    QF_CUDA(cudaMemset(p->d_status, 0, sizeof(int32_t)));
+    return fail(QFLEX_ERR_DEVICE_TIMEOUT, "a bounded device-side wait ran out");
+  }
+  return QFLEX_OK;
+}
+
+qflex_status qflex_permute(const void* in, void* out, int32_t rank, const int64_t* dims, const int32_t* perm,
+                           void* stream) {
+  if (!in || !out || rank < 0 || rank > 32 || (rank > 0 && (!dims || !perm)))
+    return fail(QFLEX_ERR_ARG, "bad permute arguments");
+  std::vector<int64_t> istr(rank);
+  int64_t total = 1;
+  for (int a = rank - 1; a >= 0; --a) {
+    if (dims[a] <= 0) return fail(QFLEX_ERR_ARG, "dims must be positive");
+    istr[a] = total;
+    total *= dims[a];
+  }
+  std::vector<int> seen(rank, 0);
+  for (int a = 0; a < rank; ++a) {
+    if (perm[a] < 0 || perm[a] >= rank || seen[perm[a]]++) return fail(QFLEX_ERR_ARG, "perm is not a permutation");
+  }
+  if (total == 0) return QFLEX_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bool pow2 = true;
+  for (int a = 0; a < rank; ++a) pow2 = pow2 && is_pow2(dims[a]);
+  cudaError_t e;
+  if (pow2) {
+    std::vector<int64_t> w;
+    for (int a = rank - 1; a >= 0; --a)
+      for (int b = 0; b < ilog2(dims[perm[a]]); ++b) w.push_back(istr[perm[a]] << b);
+    PermTile t;
+    if (!build_perm_tile(int(w.size()), w.data(), &t)) return fail(QFLEX_ERR_UNSUPPORTED, "tensor too large");
+    e = launch_permute_tiled(static_cast<const float2*>(in), 0, t, kFmtC64, 1, out, total, s);
+  } else {
+    GatherDesc g{};
+    g.rank = rank;
+    g.total = total;
+    for (int a = 0; a < rank; ++a) {
+      g.dims[a] = dims[perm[a]];
+      g.in_strides[a] = istr[perm[a]];
+    }
+    e = launch_permute_gather(static_cast<const float2*>(in), 0, g, kFmtC64, 1, out, total, s);
+  }
+  if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
+  return QFLEX_OK;
+}
+
+qflex_status qflex_cgemm_workspace_size(int32_t prec, int64_t M, int64_t N, int64_t K, size_t* bytes) {
+  if (!bytes || M < 0 || N < 0 || K < 0) return fail(QFLEX_ERR_ARG, "bad argument");
+  if (prec == QFLEX_FP32_SIMT) {
+    *bytes = 0;
+    return QFLEX_OK;
+  }
+  if (prec < 0 || prec > QFLEX_TF32_PLAIN) return fail(QFLEX_ERR_ARG, "unknown precision");
+  const int kind = (prec == QFLEX_TF32X3 || prec == QFLEX_TF32_PLAIN) ? 0 : 1;
+  const int nsplit = (prec == QFLEX_TF32X3 || prec == QFLEX_BF16X3) ? 2 : 1;
+  const size_t per = size_t(3) * nsplit * (kind == 0 ? 4 : 2);
+  *bytes = align256(per * size_t(M) * size_t(K)) + align256(per * size_t(N) * size_t(K));
+  return QFLEX_OK;
+}
+
+qflex_status qflex_cgemm(int32_t prec, int64_t M, int64_t N, int64_t K, const void* A, const void* B, void* C,
+                         void* ws, size_t ws_bytes, void* stream) {
+  if (M < 0 || N < 0 || K < 0 || (M * N > 0 && (!A || !B || !C))) return fail(QFLEX_ERR_ARG, "bad GEMM arguments");
+  if (M == 0 || N == 0) return QFLEX_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool tc = prec != QFLEX_FP32_SIMT && M >= 128 && K % 8 == 0 && K > 0 && N >= 16;
+  if (!tc) {
+    if (K == 0) QF_CUDA(cudaMemsetAsync(C, 0, size_t(M) * N * 8, s));
+    else QF_CUDA(launch_cgemm_simt(M, N, K, static_cast<const float2*>(A), static_cast<const float2*>(B),
+                                   static_cast<float2*>(C), s));
+    return QFLEX_OK;
+  }
+  size_t need = 0;
+  if (qflex_status st = qflex_cgemm_workspace_size(prec, M, N, K, &need)) return st;
+  if (!ws || ws_bytes < need) return fail(QFLEX_ERR_ARG, "workspace too small");
+  if (!tc_available()) return fail(QFLEX_ERR_UNSUPPORTED, "tensor-map encoder unavailable");
+  const int kind = (prec == QFLEX_TF32X3 || prec == QFLEX_TF32_PLAIN) ? 0 : 1;
+  const int nsplit = (prec == QFLEX_TF32X3 || prec == QFLEX_BF16X3) ? 2 : 1;
+  const size_t per = size_t(3) * nsplit * (kind == 0 ? 4 : 2);
+  char* pa = static_cast<char*>(ws);
+  char* pb = pa + align256(per * size_t(M) * size_t(K));
+  // identity "permutation" of a [rows][K] matrix into operand planes
+  auto planes = [&](const void* src, int64_t rows, void* dst) {
+    std::vector<int64_t> w;
+    const int64_t total = rows * K;
+    if (is_pow2(total)) {
+      for (int b = 0; b < ilog2(total); ++b) w.push_back(int64_t(1) << b);
+      PermTile t;
+      build_perm_tile(int(w.size()), w.data(), &t);
+      return launch_permute_tiled(static_cast<const float2*>(src), 0, t, kind == 0 ? kFmtTF32 : kFmtBF16, nsplit,
+                                  dst, total, s);
+    }
+    GatherDesc g{};
+    g.rank = 1;
+    g.total = total;
+    g.dims[0] = total;
+    g.in_strides[0] = 1;
+    return launch_permute_gather(static_cast<const float2*>(src), 0, g, kind == 0 ? kFmtTF32 : kFmtBF16, nsplit,
+                                 dst, total, s);
+  };
+  QF_CUDA(planes(A, M, pa));
+  QF_CUDA(planes(B, N, pb));
+  TcGemmMaps maps;
+  const int bn = N >= 128 ? 128 : 64;
+  if (!tc_encode_maps(kind, nsplit, bn, pa, M, pb, N, K, &maps)) return fail(QFLEX_ERR_CUDA, "tensor map encoding failed");
+  int dev = 0;
+  QF_CUDA(cudaGetDevice(&dev));
+  QF_CUDA(launch_cgemm_tc(kind, nsplit, bn, maps, M, N, K, static_cast<float2*>(C), device_status_word(dev), s));
+  return QFLEX_OK;
+}
+
+qflex_status qflex_norm(const double* amps, int64_t n, double* out, void* stream) {
+  if (!amps || !out || n < 0) return fail(QFLEX_ERR_ARG, "bad argument");
+  QF_CUDA(launch_norm(amps, n, out, static_cast<cudaStream_t>(stream)));
+  return QFLEX_OK;
+}
+
+qflex_status qflex_device_status(int device, int32_t* status) {
+  if (!status || device < 0) return fail(QFLEX_ERR_ARG, "bad argument");
+  QF_CUDA(cudaSetDevice(device));
+  QF_CUDA(cudaDeviceSynchronize());
+  int32_t* w = device_status_word(device);
+  if (!w) return fail(QFLEX_ERR_CUDA, "status word allocation failed");
+  int32_t v = 0;
+  QF_CUDA(cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost));
+  QF_CUDA(cudaMemset(w, 0, sizeof(v)));
+  *status = v ? QFLEX_ERR_DEVICE_TIMEOUT : QFLEX_OK;
+  return QFLEX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+// Internal declarations shared by the host planner (api.cpp) and the CUDA
+// kernels.  Not part of the public ABI (see include/qflex.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda.h>
+#include <stdint.h>
+
+namespace qflex {
+
+// ------------------------------------------------------------------ status
+// Device-side status bits, OR-ed into a device word by kernels whose bounded
+// waits ran out (they then skip their remaining work and return).
+enum : int32_t { kDevTimeout = 1 };
+
+// ------------------------------------------------------------------ grid tensors
+// One qubit's gate line, compiled by the planner.  Op encoding (int2):
+//   x = type | (bitpos << 8), y = angle index (or -1)
+//   type 0..3, 5..7: one-qubit gate kinds (H, T, SX, SY, RX, RY, RZ)
+//   type 8: CZ half carried by the lower-index qubit, |k><k| with k = entry bit `bitpos`
+//   type 9: CZ half carried by the higher-index qubit, Z^k
+struct GridQubitMeta {
+  int64_t offset;     // element offset of this qubit's tensor in the grid buffer
+  int32_t n_bits;     // bond bits (entries per output value = 2^n_bits)
+  int32_t op_begin;   // first op in the op array
+  int32_t op_count;
+  int32_t tile;       // 1: output leg kept open (stored outermost, dim 2)
+  int32_t qubit;
+  int32_t pad;
+};
+enum : int { kOpCzProj = 8, kOpCzZ = 9 };
+
+cudaError_t launch_gridtensor(const GridQubitMeta* d_meta, int n_qubits, int max_bits,
+                              const int2* d_ops, const double* d_angles,
+                              const uint8_t* d_bits, float2* d_grid, cudaStream_t s);
+
+// ------------------------------------------------------------------ permutation
+// A permutation of a power-of-two-sized view is a permutation of the bits of
+// the linear output index: output bit j carries input weight w_j (elements).
+// The tiled kernel moves 2^tile_bits elements per tile through shared memory:
+// loads enumerate the tile bits by increasing input weight (coalesced reads),
+// stores by increasing output position (coalesced writes).
+constexpr int kPermMaxRest = 48;
+struct PermTile {
+  int64_t in_lo[32], in_hi[32];    // input offsets of load-index bits [0,5) and [5,10)
+  int64_t out_lo[32], out_hi[32];  // output offsets of store-index bits [0,5) and [5,10)
+  int32_t sm_lo[32], sm_hi[32];    // load index of store-index bits [0,5) and [5,10)
+  int64_t rest_in[kPermMaxRest], rest_out[kPermMaxRest];  // non-tile bits
+  int64_t n_tiles;
+  int32_t tile_bits, n_rest;
+};
+
+// Output formats of the operand producer.
+enum PermFormat : int {
+  kFmtC64 = 0,        // complex64, the permuted tensor itself
+  kFmtTF32 = 1,       // 3M planes re, im, re+im, each split into tf32 hi (+ lo)
+  kFmtBF16 = 2        // same with bf16
+};
+
+// Build the tile tables for `nbits` output bits with input weights w[0..nbits).
+// Returns false if nbits exceeds the supported range.
+bool build_perm_tile(int nbits, const int64_t* w, PermTile* t);
+
+// out-of-place permutation / operand production.  `in_base` is added to
+// every input offset (cut-bond slicing).  For plane formats, `nsplit` is 1 or
+// 2 and `plane_elems` the number of entries of one plane (rows*cols).
+cudaError_t launch_permute_tiled(const float2* in, int64_t in_base, const PermTile& t,
+                                 int fmt, int nsplit, void* out, int64_t plane_elems,
+                                 cudaStream_t s);
+
+// Generic gather for any dims: out[o] = in[base + sum_a idx_a(o) * stride_a].
+constexpr int kGatherMaxRank = 32;
+struct GatherDesc {
+  int64_t dims[kGatherMaxRank];
+  int64_t in_strides[kGatherMaxRank];
+  int64_t total;
+  int32_t rank;
+};
+cudaError_t launch_permute_gather(const float2* in, int64_t in_base, const GatherDesc& d,
+                                  int fmt, int nsplit, void* out, int64_t plane_elems,
+                                  cudaStream_t s);
+
+// ------------------------------------------------------------------ complex GEMM
+// C[m][n] = sum_k A[m][k] B[n][k], complex64, row-major, FP32 accumulate.
+cudaError_t launch_cgemm_simt(int64_t M, int64_t N, int64_t K, const float2* A,
+                              const float2* B, float2* C, cudaStream_t s);
+
+// Tensor-core GEMM on split 3M planes (produced by the permutation kernel in
+// kFmtTF32 / kFmtBF16 format).  kind: 0 = tf32, 1 = bf16.  bn: 64 or 128.
+struct TcGemmMaps {
+  CUtensorMap a;
+  CUtensorMap b;
+};
+bool tc_encode_maps(int kind, int nsplit, int bn, const void* a_planes, int64_t M,
+                    const void* b_planes, int64_t N, int64_t K, TcGemmMaps* maps);
+cudaError_t launch_cgemm_tc(int kind, int nsplit, int bn, const TcGemmMaps& maps, int64_t M,
+                            int64_t N, int64_t K, float2* C, int32_t* d_status,
+                            cudaStream_t s);
+bool tc_available();   // driver entry point for tensor-map encoding found
+
+// ------------------------------------------------------------------ small kernels
+// amps[j] (complex128) += src[sum_t bit_t(j) * strides[t]] for j < 2^n_open.
+cudaError_t launch_slicesum(const float2* src, const int64_t* strides, int n_open,
+                            double* amps, cudaStream_t s);
+cudaError_t launch_norm(const double* amps, int64_t n, double* out, cudaStream_t s);
+
+int32_t* device_status_word(int device);   // library-wide status word for standalone calls
+
+}  // namespace qflex

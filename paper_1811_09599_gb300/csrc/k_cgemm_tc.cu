@@ -1,0 +1,376 @@
+// Step a3b, tensor-core form: complex GEMM on tcgen05 with TMEM accumulators.
+//
+// C[m][n] = sum_k A[m][k] B[n][k] for complex operands, by the 3-multiply
+// (Gauss) trick:
+//   T1 = Ar.Br, T2 = Ai.Bi, T3 = (Ar+Ai).(Br+Bi);  Re C = T1 - T2,
+//   Im C = T3 - T1 - T2.
+// Each real operand is split x = hi + lo (tf32 or bf16 parts) and each real
+// product is taken as hi.hi + hi.lo + lo.hi with FP32 accumulation in TMEM.
+// The operand planes (re, im, re+im; hi, lo) are written by the permutation
+// kernel (fused operand producer) in [plane][rows][K] layout.
+//
+// Kernel organisation (one 128 x BN output tile per CTA, cta_group::1):
+//   warp 0      one lane issues TMA loads of (A hi, A lo, B hi, B lo) tiles
+//               for one (k-block, part) pair per pipeline stage;
+//   warp 1      allocates TMEM (3 accumulators of BN fp32 columns) and one
+//               lane issues the tcgen05.mma instructions of each stage, then
+//               tcgen05.commit releases the stage;
+//   warps 2-5   epilogue: tcgen05.ld of T1, T2, T3, combine into Re/Im,
+//               stage through shared memory, coalesced complex64 stores.
+// Every mbarrier wait is bounded (wall-clock limit); on expiry the kernel
+// sets the status word, skips the remaining work, waits (bounded) for its
+// own copies in flight, frees TMEM and returns.
+#include "internal.h"
+
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+namespace qflex {
+namespace {
+
+constexpr int BM = 128;
+constexpr int ROW_BYTES = 128;           // one 128-byte swizzle row of K per tile row
+constexpr int NSTAGE_MAX = 4;
+constexpr uint64_t kWaitLimitNs = 4000000000ull;   // 4 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: returns false (and flags the CTA / status word) after the
+// limit, or at once when another role of the CTA has already given up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          int32_t* status) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u) {
+      if (*abort_flag) return false;
+      const uint64_t now = gtimer();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > kWaitLimitNs) {
+        *abort_flag = 1;
+        if (status) atomicOr(status, kDevTimeout);
+        return false;
+      }
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+// Shared-memory matrix descriptor: K-major tile, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= uint64_t((addr & 0x3FFFFu) >> 4);         // start address
+  d |= uint64_t(1) << 16;                         // leading byte offset (unused for SW128 K-major)
+  d |= uint64_t(1024 >> 4) << 32;                 // stride byte offset
+  d |= uint64_t(1) << 46;                         // fixed 0b001
+  d |= uint64_t(2) << 61;                         // 128-byte swizzle
+  return d;
+}
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t accum) {
+  if constexpr (KIND == 0) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+  }
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int BN, int NSPLIT>
+struct Cfg {
+  static constexpr int A_TILE = BM * ROW_BYTES;              // bytes of one A plane tile
+  static constexpr int B_TILE = BN * ROW_BYTES;
+  static constexpr int STAGE = NSPLIT * (A_TILE + B_TILE);
+  static constexpr int NSTAGE = (200 * 1024) / STAGE > NSTAGE_MAX ? NSTAGE_MAX : (200 * 1024) / STAGE;
+  static constexpr int NPROD = NSPLIT == 2 ? 3 : 1;          // hi.hi, hi.lo, lo.hi
+  static constexpr int TMEM_COLS = 3 * BN <= 256 ? 256 : 512;
+  static constexpr int SMEM = NSTAGE * STAGE + 1024 /*align*/ + 256 /*barriers*/;
+  static_assert(NSTAGE >= 2, "pipeline needs at least two stages");
+  static_assert(4 * 32 * 33 * 8 <= NSTAGE * STAGE, "epilogue staging must fit in the stages");
+};
+
+template <int KIND, int BN, int NSPLIT>
+__global__ void __launch_bounds__(192, 1)
+    k_cgemm_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+               int64_t M, int64_t N, int64_t K, float2* __restrict__ C, int32_t* status) {
+  using G = Cfg<BN, NSPLIT>;
+  constexpr int ELEM = KIND == 0 ? 4 : 2;
+  constexpr int BK = ROW_BYTES / ELEM;              // K elements per stage
+  constexpr int MMA_K = 32 / ELEM;                  // 8 (tf32) or 16 (bf16): 32 bytes
+  constexpr uint32_t IDESC = (1u << 4)                               // D = f32
+                             | (uint32_t(KIND == 0 ? 2 : 1) << 7)   // A = tf32 / bf16
+                             | (uint32_t(KIND == 0 ? 2 : 1) << 10)  // B = tf32 / bf16
+                             | (uint32_t(BN >> 3) << 17)             // N
+                             | (uint32_t(BM >> 4) << 24);            // M
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G::NSTAGE * G::STAGE);
+  // bars[0..NSTAGE): full, [NSTAGE..2NSTAGE): empty, [2NSTAGE]: accumulators ready
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * G::NSTAGE + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+  // A CTA of an earlier launch gave up on a wait: skip the work (the status
+  // word stays set until the host reads and clears it).
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = status ? *reinterpret_cast<volatile int32_t*>(status) : 0;
+  __syncthreads();
+  if (s_skip) return;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = int64_t(blockIdx.y) * BM, n0 = int64_t(blockIdx.x) * BN;
+  const int nkb = int((K + BK - 1) / BK);
+  const int total = nkb * 3;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < G::NSTAGE; ++s) {
+      mbar_init(smem_u32(&bars[s]), 1);
+      mbar_init(smem_u32(&bars[G::NSTAGE + s]), 1);
+    }
+    mbar_init(smem_u32(&bars[2 * G::NSTAGE]), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_holder)),
+                 "r"(G::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_a)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_b)) : "memory");
+      int issued = 0;
+      for (int i = 0; i < total; ++i) {
+        const int s = i % G::NSTAGE;
+        const uint32_t ph = (i / G::NSTAGE) & 1;
+        if (!mbar_wait(smem_u32(&bars[G::NSTAGE + s]), ph ^ 1, abort_flag, status)) break;
+        const int kb = i / 3, part = i % 3;
+        const uint32_t full = smem_u32(&bars[s]);
+        mbar_expect_tx(full, G::STAGE);
+        const uint32_t sa = smem_u32(smem + s * G::STAGE);
+        for (int sp = 0; sp < NSPLIT; ++sp)
+          tma_load_2d(sa + sp * G::A_TILE, &map_a, full, kb * BK,
+                      int((part * NSPLIT + sp) * M + m0));
+        for (int sp = 0; sp < NSPLIT; ++sp)
+          tma_load_2d(sa + NSPLIT * G::A_TILE + sp * G::B_TILE, &map_b, full, kb * BK,
+                      int((part * NSPLIT + sp) * N + n0));
+        issued = i + 1;
+      }
+      if (*abort_flag) {   // let the copies this lane started land before the CTA exits
+        for (int i = issued > G::NSTAGE ? issued - G::NSTAGE : 0; i < issued; ++i) {
+          volatile int never = 0;
+          mbar_wait(smem_u32(&bars[i % G::NSTAGE]), (i / G::NSTAGE) & 1, &never, nullptr);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      for (int i = 0; i < total; ++i) {
+        const int s = i % G::NSTAGE;
+        const uint32_t ph = (i / G::NSTAGE) & 1;
+        if (!mbar_wait(smem_u32(&bars[s]), ph, abort_flag, status)) break;
+        tc_fence_after();
+        const int kb = i / 3, part = i % 3;
+        const uint32_t sa = smem_u32(smem + s * G::STAGE);
+        const uint32_t sb = sa + NSPLIT * G::A_TILE;
+        const uint32_t d = tmem + uint32_t(part * BN);
+#pragma unroll
+        for (int pr = 0; pr < G::NPROD; ++pr) {
+          const int ai = pr == 2 ? 1 : 0, bi = pr == 1 ? 1 : 0;
+#pragma unroll
+          for (int ks = 0; ks < BK / MMA_K; ++ks) {
+            const uint64_t adesc = smem_desc(sa + ai * G::A_TILE + ks * 32);
+            const uint64_t bdesc = smem_desc(sb + bi * G::B_TILE + ks * 32);
+            mma<KIND>(d, adesc, bdesc, IDESC, (kb | pr | ks) != 0 ? 1u : 0u);
+          }
+        }
+        tc_commit(smem_u32(&bars[G::NSTAGE + s]));
+      }
+      tc_commit(smem_u32(&bars[2 * G::NSTAGE]));   // fires when every issued MMA is done
+    }
+  } else {
+    // epilogue warps 2..5: TMEM lane quarter = warp % 4
+    const int q = warp & 3;
+    const bool ok = mbar_wait(smem_u32(&bars[2 * G::NSTAGE]), 0, abort_flag, status);
+    tc_fence_after();
+    if (ok && !*abort_flag) {
+      float2* st = reinterpret_cast<float2*>(smem) + (warp - 2) * (32 * 33);
+      const uint32_t lane_base = tmem + (uint32_t(q * 32) << 16);
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 32) {
+        uint32_t r1[32], r2[32], r3[32];
+        tmem_ld32(lane_base + uint32_t(c), r1);
+        tmem_ld32(lane_base + uint32_t(BN + c), r2);
+        tmem_ld32(lane_base + uint32_t(2 * BN + c), r3);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float t1 = __uint_as_float(r1[j]), t2 = __uint_as_float(r2[j]),
+                      t3 = __uint_as_float(r3[j]);
+          st[lane * 33 + j] = make_float2(t1 - t2, t3 - t1 - t2);
+        }
+        __syncwarp();
+        const int64_t gn = n0 + c + lane;
+#pragma unroll 4
+        for (int r = 0; r < 32; ++r) {
+          const int64_t gm = m0 + q * 32 + r;
+          if (gm < M && gn < N) C[gm * N + gn] = st[r * 33 + lane];
+        }
+        __syncwarp();
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(G::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+bool encode(int kind, const void* ptr, int64_t rows, int64_t K, int box_rows, CUtensorMap* map) {
+  auto fn = get_encode();
+  if (!fn) return false;
+  const int elem = kind == 0 ? 4 : 2;
+  cuuint64_t gdim[2] = {cuuint64_t(K), cuuint64_t(rows)};
+  cuuint64_t gstride[1] = {cuuint64_t(K) * elem};
+  cuuint32_t box[2] = {cuuint32_t(ROW_BYTES / elem), cuuint32_t(box_rows)};
+  cuuint32_t estride[2] = {1, 1};
+  CUresult r = fn(map, kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                  2, const_cast<void*>(ptr), gdim, gstride, box, estride,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int KIND, int BN, int NSPLIT>
+cudaError_t launch_t(const TcGemmMaps& maps, int64_t M, int64_t N, int64_t K, float2* C,
+                     int32_t* status, cudaStream_t s) {
+  using G = Cfg<BN, NSPLIT>;
+  auto kern = k_cgemm_tc<KIND, BN, NSPLIT>;
+  static int configured_dev = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_dev != dev) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+    if (e != cudaSuccess) return e;
+    configured_dev = dev;
+  }
+  dim3 grid(unsigned((N + BN - 1) / BN), unsigned((M + BM - 1) / BM));
+  if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+  kern<<<grid, 192, G::SMEM, s>>>(maps.a, maps.b, M, N, K, C, status);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_available() { return get_encode() != nullptr; }
+
+bool tc_encode_maps(int kind, int nsplit, int bn, const void* a_planes, int64_t M,
+                    const void* b_planes, int64_t N, int64_t K, TcGemmMaps* maps) {
+  if (K % 8 != 0 || M <= 0 || N <= 0) return false;
+  const int64_t planes = 3 * nsplit;
+  return encode(kind, a_planes, planes * M, K, BM, &maps->a) &&
+         encode(kind, b_planes, planes * N, K, bn, &maps->b);
+}
+
+cudaError_t launch_cgemm_tc(int kind, int nsplit, int bn, const TcGemmMaps& maps, int64_t M,
+                            int64_t N, int64_t K, float2* C, int32_t* status, cudaStream_t s) {
+  if (3 * nsplit * M > INT32_MAX || 3 * nsplit * N > INT32_MAX) return cudaErrorInvalidValue;
+#define QF_TC(KD, B, S) \
+  if (kind == KD && bn == B && nsplit == S) return launch_t<KD, B, S>(maps, M, N, K, C, status, s);
+  QF_TC(0, 64, 1) QF_TC(0, 64, 2) QF_TC(0, 128, 1) QF_TC(0, 128, 2)
+  QF_TC(1, 64, 1) QF_TC(1, 64, 2) QF_TC(1, 128, 1) QF_TC(1, 128, 2)
+#undef QF_TC
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace qflex

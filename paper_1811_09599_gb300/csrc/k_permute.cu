@@ -1,0 +1,203 @@
+// Step a3a: index permutation (and the fused GEMM operand producer).
+//
+// Methods, "Cache-efficient index permutations": before every pairwise
+// contraction the operands are reordered so that the contracted indexes are
+// contiguous (row-major matrix form).  The paper's CPU design (left/right
+// moves chained L-R-L, memoised index maps) is built around CPU caches; on
+// the GPU one pass suffices: for power-of-two dimensions a permutation is a
+// permutation of the bits of the linear index, and a tile spanning the
+// input's fastest bits and the output's fastest bits is staged through
+// shared memory, so both the HBM reads and the HBM writes are coalesced.
+// The index maps are precomputed once per plan step (the analogue of the
+// paper's memoisation) as small tables.
+//
+// The same kernel can write, instead of the permuted complex64 tensor, the
+// tensor-core operand planes of the 3-multiply complex product: re, im and
+// re+im, each split into a high part and (optionally) the rounded residual
+// low part, in tf32 or bf16.
+#include "internal.h"
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <vector>
+
+namespace qflex {
+
+bool build_perm_tile(int nbits, const int64_t* w, PermTile* t) {
+  const int T = std::min(10, nbits);
+  if (nbits - T > kPermMaxRest) return false;
+  std::vector<int> by_w(nbits);
+  for (int i = 0; i < nbits; ++i) by_w[i] = i;
+  std::sort(by_w.begin(), by_w.end(), [&](int a, int b) { return w[a] < w[b]; });
+  std::vector<char> in_u(nbits, 0);
+  std::vector<int> U;
+  auto add = [&](int b) {
+    if (!in_u[b] && int(U.size()) < T) { in_u[b] = 1; U.push_back(b); }
+  };
+  for (int i = 0; i < std::min(5, nbits); ++i) add(by_w[i]);   // input-fastest bits
+  for (int i = 0; i < std::min(5, nbits); ++i) add(i);         // output-fastest bits
+  int pw = 0, po = 0;
+  while (int(U.size()) < T) {                                    // extend alternately
+    while (pw < nbits && in_u[by_w[pw]]) ++pw;
+    if (pw < nbits) add(by_w[pw]);
+    while (po < nbits && in_u[po]) ++po;
+    if (po < nbits) add(po);
+  }
+  std::vector<int> load = U, store = U;
+  std::sort(load.begin(), load.end(), [&](int a, int b) { return w[a] < w[b]; });
+  std::sort(store.begin(), store.end());
+  std::vector<int> pos_in_load(nbits, -1);
+  for (int i = 0; i < T; ++i) pos_in_load[load[i]] = i;
+  for (int a = 0; a < 32; ++a) {
+    int64_t il = 0, ih = 0, ol = 0, oh = 0;
+    int32_t sl = 0, sh = 0;
+    for (int b = 0; b < 5; ++b) {
+      if (!((a >> b) & 1)) continue;
+      if (b < T) {
+        il += w[load[b]];
+        ol += int64_t(1) << store[b];
+        sl += 1 << pos_in_load[store[b]];
+      }
+      if (5 + b < T) {
+        ih += w[load[5 + b]];
+        oh += int64_t(1) << store[5 + b];
+        sh += 1 << pos_in_load[store[5 + b]];
+      }
+    }
+    t->in_lo[a] = il; t->in_hi[a] = ih;
+    t->out_lo[a] = ol; t->out_hi[a] = oh;
+    t->sm_lo[a] = sl; t->sm_hi[a] = sh;
+  }
+  int r = 0;
+  for (int b = 0; b < nbits; ++b) {
+    if (in_u[b]) continue;
+    t->rest_in[r] = w[b];
+    t->rest_out[r] = int64_t(1) << b;
+    ++r;
+  }
+  for (int i = r; i < kPermMaxRest; ++i) t->rest_in[i] = t->rest_out[i] = 0;
+  t->n_rest = r;
+  t->tile_bits = T;
+  t->n_tiles = int64_t(1) << (nbits - T);
+  return true;
+}
+
+namespace {
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// Write one complex entry at linear output position o in the requested format.
+template <int FMT>
+__device__ __forceinline__ void put(void* out, int64_t o, float2 v, int nsplit, int64_t plane) {
+  if constexpr (FMT == kFmtC64) {
+    static_cast<float2*>(out)[o] = v;
+  } else {
+    const float part[3] = {v.x, v.y, v.x + v.y};
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      if constexpr (FMT == kFmtTF32) {
+        uint32_t* q = static_cast<uint32_t*>(out);
+        const uint32_t hi = tf32_rna(part[p]);
+        q[int64_t(p * nsplit) * plane + o] = hi;
+        if (nsplit == 2) q[int64_t(p * 2 + 1) * plane + o] = tf32_rna(part[p] - __uint_as_float(hi));
+      } else {
+        __nv_bfloat16* q = static_cast<__nv_bfloat16*>(out);
+        const __nv_bfloat16 hi = __float2bfloat16_rn(part[p]);
+        q[int64_t(p * nsplit) * plane + o] = hi;
+        if (nsplit == 2)
+          q[int64_t(p * 2 + 1) * plane + o] = __float2bfloat16_rn(part[p] - __bfloat162float(hi));
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ int swz(int j) { return j ^ ((j >> 5) & 15); }
+
+template <int FMT>
+__global__ void __launch_bounds__(256) k_permute_tiled(const float2* __restrict__ in, int64_t in_base,
+                                                       const __grid_constant__ PermTile t, void* out,
+                                                       int nsplit, int64_t plane) {
+  __shared__ float2 tile[1024];
+  __shared__ int64_t s_in_lo[32], s_in_hi[32], s_out_lo[32], s_out_hi[32];
+  __shared__ int32_t s_sm_lo[32], s_sm_hi[32];
+  if (threadIdx.x < 32) {
+    const int a = threadIdx.x;
+    s_in_lo[a] = t.in_lo[a]; s_in_hi[a] = t.in_hi[a];
+    s_out_lo[a] = t.out_lo[a]; s_out_hi[a] = t.out_hi[a];
+    s_sm_lo[a] = t.sm_lo[a]; s_sm_hi[a] = t.sm_hi[a];
+  }
+  __syncthreads();
+  const int n = 1 << t.tile_bits;
+  for (int64_t tb = blockIdx.x; tb < t.n_tiles; tb += gridDim.x) {
+    int64_t ib = in_base, ob = 0;
+    for (int r = 0; r < t.n_rest; ++r) {
+      if ((tb >> r) & 1) {
+        ib += t.rest_in[r];
+        ob += t.rest_out[r];
+      }
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x)
+      tile[swz(j)] = in[ib + s_in_lo[j & 31] + s_in_hi[j >> 5]];
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const float2 v = tile[swz(s_sm_lo[j & 31] + s_sm_hi[j >> 5])];
+      put<FMT>(out, ob + s_out_lo[j & 31] + s_out_hi[j >> 5], v, nsplit, plane);
+    }
+    __syncthreads();
+  }
+}
+
+template <int FMT>
+__global__ void k_permute_gather(const float2* __restrict__ in, int64_t in_base,
+                                 const __grid_constant__ GatherDesc d, void* out, int nsplit,
+                                 int64_t plane) {
+  for (int64_t o = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; o < d.total;
+       o += int64_t(gridDim.x) * blockDim.x) {
+    int64_t rem = o, off = in_base;
+    for (int a = d.rank - 1; a >= 0; --a) {
+      const int64_t i = rem % d.dims[a];
+      rem /= d.dims[a];
+      off += i * d.in_strides[a];
+    }
+    put<FMT>(out, o, in[off], nsplit, plane);
+  }
+}
+
+int grid_for(int64_t work_units) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t cap = int64_t(sms) * 8;
+  return int(std::max<int64_t>(1, std::min<int64_t>(cap, work_units)));
+}
+
+}  // namespace
+
+cudaError_t launch_permute_tiled(const float2* in, int64_t in_base, const PermTile& t, int fmt,
+                                 int nsplit, void* out, int64_t plane, cudaStream_t s) {
+  const int blocks = grid_for(t.n_tiles);
+  switch (fmt) {
+    case kFmtC64: k_permute_tiled<kFmtC64><<<blocks, 256, 0, s>>>(in, in_base, t, out, nsplit, plane); break;
+    case kFmtTF32: k_permute_tiled<kFmtTF32><<<blocks, 256, 0, s>>>(in, in_base, t, out, nsplit, plane); break;
+    default: k_permute_tiled<kFmtBF16><<<blocks, 256, 0, s>>>(in, in_base, t, out, nsplit, plane); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute_gather(const float2* in, int64_t in_base, const GatherDesc& d, int fmt,
+                                  int nsplit, void* out, int64_t plane, cudaStream_t s) {
+  const int blocks = grid_for((d.total + 255) / 256);
+  switch (fmt) {
+    case kFmtC64: k_permute_gather<kFmtC64><<<blocks, 256, 0, s>>>(in, in_base, d, out, nsplit, plane); break;
+    case kFmtTF32: k_permute_gather<kFmtTF32><<<blocks, 256, 0, s>>>(in, in_base, d, out, nsplit, plane); break;
+    default: k_permute_gather<kFmtBF16><<<blocks, 256, 0, s>>>(in, in_base, d, out, nsplit, plane); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace qflex

@@ -1,0 +1,86 @@
+// Steps a4 and a6: FP64 slice summation and norm reductions.
+//
+// Methods, "Cutting indexes": the amplitude is the sum of the contributions
+// of all paths (slices); Methods, "Summing a fraction of the paths": summing
+// a fraction f of them gives fidelity-f amplitudes of norm ~f.  The
+// cross-slice sum and the norm reduction are the only FP64 arithmetic on the
+// GPU.
+#include "internal.h"
+
+#include <mutex>
+#include <vector>
+
+namespace qflex {
+namespace {
+
+struct SliceSumArgs {
+  int64_t strides[32];
+  int32_t n_open;
+};
+
+__global__ void k_slicesum(const float2* __restrict__ src, const __grid_constant__ SliceSumArgs a,
+                           double* __restrict__ amps) {
+  const int64_t count = int64_t(1) << a.n_open;
+  for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < count;
+       j += int64_t(gridDim.x) * blockDim.x) {
+    int64_t idx = 0;
+    for (int t = 0; t < a.n_open; ++t)
+      if ((j >> (a.n_open - 1 - t)) & 1) idx += a.strides[t];
+    const float2 v = src[idx];
+    amps[2 * j] += double(v.x);
+    amps[2 * j + 1] += double(v.y);
+  }
+}
+
+__global__ void k_norm(const double* __restrict__ amps, int64_t n, double* __restrict__ out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double re = amps[2 * i], im = amps[2 * i + 1];
+    acc += re * re + im * im;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) *out = acc;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_slicesum(const float2* src, const int64_t* strides, int n_open, double* amps,
+                            cudaStream_t s) {
+  if (n_open < 0 || n_open > 30) return cudaErrorInvalidValue;
+  SliceSumArgs a{};
+  for (int t = 0; t < n_open; ++t) a.strides[t] = strides[t];
+  a.n_open = n_open;
+  const int64_t count = int64_t(1) << n_open;
+  const int blocks = int(count < 256 ? 1 : (count + 255) / 256 > 4096 ? 4096 : (count + 255) / 256);
+  k_slicesum<<<blocks, 256, 0, s>>>(src, a, amps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm(const double* amps, int64_t n, double* out, cudaStream_t s) {
+  k_norm<<<1, 1024, 0, s>>>(amps, n, out);
+  return cudaGetLastError();
+}
+
+int32_t* device_status_word(int device) {
+  static std::mutex mu;
+  static std::vector<int32_t*> words;
+  std::lock_guard<std::mutex> lock(mu);
+  if (device < 0) return nullptr;
+  if (int(words.size()) <= device) words.resize(device + 1, nullptr);
+  if (!words[device]) {
+    int32_t* p = nullptr;
+    if (cudaMalloc(&p, sizeof(int32_t)) != cudaSuccess) return nullptr;
+    cudaMemset(p, 0, sizeof(int32_t));
+    words[device] = p;
+  }
+  return words[device];
+}
+
+}  // namespace qflex

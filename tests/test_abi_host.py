@@ -1,0 +1,119 @@
+"""C-ABI checks that need no GPU: symbols, host-only plans, validation errors."""
+import re
+import os
+
+import numpy as np
+import pytest
+
+from oracle import network as NW
+from oracle import selection as SEL
+from qflex_inputs import c2_problem, c4_problem, grid_problem, random_circuit, grid_lattice
+from qflex_inputs.problems import Problem
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "qflex.h")
+
+
+def _declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(qflex_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared_functions()
+    assert "qflex_amplitudes" in names and "qflex_permute" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_1811_09599_gb300._lib import SIGNATURES
+    assert sorted(s[0] for s in SIGNATURES) == names
+
+
+def test_abi_version(lib):
+    assert lib.qflex_abi_version() == 1
+
+
+@pytest.fixture
+def Plan():
+    from paper_1811_09599_gb300.api import Plan
+    return Plan
+
+
+def test_host_plan_7x7_d40_sizes(Plan):
+    """SI A: 7x7x(1+40+1) with two cuts has 2^(2x5) paths and regions of 2^(6x5)."""
+    p = Plan(c4_problem(0), "bf16x3", device=-1)
+    info = p.info()
+    assert info["n_slices"] == 1024
+    assert info["max_tensor_elems"] == 2 ** 30
+    assert info["n_open"] == 6 and info["n_qubits"] == 49
+
+
+def test_host_plan_reuse_counts(Plan):
+    """A is built once per bitstring, B/pD/AB once per right-cut value, the
+    rest per slice (SI A's reuse of path-independent tensors)."""
+    prob = c2_problem(0)
+    p = Plan(prob, "fp32", device=-1)
+    c1 = p.cost(1)
+    # once: A (8 steps), B's (0,6)+(1,6) and pD's (6,6)+(5,6)+(4,6) (they touch
+    # no cut bond: the paper's partial tensors pB / ppD)
+    once = 8 + 1 + 2
+    per_right = 10 + 9 + 1       # rest of B, rest of pD, AB
+    per_slice = 4 + 1 + 12       # D column, ABD, region C
+    assert c1["steps_executed"] == once + 16 * per_right + 256 * per_slice
+    assert p.cost(3)["steps_executed"] == 3 * c1["steps_executed"]
+    # AB and ABD are 2^12 x 2^12 x 2^12 complex GEMMs at K_e = 4
+    assert c1["largest_gemm_cmacs"] == 2.0 ** 36
+
+
+def test_select_slices_matches_oracle(Plan):
+    p = Plan(c2_problem(0), "fp32", device=-1)
+    for f, seed in ((0.01, 1), (0.1, 42), (0.5, 7), (1.0, 3)):
+        assert list(p.select_slices(f, seed)) == SEL.select_slices(256, f, seed)
+
+
+def test_host_plan_refuses_compute(Plan):
+    import torch
+    from paper_1811_09599_gb300 import QFlexError
+    p = Plan(c2_problem(0), "fp32", device=-1)
+    from paper_1811_09599_gb300._lib import check
+    with pytest.raises(QFlexError) as e:
+        check(p.lib.qflex_amplitudes(p.handle, None, None, 0, None, 0, None, None))
+    assert "UNSUPPORTED" in str(e.value)
+
+
+def test_validation_errors(Plan):
+    from paper_1811_09599_gb300 import QFlexError
+    prob = grid_problem(3, 3, 8, 0, r0=1, c0=1, cuts=False, tile_rows=1, tile_cols=1)
+    # CZ on a non-edge
+    bad = grid_problem(3, 3, 8, 0, r0=1, c0=1, cuts=False, tile_rows=1, tile_cols=1)
+    for g in bad.circuit.gates:
+        if g.kind == "CZ":
+            g.q0, g.q1 = 0, 8
+            break
+    with pytest.raises(QFlexError, match="CIRCUIT"):
+        Plan(bad, "fp32", device=-1)
+    # ordering that leaves two tensors
+    short = Problem(prob.circuit, [], prob.open_tile, prob.ordering[:-1])
+    with pytest.raises(QFlexError, match="PLAN"):
+        Plan(short, "fp32", device=-1)
+    # ordering naming an absorbed tensor
+    dup = Problem(prob.circuit, [], prob.open_tile, prob.ordering + [prob.ordering[0]])
+    with pytest.raises(QFlexError, match="PLAN"):
+        Plan(dup, "fp32", device=-1)
+    # workspace budget
+    with pytest.raises(QFlexError, match="PLAN"):
+        Plan(c2_problem(0), "fp32", device=-1, workspace_bytes_max=1 << 20)
+    # slice id out of range
+    p = Plan(c2_problem(0), "fp32", device=-1)
+    with pytest.raises(QFlexError, match="ARG"):
+        p.cost(1, [256])
+    # repeated tile qubit
+    rep = Problem(prob.circuit, [], [1, 1], prob.ordering)
+    with pytest.raises(QFlexError, match="ARG"):
+        Plan(rep, "fp32", device=-1)
+
+
+def test_default_ordering_and_rotation_circuits(Plan):
+    circ = random_circuit(grid_lattice(3, 3), 16, 2, rotations=True)
+    p = Plan(Problem(circ, [], [0, 4], None), "tf32x3", device=-1)
+    info = p.info()
+    assert info["n_params"] == circ.n_params and info["n_steps"] == 8

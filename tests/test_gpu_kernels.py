@@ -1,0 +1,101 @@
+"""GPU parity of the standalone hot-path kernels through the C ABI.
+
+Permutation: bit-exact against the oracle's row-major definition.
+Complex GEMM: each precision against a complex128 product on the CPU.
+"""
+import numpy as np
+import pytest
+
+from oracle import permute as PM
+from tests.gpu_util import gemm_error
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def K():
+    from paper_1811_09599_gb300 import api
+    api._lib.load(build_if_missing=True)
+    return api
+
+
+def _rand_c64(shape, seed):
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
+
+
+def _check_perm(K, shape, perm, seed=0):
+    x = _rand_c64(shape, seed)
+    got = K.permute(torch.from_numpy(x).cuda(), perm).cpu().numpy()
+    want = PM.permute(x, perm)
+    assert got.shape == want.shape
+    assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+
+
+@pytest.mark.parametrize("m", [1, 5, 9, 12, 16, 22])
+def test_permute_binary_random(K, m):
+    rng = np.random.default_rng(m)
+    for _ in range(3):
+        _check_perm(K, (2,) * m, list(rng.permutation(m)), seed=m)
+
+
+def test_permute_specials(K):
+    m = 20
+    _check_perm(K, (2,) * m, list(range(m)))                      # identity
+    _check_perm(K, (2,) * m, list(range(m))[::-1])                # full reversal
+    rng = np.random.default_rng(1)
+    left = list(rng.permutation(m - 10)) + list(range(m - 10, m))  # L move (last 10 fixed)
+    _check_perm(K, (2,) * m, left)
+    right = list(range(m - 10)) + list(m - 10 + rng.permutation(10))  # R move
+    _check_perm(K, (2,) * m, right)
+    _check_perm(K, (16,) * 5, [4, 2, 0, 3, 1])                    # bond-like axes
+    _check_perm(K, (16, 16, 16, 4), [3, 0, 2, 1])
+    _check_perm(K, (2,) * 7, [2, 5, 4, 0, 3, 6, 1])              # abcdefg -> cfeadgb
+
+
+def test_permute_non_power_of_two_and_tiny(K):
+    _check_perm(K, (3, 5, 7), [2, 0, 1])
+    _check_perm(K, (6, 10, 4, 3), [1, 3, 0, 2])
+    _check_perm(K, (2,), [0])
+    _check_perm(K, (4, 2), [1, 0])
+    _check_perm(K, (1, 8, 1), [2, 1, 0])
+
+
+def test_permute_empty(K):
+    x = torch.zeros((0, 4), dtype=torch.complex64, device="cuda")
+    assert K.permute(x, [1, 0]).shape == (4, 0)
+
+
+def _gemm_case(K, prec, M, N, Kd, seed):
+    a = _rand_c64((M, Kd), seed)
+    b = _rand_c64((N, Kd), seed + 1)
+    got = K.cgemm(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), prec).cpu().numpy()
+    ref = a.astype(np.complex128) @ b.astype(np.complex128).T
+    return gemm_error(got, ref)
+
+
+SHAPES = [(128, 128, 64), (256, 128, 128), (300, 200, 72), (128, 64, 8), (1024, 512, 256),
+          (4096, 256, 256), (130, 33, 40), (7, 5, 3)]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5)])
+def test_cgemm_fp32(K, prec, tol):
+    for i, (M, N, Kd) in enumerate(SHAPES):
+        assert _gemm_case(K, prec, M, N, Kd, i) < tol, (M, N, Kd)
+
+
+@pytest.mark.parametrize("prec,tol", [("tf32x3", 1e-5), ("bf16x3", 1e-4)])
+def test_cgemm_tensor_core(K, prec, tol):
+    for i, (M, N, Kd) in enumerate(SHAPES):
+        err = _gemm_case(K, prec, M, N, Kd, 10 + i)
+        assert err < tol, (prec, M, N, Kd, err)
+    assert K.device_status(0) == 0
+
+
+def test_cgemm_plain_precisions_reported(K):
+    """Plain bf16 / tf32 (one product per part) are reported, not gated: they
+    must only be far better than noise."""
+    for prec in ("bf16", "tf32"):
+        err = _gemm_case(K, prec, 512, 256, 256, 99)
+        assert err < 5e-2, (prec, err)
