@@ -373,8 +373,11 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
     s.K = leg_product(shared, p.leg_dim);
     if (s.M * s.N > (int64_t(1) << 34) || s.M * s.K > (int64_t(1) << 34) || s.N * s.K > (int64_t(1) << 34))
       return fail(QFLEX_ERR_PLAN, "intermediate tensor larger than 2^34 entries at step " + std::to_string(i));
-    s.tc = tc_prec && s.M >= 128 && s.N >= 32 && s.K >= 32 && s.K % 8 == 0 &&
-           double(s.M) * s.N * s.K >= double(1 << 22);
+    // Tensor cores for contractions with enough work per output; thin
+    // absorptions of a small tensor (N <= 32 with a short K) are HBM-bound
+    // and run on the CUDA cores.
+    s.tc = tc_prec && s.M >= 128 && s.N >= 32 && s.K >= 16 && s.K % 8 == 0 &&
+           double(s.M) * s.N * s.K >= double(1 << 24) && !(s.N <= 32 && s.K <= 64);
     s.bn = s.N >= 128 ? 128 : 64;
     s.out_legs = ml;
     s.out_legs.insert(s.out_legs.end(), nl.begin(), nl.end());
@@ -576,7 +579,9 @@ cudaError_t run_step(qflex_plan_s& p, const Step& st, const std::vector<int64_t>
     return timed(p, 3, 8.0 * mnk, mma, gbytes, s, [&] {
       return launch_cgemm_tc(p.tc_kind, p.nsplit, st.bn, st.maps, st.M, st.N, st.K, C, p.d_status, s);
     });
-  return timed(p, 2, 8.0 * mnk, 0, gbytes, s, [&] { return launch_cgemm_simt(st.M, st.N, st.K, A, B, C, s); });
+  return timed(p, 2, 8.0 * mnk, 0, gbytes, s, [&] {
+    return st.N <= 32 ? launch_cgemm_thin(st.M, st.N, st.K, A, B, C, s) : launch_cgemm_simt(st.M, st.N, st.K, A, B, C, s);
+  });
 }
 
 void decode_slice(const qflex_plan_s& p, int64_t s, std::vector<int64_t>& vals) {
@@ -822,12 +827,11 @@ qflex_status qflex_plan_sync(qflex_plan p) {
 
 qflex_status qflex_permute(const void* in, void* out, int32_t rank, const int64_t* dims, const int32_t* perm,
                            void* stream) {
-  if (!in || !out || rank < 0 || rank > 32 || (rank > 0 && (!dims || !perm)))
-    return fail(QFLEX_ERR_ARG, "bad permute arguments");
+  if (rank < 0 || rank > 32 || (rank > 0 && (!dims || !perm))) return fail(QFLEX_ERR_ARG, "bad permute arguments");
   std::vector<int64_t> istr(rank);
   int64_t total = 1;
   for (int a = rank - 1; a >= 0; --a) {
-    if (dims[a] <= 0) return fail(QFLEX_ERR_ARG, "dims must be positive");
+    if (dims[a] < 0) return fail(QFLEX_ERR_ARG, "dims must be non-negative");
     istr[a] = total;
     total *= dims[a];
   }
@@ -836,6 +840,7 @@ qflex_status qflex_permute(const void* in, void* out, int32_t rank, const int64_
     if (perm[a] < 0 || perm[a] >= rank || seen[perm[a]]++) return fail(QFLEX_ERR_ARG, "perm is not a permutation");
   }
   if (total == 0) return QFLEX_OK;
+  if (!in || !out) return fail(QFLEX_ERR_ARG, "null tensor pointer");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   bool pow2 = true;
   for (int a = 0; a < rank; ++a) pow2 = pow2 && is_pow2(dims[a]);
@@ -883,8 +888,12 @@ qflex_status qflex_cgemm(int32_t prec, int64_t M, int64_t N, int64_t K, const vo
   const bool tc = prec != QFLEX_FP32_SIMT && M >= 128 && K % 8 == 0 && K > 0 && N >= 16;
   if (!tc) {
     if (K == 0) QF_CUDA(cudaMemsetAsync(C, 0, size_t(M) * N * 8, s));
-    else QF_CUDA(launch_cgemm_simt(M, N, K, static_cast<const float2*>(A), static_cast<const float2*>(B),
-                                   static_cast<float2*>(C), s));
+    else if (N <= 32)
+      QF_CUDA(launch_cgemm_thin(M, N, K, static_cast<const float2*>(A), static_cast<const float2*>(B),
+                                static_cast<float2*>(C), s));
+    else
+      QF_CUDA(launch_cgemm_simt(M, N, K, static_cast<const float2*>(A), static_cast<const float2*>(B),
+                                static_cast<float2*>(C), s));
     return QFLEX_OK;
   }
   size_t need = 0;

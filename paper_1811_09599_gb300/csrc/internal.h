@@ -39,12 +39,17 @@ cudaError_t launch_gridtensor(const GridQubitMeta* d_meta, int n_qubits, int max
 // the linear output index: output bit j carries input weight w_j (elements).
 // The tiled kernel moves 2^tile_bits elements per tile through shared memory:
 // loads enumerate the tile bits by increasing input weight (coalesced reads),
-// stores by increasing output position (coalesced writes).
+// stores by increasing output position (coalesced writes).  Shared-memory
+// slots are the load index with its low 4 bits XOR-ed by the store-fast
+// bits that sit higher up, so both 16-thread halves of a warp hit 16
+// distinct bank pairs in both phases, whatever the permutation.
 constexpr int kPermMaxRest = 48;
+constexpr int kPermTileBits = 11;   // 2048 entries per tile, 8 per thread
 struct PermTile {
-  int64_t in_lo[32], in_hi[32];    // input offsets of load-index bits [0,5) and [5,10)
-  int64_t out_lo[32], out_hi[32];  // output offsets of store-index bits [0,5) and [5,10)
-  int32_t sm_lo[32], sm_hi[32];    // load index of store-index bits [0,5) and [5,10)
+  int64_t in_lo[32], in_hi[64];    // input offsets of load-index bits [0,5) and [5,11)
+  int64_t out_lo[32], out_hi[64];  // output offsets of store-index bits [0,5) and [5,11)
+  int32_t ld_lo[32], ld_hi[64];    // shared-memory slot of load-index bits [0,5) and [5,11)
+  int32_t st_lo[32], st_hi[64];    // shared-memory slot of store-index bits [0,5) and [5,11)
   int64_t rest_in[kPermMaxRest], rest_out[kPermMaxRest];  // non-tile bits
   int64_t n_tiles;
   int32_t tile_bits, n_rest;
@@ -57,9 +62,10 @@ enum PermFormat : int {
   kFmtBF16 = 2        // same with bf16
 };
 
-// Build the tile tables for `nbits` output bits with input weights w[0..nbits).
-// Returns false if nbits exceeds the supported range.
-bool build_perm_tile(int nbits, const int64_t* w, PermTile* t);
+// Build the tile tables for a map of `nbits` index bits: bit j moves the
+// input by w_in[j] entries and the output by w_out[j] (1 << j when w_out is
+// null: contiguous output).  Returns false if nbits exceeds the supported range.
+bool build_perm_tile(int nbits, const int64_t* w_in, PermTile* t, const int64_t* w_out = nullptr);
 
 // out-of-place permutation / operand production.  `in_base` is added to
 // every input offset (cut-bond slicing).  For plane formats, `nsplit` is 1 or
@@ -83,6 +89,9 @@ cudaError_t launch_permute_gather(const float2* in, int64_t in_base, const Gathe
 // ------------------------------------------------------------------ complex GEMM
 // C[m][n] = sum_k A[m][k] B[n][k], complex64, row-major, FP32 accumulate.
 cudaError_t launch_cgemm_simt(int64_t M, int64_t N, int64_t K, const float2* A,
+                              const float2* B, float2* C, cudaStream_t s);
+// Same product for thin shapes (N <= 32): one thread per output row.
+cudaError_t launch_cgemm_thin(int64_t M, int64_t N, int64_t K, const float2* A,
                               const float2* B, float2* C, cudaStream_t s);
 
 // Tensor-core GEMM on split 3M planes (produced by the permutation kernel in

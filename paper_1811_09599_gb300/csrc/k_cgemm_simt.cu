@@ -26,7 +26,9 @@ __global__ void __launch_bounds__(256) k_cgemm_simt(int64_t M, int64_t N, int64_
   const int tid = threadIdx.x;
   const int tx = tid % (BN / TN), ty = tid / (BN / TN);
   const int64_t m0 = int64_t(blockIdx.y) * BM, n0 = int64_t(blockIdx.x) * BN;
-  float acc_re[TM][TN], acc_im[TM][TN];
+  // acc_*: running sums; p_*: the current K tile's partial sums (added to the
+  // running sums once per tile, which keeps the FP32 rounding drift ~sqrt(K/BK)).
+  float acc_re[TM][TN], acc_im[TM][TN], p_re[TM][TN], p_im[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -44,6 +46,10 @@ __global__ void __launch_bounds__(256) k_cgemm_simt(int64_t M, int64_t N, int64_
     }
     __syncthreads();
 #pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) p_re[i][j] = p_im[i][j] = 0.f;
+#pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       float2 a[TM], b[TN];
       const float4* ap = reinterpret_cast<const float4*>(&As[kk][ty * TM]);
@@ -60,12 +66,19 @@ __global__ void __launch_bounds__(256) k_cgemm_simt(int64_t M, int64_t N, int64_
       for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
-          acc_re[i][j] = fmaf(a[i].x, b[j].x, acc_re[i][j]);
-          acc_re[i][j] = fmaf(-a[i].y, b[j].y, acc_re[i][j]);
-          acc_im[i][j] = fmaf(a[i].x, b[j].y, acc_im[i][j]);
-          acc_im[i][j] = fmaf(a[i].y, b[j].x, acc_im[i][j]);
+          p_re[i][j] = fmaf(a[i].x, b[j].x, p_re[i][j]);
+          p_re[i][j] = fmaf(-a[i].y, b[j].y, p_re[i][j]);
+          p_im[i][j] = fmaf(a[i].x, b[j].y, p_im[i][j]);
+          p_im[i][j] = fmaf(a[i].y, b[j].x, p_im[i][j]);
         }
     }
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        acc_re[i][j] += p_re[i][j];
+        acc_im[i][j] += p_im[i][j];
+      }
     __syncthreads();
   }
 #pragma unroll
@@ -80,7 +93,92 @@ __global__ void __launch_bounds__(256) k_cgemm_simt(int64_t M, int64_t N, int64_
   }
 }
 
+// Thin form for N <= TBN (a large tensor absorbing a small one, HBM-bound):
+// each thread owns one output row and 16 of its columns; the B tile is
+// broadcast from shared memory.  Registers are capped so that four 256-thread
+// blocks fit per SM and enough A loads are in flight to stream HBM.
+constexpr int TBK = 16;
+template <int TBN>
+__global__ void __launch_bounds__(256, 4) k_cgemm_thin(int64_t M, int64_t N, int64_t K,
+                                                      const float2* __restrict__ A,
+                                                      const float2* __restrict__ B,
+                                                      float2* __restrict__ C) {
+  constexpr int CG = TBN / 16;            // column groups per row
+  constexpr int RB = 256 / CG;            // rows per block
+  __shared__ __align__(16) float2 As[RB][TBK + 1];
+  __shared__ __align__(16) float2 Bs[TBK][TBN];
+  const int t = threadIdx.x;
+  const int row = t / CG, cg = t % CG;
+  const int64_t m0 = int64_t(blockIdx.x) * RB, n0 = int64_t(blockIdx.y) * TBN;
+  float re[16], im[16];
+#pragma unroll
+  for (int n = 0; n < 16; ++n) re[n] = im[n] = 0.f;
+  for (int64_t k0 = 0; k0 < K; k0 += TBK) {
+#pragma unroll 4
+    for (int i = 0; i < (RB * TBK) / 256; ++i) {
+      const int e = t + i * 256;
+      const int r = e / TBK, kk = e % TBK;
+      const int64_t gm = m0 + r, gk = k0 + kk;
+      As[r][kk] = (gm < M && gk < K) ? __ldg(A + gm * K + gk) : make_float2(0.f, 0.f);
+    }
+    for (int e = t; e < TBN * TBK; e += 256) {
+      const int n = e / TBK, kk = e % TBK;
+      const int64_t gn = n0 + n, gk = k0 + kk;
+      Bs[kk][n] = (gn < N && gk < K) ? __ldg(B + gn * K + gk) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < TBK; ++kk) {
+      const float2 a = As[row][kk];
+      const float4* bp = reinterpret_cast<const float4*>(&Bs[kk][cg * 16]);
+#pragma unroll
+      for (int n = 0; n < 16; n += 2) {
+        const float4 b = bp[n / 2];
+        re[n] = fmaf(a.x, b.x, re[n]);
+        re[n] = fmaf(-a.y, b.y, re[n]);
+        im[n] = fmaf(a.x, b.y, im[n]);
+        im[n] = fmaf(a.y, b.x, im[n]);
+        re[n + 1] = fmaf(a.x, b.z, re[n + 1]);
+        re[n + 1] = fmaf(-a.y, b.w, re[n + 1]);
+        im[n + 1] = fmaf(a.x, b.w, im[n + 1]);
+        im[n + 1] = fmaf(a.y, b.z, im[n + 1]);
+      }
+    }
+    __syncthreads();
+  }
+  // each thread writes its 16 entries (contiguous, 16-byte stores when aligned)
+  const int64_t gm = m0 + row;
+  if (gm < M) {
+    const int64_t c0 = n0 + cg * 16;
+    float2* crow = C + gm * N + c0;
+    const int64_t ncols = N - c0 < 16 ? N - c0 : 16;
+    const bool vec = ((reinterpret_cast<uintptr_t>(crow) & 15) == 0);
+#pragma unroll
+    for (int n = 0; n < 16; n += 2) {
+      if (vec && n + 1 < ncols) {
+        *reinterpret_cast<float4*>(crow + n) = make_float4(re[n], im[n], re[n + 1], im[n + 1]);
+      } else {
+        if (n < ncols) crow[n] = make_float2(re[n], im[n]);
+        if (n + 1 < ncols) crow[n + 1] = make_float2(re[n + 1], im[n + 1]);
+      }
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_cgemm_thin(int64_t M, int64_t N, int64_t K, const float2* A, const float2* B,
+                              float2* C, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (N <= 16) {
+    dim3 grid(unsigned((M + 255) / 256), unsigned((N + 15) / 16));
+    k_cgemm_thin<16><<<grid, 256, 0, s>>>(M, N, K, A, B, C);
+  } else {
+    dim3 grid(unsigned((M + 127) / 128), unsigned((N + 31) / 32));
+    k_cgemm_thin<32><<<grid, 256, 0, s>>>(M, N, K, A, B, C);
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_cgemm_simt(int64_t M, int64_t N, int64_t K, const float2* A, const float2* B,
                               float2* C, cudaStream_t s) {

@@ -15,8 +15,9 @@
 //   warp 1      allocates TMEM (3 accumulators of BN fp32 columns) and one
 //               lane issues the tcgen05.mma instructions of each stage, then
 //               tcgen05.commit releases the stage;
-//   warps 2-5   epilogue: tcgen05.ld of T1, T2, T3, combine into Re/Im,
-//               stage through shared memory, coalesced complex64 stores.
+//   warps 2-9   epilogue: after each part of each K chunk, tcgen05.ld of that
+//               part, round-to-nearest FP32 promotion into Re/Im register
+//               accumulators; at the end, staged coalesced complex64 stores.
 // Every mbarrier wait is bounded (wall-clock limit); on expiry the kernel
 // sets the status word, skips the remaining work, waits (bounded) for its
 // own copies in flight, frees TMEM and returns.
@@ -147,13 +148,27 @@ struct Cfg {
   static constexpr int NSTAGE = (200 * 1024) / STAGE > NSTAGE_MAX ? NSTAGE_MAX : (200 * 1024) / STAGE;
   static constexpr int NPROD = NSPLIT == 2 ? 3 : 1;          // hi.hi, hi.lo, lo.hi
   static constexpr int TMEM_COLS = 3 * BN <= 256 ? 256 : 512;
+  static constexpr int HALF = BN / 2;                        // columns per epilogue warp
   static constexpr int SMEM = NSTAGE * STAGE + 1024 /*align*/ + 256 /*barriers*/;
   static_assert(NSTAGE >= 2, "pipeline needs at least two stages");
-  static_assert(4 * 32 * 33 * 8 <= NSTAGE * STAGE, "epilogue staging must fit in the stages");
+  static_assert(8 * 32 * 33 * 8 <= NSTAGE * STAGE, "epilogue staging must fit in the stages");
 };
+constexpr int KB_CHUNK = 4;      // k-blocks accumulated in TMEM before promotion to registers
+constexpr int EPI_WARPS = 8;
 
+// Block: warp 0 = TMA producer, warp 1 = TMEM owner + MMA issuer, warps 2..9 =
+// epilogue (two warps per TMEM lane quarter, each owning half of the BN columns).
+//
+// Accuracy: the tensor core adds each MMA's partial sum into the FP32
+// accumulator with truncation, so a long K accumulation drifts (measured:
+// relative error ~ 7e-9 * K).  The K range is therefore cut into chunks of
+// KB_CHUNK k-blocks; within a chunk the three parts (T1, T2, T3) are
+// accumulated one after another in TMEM, and after each part the epilogue
+// warps load it and add it with round-to-nearest FP32 adds into register
+// accumulators Re += T1 - T2, Im += T3 - T1 - T2, while the tensor core
+// already works on the next part.
 template <int KIND, int BN, int NSPLIT>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
     k_cgemm_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                int64_t M, int64_t N, int64_t K, float2* __restrict__ C, int32_t* status) {
   using G = Cfg<BN, NSPLIT>;
@@ -169,8 +184,10 @@ __global__ void __launch_bounds__(192, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G::NSTAGE * G::STAGE);
-  // bars[0..NSTAGE): full, [NSTAGE..2NSTAGE): empty, [2NSTAGE]: accumulators ready
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * G::NSTAGE + 1);
+  // [0,NSTAGE) full, [NSTAGE,2NSTAGE) empty, +0..2 part ready, +3..5 part drained
+  uint64_t* acc_full = bars + 2 * G::NSTAGE;
+  uint64_t* acc_empty = acc_full + 3;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + 3);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
   // A CTA of an earlier launch gave up on a wait: skip the work (the status
@@ -183,14 +200,17 @@ __global__ void __launch_bounds__(192, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t m0 = int64_t(blockIdx.y) * BM, n0 = int64_t(blockIdx.x) * BN;
   const int nkb = int((K + BK - 1) / BK);
-  const int total = nkb * 3;
+  const int nchunk = (nkb + KB_CHUNK - 1) / KB_CHUNK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < G::NSTAGE; ++s) {
       mbar_init(smem_u32(&bars[s]), 1);
       mbar_init(smem_u32(&bars[G::NSTAGE + s]), 1);
     }
-    mbar_init(smem_u32(&bars[2 * G::NSTAGE]), 1);
+    for (int p = 0; p < 3; ++p) {
+      mbar_init(smem_u32(&acc_full[p]), 1);
+      mbar_init(smem_u32(&acc_empty[p]), EPI_WARPS);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -211,78 +231,127 @@ __global__ void __launch_bounds__(192, 1)
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_a)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_b)) : "memory");
-      int issued = 0;
-      for (int i = 0; i < total; ++i) {
-        const int s = i % G::NSTAGE;
-        const uint32_t ph = (i / G::NSTAGE) & 1;
-        if (!mbar_wait(smem_u32(&bars[G::NSTAGE + s]), ph ^ 1, abort_flag, status)) break;
-        const int kb = i / 3, part = i % 3;
-        const uint32_t full = smem_u32(&bars[s]);
-        mbar_expect_tx(full, G::STAGE);
-        const uint32_t sa = smem_u32(smem + s * G::STAGE);
-        for (int sp = 0; sp < NSPLIT; ++sp)
-          tma_load_2d(sa + sp * G::A_TILE, &map_a, full, kb * BK,
-                      int((part * NSPLIT + sp) * M + m0));
-        for (int sp = 0; sp < NSPLIT; ++sp)
-          tma_load_2d(sa + NSPLIT * G::A_TILE + sp * G::B_TILE, &map_b, full, kb * BK,
-                      int((part * NSPLIT + sp) * N + n0));
-        issued = i + 1;
+      int i = 0;
+      bool ok = true;
+      for (int c = 0; c < nchunk && ok; ++c) {
+        const int kb0 = c * KB_CHUNK, kb1 = min(nkb, kb0 + KB_CHUNK);
+        for (int part = 0; part < 3 && ok; ++part) {
+          for (int kb = kb0; kb < kb1; ++kb, ++i) {
+            const int s = i % G::NSTAGE;
+            const uint32_t ph = (i / G::NSTAGE) & 1;
+            if (!mbar_wait(smem_u32(&bars[G::NSTAGE + s]), ph ^ 1, abort_flag, status)) {
+              ok = false;
+              break;
+            }
+            const uint32_t full = smem_u32(&bars[s]);
+            mbar_expect_tx(full, G::STAGE);
+            const uint32_t sa = smem_u32(smem + s * G::STAGE);
+            for (int sp = 0; sp < NSPLIT; ++sp)
+              tma_load_2d(sa + sp * G::A_TILE, &map_a, full, kb * BK,
+                          int((part * NSPLIT + sp) * M + m0));
+            for (int sp = 0; sp < NSPLIT; ++sp)
+              tma_load_2d(sa + NSPLIT * G::A_TILE + sp * G::B_TILE, &map_b, full, kb * BK,
+                          int((part * NSPLIT + sp) * N + n0));
+          }
+        }
       }
-      if (*abort_flag) {   // let the copies this lane started land before the CTA exits
-        for (int i = issued > G::NSTAGE ? issued - G::NSTAGE : 0; i < issued; ++i) {
+      if (!ok) {   // let the copies this lane started land before the CTA exits
+        for (int j = i > G::NSTAGE ? i - G::NSTAGE : 0; j < i; ++j) {
           volatile int never = 0;
-          mbar_wait(smem_u32(&bars[i % G::NSTAGE]), (i / G::NSTAGE) & 1, &never, nullptr);
+          mbar_wait(smem_u32(&bars[j % G::NSTAGE]), (j / G::NSTAGE) & 1, &never, nullptr);
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      for (int i = 0; i < total; ++i) {
-        const int s = i % G::NSTAGE;
-        const uint32_t ph = (i / G::NSTAGE) & 1;
-        if (!mbar_wait(smem_u32(&bars[s]), ph, abort_flag, status)) break;
-        tc_fence_after();
-        const int kb = i / 3, part = i % 3;
-        const uint32_t sa = smem_u32(smem + s * G::STAGE);
-        const uint32_t sb = sa + NSPLIT * G::A_TILE;
-        const uint32_t d = tmem + uint32_t(part * BN);
-#pragma unroll
-        for (int pr = 0; pr < G::NPROD; ++pr) {
-          const int ai = pr == 2 ? 1 : 0, bi = pr == 1 ? 1 : 0;
-#pragma unroll
-          for (int ks = 0; ks < BK / MMA_K; ++ks) {
-            const uint64_t adesc = smem_desc(sa + ai * G::A_TILE + ks * 32);
-            const uint64_t bdesc = smem_desc(sb + bi * G::B_TILE + ks * 32);
-            mma<KIND>(d, adesc, bdesc, IDESC, (kb | pr | ks) != 0 ? 1u : 0u);
+      int i = 0;
+      bool ok = true;
+      for (int c = 0; c < nchunk && ok; ++c) {
+        const int kb0 = c * KB_CHUNK, kb1 = min(nkb, kb0 + KB_CHUNK);
+        for (int part = 0; part < 3 && ok; ++part) {
+          if (c > 0 && !mbar_wait(smem_u32(&acc_empty[part]), (c - 1) & 1, abort_flag, status)) {
+            ok = false;
+            break;
           }
+          tc_fence_after();
+          const uint32_t d = tmem + uint32_t(part * BN);
+          for (int kb = kb0; kb < kb1; ++kb, ++i) {
+            const int s = i % G::NSTAGE;
+            const uint32_t ph = (i / G::NSTAGE) & 1;
+            if (!mbar_wait(smem_u32(&bars[s]), ph, abort_flag, status)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + s * G::STAGE);
+            const uint32_t sb = sa + NSPLIT * G::A_TILE;
+#pragma unroll
+            for (int pr = 0; pr < G::NPROD; ++pr) {
+              const int ai = pr == 2 ? 1 : 0, bi = pr == 1 ? 1 : 0;
+#pragma unroll
+              for (int ks = 0; ks < BK / MMA_K; ++ks) {
+                const uint64_t adesc = smem_desc(sa + ai * G::A_TILE + ks * 32);
+                const uint64_t bdesc = smem_desc(sb + bi * G::B_TILE + ks * 32);
+                mma<KIND>(d, adesc, bdesc, IDESC, ((kb - kb0) | pr | ks) != 0 ? 1u : 0u);
+              }
+            }
+            tc_commit(smem_u32(&bars[G::NSTAGE + s]));
+          }
+          if (ok) tc_commit(smem_u32(&acc_full[part]));   // fires when this part's MMAs are done
         }
-        tc_commit(smem_u32(&bars[G::NSTAGE + s]));
       }
-      tc_commit(smem_u32(&bars[2 * G::NSTAGE]));   // fires when every issued MMA is done
     }
   } else {
-    // epilogue warps 2..5: TMEM lane quarter = warp % 4
-    const int q = warp & 3;
-    const bool ok = mbar_wait(smem_u32(&bars[2 * G::NSTAGE]), 0, abort_flag, status);
-    tc_fence_after();
+    // epilogue warps 2..9: TMEM lane quarter q = warp % 4, column half h
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    const int col0 = h * G::HALF;
+    const uint32_t lane_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(col0);
+    float re[G::HALF], im[G::HALF];
+#pragma unroll
+    for (int j = 0; j < G::HALF; ++j) re[j] = im[j] = 0.f;
+    bool ok = true;
+    for (int c = 0; c < nchunk && ok; ++c) {
+      for (int part = 0; part < 3; ++part) {
+        if (!mbar_wait(smem_u32(&acc_full[part]), c & 1, abort_flag, status)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int sub = 0; sub < G::HALF / 32; ++sub) {
+          uint32_t r[32];
+          tmem_ld32(lane_base + uint32_t(part * BN + sub * 32), r);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float t = __uint_as_float(r[j]);
+            if (part == 0) {
+              re[sub * 32 + j] += t;
+              im[sub * 32 + j] -= t;
+            } else if (part == 1) {
+              re[sub * 32 + j] -= t;
+              im[sub * 32 + j] -= t;
+            } else {
+              im[sub * 32 + j] += t;
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[part]))
+                       : "memory");
+        }
+      }
+    }
     if (ok && !*abort_flag) {
       float2* st = reinterpret_cast<float2*>(smem) + (warp - 2) * (32 * 33);
-      const uint32_t lane_base = tmem + (uint32_t(q * 32) << 16);
-#pragma unroll 1
-      for (int c = 0; c < BN; c += 32) {
-        uint32_t r1[32], r2[32], r3[32];
-        tmem_ld32(lane_base + uint32_t(c), r1);
-        tmem_ld32(lane_base + uint32_t(BN + c), r2);
-        tmem_ld32(lane_base + uint32_t(2 * BN + c), r3);
-        tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const float t1 = __uint_as_float(r1[j]), t2 = __uint_as_float(r2[j]),
-                      t3 = __uint_as_float(r3[j]);
-          st[lane * 33 + j] = make_float2(t1 - t2, t3 - t1 - t2);
-        }
+      for (int sub = 0; sub < G::HALF / 32; ++sub) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) st[lane * 33 + j] = make_float2(re[sub * 32 + j], im[sub * 32 + j]);
         __syncwarp();
-        const int64_t gn = n0 + c + lane;
+        const int64_t gn = n0 + col0 + sub * 32 + lane;
 #pragma unroll 4
         for (int r = 0; r < 32; ++r) {
           const int64_t gm = m0 + q * 32 + r;
@@ -346,7 +415,7 @@ cudaError_t launch_t(const TcGemmMaps& maps, int64_t M, int64_t N, int64_t K, fl
   }
   dim3 grid(unsigned((N + BN - 1) / BN), unsigned((M + BM - 1) / BM));
   if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
-  kern<<<grid, 192, G::SMEM, s>>>(maps.a, maps.b, M, N, K, C, status);
+  kern<<<grid, 64 + 32 * EPI_WARPS, G::SMEM, s>>>(maps.a, maps.b, M, N, K, C, status);
   return cudaGetLastError();
 }
 

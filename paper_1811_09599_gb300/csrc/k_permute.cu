@@ -24,56 +24,95 @@
 
 namespace qflex {
 
-bool build_perm_tile(int nbits, const int64_t* w, PermTile* t) {
-  const int T = std::min(10, nbits);
+bool build_perm_tile(int nbits, const int64_t* w, PermTile* t, const int64_t* w_out) {
+  const int T = std::min(kPermTileBits, nbits);
   if (nbits - T > kPermMaxRest) return false;
-  std::vector<int> by_w(nbits);
-  for (int i = 0; i < nbits; ++i) by_w[i] = i;
+  std::vector<int64_t> wo(nbits);
+  for (int i = 0; i < nbits; ++i) wo[i] = w_out ? w_out[i] : (int64_t(1) << i);
+  std::vector<int> by_w(nbits), by_o(nbits);
+  for (int i = 0; i < nbits; ++i) by_w[i] = by_o[i] = i;
   std::sort(by_w.begin(), by_w.end(), [&](int a, int b) { return w[a] < w[b]; });
+  std::sort(by_o.begin(), by_o.end(), [&](int a, int b) { return wo[a] < wo[b]; });
   std::vector<char> in_u(nbits, 0);
   std::vector<int> U;
   auto add = [&](int b) {
     if (!in_u[b] && int(U.size()) < T) { in_u[b] = 1; U.push_back(b); }
   };
   for (int i = 0; i < std::min(5, nbits); ++i) add(by_w[i]);   // input-fastest bits
-  for (int i = 0; i < std::min(5, nbits); ++i) add(i);         // output-fastest bits
+  for (int i = 0; i < std::min(5, nbits); ++i) add(by_o[i]);   // output-fastest bits
   int pw = 0, po = 0;
   while (int(U.size()) < T) {                                    // extend alternately
     while (pw < nbits && in_u[by_w[pw]]) ++pw;
     if (pw < nbits) add(by_w[pw]);
-    while (po < nbits && in_u[po]) ++po;
-    if (po < nbits) add(po);
+    while (po < nbits && in_u[by_o[po]]) ++po;
+    if (po < nbits) add(by_o[po]);
   }
   std::vector<int> load = U, store = U;
   std::sort(load.begin(), load.end(), [&](int a, int b) { return w[a] < w[b]; });
-  std::sort(store.begin(), store.end());
+  std::sort(store.begin(), store.end(), [&](int a, int b) { return wo[a] < wo[b]; });
   std::vector<int> pos_in_load(nbits, -1);
   for (int i = 0; i < T; ++i) pos_in_load[load[i]] = i;
-  for (int a = 0; a < 32; ++a) {
+  // Slot map slot(L) = L ^ g(L): g sends each of the store-fast bits 0..3
+  // that sits at load position >= 4 onto a low position that no store-fast
+  // bit occupies, so 16 consecutive loads and 16 consecutive stores both
+  // land in 16 distinct low-4-bit slots.  slot is linear over GF(2), so it
+  // distributes over the lo/hi table split.
+  int gmask[kPermTileBits] = {0};
+  {
+    bool used[4] = {false, false, false, false};
+    for (int b = 0; b < std::min(4, T); ++b)
+      if (pos_in_load[store[b]] < 4) used[pos_in_load[store[b]]] = true;
+    int f = 0;
+    for (int b = 0; b < std::min(4, T); ++b) {
+      const int p = pos_in_load[store[b]];
+      if (p < 4) continue;
+      while (f < 4 && used[f]) ++f;
+      if (f < 4) {
+        gmask[p] = 1 << f;
+        used[f] = true;
+      }
+    }
+  }
+  auto slot = [&](int L) {
+    int x = L;
+    for (int p = 4; p < T; ++p)
+      if ((L >> p) & 1) x ^= gmask[p];
+    return x;
+  };
+  for (int a = 0; a < 64; ++a) {
     int64_t il = 0, ih = 0, ol = 0, oh = 0;
     int32_t sl = 0, sh = 0;
-    for (int b = 0; b < 5; ++b) {
+    for (int b = 0; b < 6; ++b) {
       if (!((a >> b) & 1)) continue;
-      if (b < T) {
+      if (b < 5 && b < T) {
         il += w[load[b]];
-        ol += int64_t(1) << store[b];
+        ol += wo[store[b]];
         sl += 1 << pos_in_load[store[b]];
       }
       if (5 + b < T) {
         ih += w[load[5 + b]];
-        oh += int64_t(1) << store[5 + b];
+        oh += wo[store[5 + b]];
         sh += 1 << pos_in_load[store[5 + b]];
       }
     }
-    t->in_lo[a] = il; t->in_hi[a] = ih;
-    t->out_lo[a] = ol; t->out_hi[a] = oh;
-    t->sm_lo[a] = sl; t->sm_hi[a] = sh;
+    const int la = a < (1 << std::min(5, T)) ? a : 0;
+    const int ha = T > 5 && a < (1 << (T - 5)) ? a : 0;
+    if (a < 32) {
+      t->in_lo[a] = il;
+      t->out_lo[a] = ol;
+      t->ld_lo[a] = slot(la);
+      t->st_lo[a] = slot(sl);
+    }
+    t->in_hi[a] = ih;
+    t->out_hi[a] = oh;
+    t->ld_hi[a] = slot(ha << 5);
+    t->st_hi[a] = slot(sh);
   }
   int r = 0;
   for (int b = 0; b < nbits; ++b) {
     if (in_u[b]) continue;
     t->rest_in[r] = w[b];
-    t->rest_out[r] = int64_t(1) << b;
+    t->rest_out[r] = wo[b];
     ++r;
   }
   for (int i = r; i < kPermMaxRest; ++i) t->rest_in[i] = t->rest_out[i] = 0;
@@ -116,37 +155,75 @@ __device__ __forceinline__ void put(void* out, int64_t o, float2 v, int nsplit, 
   }
 }
 
-__device__ __forceinline__ int swz(int j) { return j ^ ((j >> 5) & 15); }
-
 template <int FMT>
-__global__ void __launch_bounds__(256) k_permute_tiled(const float2* __restrict__ in, int64_t in_base,
+__global__ void __launch_bounds__(256, 6) k_permute_tiled(const float2* __restrict__ in, int64_t in_base,
                                                        const __grid_constant__ PermTile t, void* out,
                                                        int nsplit, int64_t plane) {
-  __shared__ float2 tile[1024];
-  __shared__ int64_t s_in_lo[32], s_in_hi[32], s_out_lo[32], s_out_hi[32];
-  __shared__ int32_t s_sm_lo[32], s_sm_hi[32];
-  if (threadIdx.x < 32) {
+  static_assert((1 << kPermTileBits) % 256 == 0, "tile must be a multiple of the block");
+  __shared__ float2 tile[1 << kPermTileBits];
+  __shared__ int64_t s_in_lo[32], s_in_hi[64], s_out_lo[32], s_out_hi[64];
+  __shared__ int32_t s_ld_lo[32], s_ld_hi[64], s_st_lo[32], s_st_hi[64];
+  if (threadIdx.x < 64) {
     const int a = threadIdx.x;
-    s_in_lo[a] = t.in_lo[a]; s_in_hi[a] = t.in_hi[a];
-    s_out_lo[a] = t.out_lo[a]; s_out_hi[a] = t.out_hi[a];
-    s_sm_lo[a] = t.sm_lo[a]; s_sm_hi[a] = t.sm_hi[a];
+    if (a < 32) {
+      s_in_lo[a] = t.in_lo[a];
+      s_out_lo[a] = t.out_lo[a];
+      s_ld_lo[a] = t.ld_lo[a];
+      s_st_lo[a] = t.st_lo[a];
+    }
+    s_in_hi[a] = t.in_hi[a];
+    s_out_hi[a] = t.out_hi[a];
+    s_ld_hi[a] = t.ld_hi[a];
+    s_st_hi[a] = t.st_hi[a];
   }
   __syncthreads();
+  // Software pipeline: the global loads of the next tile are issued before
+  // the stores of the current one, so HBM reads stay in flight across the
+  // shared-memory round trip.  Each thread holds kPer entries in registers.
+  constexpr int kPer = (1 << kPermTileBits) / 256;
   const int n = 1 << t.tile_bits;
-  for (int64_t tb = blockIdx.x; tb < t.n_tiles; tb += gridDim.x) {
-    int64_t ib = in_base, ob = 0;
+  auto tile_base = [&](int64_t tb, int64_t& ib, int64_t& ob) {
+    ib = in_base;
+    ob = 0;
     for (int r = 0; r < t.n_rest; ++r) {
       if ((tb >> r) & 1) {
         ib += t.rest_in[r];
         ob += t.rest_out[r];
       }
     }
-    for (int j = threadIdx.x; j < n; j += blockDim.x)
-      tile[swz(j)] = in[ib + s_in_lo[j & 31] + s_in_hi[j >> 5]];
+  };
+  float2 v[kPer];
+  int64_t tb = blockIdx.x, ib = 0, ob = 0;
+  if (tb < t.n_tiles) {
+    tile_base(tb, ib, ob);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int j = threadIdx.x + k * 256;
+      if (j < n) v[k] = __ldg(in + ib + s_in_lo[j & 31] + s_in_hi[j >> 5]);
+    }
+  }
+  for (; tb < t.n_tiles; tb += gridDim.x) {
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int j = threadIdx.x + k * 256;
+      if (j < n) tile[s_ld_lo[j & 31] ^ s_ld_hi[j >> 5]] = v[k];
+    }
     __syncthreads();
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      const float2 v = tile[swz(s_sm_lo[j & 31] + s_sm_hi[j >> 5])];
-      put<FMT>(out, ob + s_out_lo[j & 31] + s_out_hi[j >> 5], v, nsplit, plane);
+    const int64_t cur_ob = ob;
+    const int64_t nxt = tb + gridDim.x;
+    if (nxt < t.n_tiles) {
+      tile_base(nxt, ib, ob);
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        const int j = threadIdx.x + k * 256;
+        if (j < n) v[k] = __ldg(in + ib + s_in_lo[j & 31] + s_in_hi[j >> 5]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int j = threadIdx.x + k * 256;
+      if (j < n) put<FMT>(out, cur_ob + s_out_lo[j & 31] + s_out_hi[j >> 5],
+                          tile[s_st_lo[j & 31] ^ s_st_hi[j >> 5]], nsplit, plane);
     }
     __syncthreads();
   }

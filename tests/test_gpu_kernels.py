@@ -76,7 +76,8 @@ def _gemm_case(K, prec, M, N, Kd, seed):
 
 
 SHAPES = [(128, 128, 64), (256, 128, 128), (300, 200, 72), (128, 64, 8), (1024, 512, 256),
-          (4096, 256, 256), (130, 33, 40), (7, 5, 3)]
+          (4096, 256, 256), (130, 33, 40), (7, 5, 3), (65536, 16, 16), (20000, 32, 256),
+          (4096, 17, 16), (2048, 256, 16)]
 
 
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-5)])
@@ -91,6 +92,17 @@ def test_cgemm_tensor_core(K, prec, tol):
         err = _gemm_case(K, prec, M, N, Kd, 10 + i)
         assert err < tol, (prec, M, N, Kd, err)
     assert K.device_status(0) == 0
+
+
+@pytest.mark.parametrize("Kd", [4096, 32768])
+def test_cgemm_long_k_accuracy(K, Kd):
+    """Long contractions (K up to 2^15, the 7x7 1+40+1 shape) keep the split
+    tensor-core forms within their tolerances: chunked FP32 promotion of the
+    TMEM accumulators bounds the accumulation drift."""
+    tol = {"fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 1e-4}
+    for prec in ("fp32", "tf32x3", "bf16x3"):
+        err = _gemm_case(K, prec, 256, 256, Kd, 7)
+        assert err < tol[prec], (prec, Kd, err)
 
 
 def test_cgemm_plain_precisions_reported(K):
