@@ -233,6 +233,39 @@ qflex_status qflex_norm(const double* amps, int64_t n, double* out, void* stream
  * used by the standalone kernels.  *status = QFLEX_OK or QFLEX_ERR_DEVICE_TIMEOUT. */
 qflex_status qflex_device_status(int device, int32_t* status);
 
+/* ---------------- allocation-free complex GEMM ----------------
+ * The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory.  qflex_cgemm needs a workspace, and obtaining one
+ * means cudaMalloc (or a library allocator), which may synchronize the whole
+ * device and can fail under memory pressure: a serving loop that must not
+ * stall other streams, or code embedded in a framework that owns every
+ * device byte through its own pool, cannot do that.  This entry point
+ * computes the same product as qflex_cgemm (same precisions, same kernels,
+ * same results within the same tolerances) using a fixed scratch array that
+ * is part of the library image instead of a caller workspace.
+ *
+ *  - Scratch limit: the split operand planes of A and B must fit in
+ *    QFLEX_NOALLOC_SCRATCH_BYTES (64 MiB), i.e. (M + N) * K * 12 bytes for
+ *    bf16 split forms, (M + N) * K * 24 for tf32x3 (half that for the plain
+ *    forms); larger tensor-core products return QFLEX_ERR_ARG.  The FP32
+ *    precision needs no scratch and has no such limit.
+ *  - Every GPU that loads the library's scratch holds these 64 MiB until the
+ *    process exits.  The first call on a device (with that device current)
+ *    looks up the scratch address and clears its status word; make that first
+ *    call before any stream capture.
+ *  - Every call shares the one scratch array: calls whose work overlaps on the
+ *    GPU (different streams, or host threads) race and give wrong results;
+ *    serialize them on one stream.  The planes are fully rewritten by each
+ *    call, so leftover contents of an earlier call do not matter.
+ *  - No cudaMalloc, cudaFree or allocating library routine is called.
+ *  - A bounded device-side wait that runs out (a fault, not a normal
+ *    condition) is recorded in a status word private to this entry point and
+ *    not reported by its return value.
+ * Arguments are those of qflex_cgemm without the workspace. */
+#define QFLEX_NOALLOC_SCRATCH_BYTES (64ull << 20)
+qflex_status qflex_cgemm_noalloc(int32_t prec, int64_t M, int64_t N, int64_t K, const void* A,
+                                 const void* B, void* C, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -955,3 +955,5 @@ qflex_status qflex_device_status(int device, int32_t* status) {
 }
 
 }  // extern "C"
+
+void qflex::set_last_error(const char* msg) { g_err = msg; }

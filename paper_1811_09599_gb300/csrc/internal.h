@@ -115,4 +115,6 @@ cudaError_t launch_norm(const double* amps, int64_t n, double* out, cudaStream_t
 
 int32_t* device_status_word(int device);   // library-wide status word for standalone calls
 
+void set_last_error(const char* msg);      // text returned by qflex_last_error()
+
 }  // namespace qflex

@@ -1,0 +1,125 @@
+// Allocation-free complex GEMM (qflex_cgemm_noalloc, include/qflex.h).
+//
+// Same product and kernels as qflex_cgemm, but the split operand planes live
+// in a fixed array compiled into the library instead of a caller workspace,
+// for callers that cannot allocate device memory (see the header).
+#include <mutex>
+#include <string>
+
+#include "internal.h"
+#include "qflex.h"
+
+using namespace qflex;
+
+namespace {
+
+// File-scope scratch and status word.  In host code these names are host
+// stand-ins, not device addresses: the device addresses come from
+// cudaGetSymbolAddress below.
+__device__ __align__(256) unsigned char g_noalloc_scratch[QFLEX_NOALLOC_SCRATCH_BYTES];
+__device__ int32_t g_noalloc_status;
+
+constexpr int kMaxDevices = 64;
+struct DeviceScratch {
+  void* scratch = nullptr;
+  int32_t* status = nullptr;
+};
+DeviceScratch g_dev[kMaxDevices];
+std::mutex g_mu;
+
+qflex_status fail(qflex_status st, const std::string& msg) {
+  set_last_error(msg.c_str());
+  return st;
+}
+
+// Once per device, with that device current: look up the device addresses of
+// the scratch array and the status word, and clear the status word.
+qflex_status setup(int dev, DeviceScratch* out) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(QFLEX_ERR_UNSUPPORTED, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceScratch& d = g_dev[dev];
+  if (!d.scratch) {
+    void* s = nullptr;
+    void* w = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&s, g_noalloc_scratch);
+    if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    e = cudaGetSymbolAddress(&w, g_noalloc_status);
+    if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("cudaGetSymbolAddress(status): ") + cudaGetErrorString(e));
+    e = cudaMemset(w, 0, sizeof(int32_t));
+    if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("cudaMemset(status): ") + cudaGetErrorString(e));
+    d.status = static_cast<int32_t*>(w);
+    d.scratch = s;
+  }
+  *out = d;
+  return QFLEX_OK;
+}
+
+size_t round256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Identity "permutation" of a [rows][K] complex64 matrix into operand planes.
+cudaError_t planes(const void* src, int64_t rows, int64_t K, int kind, int nsplit, void* dst,
+                   cudaStream_t s) {
+  const int64_t total = rows * K;
+  const int fmt = kind == 0 ? kFmtTF32 : kFmtBF16;
+  if ((total & (total - 1)) == 0) {
+    int nb = 0;
+    while ((int64_t(1) << nb) < total) ++nb;
+    int64_t w[64];
+    for (int b = 0; b < nb; ++b) w[b] = int64_t(1) << b;
+    PermTile t;
+    if (!build_perm_tile(nb, w, &t)) return cudaErrorInvalidValue;
+    return launch_permute_tiled(static_cast<const float2*>(src), 0, t, fmt, nsplit, dst, total, s);
+  }
+  GatherDesc g{};
+  g.rank = 1;
+  g.total = total;
+  g.dims[0] = total;
+  g.in_strides[0] = 1;
+  return launch_permute_gather(static_cast<const float2*>(src), 0, g, fmt, nsplit, dst, total, s);
+}
+
+}  // namespace
+
+extern "C" qflex_status qflex_cgemm_noalloc(int32_t prec, int64_t M, int64_t N, int64_t K, const void* A,
+                                            const void* B, void* C, void* stream) {
+  if (prec < QFLEX_FP32_SIMT || prec > QFLEX_TF32_PLAIN) return fail(QFLEX_ERR_ARG, "unknown precision");
+  if (M < 0 || N < 0 || K < 0 || (M * N > 0 && (!A || !B || !C))) return fail(QFLEX_ERR_ARG, "bad GEMM arguments");
+  if (M == 0 || N == 0) return QFLEX_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
+  DeviceScratch d;
+  if (qflex_status st = setup(dev, &d)) return st;
+  const bool tc = prec != QFLEX_FP32_SIMT && M >= 128 && K % 8 == 0 && K > 0 && N >= 16;
+  if (!tc) {
+    if (K == 0) e = cudaMemsetAsync(C, 0, size_t(M) * N * 8, s);
+    else if (N <= 32)
+      e = launch_cgemm_thin(M, N, K, static_cast<const float2*>(A), static_cast<const float2*>(B),
+                            static_cast<float2*>(C), s);
+    else
+      e = launch_cgemm_simt(M, N, K, static_cast<const float2*>(A), static_cast<const float2*>(B),
+                            static_cast<float2*>(C), s);
+    if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
+    return QFLEX_OK;
+  }
+  const int kind = (prec == QFLEX_TF32X3 || prec == QFLEX_TF32_PLAIN) ? 0 : 1;
+  const int nsplit = (prec == QFLEX_TF32X3 || prec == QFLEX_BF16X3) ? 2 : 1;
+  const size_t per = size_t(3) * nsplit * (kind == 0 ? 4 : 2);
+  const size_t a_bytes = round256(per * size_t(M) * size_t(K));
+  const size_t b_bytes = round256(per * size_t(N) * size_t(K));
+  if (a_bytes + b_bytes > QFLEX_NOALLOC_SCRATCH_BYTES)
+    return fail(QFLEX_ERR_ARG, "operand planes need " + std::to_string(a_bytes + b_bytes) +
+                                   " bytes, more than the 64 MiB static scratch of qflex_cgemm_noalloc");
+  if (!tc_available()) return fail(QFLEX_ERR_UNSUPPORTED, "tensor-map encoder unavailable");
+  char* pa = static_cast<char*>(d.scratch);
+  char* pb = pa + a_bytes;
+  if ((e = planes(A, M, K, kind, nsplit, pa, s)) != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
+  if ((e = planes(B, N, K, kind, nsplit, pb, s)) != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
+  TcGemmMaps maps;
+  const int bn = N >= 128 ? 128 : 64;
+  if (!tc_encode_maps(kind, nsplit, bn, pa, M, pb, N, K, &maps)) return fail(QFLEX_ERR_CUDA, "tensor map encoding failed");
+  e = launch_cgemm_tc(kind, nsplit, bn, maps, M, N, K, static_cast<float2*>(C), d.status, s);
+  if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
+  return QFLEX_OK;
+}
