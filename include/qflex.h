@@ -166,13 +166,21 @@ qflex_status qflex_amplitudes(qflex_plan plan, const double* angles, const uint8
                               int64_t n_bs, const int64_t* slice_ids, int64_t n_slice_ids,
                               double* amps_out, void* stream);
 
+/* Allocate the workspace of qflex_amplitudes_grad (once per plan; later calls
+ * return QFLEX_OK at once): dedicated buffers that keep every intermediate of
+ * a slice for the reverse pass (checkpointed slice intermediates), their
+ * cotangents, FP64 grid-tensor cotangents and reverse-GEMM scratch.  This is
+ * the only plan call after qflex_plan_create that allocates device memory. */
+qflex_status qflex_plan_enable_gradients(qflex_plan plan);
+
 /* Amplitudes and the gradient of L = Re sum_{b,j} conj(g[b][j]) amps[b][j] with respect to
  * every angle (the paper has no gradients): environments of each grid tensor by the
  * reverse pass through the same pairwise contractions, summed over slices, then the
  * derivative of each grid tensor w.r.t. each rotation angle from prefix/suffix products of
  * its qubit's gate line.  grad_amps: device complex128 [n_bs][2^n_open] (g);
- * grad_angles: device double [n_params], overwritten.  Requires the FP32_SIMT or a
- * tensor-core precision plan; intermediates of each slice are kept (checkpointed). */
+ * grad_angles: device double [n_params], overwritten; amps_out as in qflex_amplitudes.
+ * Requires qflex_plan_enable_gradients.  The reverse GEMMs run in the plan's precision;
+ * grid-tensor cotangents and the angle gradients are summed in FP64. */
 qflex_status qflex_amplitudes_grad(qflex_plan plan, const double* angles,
                                    const uint8_t* bitstrings, int64_t n_bs,
                                    const int64_t* slice_ids, int64_t n_slice_ids,

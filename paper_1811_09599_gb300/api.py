@@ -115,8 +115,13 @@ class Plan:
                                         C.c_void_p(out.data_ptr()), _stream_handle(stream)))
         return torch.view_as_complex(out.view(n_bs, T, 2))
 
+    def enable_gradients(self):
+        """qflex_plan_enable_gradients: allocate the reverse-pass workspace once."""
+        check(self.lib.qflex_plan_enable_gradients(self.handle))
+
     def amplitudes_grad(self, bitstrings, angles, grad_amps, slice_ids=None, stream=None):
         """(amps, grad_angles) for L = Re sum conj(g) amps (qflex_amplitudes_grad)."""
+        self.enable_gradients()
         dev = torch.device("cuda", self.device)
         n_bs = bitstrings.shape[0]
         T = 1 << self.n_open

@@ -83,7 +83,24 @@ struct Step {
   int out_buf = -1;
   uint64_t dep = 0;
   std::vector<int> out_legs;
+  std::vector<int> ml, nl, sh;   // free legs of dst, free legs of src, contracted legs
   TcGemmMaps maps{};
+};
+
+// One GEMM of the reverse pass, C'[m][n] = sum_k X[m][k] Y[n][k], followed by
+// the scatter of C' into the cotangent of the step's dst (ga) or src (gb).
+struct BwdGemm {
+  int64_t M = 0, N = 0, K = 0;
+  int route = 0;                 // 0 FP32 tiled, 1 FP32 thin, 2 tensor cores
+  int bn = 128;
+  bool x_direct = false;         // X is the output cotangent itself, already [M][K]
+  PermTile xt{}, yt{}, st{};     // producers of X and Y, scatter of C'
+  Ref ysrc;                      // forward tensor feeding Y
+  Ref target;                    // view whose cotangent receives C'
+  TcGemmMaps maps{};
+};
+struct StepGrad {
+  BwdGemm ga, gb;
 };
 
 struct Buf {
@@ -128,6 +145,19 @@ struct qflex_plan_s {
   int32_t* d_status = nullptr;
   cudaStream_t last_stream = nullptr;
   // profiling: event pairs around launches
+  // gradients (qflex_plan_enable_gradients)
+  bool grad_ready = false;
+  std::vector<StepGrad> sg;
+  std::vector<size_t> fwd_off, w_off;          // dedicated forward / cotangent buffers
+  size_t grad_bytes = 0;
+  char* d_gws = nullptr;
+  char* d_garena = nullptr;
+  char* d_warena = nullptr;
+  double2* d_wgrid = nullptr;
+  void* d_gA = nullptr;
+  void* d_gB = nullptr;
+  float2* d_gC = nullptr;
+  bool grad_active = false;                    // forward runs on the dedicated buffers
   bool profiling = false;
   int32_t prof_mask = 0;
   std::vector<cudaEvent_t> ev_pool;
@@ -379,6 +409,9 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
     s.tc = tc_prec && s.M >= 128 && s.N >= 32 && s.K >= 16 && s.K % 8 == 0 &&
            double(s.M) * s.N * s.K >= double(1 << 24) && !(s.N <= 32 && s.K <= 64);
     s.bn = s.N >= 128 ? 128 : 64;
+    s.ml = ml;
+    s.nl = nl;
+    s.sh = shared;
     s.out_legs = ml;
     s.out_legs.insert(s.out_legs.end(), nl.begin(), nl.end());
     std::vector<int> ta = ml, tb = nl;
@@ -510,9 +543,13 @@ qflex_status allocate(qflex_plan_s& p) {
   return QFLEX_OK;
 }
 
+char* buf_ptr(const qflex_plan_s& p, int id) {
+  return p.grad_active ? p.d_garena + p.fwd_off[id] : p.d_arena + p.bufs[id].offset;
+}
+
 const float2* ref_ptr(const qflex_plan_s& p, const Ref& r) {
   if (r.grid) return p.d_grid + p.gmeta[r.id].offset;
-  return reinterpret_cast<const float2*>(p.d_arena + p.bufs[r.id].offset);
+  return reinterpret_cast<const float2*>(buf_ptr(p, r.id));
 }
 
 int64_t ref_base(const Ref& r, const std::vector<int64_t>& vals) {
@@ -571,7 +608,7 @@ cudaError_t run_step(qflex_plan_s& p, const Step& st, const std::vector<int64_t>
       return e;
     B = static_cast<const float2*>(p.d_opB);
   }
-  float2* C = reinterpret_cast<float2*>(p.d_arena + p.bufs[st.out_buf].offset);
+  float2* C = reinterpret_cast<float2*>(buf_ptr(p, st.out_buf));
   const double mnk = double(st.M) * double(st.N) * double(st.K);
   const double mma = st.tc ? mnk * 3.0 * (p.nsplit == 2 ? 3.0 : 1.0) * 2.0 : 0.0;
   const double gbytes = 8.0 * (double(st.M) * st.K + double(st.N) * st.K + double(st.M) * st.N);
@@ -581,6 +618,174 @@ cudaError_t run_step(qflex_plan_s& p, const Step& st, const std::vector<int64_t>
     });
   return timed(p, 2, 8.0 * mnk, 0, gbytes, s, [&] {
     return st.N <= 32 ? launch_cgemm_thin(st.M, st.N, st.K, A, B, C, s) : launch_cgemm_simt(st.M, st.N, st.K, A, B, C, s);
+  });
+}
+
+
+// ------------------------------------------------------------------ reverse pass
+int route_of(const qflex_plan_s& p, int64_t M, int64_t N, int64_t K) {
+  const bool tc = p.prec != QFLEX_FP32_SIMT && M >= 128 && N >= 32 && K >= 16 && K % 8 == 0 &&
+                  double(M) * N * K >= double(1 << 24) && !(N <= 32 && K <= 64);
+  return tc ? 2 : (N <= 32 ? 1 : 0);
+}
+
+// Tile tables of a map whose logical index runs over `order` (row-major): each
+// leg moves the input by its stride in `in` and the output by its stride in `out`.
+bool leg_map(const std::vector<int>& order, const std::vector<int>& in_legs,
+             const std::vector<int64_t>& in_strides, const std::vector<int>& out_legs,
+             const std::vector<int64_t>& out_strides, const std::vector<int64_t>& dim, PermTile* t) {
+  std::vector<int64_t> wi, wo;
+  for (int a = int(order.size()) - 1; a >= 0; --a) {
+    const int l = order[a];
+    auto ii = std::find(in_legs.begin(), in_legs.end(), l);
+    auto oo = std::find(out_legs.begin(), out_legs.end(), l);
+    if (ii == in_legs.end() || oo == out_legs.end() || !is_pow2(dim[l])) return false;
+    const int64_t si = in_strides[ii - in_legs.begin()], so = out_strides[oo - out_legs.begin()];
+    for (int b = 0; b < ilog2(dim[l]); ++b) {
+      wi.push_back(si << b);
+      wo.push_back(so << b);
+    }
+  }
+  return build_perm_tile(int(wi.size()), wi.data(), t, wo.data());
+}
+
+std::vector<int64_t> contiguous(const std::vector<int>& legs, const std::vector<int64_t>& dim) {
+  std::vector<int64_t> st(legs.size());
+  int64_t v = 1;
+  for (int a = int(legs.size()) - 1; a >= 0; --a) {
+    st[a] = v;
+    v *= dim[legs[a]];
+  }
+  return st;
+}
+
+std::vector<int> cat(const std::vector<int>& a, const std::vector<int>& b) {
+  std::vector<int> r = a;
+  r.insert(r.end(), b.begin(), b.end());
+  return r;
+}
+
+// Build one reverse GEMM: C' = X Y^T with X taken from the cotangent W of the
+// step output (legs `wlegs`, contiguous) in order xorder = (rows, inner),
+// Y from the forward view `ysrc` in order (cols, inner), and C' (rows, cols)
+// scattered into the view `target`.
+bool make_bwd(const qflex_plan_s& p, const std::vector<int>& wlegs, const std::vector<int>& rows,
+              const std::vector<int>& inner, const std::vector<int>& cols, const Ref& ysrc,
+              const Ref& target, BwdGemm* g) {
+  const auto& dim = p.leg_dim;
+  g->M = leg_product(rows, dim);
+  g->K = leg_product(inner, dim);
+  g->N = leg_product(cols, dim);
+  g->route = route_of(p, g->M, g->N, g->K);
+  g->bn = g->N >= 128 ? 128 : 64;
+  g->ysrc = ysrc;
+  g->target = target;
+  const std::vector<int> xorder = cat(rows, inner), yorder = cat(cols, inner), corder = cat(rows, cols);
+  g->x_direct = g->route != 2 && xorder == wlegs;
+  const auto wst = contiguous(wlegs, dim);
+  if (!leg_map(xorder, wlegs, wst, xorder, contiguous(xorder, dim), dim, &g->xt)) return false;
+  if (!leg_map(yorder, ysrc.legs, ysrc.strides, yorder, contiguous(yorder, dim), dim, &g->yt)) return false;
+  if (!leg_map(target.legs, corder, contiguous(corder, dim), target.legs, target.strides, dim, &g->st))
+    return false;
+  return true;
+}
+
+qflex_status build_grad(qflex_plan_s& p) {
+  p.sg.resize(p.steps.size());
+  // forward views of each step's operands, as recorded by the planner
+  for (size_t i = 0; i < p.steps.size(); ++i) {
+    const Step& st = p.steps[i];
+    const Ref& ra = st.A.ref;
+    const Ref& rb = st.B.ref;
+    StepGrad& g = p.sg[i];
+    // W_A[m][k] = sum_n W_C[m][n] B[n][k]
+    if (!make_bwd(p, st.out_legs, st.ml, st.nl, st.sh, rb, ra, &g.ga) ||
+        !make_bwd(p, st.out_legs, st.nl, st.ml, st.sh, ra, rb, &g.gb))
+      return fail(QFLEX_ERR_UNSUPPORTED, "reverse pass needs power-of-two bond dimensions");
+  }
+  size_t off = 0;
+  p.fwd_off.resize(p.bufs.size());
+  p.w_off.resize(p.bufs.size());
+  for (size_t b = 0; b < p.bufs.size(); ++b) {
+    p.fwd_off[b] = off;
+    off += align256(size_t(p.bufs[b].elems) * 8);
+  }
+  const size_t arena = off;
+  size_t xa = 0, yb = 0, cc = 0;
+  for (const StepGrad& g : p.sg)
+    for (const BwdGemm* b : {&g.ga, &g.gb}) {
+      xa = std::max(xa, operand_bytes(p, b->route == 2, b->M * b->K));
+      yb = std::max(yb, operand_bytes(p, b->route == 2, b->N * b->K));
+      cc = std::max(cc, size_t(b->M * b->N) * 8);
+    }
+  p.grad_bytes = 2 * arena + align256(size_t(p.grid_elems) * 16) + align256(xa) + align256(yb) + align256(cc);
+  if (cudaMalloc(&p.d_gws, p.grad_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p.d_gws = nullptr;
+    return fail(QFLEX_ERR_OOM, "gradient workspace allocation of " + std::to_string(p.grad_bytes) + " bytes failed");
+  }
+  char* c = p.d_gws;
+  p.d_garena = c;
+  c += arena;
+  p.d_warena = c;
+  c += arena;
+  for (size_t b = 0; b < p.bufs.size(); ++b) p.w_off[b] = p.fwd_off[b];
+  p.d_wgrid = reinterpret_cast<double2*>(c);
+  c += align256(size_t(p.grid_elems) * 16);
+  p.d_gA = c;
+  c += align256(xa);
+  p.d_gB = c;
+  c += align256(yb);
+  p.d_gC = reinterpret_cast<float2*>(c);
+  for (StepGrad& g : p.sg)
+    for (BwdGemm* b : {&g.ga, &g.gb})
+      if (b->route == 2 && !tc_encode_maps(p.tc_kind, p.nsplit, b->bn, p.d_gA, b->M, p.d_gB, b->N, b->K, &b->maps))
+        return fail(QFLEX_ERR_CUDA, "tensor map encoding failed");
+  p.grad_ready = true;
+  return QFLEX_OK;
+}
+
+cudaError_t run_bwd(qflex_plan_s& p, const Step& st, const BwdGemm& g, const std::vector<int64_t>& vals,
+                    cudaStream_t s) {
+  cudaError_t e;
+  const float2* W = reinterpret_cast<const float2*>(p.d_warena + p.w_off[st.out_buf]);
+  const int fmt = g.route == 2 ? (p.tc_kind == 0 ? kFmtTF32 : kFmtBF16) : kFmtC64;
+  const double out_per = g.route == 2 ? 3.0 * p.nsplit * (p.tc_kind == 0 ? 4 : 2) : 8.0;
+  const float2* X = W;
+  if (!g.x_direct) {
+    if ((e = timed(p, 1, 0, 0, double(g.M) * g.K * (8.0 + out_per), s, [&] {
+           return launch_permute_tiled(W, 0, g.xt, fmt, p.nsplit, p.d_gA, g.M * g.K, s);
+         })) != cudaSuccess)
+      return e;
+    X = static_cast<const float2*>(p.d_gA);
+  }
+  if ((e = timed(p, 1, 0, 0, double(g.N) * g.K * (8.0 + out_per), s, [&] {
+         return launch_permute_tiled(ref_ptr(p, g.ysrc), ref_base(g.ysrc, vals), g.yt, fmt, p.nsplit, p.d_gB,
+                                     g.N * g.K, s);
+       })) != cudaSuccess)
+    return e;
+  const float2* Y = static_cast<const float2*>(p.d_gB);
+  const double mnk = double(g.M) * double(g.N) * double(g.K);
+  if (g.route == 2) {
+    e = timed(p, 3, 8.0 * mnk, mnk * 3.0 * (p.nsplit == 2 ? 3.0 : 1.0) * 2.0, 0, s, [&] {
+      return launch_cgemm_tc(p.tc_kind, p.nsplit, g.bn, g.maps, g.M, g.N, g.K, p.d_gC, p.d_status, s);
+    });
+  } else {
+    e = timed(p, 2, 8.0 * mnk, 0, 0, s, [&] {
+      return g.route == 1 ? launch_cgemm_thin(g.M, g.N, g.K, X, Y, p.d_gC, s)
+                          : launch_cgemm_simt(g.M, g.N, g.K, X, Y, p.d_gC, s);
+    });
+  }
+  if (e != cudaSuccess) return e;
+  // scatter C' into the target's cotangent: accumulate (FP64) for grid tensors,
+  // plain write for intermediates (each is consumed by exactly one step)
+  return timed(p, 1, 0, 0, double(g.M) * g.N * 16.0, s, [&] {
+    if (g.target.grid) {
+      double2* out = p.d_wgrid + p.gmeta[g.target.id].offset + ref_base(g.target, vals);
+      return launch_permute_tiled(p.d_gC, 0, g.st, kFmtAccC128, 1, out, 0, s);
+    }
+    float2* out = reinterpret_cast<float2*>(p.d_warena + p.w_off[g.target.id]);
+    return launch_permute_tiled(p.d_gC, 0, g.st, kFmtC64, 1, out, 0, s);
   });
 }
 
@@ -666,6 +871,7 @@ void qflex_plan_destroy(qflex_plan plan) {
     cudaSetDevice(plan->device);
     cudaFree(plan->d_ws);
   }
+  if (plan->d_gws) cudaFree(plan->d_gws);
   for (cudaEvent_t e : plan->ev_pool) cudaEventDestroy(e);
   delete plan;
 }
@@ -770,9 +976,70 @@ qflex_status qflex_amplitudes(qflex_plan p, const double* angles, const uint8_t*
   });
 }
 
-qflex_status qflex_amplitudes_grad(qflex_plan, const double*, const uint8_t*, int64_t, const int64_t*, int64_t,
-                                   const double*, double*, double*, void*) {
-  return fail(QFLEX_ERR_UNSUPPORTED, "gradients are not built yet");
+qflex_status qflex_plan_enable_gradients(qflex_plan p) {
+  if (!p) return fail(QFLEX_ERR_ARG, "null plan");
+  if (p->device < 0) return fail(QFLEX_ERR_UNSUPPORTED, "host-only plan");
+  if (p->grad_ready) return QFLEX_OK;
+  QF_CUDA(cudaSetDevice(p->device));
+  if (qflex_status st = build_grad(*p)) {
+    if (p->d_gws) cudaFree(p->d_gws);
+    p->d_gws = nullptr;
+    return st;
+  }
+  return QFLEX_OK;
+}
+
+qflex_status qflex_amplitudes_grad(qflex_plan p, const double* angles, const uint8_t* bits, int64_t n_bs,
+                                   const int64_t* ids, int64_t n_ids, const double* g, double* amps,
+                                   double* grad, void* stream) {
+  if (!p) return fail(QFLEX_ERR_ARG, "null plan");
+  if (p->device < 0) return fail(QFLEX_ERR_UNSUPPORTED, "host-only plan");
+  if (!p->grad_ready) return fail(QFLEX_ERR_UNSUPPORTED, "call qflex_plan_enable_gradients first");
+  if (n_bs < 0 || (n_bs > 0 && (!bits || !amps || !g))) return fail(QFLEX_ERR_ARG, "bad bitstrings/outputs");
+  if (p->n_params > 0 && (!angles || !grad)) return fail(QFLEX_ERR_ARG, "angles and grad_angles required");
+  if (p->steps.empty()) return fail(QFLEX_ERR_UNSUPPORTED, "gradients need at least one contraction step");
+  if (qflex_status st = check_slices(*p, ids, n_ids)) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  QF_CUDA(cudaSetDevice(p->device));
+  p->last_stream = s;
+  const int64_t T = int64_t(1) << p->tile.size();
+  QF_CUDA(cudaMemsetAsync(amps, 0, size_t(n_bs) * T * 2 * sizeof(double), s));
+  if (p->n_params > 0) QF_CUDA(cudaMemsetAsync(grad, 0, size_t(p->n_params) * sizeof(double), s));
+  p->grad_active = true;
+  const int final_buf = p->final_ref.id;
+  qflex_status res = walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) -> qflex_status {
+    cudaError_t e = cudaSuccess;
+    if (i == -2) {
+      if (b > 0 && p->n_params > 0)   // gradient of the previous bitstring
+        e = launch_gridgrad(p->d_gmeta, p->n, p->max_bits, p->d_gops, angles, bits + (b - 1) * p->n,
+                            p->d_wgrid, grad, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(p->d_wgrid, 0, size_t(p->grid_elems) * 16, s);
+      if (e == cudaSuccess)
+        e = launch_gridtensor(p->d_gmeta, p->n, p->max_bits, p->d_gops, angles, bits + b * p->n, p->d_grid, s);
+    } else if (i == -1) {
+      const float2* src = ref_ptr(*p, p->final_ref);
+      e = launch_slicesum(src, p->final_strides.data(), int(p->tile.size()), amps + b * T * 2, s);
+      // reverse pass of this slice
+      if (e == cudaSuccess)
+        e = launch_init_cotangent(reinterpret_cast<float2*>(p->d_warena + p->w_off[final_buf]),
+                                  p->final_strides.data(), int(p->tile.size()), g + b * T * 2, s);
+      for (int k = int(p->steps.size()) - 1; k >= 0 && e == cudaSuccess; --k) {
+        e = run_bwd(*p, p->steps[k], p->sg[k].ga, vals, s);
+        if (e == cudaSuccess) e = run_bwd(*p, p->steps[k], p->sg[k].gb, vals, s);
+      }
+    } else {
+      e = run_step(*p, p->steps[i], vals, s);
+    }
+    if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
+    return QFLEX_OK;
+  });
+  if (res == QFLEX_OK && n_bs > 0 && p->n_params > 0) {
+    cudaError_t e = launch_gridgrad(p->d_gmeta, p->n, p->max_bits, p->d_gops, angles, bits + (n_bs - 1) * p->n,
+                                    p->d_wgrid, grad, s);
+    if (e != cudaSuccess) res = fail(QFLEX_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
+  }
+  p->grad_active = false;
+  return res;
 }
 
 qflex_status qflex_plan_profile(qflex_plan p, int32_t mode, qflex_profile* out) {

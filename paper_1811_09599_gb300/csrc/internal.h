@@ -59,7 +59,8 @@ struct PermTile {
 enum PermFormat : int {
   kFmtC64 = 0,        // complex64, the permuted tensor itself
   kFmtTF32 = 1,       // 3M planes re, im, re+im, each split into tf32 hi (+ lo)
-  kFmtBF16 = 2        // same with bf16
+  kFmtBF16 = 2,       // same with bf16
+  kFmtAccC128 = 3     // out (complex128) += entry: scatter-add of cotangents
 };
 
 // Build the tile tables for a map of `nbits` index bits: bit j moves the
@@ -112,6 +113,15 @@ bool tc_available();   // driver entry point for tensor-map encoding found
 cudaError_t launch_slicesum(const float2* src, const int64_t* strides, int n_open,
                             double* amps, cudaStream_t s);
 cudaError_t launch_norm(const double* amps, int64_t n, double* out, cudaStream_t s);
+
+// ------------------------------------------------------------------ adjoint
+// W[sum_t bit_t(j) * strides[t]] = conj(g[j]) for j < 2^n_open (complex64).
+cudaError_t launch_init_cotangent(float2* w, const int64_t* strides, int n_open, const double* g,
+                                  cudaStream_t s);
+// grad[param] += dL/dtheta from the FP64 grid-tensor cotangents of one bitstring.
+cudaError_t launch_gridgrad(const GridQubitMeta* d_meta, int n_qubits, int max_bits, const int2* d_ops,
+                            const double* d_angles, const uint8_t* d_bits, const double2* d_wgrid,
+                            double* d_grad, cudaStream_t s);
 
 int32_t* device_status_word(int device);   // library-wide status word for standalone calls
 

@@ -135,6 +135,10 @@ template <int FMT>
 __device__ __forceinline__ void put(void* out, int64_t o, float2 v, int nsplit, int64_t plane) {
   if constexpr (FMT == kFmtC64) {
     static_cast<float2*>(out)[o] = v;
+  } else if constexpr (FMT == kFmtAccC128) {
+    double2* q = static_cast<double2*>(out) + o;
+    const double2 c = *q;
+    *q = make_double2(c.x + double(v.x), c.y + double(v.y));
   } else {
     const float part[3] = {v.x, v.y, v.x + v.y};
 #pragma unroll
@@ -261,6 +265,7 @@ cudaError_t launch_permute_tiled(const float2* in, int64_t in_base, const PermTi
   switch (fmt) {
     case kFmtC64: k_permute_tiled<kFmtC64><<<blocks, 256, 0, s>>>(in, in_base, t, out, nsplit, plane); break;
     case kFmtTF32: k_permute_tiled<kFmtTF32><<<blocks, 256, 0, s>>>(in, in_base, t, out, nsplit, plane); break;
+    case kFmtAccC128: k_permute_tiled<kFmtAccC128><<<blocks, 256, 0, s>>>(in, in_base, t, out, nsplit, plane); break;
     default: k_permute_tiled<kFmtBF16><<<blocks, 256, 0, s>>>(in, in_base, t, out, nsplit, plane); break;
   }
   return cudaGetLastError();
@@ -272,6 +277,7 @@ cudaError_t launch_permute_gather(const float2* in, int64_t in_base, const Gathe
   switch (fmt) {
     case kFmtC64: k_permute_gather<kFmtC64><<<blocks, 256, 0, s>>>(in, in_base, d, out, nsplit, plane); break;
     case kFmtTF32: k_permute_gather<kFmtTF32><<<blocks, 256, 0, s>>>(in, in_base, d, out, nsplit, plane); break;
+    case kFmtAccC128: k_permute_gather<kFmtAccC128><<<blocks, 256, 0, s>>>(in, in_base, d, out, nsplit, plane); break;
     default: k_permute_gather<kFmtBF16><<<blocks, 256, 0, s>>>(in, in_base, d, out, nsplit, plane); break;
   }
   return cudaGetLastError();
