@@ -93,13 +93,30 @@ __global__ void __launch_bounds__(256) k_cgemm_simt(int64_t M, int64_t N, int64_
   }
 }
 
-// Thin form for N <= TBN (a large tensor absorbing a small one, HBM-bound):
-// each thread owns one output row and 16 of its columns; the B tile is
-// broadcast from shared memory.  Registers are capped so that four 256-thread
-// blocks fit per SM and enough A loads are in flight to stream HBM.
+// Thin forms for N <= 32 (a large tensor absorbing a small one, HBM-bound).
+// Packed FP32 pairs: P[n] = sum a.x * (b.x, b.y) and Q[n] = sum a.y * (b.x, b.y)
+// with fma.rn.f32x2, so one complex multiply-add costs two packed FMAs and
+// no register shuffling; C[n] = (P.x - Q.y, P.y + Q.x) at the end (the same
+// products and sums as the four-FMA form, in the same order per component).
+__device__ __forceinline__ unsigned long long pk(float x, float y) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ float2 upk(unsigned long long v) {
+  float x, y;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
+  return make_float2(x, y);
+}
+__device__ __forceinline__ void fma2(unsigned long long& d, unsigned long long a, unsigned long long b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
+
+// Row-per-thread form: each thread owns one output row and 16 of its
+// columns; A is staged through shared memory, B broadcast from it.
 constexpr int TBK = 16;
 template <int TBN>
-__global__ void __launch_bounds__(256, 4) k_cgemm_thin(int64_t M, int64_t N, int64_t K,
+__global__ void __launch_bounds__(256, 2) k_cgemm_thin(int64_t M, int64_t N, int64_t K,
                                                       const float2* __restrict__ A,
                                                       const float2* __restrict__ B,
                                                       float2* __restrict__ C) {
@@ -110,9 +127,9 @@ __global__ void __launch_bounds__(256, 4) k_cgemm_thin(int64_t M, int64_t N, int
   const int t = threadIdx.x;
   const int row = t / CG, cg = t % CG;
   const int64_t m0 = int64_t(blockIdx.x) * RB, n0 = int64_t(blockIdx.y) * TBN;
-  float re[16], im[16];
+  unsigned long long P[16], Q[16];
 #pragma unroll
-  for (int n = 0; n < 16; ++n) re[n] = im[n] = 0.f;
+  for (int n = 0; n < 16; ++n) P[n] = Q[n] = 0ull;
   for (int64_t k0 = 0; k0 < K; k0 += TBK) {
 #pragma unroll 4
     for (int i = 0; i < (RB * TBK) / 256; ++i) {
@@ -127,26 +144,23 @@ __global__ void __launch_bounds__(256, 4) k_cgemm_thin(int64_t M, int64_t N, int
       Bs[kk][n] = (gn < N && gk < K) ? __ldg(B + gn * K + gk) : make_float2(0.f, 0.f);
     }
     __syncthreads();
-#pragma unroll 4
+#pragma unroll 2
     for (int kk = 0; kk < TBK; ++kk) {
       const float2 a = As[row][kk];
+      const unsigned long long ax = pk(a.x, a.x), ay = pk(a.y, a.y);
       const float4* bp = reinterpret_cast<const float4*>(&Bs[kk][cg * 16]);
 #pragma unroll
       for (int n = 0; n < 16; n += 2) {
         const float4 b = bp[n / 2];
-        re[n] = fmaf(a.x, b.x, re[n]);
-        re[n] = fmaf(-a.y, b.y, re[n]);
-        im[n] = fmaf(a.x, b.y, im[n]);
-        im[n] = fmaf(a.y, b.x, im[n]);
-        re[n + 1] = fmaf(a.x, b.z, re[n + 1]);
-        re[n + 1] = fmaf(-a.y, b.w, re[n + 1]);
-        im[n + 1] = fmaf(a.x, b.w, im[n + 1]);
-        im[n + 1] = fmaf(a.y, b.z, im[n + 1]);
+        const unsigned long long b0 = pk(b.x, b.y), b1 = pk(b.z, b.w);
+        fma2(P[n], ax, b0);
+        fma2(Q[n], ay, b0);
+        fma2(P[n + 1], ax, b1);
+        fma2(Q[n + 1], ay, b1);
       }
     }
     __syncthreads();
   }
-  // each thread writes its 16 entries (contiguous, 16-byte stores when aligned)
   const int64_t gm = m0 + row;
   if (gm < M) {
     const int64_t c0 = n0 + cg * 16;
@@ -155,13 +169,56 @@ __global__ void __launch_bounds__(256, 4) k_cgemm_thin(int64_t M, int64_t N, int
     const bool vec = ((reinterpret_cast<uintptr_t>(crow) & 15) == 0);
 #pragma unroll
     for (int n = 0; n < 16; n += 2) {
+      const float2 p0 = upk(P[n]), q0 = upk(Q[n]), p1 = upk(P[n + 1]), q1 = upk(Q[n + 1]);
+      const float2 c0v = make_float2(p0.x - q0.y, p0.y + q0.x);
+      const float2 c1v = make_float2(p1.x - q1.y, p1.y + q1.x);
       if (vec && n + 1 < ncols) {
-        *reinterpret_cast<float4*>(crow + n) = make_float4(re[n], im[n], re[n + 1], im[n + 1]);
+        *reinterpret_cast<float4*>(crow + n) = make_float4(c0v.x, c0v.y, c1v.x, c1v.y);
       } else {
-        if (n < ncols) crow[n] = make_float2(re[n], im[n]);
-        if (n + 1 < ncols) crow[n + 1] = make_float2(re[n + 1], im[n + 1]);
+        if (n < ncols) crow[n] = c0v;
+        if (n + 1 < ncols) crow[n + 1] = c1v;
       }
     }
+  }
+}
+
+// Warp-per-row form for few rows and a long K (too few blocks for the
+// row-per-thread form): the lanes split K, then reduce across the warp.
+__global__ void __launch_bounds__(256) k_cgemm_rowwarp(int64_t M, int64_t N, int64_t K,
+                                                      const float2* __restrict__ A,
+                                                      const float2* __restrict__ B,
+                                                      float2* __restrict__ C) {
+  const int lane = threadIdx.x & 31;
+  const int64_t cgs = (N + 15) / 16;
+  const int64_t w = int64_t(blockIdx.x) * 8 + (threadIdx.x >> 5);
+  const int64_t m = w / cgs, n0 = (w % cgs) * 16;
+  if (m >= M) return;
+  const int nn = int(N - n0 < 16 ? N - n0 : 16);
+  unsigned long long P[16], Q[16];
+#pragma unroll
+  for (int n = 0; n < 16; ++n) P[n] = Q[n] = 0ull;
+  for (int64_t k = lane; k < K; k += 32) {
+    const float2 a = __ldg(A + m * K + k);
+    const unsigned long long ax = pk(a.x, a.x), ay = pk(a.y, a.y);
+#pragma unroll
+    for (int n = 0; n < 16; ++n) {
+      if (n < nn) {
+        const float2 b = __ldg(B + (n0 + n) * K + k);
+        const unsigned long long bb = pk(b.x, b.y);
+        fma2(P[n], ax, bb);
+        fma2(Q[n], ay, bb);
+      }
+    }
+  }
+#pragma unroll
+  for (int n = 0; n < 16; ++n) {
+    float2 p = upk(P[n]), q = upk(Q[n]);
+    float re = p.x - q.y, im = p.y + q.x;
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == n && n < nn) C[m * N + n0 + n] = make_float2(re, im);
   }
 }
 
@@ -170,6 +227,12 @@ __global__ void __launch_bounds__(256, 4) k_cgemm_thin(int64_t M, int64_t N, int
 cudaError_t launch_cgemm_thin(int64_t M, int64_t N, int64_t K, const float2* A, const float2* B,
                               float2* C, cudaStream_t s) {
   if (M <= 0 || N <= 0) return cudaSuccess;
+  const int64_t cgs = (N + 15) / 16;
+  if (K >= 64 && ((M + 255) / 256) * cgs < 256) {   // few rows, long K: warp per row
+    const int64_t warps = M * cgs;
+    k_cgemm_rowwarp<<<unsigned((warps + 7) / 8), 256, 0, s>>>(M, N, K, A, B, C);
+    return cudaGetLastError();
+  }
   if (N <= 16) {
     dim3 grid(unsigned((M + 255) / 256), unsigned((N + 15) / 16));
     k_cgemm_thin<16><<<grid, 256, 0, s>>>(M, N, K, A, B, C);
