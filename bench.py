@@ -209,6 +209,71 @@ def permute_sweep(api, torch, peaks):
     return out
 
 
+def rotation_batch_run(api, torch, precision, local):
+    """256 uneven rotation circuits (4x4..6x6 grids, depth 1+16..32+1), one
+    amplitude and the gradient w.r.t. every angle each.  Each circuit gets its
+    own plan (created, run, destroyed in turn); GPU time is the sum of CUDA
+    event intervals around the amplitude+gradient calls, wall time includes
+    planning and workspace allocation."""
+    from qflex_inputs import rotation_batch
+    batch = rotation_batch(256, 0)
+    g = torch.ones((1, 1), dtype=torch.complex128, device="cuda")
+    gpu_ms = 0.0
+    n_params = 0
+    t0 = time.perf_counter()
+    for i, prob in enumerate(batch):
+        plan = api.Plan(prob, precision, device=local)
+        plan.enable_gradients()
+        bits = torch.from_numpy(random_bitstrings(prob.n, 1, 5000 + i)).cuda()
+        th = torch.from_numpy(prob.circuit.angles).cuda()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.amplitudes_grad(bits, th, g)
+        e1.record()
+        torch.cuda.synchronize()
+        gpu_ms += e0.elapsed_time(e1)
+        n_params += prob.circuit.n_params
+        plan.close()
+    wall = time.perf_counter() - t0
+    return {"circuits": len(batch), "angles": n_params, "gpu_ms": gpu_ms, "wall_s": wall,
+            "amplitudes_per_s_gpu": len(batch) / (gpu_ms * 1e-3),
+            "gradient_entries_per_s_gpu": n_params / (gpu_ms * 1e-3),
+            "note": "one plan per circuit, created/run/destroyed in turn; not a single persistent launch"}
+
+
+def c4_subset(api, torch, precision, local):
+    """7x7 depth 1+40+1 (bond dimension 32, 2^15-sized GEMMs): the split form
+    against plain FP32 on the first two slices of one bitstring (the paper
+    also times a few paths and extrapolates).  The FP64 oracle cannot contract
+    a slice of this size in reasonable time, so the error is stated against
+    the FP32 result."""
+    from qflex_inputs import c4_problem
+    prob = c4_problem(0)
+    bits = torch.from_numpy(random_bitstrings(prob.n, 1, 2000)).cuda()
+    subset = [0, 1]
+    out = {"subset": "1 bitstring x slices 0,1 of 1024 (one AB, two ABD of 2^15 x 2^15 x 2^15)"}
+    res = {}
+    for prec in (precision, "fp32"):
+        plan = api.Plan(prob, prec, device=local)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        amp = plan.amplitudes(bits, None, subset)
+        e1.record()
+        torch.cuda.synchronize()
+        plan.sync()
+        cost = plan.cost(1, subset)
+        ms = e0.elapsed_time(e1)
+        res[prec] = amp.cpu().numpy()
+        out[f"{prec}_ms"] = ms
+        out[f"{prec}_tflops_cgemm"] = cost["cmacs"] * 8 / (ms * 1e-3) / 1e12
+        plan.close()
+        del plan
+        torch.cuda.empty_cache()
+    out["speedup"] = out["fp32_ms"] / out[f"{precision}_ms"]
+    out[f"{precision}_err_vs_fp32"] = amp_error(res[precision], res["fp32"], prob.n, 2.0 / 1024)
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -345,6 +410,9 @@ def run_ours(args):
                                 f"{args.precision}_ms": timings[args.precision],
                                 "speedup": timings["fp32"] / timings[args.precision]}
         extras["permute"] = permute_sweep(api, torch, peaks)
+        extras["rotation_batch"] = rotation_batch_run(api, torch, args.precision, local)
+        if not args.no_c4:
+            extras["grid7x7_d40"] = c4_subset(api, torch, args.precision, local)
         line.update(extras)
     if world > 1:
         dist.barrier()
@@ -362,6 +430,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "fp32"])
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-c4", action="store_true", help="skip the 7x7 depth-40 subset in the extras")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

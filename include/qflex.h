@@ -187,6 +187,16 @@ qflex_status qflex_amplitudes_grad(qflex_plan plan, const double* angles,
                                    const double* grad_amps, double* amps_out,
                                    double* grad_angles, void* stream);
 
+/* CUDA-graph launch mode (enable != 0): a qflex_amplitudes / _grad call whose
+ * arguments (pointers, n_bs, slice list) repeat those of the previous call is
+ * captured into a CUDA graph on its second occurrence and replayed from then
+ * on (one graph launch instead of thousands of kernel launches).  Inputs may
+ * change contents between calls but not addresses.  Calls on the legacy
+ * default stream (NULL) and calls while profiling run directly.  The first
+ * call with new arguments runs directly, so kernel set-up happens outside
+ * capture. */
+qflex_status qflex_plan_use_graphs(qflex_plan plan, int32_t enable);
+
 /* Per-kernel-class timing of a plan's launches, for roofline measurement.
  * Classes: 0 grid tensors, 1 permutation / operand producer, 2 FP32 GEMM,
  * 3 tensor-core GEMM, 4 slice sum.  mode != 0 is a bit mask of classes

@@ -115,6 +115,10 @@ class Plan:
                                         C.c_void_p(out.data_ptr()), _stream_handle(stream)))
         return torch.view_as_complex(out.view(n_bs, T, 2))
 
+    def use_graphs(self, enable: bool = True):
+        """qflex_plan_use_graphs: replay repeated calls from a captured CUDA graph."""
+        check(self.lib.qflex_plan_use_graphs(self.handle, int(enable)))
+
     def enable_gradients(self):
         """qflex_plan_enable_gradients: allocate the reverse-pass workspace once."""
         check(self.lib.qflex_plan_enable_gradients(self.handle))

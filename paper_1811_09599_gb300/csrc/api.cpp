@@ -157,6 +157,25 @@ struct qflex_plan_s {
   void* d_gA = nullptr;
   void* d_gB = nullptr;
   float2* d_gC = nullptr;
+  // CUDA-graph replay of qflex_amplitudes / qflex_amplitudes_grad
+  bool use_graphs = false;
+  struct GraphKey {
+    const void* angles = nullptr;
+    const void* bits = nullptr;
+    const void* out = nullptr;
+    const void* grad = nullptr;
+    const void* g = nullptr;
+    int64_t n_bs = -1;
+    int kind = -1;
+    std::vector<int64_t> ids;
+    bool all = false;
+    bool operator==(const GraphKey& o) const {
+      return angles == o.angles && bits == o.bits && out == o.out && grad == o.grad && g == o.g &&
+             n_bs == o.n_bs && kind == o.kind && ids == o.ids && all == o.all;
+    }
+  };
+  GraphKey gkey, gseen;
+  cudaGraphExec_t gexec = nullptr;
   bool grad_active = false;                    // forward runs on the dedicated buffers
   bool profiling = false;
   int32_t prof_mask = 0;
@@ -831,6 +850,47 @@ qflex_status check_slices(const qflex_plan_s& p, const int64_t* ids, int64_t n_i
   return QFLEX_OK;
 }
 
+// Run `enqueue` on stream s, through a cached CUDA graph when the plan has
+// graphs enabled (and is not profiling).  A call whose key (pointers, batch,
+// slice list) differs from the last one runs directly; the second call with
+// the same key captures its launches into a graph, and later calls with that
+// key replay it.  Streams that cannot be captured (the legacy default
+// stream) always run directly.
+template <class F>
+qflex_status with_graph(qflex_plan_s& p, const qflex_plan_s::GraphKey& key, cudaStream_t s, F&& enqueue) {
+  if (!p.use_graphs || p.profiling || s == nullptr) return enqueue();
+  if (p.gexec && p.gkey == key) {
+    QF_CUDA(cudaGraphLaunch(p.gexec, s));
+    return QFLEX_OK;
+  }
+  if (!(p.gseen == key)) {
+    p.gseen = key;
+    return enqueue();
+  }
+  if (p.gexec) {
+    cudaGraphExecDestroy(p.gexec);
+    p.gexec = nullptr;
+  }
+  QF_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  qflex_status st = enqueue();
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &graph);
+  if (st != QFLEX_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&p.gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    p.gexec = nullptr;
+    return fail(QFLEX_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  p.gkey = key;
+  QF_CUDA(cudaGraphLaunch(p.gexec, s));
+  return QFLEX_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -872,6 +932,7 @@ void qflex_plan_destroy(qflex_plan plan) {
     cudaFree(plan->d_ws);
   }
   if (plan->d_gws) cudaFree(plan->d_gws);
+  if (plan->gexec) cudaGraphExecDestroy(plan->gexec);
   for (cudaEvent_t e : plan->ev_pool) cudaEventDestroy(e);
   delete plan;
 }
@@ -956,23 +1017,33 @@ qflex_status qflex_amplitudes(qflex_plan p, const double* angles, const uint8_t*
   QF_CUDA(cudaSetDevice(p->device));
   p->last_stream = s;
   const int64_t T = int64_t(1) << p->tile.size();
-  QF_CUDA(cudaMemsetAsync(amps, 0, size_t(n_bs) * T * 2 * sizeof(double), s));
-  return walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) -> qflex_status {
-    cudaError_t e;
-    if (i == -2) {
-      e = timed(*p, 0, 0, 0, 8.0 * p->grid_elems, s, [&] {
-        return launch_gridtensor(p->d_gmeta, p->n, p->max_bits, p->d_gops, angles, bits + b * p->n, p->d_grid, s);
-      });
-    } else if (i == -1) {
-      const float2* src = ref_ptr(*p, p->final_ref) + ref_base(p->final_ref, vals);
-      e = timed(*p, 4, 0, 0, 40.0 * T, s, [&] {
-        return launch_slicesum(src, p->final_strides.data(), int(p->tile.size()), amps + b * T * 2, s);
-      });
-    } else {
-      e = run_step(*p, p->steps[i], vals, s);
-    }
-    if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
-    return QFLEX_OK;
+  qflex_plan_s::GraphKey key;
+  key.angles = angles;
+  key.bits = bits;
+  key.out = amps;
+  key.n_bs = n_bs;
+  key.kind = 0;
+  key.all = ids == nullptr;
+  if (ids) key.ids.assign(ids, ids + n_ids);
+  return with_graph(*p, key, s, [&]() -> qflex_status {
+    QF_CUDA(cudaMemsetAsync(amps, 0, size_t(n_bs) * T * 2 * sizeof(double), s));
+    return walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) -> qflex_status {
+      cudaError_t e;
+      if (i == -2) {
+        e = timed(*p, 0, 0, 0, 8.0 * p->grid_elems, s, [&] {
+          return launch_gridtensor(p->d_gmeta, p->n, p->max_bits, p->d_gops, angles, bits + b * p->n, p->d_grid, s);
+        });
+      } else if (i == -1) {
+        const float2* src = ref_ptr(*p, p->final_ref) + ref_base(p->final_ref, vals);
+        e = timed(*p, 4, 0, 0, 40.0 * T, s, [&] {
+          return launch_slicesum(src, p->final_strides.data(), int(p->tile.size()), amps + b * T * 2, s);
+        });
+      } else {
+        e = run_step(*p, p->steps[i], vals, s);
+      }
+      if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
+      return QFLEX_OK;
+    });
   });
 }
 
@@ -1003,10 +1074,21 @@ qflex_status qflex_amplitudes_grad(qflex_plan p, const double* angles, const uin
   QF_CUDA(cudaSetDevice(p->device));
   p->last_stream = s;
   const int64_t T = int64_t(1) << p->tile.size();
-  QF_CUDA(cudaMemsetAsync(amps, 0, size_t(n_bs) * T * 2 * sizeof(double), s));
-  if (p->n_params > 0) QF_CUDA(cudaMemsetAsync(grad, 0, size_t(p->n_params) * sizeof(double), s));
+  qflex_plan_s::GraphKey key;
+  key.angles = angles;
+  key.bits = bits;
+  key.out = amps;
+  key.grad = grad;
+  key.g = g;
+  key.n_bs = n_bs;
+  key.kind = 1;
+  key.all = ids == nullptr;
+  if (ids) key.ids.assign(ids, ids + n_ids);
   p->grad_active = true;
   const int final_buf = p->final_ref.id;
+  qflex_status res = with_graph(*p, key, s, [&]() -> qflex_status {
+  QF_CUDA(cudaMemsetAsync(amps, 0, size_t(n_bs) * T * 2 * sizeof(double), s));
+  if (p->n_params > 0) QF_CUDA(cudaMemsetAsync(grad, 0, size_t(p->n_params) * sizeof(double), s));
   qflex_status res = walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) -> qflex_status {
     cudaError_t e = cudaSuccess;
     if (i == -2) {
@@ -1038,8 +1120,20 @@ qflex_status qflex_amplitudes_grad(qflex_plan p, const double* angles, const uin
                                     p->d_wgrid, grad, s);
     if (e != cudaSuccess) res = fail(QFLEX_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
   }
+  return res;
+  });
   p->grad_active = false;
   return res;
+}
+
+qflex_status qflex_plan_use_graphs(qflex_plan p, int32_t enable) {
+  if (!p) return fail(QFLEX_ERR_ARG, "null plan");
+  p->use_graphs = enable != 0;
+  if (!p->use_graphs && p->gexec) {
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  return QFLEX_OK;
 }
 
 qflex_status qflex_plan_profile(qflex_plan p, int32_t mode, qflex_profile* out) {

@@ -8,4 +8,4 @@ from .circuits import (KINDS, KIND_ID, Circuit, Gate, Lattice, cz_counts,
                        random_bitstrings, random_circuit)
 from .problems import (Problem, c1_problem, c2_problem, c4_problem,
                        grid_problem, grid_region_cuts, grid_region_ordering,
-                       row_major_ordering, workload_bitstrings)
+                       rotation_batch, row_major_ordering, workload_bitstrings)

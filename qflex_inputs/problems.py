@@ -131,3 +131,20 @@ def c4_problem(seed: int = 0) -> Problem:
 
 def workload_bitstrings(problem: Problem, count: int, seed: int) -> np.ndarray:
     return random_bitstrings(problem.n, count, seed)
+
+
+def rotation_batch(count: int = 256, seed: int = 0) -> List[Problem]:
+    """Batch of uneven rotation circuits: grids I, J ~ U{4, 5, 6}, depth
+    1+t+1 with t ~ U{16..32}, every non-CZ gate R_P(theta) with P uniform in
+    {X, Y, Z} and theta ~ U[0, 2 pi), no cuts, one amplitude per circuit
+    (region ordering split at the middle row and column)."""
+    rng = np.random.default_rng([seed, 0xC5])
+    out = []
+    for i in range(count):
+        rows, cols = int(rng.integers(4, 7)), int(rng.integers(4, 7))
+        t = int(rng.integers(16, 33))
+        p = grid_problem(rows, cols, t, seed * 100003 + i, cuts=False, tile_rows=0,
+                         rotations=True)
+        p.name = f"rot{rows}x{cols}_t{t}_{i}"
+        out.append(p)
+    return out

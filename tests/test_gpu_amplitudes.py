@@ -10,7 +10,7 @@ import pytest
 from oracle import network as NW
 from oracle import selection as SEL
 from oracle import statevector as SV
-from qflex_inputs import (c1_problem, c2_problem, grid_problem, random_bitstrings)
+from qflex_inputs import (c1_problem, c2_problem, c4_problem, grid_problem, random_bitstrings)
 from tests.gpu_util import TOL, amp_error
 
 torch = pytest.importorskip("torch")
@@ -136,4 +136,49 @@ def test_c2_full_size_sampled_slices(api, prec):
         got = plan.amplitudes(b, None, [s]).cpu().numpy()
         ref = _c2_reference(prob, bs[0], s)
         assert amp_error(got, ref, prob.n, 1.0 / 256) < TOL[prec], s
+    plan.sync()
+
+
+def test_c4_full_size_split_vs_fp32(api):
+    """7x7, 1+40+1 (bond dimension 32, 2^15 x 2^15 x 2^15 GEMMs, 2^30-entry
+    tensors), slice 0 of one bitstring: bf16x3 against the FP32 path (the FP64
+    oracle cannot contract a slice of this size in test time; the 2^15-long
+    GEMM accuracy itself is pinned against complex128 in test_gpu_kernels)."""
+    prob = c4_problem(0)
+    bs = torch.from_numpy(random_bitstrings(prob.n, 1, 2000)).cuda()
+    res = {}
+    for prec in ("bf16x3", "fp32"):
+        plan = api.Plan(prob, prec, device=0)
+        res[prec] = plan.amplitudes(bs, None, [0]).cpu().numpy()
+        plan.sync()
+        plan.close()
+        torch.cuda.empty_cache()
+    assert np.all(np.isfinite(res["fp32"])) and np.max(np.abs(res["fp32"])) > 0
+    assert amp_error(res["bf16x3"], res["fp32"], prob.n, 1.0 / 1024) < TOL["bf16x3"]
+
+
+def test_cuda_graph_replay(api):
+    """qflex_plan_use_graphs: repeated calls replay a captured graph; changing
+    the contents (not the address) of the bitstring buffer is seen by the
+    replay; results equal the direct launches."""
+    prob = grid_problem(4, 5, 24, 5, r0=2, c0=2, cuts=True, tile_rows=2, tile_cols=2)
+    bs = random_bitstrings(prob.n, 3, 5)
+    direct = api.Plan(prob, "bf16x3", device=0)
+    ref = direct.amplitudes(torch.from_numpy(bs).cuda()).cpu().numpy()
+    plan = api.Plan(prob, "bf16x3", device=0)
+    plan.use_graphs(True)
+    stream = torch.cuda.Stream()
+    b = torch.from_numpy(bs).cuda()
+    out = torch.empty((3, 16, 2), dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(3):                      # direct, capture, replay
+            got = plan.amplitudes(b, None, None, out=out, stream=stream)
+        stream.synchronize()
+        assert np.max(np.abs(got.cpu().numpy() - ref)) <= 1e-12 * np.max(np.abs(ref)) + 1e-30
+        bs2 = random_bitstrings(prob.n, 3, 99)
+        b.copy_(torch.from_numpy(bs2))
+        got2 = plan.amplitudes(b, None, None, out=out, stream=stream).cpu().numpy()
+        stream.synchronize()
+    ref2 = direct.amplitudes(torch.from_numpy(bs2).cuda()).cpu().numpy()
+    assert np.max(np.abs(got2 - ref2)) <= 1e-12 * np.max(np.abs(ref2)) + 1e-30
     plan.sync()
