@@ -145,19 +145,25 @@ struct Cfg {
   static constexpr int A_TILE = BM * ROW_BYTES;              // bytes of one A plane tile
   static constexpr int B_TILE = BN * ROW_BYTES;
   static constexpr int STAGE = NSPLIT * (A_TILE + B_TILE);
-  static constexpr int NSTAGE = (200 * 1024) / STAGE > NSTAGE_MAX ? NSTAGE_MAX : (200 * 1024) / STAGE;
+  static constexpr int NSTAGE = (196 * 1024) / STAGE > NSTAGE_MAX ? NSTAGE_MAX : (196 * 1024) / STAGE;
   static constexpr int NPROD = NSPLIT == 2 ? 3 : 1;          // hi.hi, hi.lo, lo.hi
   static constexpr int TMEM_COLS = 3 * BN <= 256 ? 256 : 512;
   static constexpr int HALF = BN / 2;                        // columns per epilogue warp
-  static constexpr int SMEM = NSTAGE * STAGE + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int STAGING = 8 * 32 * 16 * 8;            // 8 warps x 32 rows x 16 complex
+  static constexpr int SMEM = NSTAGE * STAGE + STAGING + 1024 /*align*/ + 256 /*barriers*/;
   static_assert(NSTAGE >= 2, "pipeline needs at least two stages");
-  static_assert(8 * 32 * 33 * 8 <= NSTAGE * STAGE, "epilogue staging must fit in the stages");
+  static_assert(SMEM <= 232448, "shared memory per CTA");
 };
 constexpr int KB_CHUNK = 4;      // k-blocks accumulated in TMEM before promotion to registers
 constexpr int EPI_WARPS = 8;
 
-// Block: warp 0 = TMA producer, warp 1 = TMEM owner + MMA issuer, warps 2..9 =
-// epilogue (two warps per TMEM lane quarter, each owning half of the BN columns).
+// Persistent: one CTA per SM walks the output tiles (tile += gridDim.x, N
+// fastest).  Block: warp 0 = TMA producer, warp 1 = TMEM owner + MMA issuer,
+// warps 2..9 = epilogue (two warps per TMEM lane quarter, each owning half of
+// the BN columns).  Barrier set-up and TMEM allocation happen once per CTA,
+// the producer runs ahead into the next tile, and the final store of a tile
+// (from registers, through a dedicated staging area) overlaps the next tile's
+// MMAs because the accumulators are handed back part by part.
 //
 // Accuracy: the tensor core adds each MMA's partial sum into the FP32
 // accumulator with truncation, so a long K accumulation drifts (measured:
@@ -183,7 +189,8 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G::NSTAGE * G::STAGE);
+  float2* staging = reinterpret_cast<float2*>(smem + G::NSTAGE * G::STAGE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G::NSTAGE * G::STAGE + G::STAGING);
   // [0,NSTAGE) full, [NSTAGE,2NSTAGE) empty, +0..2 part ready, +3..5 part drained
   uint64_t* acc_full = bars + 2 * G::NSTAGE;
   uint64_t* acc_empty = acc_full + 3;
@@ -198,7 +205,8 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
   if (s_skip) return;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = int64_t(blockIdx.y) * BM, n0 = int64_t(blockIdx.x) * BN;
+  const int64_t n_nt = (N + BN - 1) / BN;
+  const int64_t n_tiles = ((M + BM - 1) / BM) * n_nt;
   const int nkb = int((K + BK - 1) / BK);
   const int nchunk = (nkb + KB_CHUNK - 1) / KB_CHUNK;
 
@@ -233,6 +241,8 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_b)) : "memory");
       int i = 0;
       bool ok = true;
+      for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      const int64_t m0 = (tile / n_nt) * BM, n0 = (tile % n_nt) * BN;
       for (int c = 0; c < nchunk && ok; ++c) {
         const int kb0 = c * KB_CHUNK, kb1 = min(nkb, kb0 + KB_CHUNK);
         for (int part = 0; part < 3 && ok; ++part) {
@@ -255,6 +265,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
           }
         }
       }
+      }
       if (!ok) {   // let the copies this lane started land before the CTA exits
         for (int j = i > G::NSTAGE ? i - G::NSTAGE : 0; j < i; ++j) {
           volatile int never = 0;
@@ -264,12 +275,13 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      int i = 0;
+      int i = 0, cg = 0;   // stage counter, chunk counter across tiles
       bool ok = true;
-      for (int c = 0; c < nchunk && ok; ++c) {
+      for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      for (int c = 0; c < nchunk && ok; ++c, ++cg) {
         const int kb0 = c * KB_CHUNK, kb1 = min(nkb, kb0 + KB_CHUNK);
         for (int part = 0; part < 3 && ok; ++part) {
-          if (c > 0 && !mbar_wait(smem_u32(&acc_empty[part]), (c - 1) & 1, abort_flag, status)) {
+          if (cg > 0 && !mbar_wait(smem_u32(&acc_empty[part]), (cg - 1) & 1, abort_flag, status)) {
             ok = false;
             break;
           }
@@ -300,62 +312,72 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
           if (ok) tc_commit(smem_u32(&acc_full[part]));   // fires when this part's MMAs are done
         }
       }
+      }
     }
   } else {
     // epilogue warps 2..9: TMEM lane quarter q = warp % 4, column half h
     const int q = warp & 3, h = (warp - 2) >> 2;
     const int col0 = h * G::HALF;
     const uint32_t lane_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(col0);
-    float re[G::HALF], im[G::HALF];
-#pragma unroll
-    for (int j = 0; j < G::HALF; ++j) re[j] = im[j] = 0.f;
+    float2* st = staging + (warp - 2) * (32 * 16);
     bool ok = true;
-    for (int c = 0; c < nchunk && ok; ++c) {
-      for (int part = 0; part < 3; ++part) {
-        if (!mbar_wait(smem_u32(&acc_full[part]), c & 1, abort_flag, status)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
+    int cg = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      const int64_t m0 = (tile / n_nt) * BM, n0 = (tile % n_nt) * BN;
+      float re[G::HALF], im[G::HALF];
 #pragma unroll
-        for (int sub = 0; sub < G::HALF / 32; ++sub) {
-          uint32_t r[32];
-          tmem_ld32(lane_base + uint32_t(part * BN + sub * 32), r);
-          tmem_wait_ld();
+      for (int j = 0; j < G::HALF; ++j) re[j] = im[j] = 0.f;
+      for (int c = 0; c < nchunk && ok; ++c, ++cg) {
+        for (int part = 0; part < 3; ++part) {
+          if (!mbar_wait(smem_u32(&acc_full[part]), cg & 1, abort_flag, status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const float t = __uint_as_float(r[j]);
-            if (part == 0) {
-              re[sub * 32 + j] += t;
-              im[sub * 32 + j] -= t;
-            } else if (part == 1) {
-              re[sub * 32 + j] -= t;
-              im[sub * 32 + j] -= t;
-            } else {
-              im[sub * 32 + j] += t;
+          for (int sub = 0; sub < G::HALF / 32; ++sub) {
+            uint32_t r[32];
+            tmem_ld32(lane_base + uint32_t(part * BN + sub * 32), r);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const float t = __uint_as_float(r[j]);
+              if (part == 0) {
+                re[sub * 32 + j] += t;
+                im[sub * 32 + j] -= t;
+              } else if (part == 1) {
+                re[sub * 32 + j] -= t;
+                im[sub * 32 + j] -= t;
+              } else {
+                im[sub * 32 + j] += t;
+              }
             }
           }
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) {
-          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[part]))
-                       : "memory");
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) {
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[part]))
+                         : "memory");
+          }
         }
       }
-    }
-    if (ok && !*abort_flag) {
-      float2* st = reinterpret_cast<float2*>(smem) + (warp - 2) * (32 * 33);
+      if (!ok || *abort_flag) break;
+      // final store: 16 columns at a time through this warp's staging area
+      // (row = lane, column slot XOR-swizzled by the row: conflict-free in
+      // both directions), then two 128-byte row segments per instruction.
 #pragma unroll
-      for (int sub = 0; sub < G::HALF / 32; ++sub) {
+      for (int sub = 0; sub < G::HALF / 16; ++sub) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) st[lane * 33 + j] = make_float2(re[sub * 32 + j], im[sub * 32 + j]);
+        for (int j = 0; j < 16; ++j)
+          st[lane * 16 + (j ^ (lane & 15))] = make_float2(re[sub * 16 + j], im[sub * 16 + j]);
         __syncwarp();
-        const int64_t gn = n0 + col0 + sub * 32 + lane;
+        const int cj = lane & 15;
+        const int64_t gn = n0 + col0 + sub * 16 + cj;
 #pragma unroll 4
-        for (int r = 0; r < 32; ++r) {
+        for (int r2 = 0; r2 < 32; r2 += 2) {
+          const int r = r2 + (lane >> 4);
           const int64_t gm = m0 + q * 32 + r;
-          if (gm < M && gn < N) C[gm * N + gn] = st[r * 33 + lane];
+          if (gm < M && gn < N) C[gm * N + gn] = st[r * 16 + (cj ^ (r & 15))];
         }
         __syncwarp();
       }
@@ -413,8 +435,10 @@ cudaError_t launch_t(const TcGemmMaps& maps, int64_t M, int64_t N, int64_t K, fl
     if (e != cudaSuccess) return e;
     configured_dev = dev;
   }
-  dim3 grid(unsigned((N + BN - 1) / BN), unsigned((M + BM - 1) / BM));
-  if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+  static int sms = 0;
+  if (sms == 0) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  const unsigned grid = unsigned(tiles < sms ? tiles : sms);
   kern<<<grid, 64 + 32 * EPI_WARPS, G::SMEM, s>>>(maps.a, maps.b, M, N, K, C, status);
   return cudaGetLastError();
 }
