@@ -241,6 +241,35 @@ def rotation_batch_run(api, torch, precision, local):
             "note": "one plan per circuit, created/run/destroyed in turn; not a single persistent launch"}
 
 
+def bris70_run(api, torch, precision, local):
+    """70-qubit Bristlecone-like diamond, depth 1+32+1, four cuts (2^16 paths,
+    2^28-entry intermediates), fidelity f = 0.01 (655 paths chosen by the
+    seeded Fisher-Yates rule), 8-qubit open tile: 256 amplitudes of one
+    bitstring, with the FP64 norm estimate 2^n <|a|^2> (~f expected)."""
+    from qflex_inputs import diamond_problem
+    prob = diamond_problem(32, 0)
+    plan = api.Plan(prob, precision, device=local)
+    sel = plan.select_slices(0.01, 2026)
+    bits = torch.from_numpy(random_bitstrings(prob.n, 1, 3000)).cuda()
+    plan.amplitudes(bits, None, sel[:4])                 # warm (plans, tensor maps)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    amps = plan.amplitudes(bits, None, sel)
+    e1.record()
+    torch.cuda.synchronize()
+    plan.sync()
+    ms = e0.elapsed_time(e1)
+    cost = plan.cost(1, sel)
+    nrm = api.norm(amps).item()
+    plan.close()
+    return {"paths": int(len(sel)), "of": 65536, "amplitudes": int(amps.numel()), "ms": ms,
+            "amplitudes_per_s": amps.numel() / (ms * 1e-3),
+            "tflops_cgemm": cost["cmacs"] * 8 / (ms * 1e-3) / 1e12,
+            "norm_estimate": nrm * 2.0 ** prob.n / amps.numel(),
+            "max_tensor_entries": 2 ** 28}
+
+
 def c4_subset(api, torch, precision, local):
     """7x7 depth 1+40+1 (bond dimension 32, 2^15-sized GEMMs): the split form
     against plain FP32 on the first two slices of one bitstring (the paper
@@ -411,6 +440,7 @@ def run_ours(args):
                                 "speedup": timings["fp32"] / timings[args.precision]}
         extras["permute"] = permute_sweep(api, torch, peaks)
         extras["rotation_batch"] = rotation_batch_run(api, torch, args.precision, local)
+        extras["bris70_f001"] = bris70_run(api, torch, args.precision, local)
         if not args.no_c4:
             extras["grid7x7_d40"] = c4_subset(api, torch, args.precision, local)
         line.update(extras)

@@ -148,3 +148,60 @@ def rotation_batch(count: int = 256, seed: int = 0) -> List[Problem]:
         p.name = f"rot{rows}x{cols}_t{t}_{i}"
         out.append(p)
     return out
+
+
+def diamond_problem(t: int, seed: int, size: int = 12, n_cuts: int = 4, c_split=None,
+                    c_rows: int = 2) -> Problem:
+    """Bristlecone-like diamond without its two degree-1 corners (size 12:
+    70 qubits, rows of 3,5,7,9,11,11,9,7,5,3 qubits).
+
+    The figure with the paper's regions is not available; this reading keeps
+    the structure the text gives (Methods "Cutting indexes": four cuts of
+    2^4, regions A and B contracted per path, A.B then the path-independent
+    region C holding the open tile):
+      A = columns <= c_split of the upper rows, B = the rest of the upper rows,
+      C = the last c_rows rows (the open tile, 2^|C| amplitudes);
+      cuts = the A-B bonds of the first n_cuts rows.
+    Orders: A row by row, left to right; B row by row, left to right down to
+    the widest row and right to left below it; AB = A.B; C absorbed row by
+    row.  With size 12 every intermediate stays within 7 bonds (2^28
+    entries at bond dimension 16), A has rank 6 and B rank 7.
+    """
+    lat = diamond_lattice(drop_corners=True) if size == 12 else _small_diamond(size)
+    rows = sorted({r for r, _ in lat.coords})
+    r_first, r_last = rows[0], rows[-1]
+    widths = {r: sum(1 for rr, _ in lat.coords if rr == r) for r in rows}
+    r_wide = max(rows, key=lambda r: (widths[r], -r))
+    cs = sorted({c for _, c in lat.coords})
+    c_split = (cs[0] + cs[-1]) // 2 - 1 if c_split is None else c_split
+    circ = random_circuit(lat, t, seed)
+    upper = [r for r in rows if r <= r_last - c_rows]
+    in_row = lambda r: sorted(c for rr, c in lat.coords if rr == r)
+    A = [(r, c) for r in upper for c in in_row(r) if c <= c_split]
+    B = []
+    for r in upper:
+        cols = [c for c in in_row(r) if c > c_split]
+        B += [(r, c) for c in (cols if r <= r_wide else cols[::-1])]
+    C = [(r, c) for r in rows if r > r_last - c_rows for c in in_row(r)]
+    q = lat.qid
+    steps: List[Tuple[int, int]] = []
+    a_id, b_id = q(*A[0]), q(*B[0])
+    steps += [(a_id, q(*x)) for x in A[1:]]
+    steps += [(b_id, q(*x)) for x in B[1:]]
+    steps.append((a_id, b_id))
+    steps += [(a_id, q(*x)) for x in C]
+    cut_rows = [r for r in upper if any(c == c_split for c in in_row(r))
+                and any(c == c_split + 1 for c in in_row(r))][:n_cuts]
+    cuts = [lat.edge_id((r, c_split), (r, c_split + 1)) for r in cut_rows]
+    tile = [q(*x) for x in C]
+    return Problem(circ, cuts, tile, steps, name=f"{lat.name}_t{t}_s{seed}")
+
+
+def _small_diamond(size: int) -> Lattice:
+    """Diamond of a size x size rotated lattice (size even), corners dropped."""
+    pts = []
+    for x in range(size):
+        for y in range(size):
+            if (x + y) % 2 == 0 and (x, y) not in ((0, 0), (size - 1, size - 1)):
+                pts.append(((x + y) // 2, (x - y) // 2 + size // 2 - 1))
+    return Lattice(pts, name=f"diamond{size}_{len(pts)}")

@@ -45,3 +45,17 @@ def test_golden_frugal_acceptance():
         p = 1 - (1 - 1 / g["M"]) ** nc
         assert abs(p - acc) < 5e-5
         assert abs(1e6 / p - batches) / batches < 1e-3
+
+
+def test_golden_bris70_plan_sizes():
+    """The planner, on the 70-qubit diamond with four cuts of the A-B bonds,
+    reaches exactly the sizes the paper states: 2^(4x4) paths and a largest
+    intermediate of 2^(7x4) entries (down from rank 11 without cuts)."""
+    from paper_1811_09599_gb300.api import Plan
+    from qflex_inputs import diamond_problem
+    g = GOLD["bris70_sizes"]
+    prob = diamond_problem(32, 0)
+    assert prob.n == 70 and len(prob.cut_edges) == g["n_cuts"]
+    info = Plan(prob, "bf16x3", device=-1).info()
+    assert info["n_slices"] == 2 ** (g["n_cuts"] * g["K"])
+    assert info["max_tensor_elems"] == 2 ** (g["cut_rank"] * g["K"])
