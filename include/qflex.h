@@ -247,6 +247,21 @@ qflex_status qflex_cgemm(int32_t prec, int64_t M, int64_t N, int64_t K, const vo
  * out: device double [1], overwritten. */
 qflex_status qflex_norm(const double* amps, int64_t n, double* out, void* stream);
 
+/* Frugal rejection sampling over batches of amplitudes (Methods, "Fast sampling
+ * technique"): for each batch (e.g. the 2^k open-tile amplitudes of one bitstring)
+ * the entries are visited in a uniformly random order and entry j is accepted with
+ * probability min(1, p_j N / M), p_j = |amp_j|^2, N = 2^n_qubits; the first
+ * acceptance ends the batch (at most one per batch, which avoids correlations
+ * inside a batch); the probability of a sample per batch is 1 - (1 - 1/M)^n_c.
+ * Randomness: SplitMix64 stream per batch starting at seed + b * 0xD1B54A32D192ED03,
+ * order by a forward Fisher-Yates walk (step k swaps entry k with entry
+ * k + (x mod (n_c - k))), uniform u = (x >> 11) * 2^-53, acceptance u < p * (N / M)
+ * with FP64 products rounded separately.
+ * amps: device complex128 [n_batches][n_c], n_c <= 4096; accepted: device int32
+ * [n_batches], the accepted index within the batch or -1. */
+qflex_status qflex_frugal_sample(const double* amps, int64_t n_batches, int32_t n_c, int32_t n_qubits,
+                                 double M, uint64_t seed, int32_t* accepted, void* stream);
+
 /* Synchronize `device` and read (and clear) the library's device status word
  * used by the standalone kernels.  *status = QFLEX_OK or QFLEX_ERR_DEVICE_TIMEOUT. */
 qflex_status qflex_device_status(int device, int32_t* status);

@@ -48,6 +48,36 @@ def select_slices(P: int, fidelity: float, seed: int) -> List[int]:
     return sorted(a[:n_selected(fidelity, P)])
 
 
+def frugal_sample(amps: np.ndarray, n_qubits: int, M: float, seed: int) -> np.ndarray:
+    """Frugal rejection sampling over batches (Methods, "Fast sampling technique").
+
+    For each batch (row) the entries are visited in a uniformly random order
+    and the first one with u < p N / M is accepted (p = |amp|^2, N = 2^n); at
+    most one sample per batch, -1 if the batch is exhausted.  Randomness, as
+    specified for both implementations: a SplitMix64 stream per batch from
+    seed + b * 0xD1B54A32D192ED03; visiting order by a forward Fisher-Yates
+    walk (step k swaps entries k and k + x mod (n_c - k)); u = (x >> 11) 2^-53.
+    """
+    amps = np.atleast_2d(np.asarray(amps, dtype=np.complex128))
+    n_b, n_c = amps.shape
+    scale = float(2.0 ** n_qubits) / M
+    out = np.full(n_b, -1, dtype=np.int32)
+    for b in range(n_b):
+        rng = SplitMix64((seed + b * 0xD1B54A32D192ED03) & _M64)
+        order = list(range(n_c))
+        for k in range(n_c):
+            j = k + rng.next() % (n_c - k)
+            order[k], order[j] = order[j], order[k]
+            idx = order[k]
+            a = amps[b, idx]
+            p = a.real * a.real + a.imag * a.imag
+            u = (rng.next() >> 11) * 2.0 ** -53
+            if u < p * scale:
+                out[b] = idx
+                break
+    return out
+
+
 def norm_estimate(amps: np.ndarray, n_qubits: int) -> float:
     """Estimated <psi~|psi~> from a sample of amplitudes: 2^n * mean |a|^2."""
     a = np.asarray(amps).reshape(-1)

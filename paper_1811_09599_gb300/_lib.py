@@ -92,6 +92,8 @@ SIGNATURES = [
     ("qflex_cgemm", C.c_int, [C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
                               C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     ("qflex_norm", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    ("qflex_frugal_sample", C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_double,
+                                      C.c_uint64, C.c_void_p, C.c_void_p]),
     ("qflex_device_status", C.c_int, [C.c_int, C.POINTER(C.c_int32)]),
     ("qflex_cgemm_noalloc", C.c_int, [C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p]),

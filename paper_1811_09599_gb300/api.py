@@ -237,6 +237,19 @@ def norm(amps: torch.Tensor, stream=None) -> torch.Tensor:
     return out
 
 
+def frugal_sample(amps: torch.Tensor, n_qubits: int, M: float = 10.0, seed: int = 0,
+                  stream=None) -> torch.Tensor:
+    """qflex_frugal_sample: one accepted index (or -1) per batch (row of amps)."""
+    lib = _lib.load()
+    a = amps.contiguous()
+    assert a.dtype == torch.complex128 and a.is_cuda and a.dim() == 2
+    out = torch.empty(a.shape[0], dtype=torch.int32, device=a.device)
+    check(lib.qflex_frugal_sample(C.c_void_p(a.data_ptr()), a.shape[0], a.shape[1], n_qubits,
+                                  float(M), C.c_uint64(seed), C.c_void_p(out.data_ptr()),
+                                  _stream_handle(stream)))
+    return out
+
+
 def device_status(device: int = 0) -> int:
     lib = _lib.load()
     v = C.c_int32()

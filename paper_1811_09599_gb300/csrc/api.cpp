@@ -1302,6 +1302,17 @@ qflex_status qflex_norm(const double* amps, int64_t n, double* out, void* stream
   return QFLEX_OK;
 }
 
+qflex_status qflex_frugal_sample(const double* amps, int64_t n_batches, int32_t n_c, int32_t n_qubits,
+                                 double M, uint64_t seed, int32_t* accepted, void* stream) {
+  if (n_batches < 0 || n_c < 1 || n_c > 4096 || n_qubits < 0 || n_qubits > 1000 || !(M > 0.0))
+    return fail(QFLEX_ERR_ARG, "bad sampling arguments");
+  if (n_batches == 0) return QFLEX_OK;
+  if (!amps || !accepted) return fail(QFLEX_ERR_ARG, "null pointer");
+  const double scale = std::ldexp(1.0, n_qubits) / M;
+  QF_CUDA(launch_frugal(amps, n_batches, n_c, scale, seed, accepted, static_cast<cudaStream_t>(stream)));
+  return QFLEX_OK;
+}
+
 qflex_status qflex_device_status(int device, int32_t* status) {
   if (!status || device < 0) return fail(QFLEX_ERR_ARG, "bad argument");
   QF_CUDA(cudaSetDevice(device));

@@ -184,8 +184,14 @@ __global__ void __launch_bounds__(256, 6) k_permute_tiled(const float2* __restri
   // Software pipeline: the global loads of the next tile are issued before
   // the stores of the current one, so HBM reads stay in flight across the
   // shared-memory round trip.  Each thread holds kPer entries in registers.
+  // Entry j = threadIdx.x + 256 k: its low 5 bits are the lane, its high bits
+  // warp + 8 k, so the lane's table entries are read once per kernel and the
+  // high ones are warp-uniform.
   constexpr int kPer = (1 << kPermTileBits) / 256;
   const int n = 1 << t.tile_bits;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t in_lo = s_in_lo[lane], out_lo = s_out_lo[lane];
+  const int ld_lo = s_ld_lo[lane], st_lo = s_st_lo[lane];
   auto tile_base = [&](int64_t tb, int64_t& ib, int64_t& ob) {
     ib = in_base;
     ob = 0;
@@ -202,15 +208,15 @@ __global__ void __launch_bounds__(256, 6) k_permute_tiled(const float2* __restri
     tile_base(tb, ib, ob);
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
-      const int j = threadIdx.x + k * 256;
-      if (j < n) v[k] = __ldg(in + ib + s_in_lo[j & 31] + s_in_hi[j >> 5]);
+      const int h = wid + 8 * k;
+      if (h * 32 < n) v[k] = __ldg(in + ib + in_lo + s_in_hi[h]);
     }
   }
   for (; tb < t.n_tiles; tb += gridDim.x) {
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
-      const int j = threadIdx.x + k * 256;
-      if (j < n) tile[s_ld_lo[j & 31] ^ s_ld_hi[j >> 5]] = v[k];
+      const int h = wid + 8 * k;
+      if (h * 32 + lane < n) tile[ld_lo ^ s_ld_hi[h]] = v[k];
     }
     __syncthreads();
     const int64_t cur_ob = ob;
@@ -219,15 +225,15 @@ __global__ void __launch_bounds__(256, 6) k_permute_tiled(const float2* __restri
       tile_base(nxt, ib, ob);
 #pragma unroll
       for (int k = 0; k < kPer; ++k) {
-        const int j = threadIdx.x + k * 256;
-        if (j < n) v[k] = __ldg(in + ib + s_in_lo[j & 31] + s_in_hi[j >> 5]);
+        const int h = wid + 8 * k;
+        if (h * 32 < n) v[k] = __ldg(in + ib + in_lo + s_in_hi[h]);
       }
     }
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
-      const int j = threadIdx.x + k * 256;
-      if (j < n) put<FMT>(out, cur_ob + s_out_lo[j & 31] + s_out_hi[j >> 5],
-                          tile[s_st_lo[j & 31] ^ s_st_hi[j >> 5]], nsplit, plane);
+      const int h = wid + 8 * k;
+      if (h * 32 + lane < n)
+        put<FMT>(out, cur_ob + out_lo + s_out_hi[h], tile[st_lo ^ s_st_hi[h]], nsplit, plane);
     }
     __syncthreads();
   }

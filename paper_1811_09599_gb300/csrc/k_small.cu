@@ -49,7 +49,59 @@ __global__ void k_norm(const double* __restrict__ amps, int64_t n, double* __res
   }
 }
 
+// Frugal rejection sampling (Methods, "Fast sampling technique"): one thread
+// per batch.  Entries are visited in a uniformly random order by a forward
+// Fisher-Yates walk (step k swaps a[k] with a[k + (x mod (n_c - k))]); entry
+// a[k] is accepted when u < p N / M with p = |amp|^2 and u = (x >> 11) 2^-53,
+// x drawn from SplitMix64; the first acceptance ends the batch (at most one
+// per batch), none gives -1.  The stream of batch b starts at
+// seed + b * 0xD1B54A32D192ED03.  FP64 products are rounded separately (no
+// contraction) so that every decision is reproducible on the host.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t& x) {
+  x += 0x9E3779B97F4A7C15ull;
+  uint64_t z = x;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+constexpr int kMaxBatch = 4096;
+
+__global__ void k_frugal(const double* __restrict__ amps, int64_t n_batches, int n_c, double scale,
+                         uint64_t seed, int32_t* __restrict__ accepted) {
+  const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (b >= n_batches) return;
+  uint16_t a[kMaxBatch];
+  for (int i = 0; i < n_c; ++i) a[i] = uint16_t(i);
+  uint64_t x = seed + uint64_t(b) * 0xD1B54A32D192ED03ull;
+  const double* amp = amps + 2 * b * n_c;
+  int32_t res = -1;
+  for (int k = 0; k < n_c; ++k) {
+    const int j = k + int(splitmix64(x) % uint64_t(n_c - k));
+    const uint16_t t = a[k];
+    a[k] = a[j];
+    a[j] = t;
+    const int idx = a[k];
+    const double re = amp[2 * idx], im = amp[2 * idx + 1];
+    const double p = __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
+    const double u = double(splitmix64(x) >> 11) * 0x1.0p-53;
+    if (u < __dmul_rn(p, scale)) {
+      res = idx;
+      break;
+    }
+  }
+  accepted[b] = res;
+}
+
 }  // namespace
+
+cudaError_t launch_frugal(const double* amps, int64_t n_batches, int n_c, double scale, uint64_t seed,
+                          int32_t* accepted, cudaStream_t s) {
+  if (n_c < 1 || n_c > kMaxBatch) return cudaErrorInvalidValue;
+  if (n_batches <= 0) return cudaSuccess;
+  k_frugal<<<unsigned((n_batches + 127) / 128), 128, 0, s>>>(amps, n_batches, n_c, scale, seed, accepted);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_slicesum(const float2* src, const int64_t* strides, int n_open, double* amps,
                             cudaStream_t s) {

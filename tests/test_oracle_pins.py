@@ -250,3 +250,27 @@ def test_all_slices_give_unit_norm_and_fraction_norm_is_reported():
     assert 0.0 < nrm < 1.0                           # norm ~ f; value is reported, not gated
     f = SEL.overlap_fidelity(full, part)
     assert 0.0 < f <= 1.0 + 1e-12
+
+
+def test_frugal_sampling_acceptance_closed_form():
+    """Methods, "Fast sampling technique": with Porter-Thomas amplitudes the
+    probability that a batch of N_C yields a sample is 1 - (1 - 1/M)^N_C
+    (95.76% for M = 10, N_C = 30); at most one sample per batch, and the
+    accepted entries are distributed as min(1, pN/M)-weighted draws."""
+    n = 20
+    rng = np.random.default_rng(11)
+    nb, nc = 3000, 30
+    amps = (rng.standard_normal((nb, nc)) + 1j * rng.standard_normal((nb, nc))) * np.sqrt(0.5 * 2.0 ** -n)
+    acc = SEL.frugal_sample(amps, n, 10.0, seed=5)
+    rate = float(np.mean(acc >= 0))
+    assert abs(rate - (1 - (1 - 0.1) ** 30)) < 0.012
+    assert np.all((acc >= -1) & (acc < nc))
+    # a batch of zeros never accepts; a batch with one entry p N >= M always does
+    z = np.zeros((1, 8), dtype=np.complex128)
+    assert SEL.frugal_sample(z, n, 10.0, 1)[0] == -1
+    z[0, 5] = np.sqrt(20.0 * 2.0 ** -n)
+    assert SEL.frugal_sample(z, n, 10.0, 1)[0] == 5
+    # accepted samples favour large |amp|^2 (mean p N of accepted > 1)
+    p = np.abs(amps) ** 2 * 2.0 ** n
+    sel = acc[acc >= 0]
+    assert np.mean(p[np.arange(nb)[acc >= 0], sel]) > 1.5
