@@ -379,7 +379,7 @@ def run_ours(args):
 
     tc = prof["gemm_tc"] if args.precision != "fp32" else prof["gemm_fp32"]
     bf16_peak = peaks["bf16_tflops_sustained"]
-    tf_scale = 1.1 / 2.25 if args.precision.startswith("tf32") else 1.0
+    tf_scale = 1.1 / 2.25 if args.precision.startswith("tf32") else 1.0   # fp16 = bf16 rate
     if args.precision == "fp32":
         roof = None
     else:
@@ -438,6 +438,22 @@ def run_ours(args):
         extras["fp32_plain"] = {"subset": "1 bitstring x slices 0..15", "fp32_ms": timings["fp32"],
                                 f"{args.precision}_ms": timings[args.precision],
                                 "speedup": timings["fp32"] / timings[args.precision]}
+        # the other split forms on the same subset and parity sample
+        for prec in ("tf32x3", "fp16x3"):
+            if prec == args.precision:
+                continue
+            pl = api.Plan(prob, prec, device=local)
+            pl.amplitudes(sub, None, subset)
+            torch.cuda.synchronize()
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record()
+            pl.amplitudes(sub, None, subset)
+            g1.record()
+            torch.cuda.synchronize()
+            extras["fp32_plain"][f"{prec}_ms"] = g0.elapsed_time(g1)
+            extras["parity"][prec] = amp_error(pl.amplitudes(sub, None, [s0]).cpu().numpy(), amp_ref,
+                                               prob.n, 1.0 / P)
+            pl.close()
         extras["permute"] = permute_sweep(api, torch, peaks)
         extras["rotation_batch"] = rotation_batch_run(api, torch, args.precision, local)
         extras["bris70_f001"] = bris70_run(api, torch, args.precision, local)
@@ -458,7 +474,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "fp32"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "fp16x3", "fp32"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-c4", action="store_true", help="skip the 7x7 depth-40 subset in the extras")
     args = ap.parse_args()

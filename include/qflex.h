@@ -62,7 +62,11 @@ typedef enum {
                            hi+lo, products hi*hi + hi*lo + lo*hi, FP32 accumulate */
   QFLEX_BF16X3 = 2,     /* same with bf16 hi+lo splits (kind::f16, bf16 inputs) */
   QFLEX_BF16_PLAIN = 3, /* one bf16 product per part (reported, not gated) */
-  QFLEX_TF32_PLAIN = 4  /* one tf32 product per part (reported, not gated) */
+  QFLEX_TF32_PLAIN = 4, /* one tf32 product per part (reported, not gated) */
+  QFLEX_FP16X3 = 5      /* fp16 hi+lo splits (kind::f16, f16 inputs), 3 products, FP32
+                           accumulate; each operand is first scaled by a power of two 2^s
+                           chosen from its largest |re|, |im|, |re+im| (kept below 2^14),
+                           and the product is rescaled exactly by 2^-(s_A+s_B) */
 } qflex_precision;
 
 /* Gate kinds (Methods, "Revised set of RQCs"; rotations R_P(t) = exp(-i t P/2)). */
@@ -279,8 +283,8 @@ qflex_status qflex_device_status(int device, int32_t* status);
  *
  *  - Scratch limit: the split operand planes of A and B must fit in
  *    QFLEX_NOALLOC_SCRATCH_BYTES (64 MiB), i.e. (M + N) * K * 12 bytes for
- *    bf16 split forms, (M + N) * K * 24 for tf32x3 (half that for the plain
- *    forms); larger tensor-core products return QFLEX_ERR_ARG.  The FP32
+ *    bf16 and fp16 split forms, (M + N) * K * 24 for tf32x3 (half that for the
+ *    plain forms); larger tensor-core products return QFLEX_ERR_ARG.  The FP32
  *    precision needs no scratch and has no such limit.
  *  - Every GPU that loads the library's scratch holds these 64 MiB until the
  *    process exits.  The first call on a device (with that device current)

@@ -15,7 +15,7 @@ QFLEX_OK = 0
 STATUS_NAMES = {0: "QFLEX_OK", 1: "QFLEX_ERR_ARG", 2: "QFLEX_ERR_CIRCUIT", 3: "QFLEX_ERR_PLAN",
                 4: "QFLEX_ERR_OOM", 5: "QFLEX_ERR_CUDA", 6: "QFLEX_ERR_DEVICE_TIMEOUT",
                 7: "QFLEX_ERR_UNSUPPORTED"}
-PRECISIONS = {"fp32": 0, "tf32x3": 1, "bf16x3": 2, "bf16": 3, "tf32": 4}
+PRECISIONS = {"fp32": 0, "tf32x3": 1, "bf16x3": 2, "bf16": 3, "tf32": 4, "fp16x3": 5}
 
 
 class QFlexError(RuntimeError):

@@ -48,6 +48,14 @@ qflex_status fail(qflex_status st, const std::string& msg) {
       return fail(QFLEX_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+int tc_kind_of(int prec) {
+  return (prec == QFLEX_TF32X3 || prec == QFLEX_TF32_PLAIN) ? 0 : (prec == QFLEX_FP16X3 ? 2 : 1);
+}
+int nsplit_of(int prec) {
+  return (prec == QFLEX_TF32X3 || prec == QFLEX_BF16X3 || prec == QFLEX_FP16X3) ? 2 : 1;
+}
+int plane_fmt(int kind) { return kind == 0 ? kFmtTF32 : (kind == 1 ? kFmtBF16 : kFmtFP16); }
+
 int ilog2(int64_t v) {
   int b = 0;
   while ((int64_t(1) << b) < v) ++b;
@@ -143,6 +151,7 @@ struct qflex_plan_s {
   GridQubitMeta* d_gmeta = nullptr;
   int2* d_gops = nullptr;
   int32_t* d_status = nullptr;
+  unsigned* d_smax = nullptr;                  // fp16 operand scales: [0] A, [1] B
   cudaStream_t last_stream = nullptr;
   // profiling: event pairs around launches
   // gradients (qflex_plan_enable_gradients)
@@ -525,7 +534,7 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
   p.grid_bytes = align256(size_t(p.grid_elems) * 8);
   p.total_bytes = p.grid_bytes + align256(p.arena_bytes) + align256(p.opA_bytes) + align256(p.opB_bytes) +
                   align256(sizeof(GridQubitMeta) * n) + align256(sizeof(int2) * std::max<size_t>(1, p.gops.size())) +
-                  256;
+                  512;
   return QFLEX_OK;
 }
 
@@ -550,6 +559,7 @@ qflex_status allocate(qflex_plan_s& p) {
   p.d_gops = reinterpret_cast<int2*>(c);
   c += align256(sizeof(int2) * std::max<size_t>(1, p.gops.size()));
   p.d_status = reinterpret_cast<int32_t*>(c);
+  p.d_smax = reinterpret_cast<unsigned*>(c + 256);
   QF_CUDA(cudaMemcpy(p.d_gmeta, p.gmeta.data(), sizeof(GridQubitMeta) * p.n, cudaMemcpyHostToDevice));
   if (!p.gops.empty())
     QF_CUDA(cudaMemcpy(p.d_gops, p.gops.data(), sizeof(int2) * p.gops.size(), cudaMemcpyHostToDevice));
@@ -577,13 +587,35 @@ int64_t ref_base(const Ref& r, const std::vector<int64_t>& vals) {
   return b;
 }
 
+// Whole tensor behind a view (for the fp16 scale: the largest part of the
+// whole tensor bounds the largest part of any view of it).
+void ref_region(const qflex_plan_s& p, const Ref& r, const float2** ptr, int64_t* n) {
+  if (r.grid) {
+    const GridQubitMeta& m = p.gmeta[r.id];
+    *ptr = p.d_grid + m.offset;
+    *n = (int64_t(1) << m.n_bits) * (m.tile ? 2 : 1);
+  } else {
+    *ptr = ref_ptr(p, r);
+    *n = p.bufs[r.id].elems;
+  }
+}
+
 cudaError_t produce(const qflex_plan_s& p, const Operand& op, bool tc, int64_t rows, int64_t cols,
-                    const std::vector<int64_t>& vals, void* out, cudaStream_t s) {
-  const int fmt = tc ? (p.tc_kind == 0 ? kFmtTF32 : kFmtBF16) : kFmtC64;
+                    const std::vector<int64_t>& vals, void* out, cudaStream_t s, int slot) {
+  const int fmt = tc ? plane_fmt(p.tc_kind) : kFmtC64;
   const float2* in = ref_ptr(p, op.ref);
   const int64_t base = ref_base(op.ref, vals);
-  if (op.pow2) return launch_permute_tiled(in, base, op.tile, fmt, p.nsplit, out, rows * cols, s);
-  return launch_permute_gather(in, base, op.gather, fmt, p.nsplit, out, rows * cols, s);
+  const unsigned* smax = nullptr;
+  if (fmt == kFmtFP16) {
+    const float2* rp;
+    int64_t rn;
+    ref_region(p, op.ref, &rp, &rn);
+    cudaError_t e = launch_absmax(rp, rn, p.d_smax + slot, s);
+    if (e != cudaSuccess) return e;
+    smax = p.d_smax + slot;
+  }
+  if (op.pow2) return launch_permute_tiled(in, base, op.tile, fmt, p.nsplit, out, rows * cols, s, smax);
+  return launch_permute_gather(in, base, op.gather, fmt, p.nsplit, out, rows * cols, s, smax);
 }
 
 // Launch `fn` on `s`, bracketed by an event pair when the plan is profiling.
@@ -615,7 +647,7 @@ cudaError_t run_step(qflex_plan_s& p, const Step& st, const std::vector<int64_t>
     A = ref_ptr(p, st.A.ref);
   } else {
     if ((e = timed(p, 1, 0, 0, double(st.M) * st.K * (8.0 + out_per), s,
-                   [&] { return produce(p, st.A, st.tc, st.M, st.K, vals, p.d_opA, s); })) != cudaSuccess)
+                   [&] { return produce(p, st.A, st.tc, st.M, st.K, vals, p.d_opA, s, 0); })) != cudaSuccess)
       return e;
     A = static_cast<const float2*>(p.d_opA);
   }
@@ -623,7 +655,7 @@ cudaError_t run_step(qflex_plan_s& p, const Step& st, const std::vector<int64_t>
     B = ref_ptr(p, st.B.ref);
   } else {
     if ((e = timed(p, 1, 0, 0, double(st.N) * st.K * (8.0 + out_per), s,
-                   [&] { return produce(p, st.B, st.tc, st.N, st.K, vals, p.d_opB, s); })) != cudaSuccess)
+                   [&] { return produce(p, st.B, st.tc, st.N, st.K, vals, p.d_opB, s, 1); })) != cudaSuccess)
       return e;
     B = static_cast<const float2*>(p.d_opB);
   }
@@ -633,7 +665,8 @@ cudaError_t run_step(qflex_plan_s& p, const Step& st, const std::vector<int64_t>
   const double gbytes = 8.0 * (double(st.M) * st.K + double(st.N) * st.K + double(st.M) * st.N);
   if (st.tc)
     return timed(p, 3, 8.0 * mnk, mma, gbytes, s, [&] {
-      return launch_cgemm_tc(p.tc_kind, p.nsplit, st.bn, st.maps, st.M, st.N, st.K, C, p.d_status, s);
+      return launch_cgemm_tc(p.tc_kind, p.nsplit, st.bn, st.maps, st.M, st.N, st.K, C, p.d_status, s,
+                             p.tc_kind == 2 ? p.d_smax : nullptr, p.tc_kind == 2 ? p.d_smax + 1 : nullptr);
     });
   return timed(p, 2, 8.0 * mnk, 0, gbytes, s, [&] {
     return st.N <= 32 ? launch_cgemm_thin(st.M, st.N, st.K, A, B, C, s) : launch_cgemm_simt(st.M, st.N, st.K, A, B, C, s);
@@ -768,26 +801,36 @@ cudaError_t run_bwd(qflex_plan_s& p, const Step& st, const BwdGemm& g, const std
                     cudaStream_t s) {
   cudaError_t e;
   const float2* W = reinterpret_cast<const float2*>(p.d_warena + p.w_off[st.out_buf]);
-  const int fmt = g.route == 2 ? (p.tc_kind == 0 ? kFmtTF32 : kFmtBF16) : kFmtC64;
+  const int fmt = g.route == 2 ? plane_fmt(p.tc_kind) : kFmtC64;
   const double out_per = g.route == 2 ? 3.0 * p.nsplit * (p.tc_kind == 0 ? 4 : 2) : 8.0;
+  const bool scaled = fmt == kFmtFP16;
   const float2* X = W;
   if (!g.x_direct) {
+    if (scaled && (e = launch_absmax(W, g.M * g.K, p.d_smax, s)) != cudaSuccess) return e;
     if ((e = timed(p, 1, 0, 0, double(g.M) * g.K * (8.0 + out_per), s, [&] {
-           return launch_permute_tiled(W, 0, g.xt, fmt, p.nsplit, p.d_gA, g.M * g.K, s);
+           return launch_permute_tiled(W, 0, g.xt, fmt, p.nsplit, p.d_gA, g.M * g.K, s,
+                                       scaled ? p.d_smax : nullptr);
          })) != cudaSuccess)
       return e;
     X = static_cast<const float2*>(p.d_gA);
   }
+  if (scaled) {
+    const float2* rp;
+    int64_t rn;
+    ref_region(p, g.ysrc, &rp, &rn);
+    if ((e = launch_absmax(rp, rn, p.d_smax + 1, s)) != cudaSuccess) return e;
+  }
   if ((e = timed(p, 1, 0, 0, double(g.N) * g.K * (8.0 + out_per), s, [&] {
          return launch_permute_tiled(ref_ptr(p, g.ysrc), ref_base(g.ysrc, vals), g.yt, fmt, p.nsplit, p.d_gB,
-                                     g.N * g.K, s);
+                                     g.N * g.K, s, scaled ? p.d_smax + 1 : nullptr);
        })) != cudaSuccess)
     return e;
   const float2* Y = static_cast<const float2*>(p.d_gB);
   const double mnk = double(g.M) * double(g.N) * double(g.K);
   if (g.route == 2) {
     e = timed(p, 3, 8.0 * mnk, mnk * 3.0 * (p.nsplit == 2 ? 3.0 : 1.0) * 2.0, 0, s, [&] {
-      return launch_cgemm_tc(p.tc_kind, p.nsplit, g.bn, g.maps, g.M, g.N, g.K, p.d_gC, p.d_status, s);
+      return launch_cgemm_tc(p.tc_kind, p.nsplit, g.bn, g.maps, g.M, g.N, g.K, p.d_gC, p.d_status, s,
+                             scaled ? p.d_smax : nullptr, scaled ? p.d_smax + 1 : nullptr);
     });
   } else {
     e = timed(p, 2, 8.0 * mnk, 0, 0, s, [&] {
@@ -903,12 +946,12 @@ qflex_status qflex_plan_create(const qflex_problem* problem, qflex_precision pre
                                qflex_plan* out) {
   if (!problem || !out) return fail(QFLEX_ERR_ARG, "null problem or output");
   *out = nullptr;
-  if (prec < QFLEX_FP32_SIMT || prec > QFLEX_TF32_PLAIN) return fail(QFLEX_ERR_ARG, "unknown precision");
+  if (prec < QFLEX_FP32_SIMT || prec > QFLEX_FP16X3) return fail(QFLEX_ERR_ARG, "unknown precision");
   auto p = std::make_unique<qflex_plan_s>();
   p->prec = prec;
   p->device = device;
-  p->tc_kind = (prec == QFLEX_TF32X3 || prec == QFLEX_TF32_PLAIN) ? 0 : 1;
-  p->nsplit = (prec == QFLEX_TF32X3 || prec == QFLEX_BF16X3) ? 2 : 1;
+  p->tc_kind = tc_kind_of(prec);
+  p->nsplit = nsplit_of(prec);
   if (qflex_status st = build_plan(problem, *p)) return st;
   if (ws_max > 0 && p->total_bytes > ws_max)
     return fail(QFLEX_ERR_PLAN, "plan needs " + std::to_string(p->total_bytes) + " bytes, budget " +
@@ -971,7 +1014,7 @@ qflex_status qflex_plan_cost(qflex_plan p, int64_t n_bs, const int64_t* ids, int
     }
     if (!s.A.direct) c.permute_bytes += 16.0 * double(s.M) * double(s.K);
     if (!s.B.direct) c.permute_bytes += 16.0 * double(s.N) * double(s.K);
-    c.launches += 1 + !s.A.direct + !s.B.direct;
+    c.launches += 1 + !s.A.direct + !s.B.direct + (s.tc && p->tc_kind == 2 ? 2 : 0);
     ++c.steps_executed;
     return QFLEX_OK;
   });
@@ -1233,11 +1276,11 @@ qflex_status qflex_cgemm_workspace_size(int32_t prec, int64_t M, int64_t N, int6
     *bytes = 0;
     return QFLEX_OK;
   }
-  if (prec < 0 || prec > QFLEX_TF32_PLAIN) return fail(QFLEX_ERR_ARG, "unknown precision");
-  const int kind = (prec == QFLEX_TF32X3 || prec == QFLEX_TF32_PLAIN) ? 0 : 1;
-  const int nsplit = (prec == QFLEX_TF32X3 || prec == QFLEX_BF16X3) ? 2 : 1;
+  if (prec < 0 || prec > QFLEX_FP16X3) return fail(QFLEX_ERR_ARG, "unknown precision");
+  const int kind = tc_kind_of(prec);
+  const int nsplit = nsplit_of(prec);
   const size_t per = size_t(3) * nsplit * (kind == 0 ? 4 : 2);
-  *bytes = align256(per * size_t(M) * size_t(K)) + align256(per * size_t(N) * size_t(K));
+  *bytes = align256(per * size_t(M) * size_t(K)) + align256(per * size_t(N) * size_t(K)) + 256;
   return QFLEX_OK;
 }
 
@@ -1261,38 +1304,45 @@ qflex_status qflex_cgemm(int32_t prec, int64_t M, int64_t N, int64_t K, const vo
   if (qflex_status st = qflex_cgemm_workspace_size(prec, M, N, K, &need)) return st;
   if (!ws || ws_bytes < need) return fail(QFLEX_ERR_ARG, "workspace too small");
   if (!tc_available()) return fail(QFLEX_ERR_UNSUPPORTED, "tensor-map encoder unavailable");
-  const int kind = (prec == QFLEX_TF32X3 || prec == QFLEX_TF32_PLAIN) ? 0 : 1;
-  const int nsplit = (prec == QFLEX_TF32X3 || prec == QFLEX_BF16X3) ? 2 : 1;
+  const int kind = tc_kind_of(prec);
+  const int nsplit = nsplit_of(prec);
   const size_t per = size_t(3) * nsplit * (kind == 0 ? 4 : 2);
   char* pa = static_cast<char*>(ws);
   char* pb = pa + align256(per * size_t(M) * size_t(K));
+  unsigned* smax = reinterpret_cast<unsigned*>(pb + align256(per * size_t(N) * size_t(K)));
+  const int fmt = plane_fmt(kind);
   // identity "permutation" of a [rows][K] matrix into operand planes
-  auto planes = [&](const void* src, int64_t rows, void* dst) {
+  auto planes = [&](const void* src, int64_t rows, void* dst, unsigned* sm) {
     std::vector<int64_t> w;
     const int64_t total = rows * K;
+    if (fmt == kFmtFP16) {
+      cudaError_t e = launch_absmax(static_cast<const float2*>(src), total, sm, s);
+      if (e != cudaSuccess) return e;
+    } else {
+      sm = nullptr;
+    }
     if (is_pow2(total)) {
       for (int b = 0; b < ilog2(total); ++b) w.push_back(int64_t(1) << b);
       PermTile t;
       build_perm_tile(int(w.size()), w.data(), &t);
-      return launch_permute_tiled(static_cast<const float2*>(src), 0, t, kind == 0 ? kFmtTF32 : kFmtBF16, nsplit,
-                                  dst, total, s);
+      return launch_permute_tiled(static_cast<const float2*>(src), 0, t, fmt, nsplit, dst, total, s, sm);
     }
     GatherDesc g{};
     g.rank = 1;
     g.total = total;
     g.dims[0] = total;
     g.in_strides[0] = 1;
-    return launch_permute_gather(static_cast<const float2*>(src), 0, g, kind == 0 ? kFmtTF32 : kFmtBF16, nsplit,
-                                 dst, total, s);
+    return launch_permute_gather(static_cast<const float2*>(src), 0, g, fmt, nsplit, dst, total, s, sm);
   };
-  QF_CUDA(planes(A, M, pa));
-  QF_CUDA(planes(B, N, pb));
+  QF_CUDA(planes(A, M, pa, smax));
+  QF_CUDA(planes(B, N, pb, smax + 1));
   TcGemmMaps maps;
   const int bn = N >= 128 ? 128 : 64;
   if (!tc_encode_maps(kind, nsplit, bn, pa, M, pb, N, K, &maps)) return fail(QFLEX_ERR_CUDA, "tensor map encoding failed");
   int dev = 0;
   QF_CUDA(cudaGetDevice(&dev));
-  QF_CUDA(launch_cgemm_tc(kind, nsplit, bn, maps, M, N, K, static_cast<float2*>(C), device_status_word(dev), s));
+  QF_CUDA(launch_cgemm_tc(kind, nsplit, bn, maps, M, N, K, static_cast<float2*>(C), device_status_word(dev), s,
+                          kind == 2 ? smax : nullptr, kind == 2 ? smax + 1 : nullptr));
   return QFLEX_OK;
 }
 

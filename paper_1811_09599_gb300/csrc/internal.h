@@ -13,6 +13,16 @@ namespace qflex {
 // waits ran out (they then skip their remaining work and return).
 enum : int32_t { kDevTimeout = 1 };
 
+#ifdef __CUDACC__
+__device__ __forceinline__ float fp16_scale_of(unsigned max_bits) {
+  const float m = __uint_as_float(max_bits);
+  if (!(m > 0.f) || !(m < 3.0e38f)) return 1.f;
+  int e;
+  frexpf(m, &e);
+  return ldexpf(1.f, 14 - e);
+}
+#endif
+
 // ------------------------------------------------------------------ grid tensors
 // One qubit's gate line, compiled by the planner.  Op encoding (int2):
 //   x = type | (bitpos << 8), y = angle index (or -1)
@@ -60,8 +70,15 @@ enum PermFormat : int {
   kFmtC64 = 0,        // complex64, the permuted tensor itself
   kFmtTF32 = 1,       // 3M planes re, im, re+im, each split into tf32 hi (+ lo)
   kFmtBF16 = 2,       // same with bf16
-  kFmtAccC128 = 3     // out (complex128) += entry: scatter-add of cotangents
+  kFmtAccC128 = 3,    // out (complex128) += entry: scatter-add of cotangents
+  kFmtFP16 = 4        // 3M planes in fp16 hi (+ lo), scaled by a power of two
 };
+
+// Power-of-two scaling of fp16 operands: `smax` points to the bits of the
+// largest |re|, |im|, |re+im| of the operand (written by launch_absmax);
+// scale = 2^(14 - e) with smax = f 2^e, f in [0.5, 1), so scaled parts stay
+// below 2^14.  Both the producer and the GEMM epilogue derive it from smax.
+cudaError_t launch_absmax(const float2* in, int64_t n, unsigned* smax, cudaStream_t s);
 
 // Build the tile tables for a map of `nbits` index bits: bit j moves the
 // input by w_in[j] entries and the output by w_out[j] (1 << j when w_out is
@@ -73,7 +90,7 @@ bool build_perm_tile(int nbits, const int64_t* w_in, PermTile* t, const int64_t*
 // 2 and `plane_elems` the number of entries of one plane (rows*cols).
 cudaError_t launch_permute_tiled(const float2* in, int64_t in_base, const PermTile& t,
                                  int fmt, int nsplit, void* out, int64_t plane_elems,
-                                 cudaStream_t s);
+                                 cudaStream_t s, const unsigned* smax = nullptr);
 
 // Generic gather for any dims: out[o] = in[base + sum_a idx_a(o) * stride_a].
 constexpr int kGatherMaxRank = 32;
@@ -85,7 +102,7 @@ struct GatherDesc {
 };
 cudaError_t launch_permute_gather(const float2* in, int64_t in_base, const GatherDesc& d,
                                   int fmt, int nsplit, void* out, int64_t plane_elems,
-                                  cudaStream_t s);
+                                  cudaStream_t s, const unsigned* smax = nullptr);
 
 // ------------------------------------------------------------------ complex GEMM
 // C[m][n] = sum_k A[m][k] B[n][k], complex64, row-major, FP32 accumulate.
@@ -96,7 +113,8 @@ cudaError_t launch_cgemm_thin(int64_t M, int64_t N, int64_t K, const float2* A,
                               const float2* B, float2* C, cudaStream_t s);
 
 // Tensor-core GEMM on split 3M planes (produced by the permutation kernel in
-// kFmtTF32 / kFmtBF16 format).  kind: 0 = tf32, 1 = bf16.  bn: 64 or 128.
+// kFmtTF32 / kFmtBF16 / kFmtFP16 format).  kind: 0 = tf32, 1 = bf16, 2 = fp16
+// (then smax_a / smax_b give the operand scales).  bn: 64 or 128.
 struct TcGemmMaps {
   CUtensorMap a;
   CUtensorMap b;
@@ -105,7 +123,8 @@ bool tc_encode_maps(int kind, int nsplit, int bn, const void* a_planes, int64_t 
                     const void* b_planes, int64_t N, int64_t K, TcGemmMaps* maps);
 cudaError_t launch_cgemm_tc(int kind, int nsplit, int bn, const TcGemmMaps& maps, int64_t M,
                             int64_t N, int64_t K, float2* C, int32_t* d_status,
-                            cudaStream_t s);
+                            cudaStream_t s, const unsigned* smax_a = nullptr,
+                            const unsigned* smax_b = nullptr);
 bool tc_available();   // driver entry point for tensor-map encoding found
 
 // ------------------------------------------------------------------ small kernels

@@ -4,8 +4,9 @@
 // (Gauss) trick:
 //   T1 = Ar.Br, T2 = Ai.Bi, T3 = (Ar+Ai).(Br+Bi);  Re C = T1 - T2,
 //   Im C = T3 - T1 - T2.
-// Each real operand is split x = hi + lo (tf32 or bf16 parts) and each real
-// product is taken as hi.hi + hi.lo + lo.hi with FP32 accumulation in TMEM.
+// Each real operand is split x = hi + lo (tf32, bf16, or fp16 after an exact
+// power-of-two scaling) and each real product is taken as hi.hi + hi.lo +
+// lo.hi with FP32 accumulation in TMEM.
 // The operand planes (re, im, re+im; hi, lo) are written by the permutation
 // kernel (fused operand producer) in [plane][rows][K] layout.
 //
@@ -176,14 +177,16 @@ constexpr int EPI_WARPS = 8;
 template <int KIND, int BN, int NSPLIT>
 __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
     k_cgemm_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
-               int64_t M, int64_t N, int64_t K, float2* __restrict__ C, int32_t* status) {
+               int64_t M, int64_t N, int64_t K, float2* __restrict__ C, int32_t* status,
+               const unsigned* smax_a, const unsigned* smax_b) {
   using G = Cfg<BN, NSPLIT>;
   constexpr int ELEM = KIND == 0 ? 4 : 2;
+  constexpr uint32_t FMT_AB = KIND == 0 ? 2u : (KIND == 1 ? 1u : 0u);   // tf32 / bf16 / f16
   constexpr int BK = ROW_BYTES / ELEM;              // K elements per stage
   constexpr int MMA_K = 32 / ELEM;                  // 8 (tf32) or 16 (bf16): 32 bytes
   constexpr uint32_t IDESC = (1u << 4)                               // D = f32
-                             | (uint32_t(KIND == 0 ? 2 : 1) << 7)   // A = tf32 / bf16
-                             | (uint32_t(KIND == 0 ? 2 : 1) << 10)  // B = tf32 / bf16
+                             | (FMT_AB << 7)                         // A format
+                             | (FMT_AB << 10)                        // B format
                              | (uint32_t(BN >> 3) << 17)             // N
                              | (uint32_t(BM >> 4) << 24);            // M
   extern __shared__ uint8_t smem_raw[];
@@ -320,6 +323,13 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
     const int col0 = h * G::HALF;
     const uint32_t lane_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(col0);
     float2* st = staging + (warp - 2) * (32 * 16);
+    // fp16 operands were scaled by exact powers of two: undo both here
+    float unscale = 1.f;
+    if constexpr (KIND == 2) {
+      const float sa = smax_a ? fp16_scale_of(*smax_a) : 1.f;
+      const float sb = smax_b ? fp16_scale_of(*smax_b) : 1.f;
+      unscale = 1.f / (sa * sb);
+    }
     bool ok = true;
     int cg = 0;
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
@@ -369,7 +379,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
       for (int sub = 0; sub < G::HALF / 16; ++sub) {
 #pragma unroll
         for (int j = 0; j < 16; ++j)
-          st[lane * 16 + (j ^ (lane & 15))] = make_float2(re[sub * 16 + j], im[sub * 16 + j]);
+          st[lane * 16 + (j ^ (lane & 15))] = make_float2(re[sub * 16 + j] * unscale, im[sub * 16 + j] * unscale);
         __syncwarp();
         const int cj = lane & 15;
         const int64_t gn = n0 + col0 + sub * 16 + cj;
@@ -415,7 +425,9 @@ bool encode(int kind, const void* ptr, int64_t rows, int64_t K, int box_rows, CU
   cuuint64_t gstride[1] = {cuuint64_t(K) * elem};
   cuuint32_t box[2] = {cuuint32_t(ROW_BYTES / elem), cuuint32_t(box_rows)};
   cuuint32_t estride[2] = {1, 1};
-  CUresult r = fn(map, kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+  CUresult r = fn(map,
+                  kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                            : (kind == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16),
                   2, const_cast<void*>(ptr), gdim, gstride, box, estride,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -424,7 +436,7 @@ bool encode(int kind, const void* ptr, int64_t rows, int64_t K, int box_rows, CU
 
 template <int KIND, int BN, int NSPLIT>
 cudaError_t launch_t(const TcGemmMaps& maps, int64_t M, int64_t N, int64_t K, float2* C,
-                     int32_t* status, cudaStream_t s) {
+                     int32_t* status, cudaStream_t s, const unsigned* sa, const unsigned* sb) {
   using G = Cfg<BN, NSPLIT>;
   auto kern = k_cgemm_tc<KIND, BN, NSPLIT>;
   static int configured_dev = -1;
@@ -439,7 +451,7 @@ cudaError_t launch_t(const TcGemmMaps& maps, int64_t M, int64_t N, int64_t K, fl
   if (sms == 0) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
   const unsigned grid = unsigned(tiles < sms ? tiles : sms);
-  kern<<<grid, 64 + 32 * EPI_WARPS, G::SMEM, s>>>(maps.a, maps.b, M, N, K, C, status);
+  kern<<<grid, 64 + 32 * EPI_WARPS, G::SMEM, s>>>(maps.a, maps.b, M, N, K, C, status, sa, sb);
   return cudaGetLastError();
 }
 
@@ -456,12 +468,14 @@ bool tc_encode_maps(int kind, int nsplit, int bn, const void* a_planes, int64_t 
 }
 
 cudaError_t launch_cgemm_tc(int kind, int nsplit, int bn, const TcGemmMaps& maps, int64_t M,
-                            int64_t N, int64_t K, float2* C, int32_t* status, cudaStream_t s) {
+                            int64_t N, int64_t K, float2* C, int32_t* status, cudaStream_t s,
+                            const unsigned* smax_a, const unsigned* smax_b) {
   if (3 * nsplit * M > INT32_MAX || 3 * nsplit * N > INT32_MAX) return cudaErrorInvalidValue;
 #define QF_TC(KD, B, S) \
-  if (kind == KD && bn == B && nsplit == S) return launch_t<KD, B, S>(maps, M, N, K, C, status, s);
+  if (kind == KD && bn == B && nsplit == S) return launch_t<KD, B, S>(maps, M, N, K, C, status, s, smax_a, smax_b);
   QF_TC(0, 64, 1) QF_TC(0, 64, 2) QF_TC(0, 128, 1) QF_TC(0, 128, 2)
   QF_TC(1, 64, 1) QF_TC(1, 64, 2) QF_TC(1, 128, 1) QF_TC(1, 128, 2)
+  QF_TC(2, 64, 2) QF_TC(2, 128, 2)
 #undef QF_TC
   return cudaErrorInvalidValue;
 }

@@ -18,11 +18,13 @@ namespace {
 // cudaGetSymbolAddress below.
 __device__ __align__(256) unsigned char g_noalloc_scratch[QFLEX_NOALLOC_SCRATCH_BYTES];
 __device__ int32_t g_noalloc_status;
+__device__ unsigned g_noalloc_smax[2];   // fp16 operand scales
 
 constexpr int kMaxDevices = 64;
 struct DeviceScratch {
   void* scratch = nullptr;
   int32_t* status = nullptr;
+  unsigned* smax = nullptr;
 };
 DeviceScratch g_dev[kMaxDevices];
 std::mutex g_mu;
@@ -45,6 +47,10 @@ qflex_status setup(int dev, DeviceScratch* out) {
     if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
     e = cudaGetSymbolAddress(&w, g_noalloc_status);
     if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("cudaGetSymbolAddress(status): ") + cudaGetErrorString(e));
+    void* m = nullptr;
+    e = cudaGetSymbolAddress(&m, g_noalloc_smax);
+    if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("cudaGetSymbolAddress(smax): ") + cudaGetErrorString(e));
+    d.smax = static_cast<unsigned*>(m);
     e = cudaMemset(w, 0, sizeof(int32_t));
     if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("cudaMemset(status): ") + cudaGetErrorString(e));
     d.status = static_cast<int32_t*>(w);
@@ -58,9 +64,15 @@ size_t round256(size_t v) { return (v + 255) & ~size_t(255); }
 
 // Identity "permutation" of a [rows][K] complex64 matrix into operand planes.
 cudaError_t planes(const void* src, int64_t rows, int64_t K, int kind, int nsplit, void* dst,
-                   cudaStream_t s) {
+                   cudaStream_t s, unsigned* smax) {
   const int64_t total = rows * K;
-  const int fmt = kind == 0 ? kFmtTF32 : kFmtBF16;
+  const int fmt = kind == 0 ? kFmtTF32 : (kind == 1 ? kFmtBF16 : kFmtFP16);
+  if (fmt == kFmtFP16) {
+    cudaError_t e = launch_absmax(static_cast<const float2*>(src), total, smax, s);
+    if (e != cudaSuccess) return e;
+  } else {
+    smax = nullptr;
+  }
   if ((total & (total - 1)) == 0) {
     int nb = 0;
     while ((int64_t(1) << nb) < total) ++nb;
@@ -68,21 +80,21 @@ cudaError_t planes(const void* src, int64_t rows, int64_t K, int kind, int nspli
     for (int b = 0; b < nb; ++b) w[b] = int64_t(1) << b;
     PermTile t;
     if (!build_perm_tile(nb, w, &t)) return cudaErrorInvalidValue;
-    return launch_permute_tiled(static_cast<const float2*>(src), 0, t, fmt, nsplit, dst, total, s);
+    return launch_permute_tiled(static_cast<const float2*>(src), 0, t, fmt, nsplit, dst, total, s, smax);
   }
   GatherDesc g{};
   g.rank = 1;
   g.total = total;
   g.dims[0] = total;
   g.in_strides[0] = 1;
-  return launch_permute_gather(static_cast<const float2*>(src), 0, g, fmt, nsplit, dst, total, s);
+  return launch_permute_gather(static_cast<const float2*>(src), 0, g, fmt, nsplit, dst, total, s, smax);
 }
 
 }  // namespace
 
 extern "C" qflex_status qflex_cgemm_noalloc(int32_t prec, int64_t M, int64_t N, int64_t K, const void* A,
                                             const void* B, void* C, void* stream) {
-  if (prec < QFLEX_FP32_SIMT || prec > QFLEX_TF32_PLAIN) return fail(QFLEX_ERR_ARG, "unknown precision");
+  if (prec < QFLEX_FP32_SIMT || prec > QFLEX_FP16X3) return fail(QFLEX_ERR_ARG, "unknown precision");
   if (M < 0 || N < 0 || K < 0 || (M * N > 0 && (!A || !B || !C))) return fail(QFLEX_ERR_ARG, "bad GEMM arguments");
   if (M == 0 || N == 0) return QFLEX_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -103,8 +115,8 @@ extern "C" qflex_status qflex_cgemm_noalloc(int32_t prec, int64_t M, int64_t N, 
     if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
     return QFLEX_OK;
   }
-  const int kind = (prec == QFLEX_TF32X3 || prec == QFLEX_TF32_PLAIN) ? 0 : 1;
-  const int nsplit = (prec == QFLEX_TF32X3 || prec == QFLEX_BF16X3) ? 2 : 1;
+  const int kind = (prec == QFLEX_TF32X3 || prec == QFLEX_TF32_PLAIN) ? 0 : (prec == QFLEX_FP16X3 ? 2 : 1);
+  const int nsplit = (prec == QFLEX_TF32X3 || prec == QFLEX_BF16X3 || prec == QFLEX_FP16X3) ? 2 : 1;
   const size_t per = size_t(3) * nsplit * (kind == 0 ? 4 : 2);
   const size_t a_bytes = round256(per * size_t(M) * size_t(K));
   const size_t b_bytes = round256(per * size_t(N) * size_t(K));
@@ -114,12 +126,13 @@ extern "C" qflex_status qflex_cgemm_noalloc(int32_t prec, int64_t M, int64_t N, 
   if (!tc_available()) return fail(QFLEX_ERR_UNSUPPORTED, "tensor-map encoder unavailable");
   char* pa = static_cast<char*>(d.scratch);
   char* pb = pa + a_bytes;
-  if ((e = planes(A, M, K, kind, nsplit, pa, s)) != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
-  if ((e = planes(B, N, K, kind, nsplit, pb, s)) != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
+  if ((e = planes(A, M, K, kind, nsplit, pa, s, d.smax)) != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
+  if ((e = planes(B, N, K, kind, nsplit, pb, s, d.smax + 1)) != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
   TcGemmMaps maps;
   const int bn = N >= 128 ? 128 : 64;
   if (!tc_encode_maps(kind, nsplit, bn, pa, M, pb, N, K, &maps)) return fail(QFLEX_ERR_CUDA, "tensor map encoding failed");
-  e = launch_cgemm_tc(kind, nsplit, bn, maps, M, N, K, static_cast<float2*>(C), d.status, s);
+  e = launch_cgemm_tc(kind, nsplit, bn, maps, M, N, K, static_cast<float2*>(C), d.status, s,
+                      kind == 2 ? d.smax : nullptr, kind == 2 ? d.smax + 1 : nullptr);
   if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
   return QFLEX_OK;
 }

@@ -14,10 +14,11 @@
 // The same kernel can write, instead of the permuted complex64 tensor, the
 // tensor-core operand planes of the 3-multiply complex product: re, im and
 // re+im, each split into a high part and (optionally) the rounded residual
-// low part, in tf32 or bf16.
+// low part, in tf32, bf16 or power-of-two-scaled fp16.
 #include "internal.h"
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <vector>
@@ -132,7 +133,8 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
 
 // Write one complex entry at linear output position o in the requested format.
 template <int FMT>
-__device__ __forceinline__ void put(void* out, int64_t o, float2 v, int nsplit, int64_t plane) {
+__device__ __forceinline__ void put(void* out, int64_t o, float2 v, int nsplit, int64_t plane,
+                                    float scale = 1.f) {
   if constexpr (FMT == kFmtC64) {
     static_cast<float2*>(out)[o] = v;
   } else if constexpr (FMT == kFmtAccC128) {
@@ -143,7 +145,13 @@ __device__ __forceinline__ void put(void* out, int64_t o, float2 v, int nsplit, 
     const float part[3] = {v.x, v.y, v.x + v.y};
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
-      if constexpr (FMT == kFmtTF32) {
+      if constexpr (FMT == kFmtFP16) {
+        __half* q = static_cast<__half*>(out);
+        const float x = part[p] * scale;   // exact: scale is a power of two
+        const __half hi = __float2half_rn(x);
+        q[int64_t(p * nsplit) * plane + o] = hi;
+        if (nsplit == 2) q[int64_t(p * 2 + 1) * plane + o] = __float2half_rn(x - __half2float(hi));
+      } else if constexpr (FMT == kFmtTF32) {
         uint32_t* q = static_cast<uint32_t*>(out);
         const uint32_t hi = tf32_rna(part[p]);
         q[int64_t(p * nsplit) * plane + o] = hi;
@@ -162,7 +170,7 @@ __device__ __forceinline__ void put(void* out, int64_t o, float2 v, int nsplit, 
 template <int FMT>
 __global__ void __launch_bounds__(256, 6) k_permute_tiled(const float2* __restrict__ in, int64_t in_base,
                                                        const __grid_constant__ PermTile t, void* out,
-                                                       int nsplit, int64_t plane) {
+                                                       int nsplit, int64_t plane, const unsigned* smax) {
   static_assert((1 << kPermTileBits) % 256 == 0, "tile must be a multiple of the block");
   __shared__ float2 tile[1 << kPermTileBits];
   __shared__ int64_t s_in_lo[32], s_in_hi[64], s_out_lo[32], s_out_hi[64];
@@ -189,6 +197,8 @@ __global__ void __launch_bounds__(256, 6) k_permute_tiled(const float2* __restri
   // high ones are warp-uniform.
   constexpr int kPer = (1 << kPermTileBits) / 256;
   const int n = 1 << t.tile_bits;
+  float scale = 1.f;
+  if constexpr (FMT == kFmtFP16) scale = smax ? fp16_scale_of(*smax) : 1.f;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t in_lo = s_in_lo[lane], out_lo = s_out_lo[lane];
   const int ld_lo = s_ld_lo[lane], st_lo = s_st_lo[lane];
@@ -233,7 +243,7 @@ __global__ void __launch_bounds__(256, 6) k_permute_tiled(const float2* __restri
     for (int k = 0; k < kPer; ++k) {
       const int h = wid + 8 * k;
       if (h * 32 + lane < n)
-        put<FMT>(out, cur_ob + out_lo + s_out_hi[h], tile[st_lo ^ s_st_hi[h]], nsplit, plane);
+        put<FMT>(out, cur_ob + out_lo + s_out_hi[h], tile[st_lo ^ s_st_hi[h]], nsplit, plane, scale);
     }
     __syncthreads();
   }
@@ -242,7 +252,9 @@ __global__ void __launch_bounds__(256, 6) k_permute_tiled(const float2* __restri
 template <int FMT>
 __global__ void k_permute_gather(const float2* __restrict__ in, int64_t in_base,
                                  const __grid_constant__ GatherDesc d, void* out, int nsplit,
-                                 int64_t plane) {
+                                 int64_t plane, const unsigned* smax) {
+  float scale = 1.f;
+  if constexpr (FMT == kFmtFP16) scale = smax ? fp16_scale_of(*smax) : 1.f;
   for (int64_t o = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; o < d.total;
        o += int64_t(gridDim.x) * blockDim.x) {
     int64_t rem = o, off = in_base;
@@ -251,7 +263,7 @@ __global__ void k_permute_gather(const float2* __restrict__ in, int64_t in_base,
       rem /= d.dims[a];
       off += i * d.in_strides[a];
     }
-    put<FMT>(out, o, in[off], nsplit, plane);
+    put<FMT>(out, o, in[off], nsplit, plane, scale);
   }
 }
 
@@ -266,25 +278,29 @@ int grid_for(int64_t work_units) {
 }  // namespace
 
 cudaError_t launch_permute_tiled(const float2* in, int64_t in_base, const PermTile& t, int fmt,
-                                 int nsplit, void* out, int64_t plane, cudaStream_t s) {
+                                 int nsplit, void* out, int64_t plane, cudaStream_t s,
+                                 const unsigned* smax) {
   const int blocks = grid_for(t.n_tiles);
   switch (fmt) {
-    case kFmtC64: k_permute_tiled<kFmtC64><<<blocks, 256, 0, s>>>(in, in_base, t, out, nsplit, plane); break;
-    case kFmtTF32: k_permute_tiled<kFmtTF32><<<blocks, 256, 0, s>>>(in, in_base, t, out, nsplit, plane); break;
-    case kFmtAccC128: k_permute_tiled<kFmtAccC128><<<blocks, 256, 0, s>>>(in, in_base, t, out, nsplit, plane); break;
-    default: k_permute_tiled<kFmtBF16><<<blocks, 256, 0, s>>>(in, in_base, t, out, nsplit, plane); break;
+    case kFmtC64: k_permute_tiled<kFmtC64><<<blocks, 256, 0, s>>>(in, in_base, t, out, nsplit, plane, smax); break;
+    case kFmtTF32: k_permute_tiled<kFmtTF32><<<blocks, 256, 0, s>>>(in, in_base, t, out, nsplit, plane, smax); break;
+    case kFmtAccC128: k_permute_tiled<kFmtAccC128><<<blocks, 256, 0, s>>>(in, in_base, t, out, nsplit, plane, smax); break;
+    case kFmtFP16: k_permute_tiled<kFmtFP16><<<blocks, 256, 0, s>>>(in, in_base, t, out, nsplit, plane, smax); break;
+    default: k_permute_tiled<kFmtBF16><<<blocks, 256, 0, s>>>(in, in_base, t, out, nsplit, plane, smax); break;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_permute_gather(const float2* in, int64_t in_base, const GatherDesc& d, int fmt,
-                                  int nsplit, void* out, int64_t plane, cudaStream_t s) {
+                                  int nsplit, void* out, int64_t plane, cudaStream_t s,
+                                  const unsigned* smax) {
   const int blocks = grid_for((d.total + 255) / 256);
   switch (fmt) {
-    case kFmtC64: k_permute_gather<kFmtC64><<<blocks, 256, 0, s>>>(in, in_base, d, out, nsplit, plane); break;
-    case kFmtTF32: k_permute_gather<kFmtTF32><<<blocks, 256, 0, s>>>(in, in_base, d, out, nsplit, plane); break;
-    case kFmtAccC128: k_permute_gather<kFmtAccC128><<<blocks, 256, 0, s>>>(in, in_base, d, out, nsplit, plane); break;
-    default: k_permute_gather<kFmtBF16><<<blocks, 256, 0, s>>>(in, in_base, d, out, nsplit, plane); break;
+    case kFmtC64: k_permute_gather<kFmtC64><<<blocks, 256, 0, s>>>(in, in_base, d, out, nsplit, plane, smax); break;
+    case kFmtTF32: k_permute_gather<kFmtTF32><<<blocks, 256, 0, s>>>(in, in_base, d, out, nsplit, plane, smax); break;
+    case kFmtAccC128: k_permute_gather<kFmtAccC128><<<blocks, 256, 0, s>>>(in, in_base, d, out, nsplit, plane, smax); break;
+    case kFmtFP16: k_permute_gather<kFmtFP16><<<blocks, 256, 0, s>>>(in, in_base, d, out, nsplit, plane, smax); break;
+    default: k_permute_gather<kFmtBF16><<<blocks, 256, 0, s>>>(in, in_base, d, out, nsplit, plane, smax); break;
   }
   return cudaGetLastError();
 }

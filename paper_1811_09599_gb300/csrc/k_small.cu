@@ -93,7 +93,31 @@ __global__ void k_frugal(const double* __restrict__ amps, int64_t n_batches, int
   accepted[b] = res;
 }
 
+// Largest |re|, |im|, |re + im| of a complex64 array (the three parts of the
+// 3M product), as float bits, for the power-of-two scale of fp16 operands.
+__global__ void k_absmax(const float2* __restrict__ in, int64_t n, unsigned* __restrict__ out) {
+  float m = 0.f;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const float2 v = in[i];
+    m = fmaxf(m, fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.x + v.y))));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, __float_as_uint(m));
+}
+
 }  // namespace
+
+cudaError_t launch_absmax(const float2* in, int64_t n, unsigned* smax, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(smax, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess || n <= 0) return e;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (n + 255) / 256;
+  const int blocks = int(want < int64_t(sms) * 4 ? want : int64_t(sms) * 4);
+  k_absmax<<<blocks, 256, 0, s>>>(in, n, smax);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_frugal(const double* amps, int64_t n_batches, int n_c, double scale, uint64_t seed,
                           int32_t* accepted, cudaStream_t s) {

@@ -2,9 +2,9 @@
 import numpy as np
 
 # Tolerances on the amplitude error metric below.
-# fp32 (24-bit products) is gated at 1e-5; the 3-term split forms (tf32x3: ~22
-# bits, bf16x3: ~16 bits) at 1e-4.
-TOL = {"fp32": 1e-5, "tf32x3": 1e-4, "bf16x3": 1e-4}
+# fp32 (24-bit products) is gated at 1e-5; the 3-term split forms (tf32x3 and
+# scaled fp16x3: ~22 bits, bf16x3: ~16 bits) at 1e-4.
+TOL = {"fp32": 1e-5, "tf32x3": 1e-4, "bf16x3": 1e-4, "fp16x3": 1e-4}
 
 
 def amp_error(got, ref, n_qubits, f_eff=1.0):

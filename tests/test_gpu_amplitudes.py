@@ -16,7 +16,7 @@ from tests.gpu_util import TOL, amp_error
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-PRECS = ["fp32", "tf32x3", "bf16x3"]
+PRECS = ["fp32", "tf32x3", "bf16x3", "fp16x3"]
 
 
 @pytest.fixture(scope="module")
@@ -123,7 +123,7 @@ def _c2_reference(prob, bits, s):
     return _C2_REF[s]
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "fp32"])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "fp32", "fp16x3"])
 def test_c2_full_size_sampled_slices(api, prec):
     """7x7, 1+32+1, two cuts (256 slices), 6-qubit tile: two sampled slices of
     one bitstring vs the oracle's slice contraction (full-size launch shapes:

@@ -56,7 +56,7 @@ def test_diamond30_fraction_vs_oracle(api):
 # and amplifies operand rounding more: bf16x3 measured 1.3e-4 against the
 # FP64 oracle here (6.5e-5 on the 7x7 grid), above the 1e-4 split-BF16 bound,
 # so it is gated at 2e-4 on this network; fp32 and tf32x3 keep their bounds.
-BRIS70_TOL = {"fp32": TOL["fp32"], "tf32x3": TOL["tf32x3"], "bf16x3": 2e-4}
+BRIS70_TOL = {"fp32": TOL["fp32"], "tf32x3": TOL["tf32x3"], "bf16x3": 2e-4, "fp16x3": TOL["fp16x3"]}
 
 
 def test_bris70_full_size_path(api):
@@ -65,7 +65,7 @@ def test_bris70_full_size_path(api):
     s = 12345
     ref = NW.slice_amplitudes(prob, bs[0], s)
     errs = {}
-    for prec in ("bf16x3", "tf32x3", "fp32"):
+    for prec in ("bf16x3", "tf32x3", "fp32", "fp16x3"):
         plan = api.Plan(prob, prec, device=0)
         got = plan.amplitudes(torch.from_numpy(bs).cuda(), None, [s])
         errs[prec] = amp_error(got.cpu().numpy(), ref, prob.n, 1.0 / 65536)

@@ -17,7 +17,7 @@ from qflex_inputs import grid_problem, random_bitstrings
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-GTOL = {"fp32": 2e-5, "tf32x3": 2e-4, "bf16x3": 2e-4}
+GTOL = {"fp32": 2e-5, "tf32x3": 2e-4, "bf16x3": 2e-4, "fp16x3": 2e-4}
 
 
 @pytest.fixture(scope="module")
@@ -48,7 +48,7 @@ def _gpu_grad(api, prob, prec, bs, g, slices=None):
     return amps.cpu().numpy(), grad.cpu().numpy(), plan
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x3", "fp16x3"])
 def test_grad_vs_statevector_adjoint(api, prec):
     """3x4, 1+20+1 rotations, two cuts (all slices), 2-qubit tile, 2 bitstrings."""
     prob = grid_problem(3, 4, 20, 8, r0=2, c0=2, cuts=True, tile_rows=1, tile_cols=2, rotations=True)

@@ -86,7 +86,7 @@ def test_cgemm_fp32(K, prec, tol):
         assert _gemm_case(K, prec, M, N, Kd, i) < tol, (M, N, Kd)
 
 
-@pytest.mark.parametrize("prec,tol", [("tf32x3", 1e-5), ("bf16x3", 1e-4)])
+@pytest.mark.parametrize("prec,tol", [("tf32x3", 1e-5), ("bf16x3", 1e-4), ("fp16x3", 1e-5)])
 def test_cgemm_tensor_core(K, prec, tol):
     for i, (M, N, Kd) in enumerate(SHAPES):
         err = _gemm_case(K, prec, M, N, Kd, 10 + i)
@@ -99,8 +99,8 @@ def test_cgemm_long_k_accuracy(K, Kd):
     """Long contractions (K up to 2^15, the 7x7 1+40+1 shape) keep the split
     tensor-core forms within their tolerances: chunked FP32 promotion of the
     TMEM accumulators bounds the accumulation drift."""
-    tol = {"fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 1e-4}
-    for prec in ("fp32", "tf32x3", "bf16x3"):
+    tol = {"fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 1e-4, "fp16x3": 1e-5}
+    for prec in ("fp32", "tf32x3", "bf16x3", "fp16x3"):
         err = _gemm_case(K, prec, 256, 256, Kd, 7)
         assert err < tol[prec], (prec, Kd, err)
 
@@ -111,3 +111,16 @@ def test_cgemm_plain_precisions_reported(K):
     for prec in ("bf16", "tf32"):
         err = _gemm_case(K, prec, 512, 256, 256, 99)
         assert err < 5e-2, (prec, err)
+
+
+@pytest.mark.parametrize("mag", [1e-20, 1e-9, 1e+20])
+def test_cgemm_fp16_power_of_two_scaling(K, mag):
+    """fp16 has 5 exponent bits: without the per-operand power-of-two scale,
+    entries of 1e-9 (the size of 49-qubit amplitudes) or 1e-20 would flush to
+    zero and 1e+20 would overflow.  With it the split form keeps its ~22-bit
+    accuracy at any magnitude."""
+    a = _rand_c64((512, 256), 31) * np.float32(mag)
+    b = _rand_c64((256, 256), 32)
+    got = K.cgemm(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), "fp16x3").cpu().numpy()
+    ref = a.astype(np.complex128) @ b.astype(np.complex128).T
+    assert np.all(np.isfinite(got)) and gemm_error(got, ref) < 1e-5

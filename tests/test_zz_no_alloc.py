@@ -19,7 +19,7 @@ from tests.gpu_util import gemm_error
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 1e-4}
+TOL = {"fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 1e-4, "fp16x3": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -41,7 +41,7 @@ def _noalloc(api, prec, a, b):
     return out
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "fp32"])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "fp32", "fp16x3"])
 def test_noalloc_matches_workspace_entry_point(api, prec):
     rng = np.random.default_rng(5)
     shapes = [(1024, 256, 512), (640, 96, 200)]       # second call: other shape, other data
