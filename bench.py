@@ -319,6 +319,7 @@ def run_ours(args):
     prob = c2_problem(0)
     bits = random_bitstrings(prob.n, N_BS, 1000 + rank)
     plan = api.Plan(prob, args.precision, device=local)
+    tune = plan.autotune(3)
     P = plan.n_slices
     tile = len(prob.open_tile)
     n_amps = N_BS * (1 << tile)
@@ -403,6 +404,7 @@ def run_ours(args):
                        "l2": "working set > L2 (1.2 GB workspace streamed per step)",
                        "circuit_seed": 0, "bitstring_seed": f"1000+rank"},
             "tflops_cgemm": round(cost["cmacs"] * 8 / (ms * 1e-3) / 1e12, 2),
+            "autotune": tune,
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(bits.nbytes),
                     "d2h_bytes_per_step": int(N_BS * (1 << tile) * 16)},

@@ -191,6 +191,16 @@ qflex_status qflex_amplitudes_grad(qflex_plan plan, const double* angles,
                                    const double* grad_amps, double* amps_out,
                                    double* grad_angles, void* stream);
 
+/* Tile-shape autotuner: for every distinct contraction shape of the plan,
+ * time the candidate kernel configurations on the plan's own workspace
+ * (`reps` launches each, CUDA events, on a private stream) and keep the
+ * fastest for all steps of that shape: tensor-core tile width BN in {128, 64},
+ * and for narrow FP32 shapes (N <= 32) the row-per-thread thin kernel or the
+ * tiled one.  Synchronous; call after qflex_plan_create and before any
+ * capture.  n_shapes / gain_ms (may be NULL): shapes tuned and the estimated
+ * time saved per pass over all steps against the default choice. */
+qflex_status qflex_plan_autotune(qflex_plan plan, int32_t reps, int32_t* n_shapes, double* gain_ms);
+
 /* CUDA-graph launch mode (enable != 0): a qflex_amplitudes / _grad call whose
  * arguments (pointers, n_bs, slice list) repeat those of the previous call is
  * captured into a CUDA graph on its second occurrence and replayed from then

@@ -84,6 +84,8 @@ SIGNATURES = [
     ("qflex_plan_sync", C.c_int, [C.c_void_p]),
     ("qflex_plan_enable_gradients", C.c_int, [C.c_void_p]),
     ("qflex_plan_use_graphs", C.c_int, [C.c_void_p, C.c_int32]),
+    ("qflex_plan_autotune", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32),
+                                      C.POINTER(C.c_double)]),
     ("qflex_plan_profile", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Profile)]),
     ("qflex_permute", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int64),
                                 C.POINTER(C.c_int32), C.c_void_p]),

@@ -115,6 +115,13 @@ class Plan:
                                         C.c_void_p(out.data_ptr()), _stream_handle(stream)))
         return torch.view_as_complex(out.view(n_bs, T, 2))
 
+    def autotune(self, reps: int = 3) -> dict:
+        """qflex_plan_autotune: pick the fastest kernel configuration per shape."""
+        n = C.c_int32()
+        g = C.c_double()
+        check(self.lib.qflex_plan_autotune(self.handle, reps, C.byref(n), C.byref(g)))
+        return {"shapes": n.value, "gain_ms": g.value}
+
     def use_graphs(self, enable: bool = True):
         """qflex_plan_use_graphs: replay repeated calls from a captured CUDA graph."""
         check(self.lib.qflex_plan_use_graphs(self.handle, int(enable)))

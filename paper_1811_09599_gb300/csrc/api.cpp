@@ -23,6 +23,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <tuple>
 #include <memory>
 #include <numeric>
 #include <string>
@@ -88,6 +90,7 @@ struct Step {
   int64_t M = 1, N = 1, K = 1;
   bool tc = false;
   int bn = 128;
+  int fp32_kernel = 0;   // CUDA-core form: 0 = by shape, 1 = thin, 2 = tiled
   int out_buf = -1;
   uint64_t dep = 0;
   std::vector<int> out_legs;
@@ -668,8 +671,9 @@ cudaError_t run_step(qflex_plan_s& p, const Step& st, const std::vector<int64_t>
       return launch_cgemm_tc(p.tc_kind, p.nsplit, st.bn, st.maps, st.M, st.N, st.K, C, p.d_status, s,
                              p.tc_kind == 2 ? p.d_smax : nullptr, p.tc_kind == 2 ? p.d_smax + 1 : nullptr);
     });
+  const bool thin = st.fp32_kernel == 1 || (st.fp32_kernel == 0 && st.N <= 32);
   return timed(p, 2, 8.0 * mnk, 0, gbytes, s, [&] {
-    return st.N <= 32 ? launch_cgemm_thin(st.M, st.N, st.K, A, B, C, s) : launch_cgemm_simt(st.M, st.N, st.K, A, B, C, s);
+    return thin ? launch_cgemm_thin(st.M, st.N, st.K, A, B, C, s) : launch_cgemm_simt(st.M, st.N, st.K, A, B, C, s);
   });
 }
 
@@ -1167,6 +1171,107 @@ qflex_status qflex_amplitudes_grad(qflex_plan p, const double* angles, const uin
   });
   p->grad_active = false;
   return res;
+}
+
+qflex_status qflex_plan_autotune(qflex_plan p, int32_t reps, int32_t* n_shapes, double* gain_ms) {
+  if (!p) return fail(QFLEX_ERR_ARG, "null plan");
+  if (p->device < 0) return fail(QFLEX_ERR_UNSUPPORTED, "host-only plan");
+  if (reps < 1 || reps > 100) return fail(QFLEX_ERR_ARG, "reps must be in [1, 100]");
+  QF_CUDA(cudaSetDevice(p->device));
+  cudaStream_t s = nullptr;
+  QF_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  cudaEvent_t e0, e1;
+  QF_CUDA(cudaEventCreate(&e0));
+  QF_CUDA(cudaEventCreate(&e1));
+  struct Key {
+    int64_t M, N, K;
+    bool tc;
+    bool operator<(const Key& o) const {
+      return std::tie(M, N, K, tc) < std::tie(o.M, o.N, o.K, o.tc);
+    }
+  };
+  std::map<Key, std::vector<size_t>> groups;
+  for (size_t i = 0; i < p->steps.size(); ++i) {
+    const Step& st = p->steps[i];
+    groups[{st.M, st.N, st.K, st.tc}].push_back(i);
+  }
+  int tuned = 0;
+  double gain = 0.0;
+  qflex_status res = QFLEX_OK;
+  for (auto& [key, idx] : groups) {
+    Step& st = p->steps[idx.front()];
+    float2* C = reinterpret_cast<float2*>(p->d_arena + p->bufs[st.out_buf].offset);
+    std::vector<int> cands;
+    if (key.tc) cands = {128, 64};
+    else if (key.N <= 32) cands = {1, 2};
+    else continue;
+    std::vector<TcGemmMaps> maps(cands.size());
+    float best = 1e30f, first = 0.f;
+    int best_c = -1;
+    for (size_t c = 0; c < cands.size(); ++c) {
+      if (key.tc && !tc_encode_maps(p->tc_kind, p->nsplit, cands[c], p->d_opA, st.M, p->d_opB, st.N, st.K, &maps[c])) {
+        res = fail(QFLEX_ERR_CUDA, "tensor map encoding failed");
+        break;
+      }
+      auto launch = [&]() -> cudaError_t {
+        if (key.tc)
+          return launch_cgemm_tc(p->tc_kind, p->nsplit, cands[c], maps[c], st.M, st.N, st.K, C, p->d_status, s,
+                                 p->tc_kind == 2 ? p->d_smax : nullptr, p->tc_kind == 2 ? p->d_smax + 1 : nullptr);
+        // operands as the step reads them: in place when consumed directly
+        // (the scratch is only sized for produced operands), else the scratch
+        const float2* A = st.A.direct ? ref_ptr(*p, st.A.ref) : static_cast<const float2*>(p->d_opA);
+        const float2* B = st.B.direct ? ref_ptr(*p, st.B.ref) : static_cast<const float2*>(p->d_opB);
+        return cands[c] == 1 ? launch_cgemm_thin(st.M, st.N, st.K, A, B, C, s)
+                             : launch_cgemm_simt(st.M, st.N, st.K, A, B, C, s);
+      };
+      cudaError_t e = launch();   // warm-up
+      for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+        if (r == 0) e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = launch();
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        res = fail(QFLEX_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+        break;
+      }
+      ms /= float(reps);
+      if (c == 0) first = ms;
+      if (ms < best) {
+        best = ms;
+        best_c = int(c);
+      }
+    }
+    if (res != QFLEX_OK) break;
+    for (size_t i : idx) {
+      Step& t = p->steps[i];
+      if (key.tc) {
+        t.bn = cands[best_c];
+        t.maps = maps[best_c];
+      } else {
+        t.fp32_kernel = cands[best_c];
+      }
+    }
+    ++tuned;
+    gain += double(first - best) * double(idx.size());
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  if (res != QFLEX_OK) return res;
+  int32_t w = 0;
+  QF_CUDA(cudaMemcpy(&w, p->d_status, sizeof(w), cudaMemcpyDeviceToHost));
+  if (w) return fail(QFLEX_ERR_DEVICE_TIMEOUT, "a bounded device-side wait ran out during autotuning");
+  if (p->gexec) {   // cached graph holds the old configuration
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+    p->gseen = qflex_plan_s::GraphKey{};
+  }
+  if (n_shapes) *n_shapes = tuned;
+  if (gain_ms) *gain_ms = gain;
+  return QFLEX_OK;
 }
 
 qflex_status qflex_plan_use_graphs(qflex_plan p, int32_t enable) {

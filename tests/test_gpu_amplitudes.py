@@ -182,3 +182,28 @@ def test_cuda_graph_replay(api):
     ref2 = direct.amplitudes(torch.from_numpy(bs2).cuda()).cpu().numpy()
     assert np.max(np.abs(got2 - ref2)) <= 1e-12 * np.max(np.abs(ref2)) + 1e-30
     plan.sync()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
+def test_autotune_keeps_results(api, prec):
+    """qflex_plan_autotune only changes kernel configurations (tile width of
+    the tensor-core GEMM, thin or tiled FP32 kernel for narrow steps).  The
+    FP32 kernels sum in different orders, so the tuned path is not bitwise
+    equal to the untuned one: a one-ulp change of an FP32 operand re-draws
+    the low bits a bf16 hi/lo split drops, so the split error is re-drawn
+    too.  Both runs must stay within the precision's tolerance of the oracle,
+    and repeated tuned runs must be bitwise reproducible."""
+    prob = c2_problem(0)
+    bits = random_bitstrings(prob.n, 1, 1234)
+    bs = torch.from_numpy(bits).cuda()
+    plan = api.Plan(prob, prec, device=0)
+    before = plan.amplitudes(bs, None, [5]).cpu().numpy()
+    info = plan.autotune(2)
+    assert info["shapes"] > 0 and info["gain_ms"] >= 0.0
+    after = plan.amplitudes(bs, None, [5]).cpu().numpy()
+    again = plan.amplitudes(bs, None, [5]).cpu().numpy()
+    ref = _c2_reference(prob, bits[0], 5)
+    assert amp_error(before, ref, prob.n, 1.0 / 256) < TOL[prec]
+    assert amp_error(after, ref, prob.n, 1.0 / 256) < TOL[prec]
+    assert np.array_equal(after, again)
+    plan.sync()
