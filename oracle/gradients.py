@@ -18,7 +18,7 @@ from typing import Callable, Optional, Sequence
 import numpy as np
 
 from . import gates as G
-from .statevector import _apply_1q, _cz
+from .statevector import _apply_1q, _apply_2q, _cz
 
 
 def shift_rule(amp_fn: Callable[[np.ndarray], np.ndarray], angles: np.ndarray,
@@ -67,6 +67,8 @@ def statevector_adjoint(circ, bitstrings: np.ndarray, tile: Sequence[int],
     for g in seq:
         if g.kind == "CZ":
             psi = _cz(psi, g.q0, g.q1)
+        elif g.kind == "ISWAP":
+            psi = _apply_2q(psi, G.ISWAP, min(g.q0, g.q1), max(g.q0, g.q1))
         else:
             psi = _apply_1q(psi, G.single_qubit_matrix(g.kind, angles, g.param), g.q0)
     chi = np.zeros_like(psi)
@@ -84,6 +86,11 @@ def statevector_adjoint(circ, bitstrings: np.ndarray, tile: Sequence[int],
         if g.kind == "CZ":
             psi = _cz(psi, g.q0, g.q1)          # CZ is its own inverse
             chi = _cz(chi, g.q0, g.q1)
+            continue
+        if g.kind == "ISWAP":                   # step back with U^dagger
+            a, b = min(g.q0, g.q1), max(g.q0, g.q1)
+            psi = _apply_2q(psi, G.ISWAP.conj().T, a, b)
+            chi = _apply_2q(chi, G.ISWAP.conj().T, a, b)
             continue
         U = G.single_qubit_matrix(g.kind, angles, g.param)
         psi = _apply_1q(psi, U.conj().T, g.q0)  # phi_{k-1}

@@ -7,9 +7,11 @@ Follows the paper's construction step by step, in plain NumPy:
   into one tensor T_q[o, e_1, ..., e_d].  One-qubit gates are rank-2 tensors;
   each CZ contributes one binary bond index through its rank-2 Schmidt split
   (-1)^{ab} = sum_k d_{a,k} (-1)^{k b} (lower-index qubit: |k><k|, the other:
-  Z^k).  The bits of one edge, in time order with the first most
-  significant, form that edge's bond of dimension 2^{K_e}; bonds are ordered
-  by neighbour id; o is the output leg (input |0>).
+  Z^k); each iSWAP contributes two bits through its rank-4 split
+  iSWAP = sum_k A_k (x) B_k (gates.iswap_half).  The bits of one edge, in
+  time order with the first most significant, form that edge's bond of
+  dimension 2^{K_e}; bonds are ordered by neighbour id; o is the output leg
+  (input |0>).
 * Cuts (Methods, "Cutting indexes"): fixing the value of every cut bond gives
   a "path"; the amplitude is the sum over all paths.  Slice id s is decoded in
   mixed radix 2^{K_e} over the cut list, first cut most significant.
@@ -29,12 +31,15 @@ import numpy as np
 from . import gates as G
 
 
+_GATE_BITS = {"CZ": 1, "ISWAP": 2}
+
+
 def bond_exponents(circ) -> np.ndarray:
-    """K_e: number of CZs on each edge (bond dimension 2^{K_e})."""
+    """K_e: bond bits of each edge, 1 per CZ and 2 per iSWAP (bond dimension 2^{K_e})."""
     K = np.zeros(len(circ.edges), dtype=np.int64)
     for g in circ.gates:
-        if g.kind == "CZ":
-            K[circ.lattice.edge_index[(min(g.q0, g.q1), max(g.q0, g.q1))]] += 1
+        if g.kind in _GATE_BITS:
+            K[circ.lattice.edge_index[(min(g.q0, g.q1), max(g.q0, g.q1))]] += _GATE_BITS[g.kind]
     return K
 
 
@@ -54,6 +59,13 @@ def grid_tensor(circ, q: int, angles: Optional[np.ndarray] = None
             shp = (2,) + (1,) * (t.ndim - 1)
             t = np.stack([d0.reshape(shp) * t, d1.reshape(shp) * t], axis=-1)
             bit_edges.append(lat.edge_index[(min(q, other), max(q, other))])
+        elif g.kind == "ISWAP":
+            other = g.q1 if g.q0 == q else g.q0
+            role = "a" if q < other else "b"
+            terms = [np.tensordot(G.iswap_half(role, k), t, axes=([1], [0])) for k in range(4)]
+            t = np.stack(terms, axis=-1).reshape(t.shape + (2, 2))   # k = 2 hi + lo, hi first
+            e = lat.edge_index[(min(q, other), max(q, other))]
+            bit_edges.extend([e, e])
         else:
             U = G.single_qubit_matrix(g.kind, angles, g.param)
             t = np.tensordot(U, t, axes=([1], [0]))

@@ -13,6 +13,8 @@ its multi-index to a value v; under the CZ split reading (lower-index qubit
 carries |k><k|, the other Z^k; bond multi-index sum_m k_m 2^{K_e-1-m} with the
 edge's CZs in time order, first most significant), the slice equals the same
 circuit with every CZ on e replaced by the non-unitary |k_m><k_m| (x) Z^{k_m}.
+An iSWAP takes 2 bits k of the bond value (high bit first) and is replaced by
+A_k (x) B_k of its Pauli split (gates.iswap_half).
 """
 from __future__ import annotations
 
@@ -37,6 +39,17 @@ def _apply_diag2(psi: np.ndarray, da: np.ndarray, a: int, db: np.ndarray, b: int
     return psi * db.reshape(shape)
 
 
+def _apply_2q(psi: np.ndarray, U: np.ndarray, a: int, b: int) -> np.ndarray:
+    """Apply a 4x4 matrix on qubits (a, b), a the first (most significant) factor."""
+    out = np.tensordot(U.reshape(2, 2, 2, 2), psi, axes=([2, 3], [a, b]))
+    return np.moveaxis(out, (0, 1), (a, b))
+
+
+def gate_bits(kind: str) -> int:
+    """Bond bits one two-qubit gate adds to its edge (Schmidt rank 2 or 4)."""
+    return {"CZ": 1, "ISWAP": 2}.get(kind, 0)
+
+
 def _cz(psi: np.ndarray, a: int, b: int) -> np.ndarray:
     psi = psi.copy()
     idx = [slice(None)] * psi.ndim
@@ -54,24 +67,30 @@ def final_state(circ, angles: Optional[np.ndarray] = None,
     cut_values = cut_values or {}
     K = {}
     for g in circ.gates:
-        if g.kind == "CZ":
+        if gate_bits(g.kind):
             e = circ.lattice.edge_index[(min(g.q0, g.q1), max(g.q0, g.q1))]
-            K[e] = K.get(e, 0) + 1
+            K[e] = K.get(e, 0) + gate_bits(g.kind)
     seen: Dict[int, int] = {}
     psi = np.zeros((2,) * n, dtype=np.complex128)
     psi[(0,) * n] = 1.0
     for g in sorted(circ.gates, key=lambda g: g.cycle):
-        if g.kind == "CZ":
+        w = gate_bits(g.kind)
+        if w:
             a, b = min(g.q0, g.q1), max(g.q0, g.q1)
             e = circ.lattice.edge_index[(a, b)]
+            used = seen.get(e, 0)
             if e in cut_values:
-                m = seen.get(e, 0)
-                k = (cut_values[e] >> (K[e] - 1 - m)) & 1
-                psi = _apply_diag2(psi, np.diag(G.cz_half("proj", k)), a,
-                                   np.diag(G.cz_half("z", k)), b)
-            else:
+                k = (cut_values[e] >> (K[e] - used - w)) & ((1 << w) - 1)
+                if g.kind == "CZ":
+                    psi = _apply_diag2(psi, np.diag(G.cz_half("proj", k)), a,
+                                       np.diag(G.cz_half("z", k)), b)
+                else:
+                    psi = _apply_1q(_apply_1q(psi, G.iswap_half("a", k), a), G.iswap_half("b", k), b)
+            elif g.kind == "CZ":
                 psi = _cz(psi, a, b)
-            seen[e] = seen.get(e, 0) + 1
+            else:
+                psi = _apply_2q(psi, G.ISWAP, a, b)
+            seen[e] = used + w
         else:
             psi = _apply_1q(psi, G.single_qubit_matrix(g.kind, angles, g.param), g.q0)
     return psi

@@ -26,6 +26,12 @@ horizontal or vertical layers):
 
 The rotation variant replaces every non-CZ gate (including the H and T slots)
 by R_P(theta), P uniform in {X, Y, Z}, theta uniform in [0, 2 pi).
+
+The iSWAP variant (Methods, "Revised set of RQCs": replacing the CZs by
+iSWAPs makes the circuits harder) places an ISWAP wherever the CZ variant
+places a CZ, with the same layer patterns and the same single-qubit rules
+(rule (3) keyed on "a two-qubit gate in the previous cycle"); for the same
+seed the two variants share every placement draw.
 """
 from __future__ import annotations
 
@@ -35,7 +41,8 @@ from typing import List, Optional, Sequence, Tuple
 import numpy as np
 
 # Gate kind names; the integer codes are the C-ABI's gate kinds.
-KINDS = ("H", "T", "SX", "SY", "CZ", "RX", "RY", "RZ")
+KINDS = ("H", "T", "SX", "SY", "CZ", "RX", "RY", "RZ", "ISWAP")
+TWO_QUBIT = ("CZ", "ISWAP")
 KIND_ID = {k: i for i, k in enumerate(KINDS)}
 
 _LAYER_ORDER = (("H", 0, 0), ("V", 0, 0), ("H", 1, 1), ("V", 1, 1),
@@ -167,12 +174,16 @@ class Circuit:
                        np.asarray(angles, dtype=np.float64).copy(), self.seed)
 
 
-def random_circuit(lat: Lattice, t: int, seed: int, rotations: bool = False) -> Circuit:
+def random_circuit(lat: Lattice, t: int, seed: int, rotations: bool = False,
+                   two_qubit: str = "CZ") -> Circuit:
     """Seeded RQC of depth 1+t+1 on `lat` (rules (1)-(5) above).
 
     Layout draws and rotation draws come from separate streams, so the
     rotation variant keeps the gate placement of the plain circuit.
+    `two_qubit` is "CZ" or "ISWAP" (the gate placed on every active edge).
     """
+    if two_qubit not in TWO_QUBIT:
+        raise ValueError(f"two_qubit must be one of {TWO_QUBIT}")
     rng = np.random.default_rng([seed, 0x51F1])
     rrng = np.random.default_rng([seed, 0x52A7])
     n = lat.n
@@ -187,10 +198,10 @@ def random_circuit(lat: Lattice, t: int, seed: int, rotations: bool = False) -> 
         cur: List[Optional[str]] = [None] * n
         for q in range(n):
             if q in busy:
-                cur[q] = "CZ"
+                cur[q] = two_qubit
                 continue
             g = None
-            if prev[q] == "CZ":
+            if prev[q] == two_qubit:
                 g = "SX" if int(rng.integers(2)) == 0 else "SY"
             elif prev[q] in ("SX", "SY", "H"):
                 g = "T"
@@ -198,13 +209,13 @@ def random_circuit(lat: Lattice, t: int, seed: int, rotations: bool = False) -> 
                 gates.append(Gate(k, g, q))
                 cur[q] = g
         for (p, q) in active:
-            gates.append(Gate(k, "CZ", p, q))
+            gates.append(Gate(k, two_qubit, p, q))
         prev = cur
     gates.extend(Gate(t + 1, "H", q) for q in range(n))
     angles: List[float] = []
     if rotations:
         for g in gates:
-            if g.kind != "CZ":
+            if g.kind not in TWO_QUBIT:
                 g.kind = ("RX", "RY", "RZ")[int(rrng.integers(3))]
                 g.param = len(angles)
                 angles.append(float(rrng.uniform(0.0, 2.0 * np.pi)))
@@ -215,6 +226,16 @@ def random_bitstrings(n_qubits: int, count: int, seed: int) -> np.ndarray:
     """uint8 [count, n_qubits] uniform random output bits (index = qubit id)."""
     rng = np.random.default_rng([seed, 0xB175])
     return rng.integers(0, 2, size=(count, n_qubits), dtype=np.uint8)
+
+
+def two_qubit_counts(circ: Circuit) -> np.ndarray:
+    """Number of two-qubit gates (CZ or ISWAP) on each lattice edge."""
+    cnt = np.zeros(len(circ.edges), dtype=np.int64)
+    idx = circ.lattice.edge_index
+    for g in circ.gates:
+        if g.kind in TWO_QUBIT:
+            cnt[idx[(min(g.q0, g.q1), max(g.q0, g.q1))]] += 1
+    return cnt
 
 
 def cz_counts(circ: Circuit) -> np.ndarray:

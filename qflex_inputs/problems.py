@@ -79,7 +79,8 @@ def grid_region_cuts(lat: Lattice, rows: int, cols: int, r0: int, c0: int) -> Li
 
 def grid_problem(rows: int, cols: int, t: int, seed: int, *, r0: Optional[int] = None,
                  c0: Optional[int] = None, cuts: bool = True, tile_rows: int = 2,
-                 tile_cols: Optional[int] = None, rotations: bool = False) -> Problem:
+                 tile_cols: Optional[int] = None, rotations: bool = False,
+                 two_qubit: str = "CZ") -> Problem:
     """Rectangular-grid problem with the region ordering and an open tile.
 
     The tile is the last `tile_rows` rows x first `tile_cols` columns (inside
@@ -89,13 +90,13 @@ def grid_problem(rows: int, cols: int, t: int, seed: int, *, r0: Optional[int] =
     r0 = rows // 2 if r0 is None else r0
     c0 = cols // 2 if c0 is None else c0
     tile_cols = c0 if tile_cols is None else tile_cols
-    circ = random_circuit(lat, t, seed, rotations=rotations)
+    circ = random_circuit(lat, t, seed, rotations=rotations, two_qubit=two_qubit)
     tile = [lat.qid(r, c) for r in range(rows - tile_rows, rows) for c in range(tile_cols)]
     return Problem(circ,
                    cut_edges=grid_region_cuts(lat, rows, cols, r0, c0) if cuts else [],
                    open_tile=tile,
                    ordering=grid_region_ordering(lat, rows, cols, r0, c0),
-                   name=f"grid{rows}x{cols}_t{t}_s{seed}")
+                   name=f"grid{rows}x{cols}_t{t}_s{seed}" + ("_iswap" if two_qubit == "ISWAP" else ""))
 
 
 def row_major_ordering(lat: Lattice) -> List[Tuple[int, int]]:
@@ -117,10 +118,15 @@ def c1_problem(seed: int = 0, full_tile: bool = False) -> Problem:
                    name=f"c1_4x4_t16_s{seed}")
 
 
-def c2_problem(seed: int = 0, t: int = 32) -> Problem:
-    """7x7 grid, depth 1+t+1, 2 cuts, 6-qubit open tile (rows 5-6, cols 0-2)."""
-    p = grid_problem(7, 7, t, seed, r0=3, c0=3, cuts=True, tile_rows=2, tile_cols=3)
-    p.name = f"grid7x7_t{t}_s{seed}"
+def c2_problem(seed: int = 0, t: int = 32, two_qubit: str = "CZ") -> Problem:
+    """7x7 grid, depth 1+t+1, 2 cuts, 6-qubit open tile (rows 5-6, cols 0-2).
+
+    With two_qubit="ISWAP" every bond carries 2 bits per gate, so depth
+    1+t/2+1 with iSWAPs has the bond dimensions of depth 1+t+1 with CZs
+    (Methods, "Overview of the simulator": Schmidt rank 4 vs 2)."""
+    p = grid_problem(7, 7, t, seed, r0=3, c0=3, cuts=True, tile_rows=2, tile_cols=3,
+                     two_qubit=two_qubit)
+    p.name = f"grid7x7_t{t}_s{seed}" + ("_iswap" if two_qubit == "ISWAP" else "")
     return p
 
 

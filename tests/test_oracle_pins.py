@@ -45,6 +45,33 @@ def test_cz_schmidt_split_sums_to_cz():
 
 
 # ---------------------------------------------------------------- state vector
+def _iswap_ketbra():
+    """|00><00| + |11><11| + i|01><10| + i|10><01| (Methods, "Revised set of RQCs")."""
+    ket = {b: np.eye(4)[int(b, 2)].reshape(4, 1) for b in ("00", "01", "10", "11")}
+    return (ket["00"] @ ket["00"].T + ket["11"] @ ket["11"].T
+            + 1j * ket["01"] @ ket["10"].T + 1j * ket["10"] @ ket["01"].T)
+
+
+def test_iswap_split_sums_to_definition():
+    ref = _iswap_ketbra()
+    assert np.allclose(G.ISWAP, ref)
+    acc = sum(np.kron(G.iswap_half("a", k), G.iswap_half("b", k)) for k in range(4))
+    assert np.allclose(acc, ref, atol=1e-15)
+    assert np.allclose(ref @ ref.conj().T, np.eye(4))
+
+
+def _operator_schmidt_rank(U4):
+    # U[(a b), (a' b')] -> M[(a a'), (b b')]; its rank is the operator-Schmidt rank
+    M = U4.reshape(2, 2, 2, 2).transpose(0, 2, 1, 3).reshape(4, 4)
+    return int(np.sum(np.linalg.svd(M, compute_uv=False) > 1e-12))
+
+
+def test_schmidt_ranks_of_two_qubit_gates():
+    # Methods, "Overview of the simulator": 2 for CZ (any diagonal gate), 4 for iSWAP
+    assert _operator_schmidt_rank(G.CZ) == 2
+    assert _operator_schmidt_rank(_iswap_ketbra()) == 4
+
+
 def _kron_unitary(circ):
     n = circ.n
     U = np.eye(1 << n, dtype=np.complex128)
@@ -55,6 +82,16 @@ def _kron_unitary(circ):
                 if (idx >> (n - 1 - g.q0)) & 1 and (idx >> (n - 1 - g.q1)) & 1:
                     d[idx] = -1
             M = np.diag(d)
+        elif g.kind == "ISWAP":
+            # brute force on basis states: |..0_a..1_b..> -> i|..1_a..0_b..> and back
+            M = np.zeros((1 << n, 1 << n), dtype=np.complex128)
+            ba, bb = n - 1 - g.q0, n - 1 - g.q1
+            for idx in range(1 << n):
+                xa, xb = (idx >> ba) & 1, (idx >> bb) & 1
+                if xa == xb:
+                    M[idx, idx] = 1
+                else:
+                    M[idx ^ (1 << ba) ^ (1 << bb), idx] = 1j
         else:
             ops = [np.eye(2)] * n
             ops[g.q0] = G.single_qubit_matrix(g.kind, circ.angles, g.param)
@@ -65,9 +102,9 @@ def _kron_unitary(circ):
     return U
 
 
-@pytest.mark.parametrize("rot", [False, True])
-def test_statevector_vs_kronecker_unitary(rot):
-    circ = random_circuit(grid_lattice(2, 3), 10, seed=4, rotations=rot)
+@pytest.mark.parametrize("rot,two", [(False, "CZ"), (True, "CZ"), (False, "ISWAP"), (True, "ISWAP")])
+def test_statevector_vs_kronecker_unitary(rot, two):
+    circ = random_circuit(grid_lattice(2, 3), 10, seed=4, rotations=rot, two_qubit=two)
     U = _kron_unitary(circ)
     psi = SV.final_state(circ).reshape(-1)
     assert np.allclose(psi, U[:, 0], atol=1e-13)
@@ -87,6 +124,63 @@ def test_contraction_matches_statevector(rows, cols, t, seed):
     a = NW.amplitudes(p, bs)
     r = SV.amplitudes(p.circuit, bs, p.open_tile)
     assert np.max(np.abs(a - r)) < 1e-14
+
+
+@pytest.mark.parametrize("rows,cols,t,seed", [(2, 3, 8, 0), (3, 3, 8, 1), (2, 3, 16, 2)])
+def test_iswap_contraction_matches_statevector(rows, cols, t, seed):
+    p = grid_problem(rows, cols, t, seed, r0=1, c0=1, cuts=False, tile_rows=1, tile_cols=1,
+                     two_qubit="ISWAP")
+    bs = random_bitstrings(p.n, 3, seed)
+    a = NW.amplitudes(p, bs)
+    r = SV.amplitudes(p.circuit, bs, p.open_tile)
+    assert np.max(np.abs(a - r)) < 1e-14
+
+
+def test_iswap_bonds_match_cz_at_twice_the_depth():
+    # Methods, "Revised set of RQCs" / "Overview of the simulator": depth
+    # 1+t/2+1 with iSWAPs costs what depth 1+t+1 with CZs costs (t/2 a
+    # multiple of the 8-cycle layer period, so every edge is covered)
+    for t in (16, 32, 48):
+        cz = random_circuit(grid_lattice(4, 5), t, 3)
+        isw = random_circuit(grid_lattice(4, 5), t // 2, 3, two_qubit="ISWAP")
+        assert np.array_equal(NW.bond_exponents(cz), NW.bond_exponents(isw))
+
+
+def test_iswap_slice_sum_and_per_slice_substitution():
+    p = grid_problem(3, 4, 8, 3, r0=2, c0=2, cuts=True, tile_rows=1, tile_cols=2, two_qubit="ISWAP")
+    P = NW.n_slices(p.circuit, p.cut_edges)
+    assert P == 16                      # two cut edges, one iSWAP (2 bits) each
+    bs = random_bitstrings(p.n, 2, 5)
+    full = NW.amplitudes(p, bs)
+    ref = SV.amplitudes(p.circuit, bs, p.open_tile)
+    assert np.max(np.abs(full - ref)) < 1e-15
+    for s in (0, 6, 9, 15):
+        vals = NW.slice_values(p.circuit, p.cut_edges, s)
+        got = NW.slice_amplitudes(p, bs[1], s)
+        want = SV.amplitudes(p.circuit, bs[1:], p.open_tile, cut_values=vals)[0]
+        assert np.max(np.abs(got - want)) < 1e-15
+
+
+def test_iswap_planted_mistakes_fail_a_pin(monkeypatch):
+    p = grid_problem(3, 4, 8, 3, r0=2, c0=2, cuts=True, tile_rows=1, tile_cols=2, two_qubit="ISWAP")
+    bs = random_bitstrings(p.n, 1, 5)
+    ref = SV.amplitudes(p.circuit, bs, p.open_tile)
+    orig = G.iswap_half
+    # (a) a conjugated coefficient (-i/2 for i/2): the full sum moves
+    monkeypatch.setattr(G, "iswap_half", lambda role, k: orig(role, k).conj() if role == "b" and k >= 2
+                        else orig(role, k))
+    assert np.max(np.abs(NW.amplitudes(p, bs) - ref)) > 1e-6
+    # (b) the two bits of k swapped in the bond index: the full sum is a
+    #     relabelling and still matches, a per-slice value does not
+    flip = lambda role, k: orig(role, ((k & 1) << 1) | (k >> 1))
+    monkeypatch.setattr(G, "iswap_half", flip)
+    assert np.max(np.abs(NW.amplitudes(p, bs) - ref)) < 1e-14
+    vals = NW.slice_values(p.circuit, p.cut_edges, 6)
+    monkeypatch.setattr(G, "iswap_half", orig)
+    want = SV.amplitudes(p.circuit, bs, p.open_tile, cut_values=vals)[0]
+    monkeypatch.setattr(G, "iswap_half", flip)
+    got = NW.slice_amplitudes(p, bs[0], 6)
+    assert np.max(np.abs(got - want)) > 1e-6
 
 
 def test_c1_full_tile_norm_and_statevector():
@@ -156,6 +250,23 @@ def test_shift_rule_fd_and_adjoint_agree():
     fd = GR.finite_difference(amp, circ.angles, params)
     assert np.max(np.abs(sr - fd)) < 1e-8
     g = (np.random.default_rng(0).normal(size=4) + 1j * np.random.default_rng(1).normal(size=4))
+    adj = GR.statevector_adjoint(circ, bs, tile, g)
+    assert np.max(np.abs(adj - GR.loss_gradient(sr, g))) < 1e-12
+
+
+def test_iswap_rotation_gradients_agree():
+    circ = random_circuit(grid_lattice(2, 3), 8, seed=11, rotations=True, two_qubit="ISWAP")
+    bs = random_bitstrings(circ.n, 1, 3)
+    tile = [3, 4]
+
+    def amp(th):
+        return SV.amplitudes(circ, bs, tile, angles=th)[0]
+
+    params = list(range(circ.n_params))
+    sr = GR.shift_rule(amp, circ.angles, params)
+    fd = GR.finite_difference(amp, circ.angles, params)
+    assert np.max(np.abs(sr - fd)) < 1e-8
+    g = (np.random.default_rng(2).normal(size=4) + 1j * np.random.default_rng(3).normal(size=4))
     adj = GR.statevector_adjoint(circ, bs, tile, g)
     assert np.max(np.abs(adj - GR.loss_gradient(sr, g))) < 1e-12
 
