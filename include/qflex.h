@@ -69,10 +69,15 @@ typedef enum {
                            and the product is rescaled exactly by 2^-(s_A+s_B) */
 } qflex_precision;
 
-/* Gate kinds (Methods, "Revised set of RQCs"; rotations R_P(t) = exp(-i t P/2)). */
+/* Gate kinds (Methods, "Revised set of RQCs"; rotations R_P(t) = exp(-i t P/2)).
+ * Two-qubit kinds act on a lattice edge and add bits to its bond: CZ 1 bit
+ * (Schmidt rank 2), ISWAP = |00><00| + |11><11| + i|01><10| + i|10><01|
+ * 2 bits (rank 4, Methods "Overview of the simulator"); a bond carries at
+ * most 20 bits. */
 enum {
   QFLEX_GATE_H = 0, QFLEX_GATE_T = 1, QFLEX_GATE_SX = 2, QFLEX_GATE_SY = 3,
-  QFLEX_GATE_CZ = 4, QFLEX_GATE_RX = 5, QFLEX_GATE_RY = 6, QFLEX_GATE_RZ = 7
+  QFLEX_GATE_CZ = 4, QFLEX_GATE_RX = 5, QFLEX_GATE_RY = 6, QFLEX_GATE_RZ = 7,
+  QFLEX_GATE_ISWAP = 8
 };
 
 /* One gate: cycle (time step, gates sorted by it), kind, qubits (q1 = -1 for

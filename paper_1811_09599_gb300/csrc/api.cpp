@@ -2,8 +2,9 @@
 //
 // The planner turns the paper's problem statement into a fixed schedule:
 //  * network metadata (Methods, "Overview of the simulator"): bond exponent
-//    K_e per edge (number of CZs), per-qubit gate lines compiled into ops for
-//    the grid-tensor kernel, grid-tensor layouts [o?][bonds by neighbour id];
+//    K_e per edge (bond bits: 1 per CZ, 2 per iSWAP), per-qubit gate lines
+//    compiled into ops for the grid-tensor kernel, grid-tensor layouts
+//    [o?][bonds by neighbour id];
 //  * cuts (Methods, "Cutting indexes"): slice id s in mixed radix 2^{K_e} over
 //    the cut list, first cut most significant; a cut bond is removed from the
 //    views of its two grid tensors and contributes value * stride to their
@@ -284,7 +285,8 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
       const int oy = ed[y].first == q ? ed[y].second : ed[y].first;
       return ox < oy;
     });
-  // gates: validate, count CZs per edge, per-qubit lines in time order
+  // gates: validate, count bond bits per edge (1 per CZ, 2 per iSWAP),
+  // per-qubit lines in time order
   std::vector<int64_t> order(size_t(c->n_gates));
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(),
@@ -293,13 +295,14 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
   std::vector<std::vector<std::pair<int64_t, int>>> line(n);   // (gate index, edge or -1)
   for (int64_t gi : order) {
     const qflex_gate& g = c->gates[gi];
-    if (g.kind < 0 || g.kind > 7) return fail(QFLEX_ERR_CIRCUIT, "unknown gate kind");
+    if (g.kind < 0 || g.kind > 8) return fail(QFLEX_ERR_CIRCUIT, "unknown gate kind");
     if (g.q0 < 0 || g.q0 >= n) return fail(QFLEX_ERR_CIRCUIT, "gate qubit out of range");
-    if (g.kind == QFLEX_GATE_CZ) {
-      if (g.q1 < 0 || g.q1 >= n || g.q1 == g.q0) return fail(QFLEX_ERR_CIRCUIT, "bad CZ qubits");
+    if (g.kind == QFLEX_GATE_CZ || g.kind == QFLEX_GATE_ISWAP) {
+      if (g.q1 < 0 || g.q1 >= n || g.q1 == g.q0) return fail(QFLEX_ERR_CIRCUIT, "bad two-qubit gate qubits");
       const int e = edge_of(g.q0, g.q1);
-      if (e < 0) return fail(QFLEX_ERR_CIRCUIT, "CZ on a pair that is not a lattice edge");
-      ++p.K[e];
+      if (e < 0) return fail(QFLEX_ERR_CIRCUIT, "two-qubit gate on a pair that is not a lattice edge");
+      p.K[e] += g.kind == QFLEX_GATE_ISWAP ? 2 : 1;
+      if (p.K[e] > 20) return fail(QFLEX_ERR_PLAN, "bond with more than 20 bits");
       line[g.q0].push_back({gi, e});
       line[g.q1].push_back({gi, e});
     } else {
@@ -308,8 +311,6 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
       line[g.q0].push_back({gi, -1});
     }
   }
-  for (int e = 0; e < E; ++e)
-    if (p.K[e] > 20) return fail(QFLEX_ERR_PLAN, "bond with more than 20 CZs");
   // legs
   p.leg_dim.assign(E + n, 2);
   for (int e = 0; e < E; ++e) p.leg_dim[e] = int64_t(1) << p.K[e];
@@ -336,7 +337,7 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
     p.tile.push_back(q);
   }
   // grid tensors: [o if tile][bond legs by neighbour id], bits per bond leg,
-  // first CZ in time = most significant bit of the leg
+  // first two-qubit gate in time = most significant bit(s) of the leg
   p.gmeta.resize(n);
   p.grid_ref.resize(n);
   int64_t off = 0;
@@ -361,8 +362,11 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
         p.gops.push_back(make_int2(g.kind, g.kind >= QFLEX_GATE_RX ? g.param : -1));
       } else {
         const int other = g.q0 == q ? g.q1 : g.q0;
-        const int bitpos = low[e] + p.K[e] - 1 - seen[e]++;
-        p.gops.push_back(make_int2((q < other ? kOpCzProj : kOpCzZ) | (bitpos << 8), -1));
+        const bool isw = g.kind == QFLEX_GATE_ISWAP;
+        seen[e] += isw ? 2 : 1;
+        const int bitpos = low[e] + p.K[e] - seen[e];   // lowest bit of this gate's k
+        const int type = isw ? (q < other ? kOpIswA : kOpIswB) : (q < other ? kOpCzProj : kOpCzZ);
+        p.gops.push_back(make_int2(type | (bitpos << 8), -1));
       }
     }
     m.op_count = int(p.gops.size()) - m.op_begin;

@@ -29,6 +29,10 @@ __device__ __forceinline__ float fp16_scale_of(unsigned max_bits) {
 //   type 0..3, 5..7: one-qubit gate kinds (H, T, SX, SY, RX, RY, RZ)
 //   type 8: CZ half carried by the lower-index qubit, |k><k| with k = entry bit `bitpos`
 //   type 9: CZ half carried by the higher-index qubit, Z^k
+//   type 10: iSWAP half carried by the lower-index qubit, P_k with
+//            P = (I, Z, X, Y) and k = entry bits [bitpos, bitpos + 2)
+//   type 11: iSWAP half carried by the higher-index qubit, c_k P_k,
+//            c = (1/2, 1/2, i/2, i/2)  (iSWAP = (II + ZZ)/2 + i (XX + YY)/2)
 struct GridQubitMeta {
   int64_t offset;     // element offset of this qubit's tensor in the grid buffer
   int32_t n_bits;     // bond bits (entries per output value = 2^n_bits)
@@ -38,7 +42,58 @@ struct GridQubitMeta {
   int32_t qubit;
   int32_t pad;
 };
-enum : int { kOpCzProj = 8, kOpCzZ = 9 };
+enum : int { kOpCzProj = 8, kOpCzZ = 9, kOpIswA = 10, kOpIswB = 11 };
+
+#ifdef __CUDACC__
+// Column form v <- H v of an iSWAP half (type 10 or 11, 2-bit value k).
+__device__ __forceinline__ void iswap_half_col(int type, int k, float2& v0, float2& v1) {
+  float2 n0 = v0, n1 = v1;
+  if (k == 1) {
+    n1 = make_float2(-v1.x, -v1.y);
+  } else if (k == 2) {
+    n0 = v1;
+    n1 = v0;
+  } else if (k == 3) {            // Y = [[0, -i], [i, 0]]
+    n0 = make_float2(v1.y, -v1.x);
+    n1 = make_float2(-v0.y, v0.x);
+  }
+  if (type == kOpIswB) {          // c_k = 1/2 or i/2
+    if (k < 2) {
+      n0 = make_float2(0.5f * n0.x, 0.5f * n0.y);
+      n1 = make_float2(0.5f * n1.x, 0.5f * n1.y);
+    } else {
+      n0 = make_float2(-0.5f * n0.y, 0.5f * n0.x);
+      n1 = make_float2(-0.5f * n1.y, 0.5f * n1.x);
+    }
+  }
+  v0 = n0;
+  v1 = n1;
+}
+// Row form u <- u H of the same half.
+__device__ __forceinline__ void iswap_half_row(int type, int k, float2& u0, float2& u1) {
+  float2 n0 = u0, n1 = u1;
+  if (k == 1) {
+    n1 = make_float2(-u1.x, -u1.y);
+  } else if (k == 2) {
+    n0 = u1;
+    n1 = u0;
+  } else if (k == 3) {            // (u0, u1) Y = (i u1, -i u0)
+    n0 = make_float2(-u1.y, u1.x);
+    n1 = make_float2(u0.y, -u0.x);
+  }
+  if (type == kOpIswB) {
+    if (k < 2) {
+      n0 = make_float2(0.5f * n0.x, 0.5f * n0.y);
+      n1 = make_float2(0.5f * n1.x, 0.5f * n1.y);
+    } else {
+      n0 = make_float2(-0.5f * n0.y, 0.5f * n0.x);
+      n1 = make_float2(-0.5f * n1.y, 0.5f * n1.x);
+    }
+  }
+  u0 = n0;
+  u1 = n1;
+}
+#endif
 
 cudaError_t launch_gridtensor(const GridQubitMeta* d_meta, int n_qubits, int max_bits,
                               const int2* d_ops, const double* d_angles,

@@ -92,6 +92,10 @@ __global__ void __launch_bounds__(256) k_gridgrad(const GridQubitMeta* __restric
       }
       continue;
     }
+    if (type == kOpIswA || type == kOpIswB) {
+      iswap_half_col(type, int((e >> (op.x >> 8)) & 3), v0, v1);
+      continue;
+    }
     M2 g;
     if (type >= 5) {
       if (nrot < kMaxRot) {
@@ -133,6 +137,10 @@ __global__ void __launch_bounds__(256) k_gridgrad(const GridQubitMeta* __restric
       } else if (k) {
         u1 = make_float2(-u1.x, -u1.y);
       }
+      continue;
+    }
+    if (type == kOpIswA || type == kOpIswB) {
+      iswap_half_row(type, int((e >> (op.x >> 8)) & 3), u0, u1);
       continue;
     }
     M2 g;

@@ -8,7 +8,9 @@
 //   (-1)^{ab} = sum_k d_{a,k} (-1)^{k b}:
 // the lower-index qubit applies |k><k|, the higher-index one applies Z^k,
 // with k one bit of the bond multi-index (first CZ in time = most
-// significant bit of that bond).
+// significant bit of that bond).  An iSWAP enters through its rank-4 split
+// iSWAP = (II + ZZ)/2 + i (XX + YY)/2: the lower-index qubit applies P_k,
+// the other c_k P_k, with k two bits of the bond multi-index.
 //
 // One thread per bond-index entry evolves the qubit's 2-vector through its
 // gate line (FP32) with the CZ halves selected by the entry's bits, and
@@ -77,6 +79,8 @@ __global__ void k_gridtensor(const GridQubitMeta* __restrict__ meta, const int2*
       } else if (k) {
         v1 = make_float2(-v1.x, -v1.y);
       }
+    } else if (type == kOpIswA || type == kOpIswB) {
+      iswap_half_col(type, int((e >> (op.x >> 8)) & 3), v0, v1);
     } else {
       const C2 g = gate_matrix(type, angles, op.y);
       const float2 n0 = cadd(cmul(g.m00, v0), cmul(g.m01, v1));

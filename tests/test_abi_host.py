@@ -117,3 +117,35 @@ def test_default_ordering_and_rotation_circuits(Plan):
     p = Plan(Problem(circ, [], [0, 4], None), "tf32x3", device=-1)
     info = p.info()
     assert info["n_params"] == circ.n_params and info["n_steps"] == 8
+
+
+def test_iswap_plan_costs_what_cz_at_twice_the_depth(Plan):
+    """Methods, "Revised set of RQCs": an iSWAP circuit of depth 1+t/2+1 costs
+    what a CZ circuit of depth 1+t+1 costs (each iSWAP adds 2 bond bits).  The
+    planner's own accounting of the 7x7 two-cut workload agrees exactly."""
+    cz = Plan(c2_problem(0, t=32), "bf16x3", device=-1)
+    isw = Plan(c2_problem(0, t=16, two_qubit="ISWAP"), "bf16x3", device=-1)
+    a, b = cz.info(), isw.info()
+    for k in ("n_slices", "max_tensor_elems", "n_steps", "n_tc_steps"):
+        assert a[k] == b[k], k
+    # the workspace also holds the compiled gate lines (578 gates vs 1050)
+    assert abs(a["workspace_bytes"] - b["workspace_bytes"]) < 64 << 10
+    ca, cb = cz.cost(1), isw.cost(1)
+    for k in ("steps_executed", "largest_gemm_cmacs", "cmacs", "tc_mma_flops", "permute_bytes", "launches"):
+        assert ca[k] == cb[k], k
+
+
+def test_iswap_validation(Plan):
+    from paper_1811_09599_gb300 import QFlexError
+    # an iSWAP on a pair that is not a lattice edge
+    bad = grid_problem(3, 3, 8, 0, r0=1, c0=1, cuts=False, tile_rows=1, tile_cols=1, two_qubit="ISWAP")
+    for g in bad.circuit.gates:
+        if g.kind == "ISWAP":
+            g.q0, g.q1 = 0, 8
+            break
+    with pytest.raises(QFlexError, match="CIRCUIT"):
+        Plan(bad, "fp32", device=-1)
+    # more than 20 bond bits on one edge: 11 iSWAPs (22 bits)
+    deep = random_circuit(grid_lattice(2, 2), 88, 0, two_qubit="ISWAP")
+    with pytest.raises(QFlexError, match="PLAN"):
+        Plan(Problem(deep, [], [], None), "fp32", device=-1)
