@@ -1,4 +1,4 @@
-"""Fraction-f slice choice and norm estimates (oracle; test infrastructure only).
+"""Fraction-f slice choice, sampling and norm estimates (oracle; test infrastructure only).
 
 Methods, "Summing a fraction of the paths": summing a randomly chosen fraction
 f of the paths yields a state of norm ~f and fidelity ~f (Eq. fidelity_1);
@@ -89,3 +89,62 @@ def overlap_fidelity(psi_exact: np.ndarray, psi_partial: np.ndarray) -> float:
     a = np.asarray(psi_exact).reshape(-1)
     b = np.asarray(psi_partial).reshape(-1)
     return float(abs(np.vdot(a, b)) ** 2 / np.vdot(b, b).real)
+
+
+STREAM_STEP = 0xD1B54A32D192ED03
+
+
+def fidelity_samples(batch_bits: np.ndarray, accepted: np.ndarray, tile, fidelity: float,
+                     seed: int, n_samples: int):
+    """Fidelity-f samples from perfect-fidelity amplitudes (Methods, "Fraction
+    of perfect fidelity amplitudes"): a fidelity-f circuit outputs
+    rho = f |psi><psi| + (1 - f) I / N, so each sample is, with probability f,
+    an exact sample of |psi> and otherwise a uniformly random bitstring.
+
+    Exact samples are the batches that frugal rejection sampling accepted
+    (accepted[b] = tile index j, or -1), used in batch order; the k-th exact
+    sample takes the k-th accepted batch: its bits batch_bits[b] with tile
+    qubit t set to bit (|tile| - 1 - t) of j.  Randomness, as specified for
+    both implementations: sample i runs its own SplitMix64 stream from
+    seed + i * 0xD1B54A32D192ED03; the first draw x gives u = (x >> 11) 2^-53
+    and the sample is exact when u < f; a uniform sample takes qubit q from
+    bit 63 - (q mod 64) of draw number 1 + q div 64.
+
+    Returns (samples uint8 [n_samples, n], source int32 [n_samples] with the
+    batch index of an exact sample, -1 for a uniform one and -2 for an exact
+    one beyond the accepted batches (its bits are zero), n_exact).
+    """
+    batch_bits = np.asarray(batch_bits, dtype=np.uint8)
+    accepted = np.asarray(accepted, dtype=np.int64).reshape(-1)
+    n = batch_bits.shape[1] if batch_bits.ndim == 2 else int(len(batch_bits))
+    nt = len(tile)
+    pool = [b for b in range(len(accepted)) if accepted[b] >= 0]
+    samples = np.zeros((n_samples, n), dtype=np.uint8)
+    source = np.full(n_samples, -1, dtype=np.int32)
+    k = 0
+    for i in range(n_samples):
+        rng = SplitMix64((seed + i * STREAM_STEP) & _M64)
+        u = (rng.next() >> 11) * 2.0 ** -53
+        if u < fidelity:
+            if k < len(pool):
+                b = pool[k]
+                source[i] = b
+                samples[i] = batch_bits[b]
+                j = int(accepted[b])
+                for t, q in enumerate(tile):
+                    samples[i, q] = (j >> (nt - 1 - t)) & 1
+            else:
+                source[i] = -2
+            k += 1
+        else:
+            w = 0
+            for q in range(n):
+                if q % 64 == 0:
+                    w = rng.next()
+                samples[i, q] = (w >> (63 - q % 64)) & 1
+    return samples, source, k
+
+
+def linear_xeb(probabilities: np.ndarray, n_qubits: int) -> float:
+    """Linear cross-entropy fidelity estimate N <p(x)> - 1 over sampled x."""
+    return float((2.0 ** n_qubits) * np.mean(np.asarray(probabilities)) - 1.0)

@@ -385,3 +385,66 @@ def test_frugal_sampling_acceptance_closed_form():
     p = np.abs(amps) ** 2 * 2.0 ** n
     sel = acc[acc >= 0]
     assert np.mean(p[np.arange(nb)[acc >= 0], sel]) > 1.5
+
+
+# ---------------------------------------------------------------- fidelity-f samples
+def test_fidelity_samples_special_cases_and_rates():
+    """Methods, "Fraction of perfect fidelity amplitudes": f = 1 takes only
+    exact samples (accepted batches, in batch order, tile bits from the
+    accepted index); f = 0 only uniform bitstrings; otherwise the exact
+    fraction is Binomial(n, f) and uniform bits are fair and independent."""
+    rng = np.random.default_rng(3)
+    n, nb, tile = 70, 4000, [60, 61, 62, 63, 64, 65]
+    bits = rng.integers(0, 2, size=(nb, n), dtype=np.uint8)
+    acc = rng.integers(-1, 64, size=nb).astype(np.int32)
+    pool = np.flatnonzero(acc >= 0)
+    s1, src1, k1 = SEL.fidelity_samples(bits, acc, tile, 1.0, 9, 500)
+    assert k1 == 500 and np.array_equal(src1, pool[:500])
+    for i in (0, 77, 499):
+        b = pool[i]
+        want = bits[b].copy()
+        for t, q in enumerate(tile):
+            want[q] = (acc[b] >> (5 - t)) & 1
+        assert np.array_equal(s1[i], want)
+    s0, src0, k0 = SEL.fidelity_samples(bits, acc, tile, 0.0, 9, 20000)
+    assert k0 == 0 and np.all(src0 == -1)
+    sd = 0.5 / np.sqrt(20000)
+    assert np.max(np.abs(s0.mean(axis=0) - 0.5)) < 5 * sd
+    # independence across the 64-bit word boundary (qubits 63 and 64) and within a word
+    for a, b in ((63, 64), (0, 1), (10, 69)):
+        assert abs(np.mean(s0[:, a] ^ s0[:, b]) - 0.5) < 5 * sd
+    f = 0.37
+    _, src, k = SEL.fidelity_samples(bits, acc, tile, f, 4, 3000)
+    sd = np.sqrt(f * (1 - f) / 3000)
+    assert abs(k / 3000 - f) < 5 * sd and np.sum(src >= 0) == k
+    # too few accepted batches: the surplus exact samples are marked -2
+    _, src, k = SEL.fidelity_samples(bits[:10], acc[:10], tile, 1.0, 4, 20)
+    assert k == 20 and np.sum(src == -2) == 20 - np.sum(acc[:10] >= 0)
+
+
+@pytest.mark.parametrize("f", [0.25, 0.6])
+def test_fidelity_samples_linear_xeb_equals_f(f):
+    """The mixture's linear XEB, N <p(x)> - 1, is f times that of exact
+    samples (uniform samples contribute 0), and exact samples of a
+    Porter-Thomas circuit give N sum p^2 - 1 ~ 1.  Exact samples here come
+    from frugal rejection over 64-entry open-tile batches of state-vector
+    amplitudes of a 12-qubit RQC."""
+    p_ = grid_problem(3, 4, 24, 5, r0=1, c0=2, cuts=False, tile_rows=2, tile_cols=3)
+    n = p_.n
+    psi = SV.final_state(p_.circuit)
+    prob = np.abs(psi.reshape(-1)) ** 2
+    nb = 12000
+    bits = random_bitstrings(n, nb, 21)
+    amps = np.stack([SV.tile_amplitudes_from_state(psi, b, p_.open_tile) for b in bits])
+    acc = SEL.frugal_sample(amps, n, 10.0, seed=8)
+    ns = 16000
+    samples, src, k = SEL.fidelity_samples(bits, acc, p_.open_tile, f, 31, ns)
+    assert np.all(src >= -1)
+    idx = samples.astype(np.int64) @ (1 << np.arange(n - 1, -1, -1))
+    xeb = SEL.linear_xeb(prob[idx], n)
+    exact_xeb = SEL.linear_xeb(prob[idx[src >= 0]], n)
+    ideal = (2.0 ** n) * np.sum(prob ** 2) - 1.0
+    assert abs(exact_xeb - ideal) < 0.1 * ideal
+    # N p(x) has variance ~2 under Porter-Thomas: 5 sigma over ns samples
+    assert abs(xeb - f * exact_xeb) < 5 * np.sqrt(2.0 / ns) + 5 * np.sqrt(f * (1 - f) / ns) * exact_xeb
+    assert abs(xeb - f * ideal) < 0.1 * ideal
