@@ -281,6 +281,32 @@ qflex_status qflex_norm(const double* amps, int64_t n, double* out, void* stream
 qflex_status qflex_frugal_sample(const double* amps, int64_t n_batches, int32_t n_c, int32_t n_qubits,
                                  double M, uint64_t seed, int32_t* accepted, void* stream);
 
+/* Fidelity-f samples from perfect-fidelity amplitudes (Methods, "Fraction of
+ * perfect fidelity amplitudes"): the output of a circuit run at fidelity f is
+ * rho = f |psi><psi| + (1 - f) I / N, so each of the n_samples draws is, with
+ * probability f, an exact sample of |psi> and otherwise a uniformly random
+ * bitstring.  Exact samples are the batches that qflex_frugal_sample accepted,
+ * used in batch order: the k-th exact draw takes the k-th accepted batch b,
+ * i.e. batch_bits[b] with tile qubit t set to bit (n_tile - 1 - t) of
+ * accepted[b].  Randomness: draw i runs a SplitMix64 stream from
+ * seed + i * 0xD1B54A32D192ED03; its first value x gives u = (x >> 11) 2^-53
+ * and the draw is exact when u < fidelity; a uniform draw takes qubit q from
+ * bit 63 - (q mod 64) of value number 1 + q div 64 of the stream.
+ * batch_bits: device uint8 [n_batches][n_qubits] (the bitstring each batch was
+ * computed for; its tile bits are ignored); accepted: device int32 [n_batches]
+ * from qflex_frugal_sample; tile: host int32 [n_tile] qubit ids (n_tile <= 30,
+ * the plan's open tile order); samples: device uint8 [n_samples][n_qubits];
+ * source: device int32 [n_samples], the batch of an exact draw, -1 for a
+ * uniform draw, -2 for an exact draw past the accepted batches (bits zero).
+ * *n_exact (host) = number of exact draws.  Uses stream-ordered scratch of
+ * 4 * n_batches + 16 bytes and synchronizes the stream before returning.
+ * Returns QFLEX_ERR_ARG (outputs written) when more exact draws are needed
+ * than batches were accepted: compute more batches. */
+qflex_status qflex_fidelity_samples(const uint8_t* batch_bits, const int32_t* accepted, int64_t n_batches,
+                                    const int32_t* tile, int32_t n_tile, int32_t n_qubits, double fidelity,
+                                    uint64_t seed, int64_t n_samples, uint8_t* samples, int32_t* source,
+                                    int64_t* n_exact, void* stream);
+
 /* Synchronize `device` and read (and clear) the library's device status word
  * used by the standalone kernels.  *status = QFLEX_OK or QFLEX_ERR_DEVICE_TIMEOUT. */
 qflex_status qflex_device_status(int device, int32_t* status);

@@ -96,6 +96,9 @@ SIGNATURES = [
     ("qflex_norm", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     ("qflex_frugal_sample", C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_double,
                                       C.c_uint64, C.c_void_p, C.c_void_p]),
+    ("qflex_fidelity_samples", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int32,
+                                         C.c_int32, C.c_double, C.c_uint64, C.c_int64, C.c_void_p,
+                                         C.c_void_p, C.POINTER(C.c_int64), C.c_void_p]),
     ("qflex_device_status", C.c_int, [C.c_int, C.POINTER(C.c_int32)]),
     ("qflex_cgemm_noalloc", C.c_int, [C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p]),

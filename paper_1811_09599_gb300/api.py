@@ -257,6 +257,30 @@ def frugal_sample(amps: torch.Tensor, n_qubits: int, M: float = 10.0, seed: int 
     return out
 
 
+def fidelity_samples(batch_bits: torch.Tensor, accepted: torch.Tensor, tile, fidelity: float,
+                     n_samples: int, seed: int = 0, stream=None):
+    """qflex_fidelity_samples: n_samples bitstrings of a fidelity-f sampler
+    (exact with probability f, from the accepted batches in order; uniform
+    otherwise).  Returns (samples uint8 [n_samples, n], source int32
+    [n_samples], n_exact); raises QFlexError when too few batches were
+    accepted for the exact draws."""
+    lib = _lib.load()
+    bb = batch_bits.contiguous()
+    acc = accepted.contiguous()
+    assert bb.dtype == torch.uint8 and bb.is_cuda and bb.dim() == 2
+    assert acc.dtype == torch.int32 and acc.is_cuda and acc.numel() == bb.shape[0]
+    n = bb.shape[1]
+    t = (C.c_int32 * max(1, len(tile)))(*[int(q) for q in tile])
+    samples = torch.empty((n_samples, n), dtype=torch.uint8, device=bb.device)
+    source = torch.empty(n_samples, dtype=torch.int32, device=bb.device)
+    n_exact = C.c_int64()
+    check(lib.qflex_fidelity_samples(C.c_void_p(bb.data_ptr()), C.c_void_p(acc.data_ptr()), bb.shape[0], t,
+                                     len(tile), n, float(fidelity), C.c_uint64(seed), int(n_samples),
+                                     C.c_void_p(samples.data_ptr()), C.c_void_p(source.data_ptr()),
+                                     C.byref(n_exact), _stream_handle(stream)))
+    return samples, source, n_exact.value
+
+
 def device_status(device: int = 0) -> int:
     lib = _lib.load()
     v = C.c_int32()

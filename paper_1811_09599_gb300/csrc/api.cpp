@@ -1472,6 +1472,44 @@ qflex_status qflex_frugal_sample(const double* amps, int64_t n_batches, int32_t 
   return QFLEX_OK;
 }
 
+qflex_status qflex_fidelity_samples(const uint8_t* batch_bits, const int32_t* accepted, int64_t n_batches,
+                                    const int32_t* tile, int32_t n_tile, int32_t n_qubits, double fidelity,
+                                    uint64_t seed, int64_t n_samples, uint8_t* samples, int32_t* source,
+                                    int64_t* n_exact, void* stream) {
+  if (!n_exact || n_batches < 0 || n_samples < 0 || n_qubits < 1 || n_qubits > 100000 || n_tile < 0 ||
+      n_tile > 30 || n_tile > n_qubits || !(fidelity >= 0.0 && fidelity <= 1.0))
+    return fail(QFLEX_ERR_ARG, "bad fidelity-sampling arguments");
+  if (n_batches > INT32_MAX) return fail(QFLEX_ERR_ARG, "more than 2^31 - 1 batches");
+  std::vector<char> seen(size_t(n_qubits), 0);
+  for (int t = 0; t < n_tile; ++t) {
+    if (!tile || tile[t] < 0 || tile[t] >= n_qubits || seen[tile[t]]) return fail(QFLEX_ERR_ARG, "bad tile qubit");
+    seen[tile[t]] = 1;
+  }
+  *n_exact = 0;
+  if (n_samples == 0) return QFLEX_OK;
+  if (!samples || !source || (n_batches > 0 && (!batch_bits || !accepted))) return fail(QFLEX_ERR_ARG, "null pointer");
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void* scratch = nullptr;
+  const size_t pool_bytes = (size_t(n_batches) * 4 + 15) / 16 * 16;
+  QF_CUDA(cudaMallocAsync(&scratch, pool_bytes + 16, s));
+  int32_t* pool = static_cast<int32_t*>(scratch);
+  int64_t* counts = reinterpret_cast<int64_t*>(static_cast<char*>(scratch) + pool_bytes);
+  int64_t host_counts[2] = {0, 0};
+  cudaError_t e = launch_fidelity_mix(batch_bits, accepted, n_batches, tile, n_tile, n_qubits, fidelity, seed,
+                                      n_samples, pool, source, counts, samples, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_counts, counts, sizeof(host_counts), cudaMemcpyDeviceToHost, s);
+  const cudaError_t ef = cudaFreeAsync(scratch, s);
+  if (e == cudaSuccess) e = ef;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("fidelity sampling: ") + cudaGetErrorString(e));
+  *n_exact = host_counts[0];
+  if (host_counts[0] > host_counts[1])
+    return fail(QFLEX_ERR_ARG, "fidelity sampling needs " + std::to_string(host_counts[0]) +
+                                   " exact samples but only " + std::to_string(host_counts[1]) +
+                                   " batches were accepted; compute more batches");
+  return QFLEX_OK;
+}
+
 qflex_status qflex_device_status(int device, int32_t* status) {
   if (!status || device < 0) return fail(QFLEX_ERR_ARG, "bad argument");
   QF_CUDA(cudaSetDevice(device));

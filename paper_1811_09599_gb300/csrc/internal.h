@@ -133,6 +133,12 @@ enum PermFormat : int {
 // largest |re|, |im|, |re+im| of the operand (written by launch_absmax);
 // scale = 2^(14 - e) with smax = f 2^e, f in [0.5, 1), so scaled parts stay
 // below 2^14.  Both the producer and the GEMM epilogue derive it from smax.
+// Fidelity-f mixture of exact (accepted) and uniform samples; pool:
+// [n_batches] scratch, source: [n_samples], counts: 2 x int64 (device).
+cudaError_t launch_fidelity_mix(const uint8_t* batch_bits, const int32_t* accepted, int64_t n_batches,
+                               const int32_t* tile, int n_tile, int n_qubits, double f, uint64_t seed,
+                               int64_t n_samples, int32_t* pool, int32_t* source, int64_t* counts,
+                               uint8_t* out, cudaStream_t s);
 cudaError_t launch_absmax(const float2* in, int64_t n, unsigned* smax, cudaStream_t s);
 
 // Build the tile tables for a map of `nbits` index bits: bit j moves the

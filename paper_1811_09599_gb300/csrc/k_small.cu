@@ -93,6 +93,116 @@ __global__ void k_frugal(const double* __restrict__ amps, int64_t n_batches, int
   accepted[b] = res;
 }
 
+// Fidelity-f samples (Methods, "Fraction of perfect fidelity amplitudes"):
+// the output of a fidelity-f circuit is f |psi><psi| + (1 - f) I / N, so
+// sample i is exact with probability f and uniform otherwise.  Sample i runs
+// its own SplitMix64 stream from seed + i * 0xD1B54A32D192ED03: the first
+// draw x gives u = (x >> 11) 2^-53, exact when u < f; a uniform sample takes
+// qubit q from bit 63 - (q mod 64) of draw 1 + q div 64.  The k-th exact
+// sample takes the k-th batch that frugal rejection sampling accepted.
+constexpr uint64_t kStreamStep = 0xD1B54A32D192ED03ull;
+constexpr int kMixThreads = 1024;
+constexpr int kMaxMixTile = 30;
+
+struct MixTile {
+  int32_t q[kMaxMixTile];
+  int32_t n;
+};
+
+// Exclusive block-wide prefix sum of v (one value per thread); `total` gets
+// the block's sum.  Uses sh[32]; ends with a barrier so sh can be reused.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* sh, int& total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int t = lane < nw ? sh[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    sh[lane] = t;
+  }
+  __syncthreads();
+  const int before = (w > 0 ? sh[w - 1] : 0) + x - v;
+  total = sh[nw - 1];
+  __syncthreads();
+  return before;
+}
+
+// One block: compacts the accepted batches (batch order) into `pool`, then
+// walks the samples in order, deciding exact or uniform and numbering the
+// exact ones; source[i] = pool[k] for the k-th exact sample (-2 past the
+// pool), -1 for a uniform one.  counts = {exact samples, accepted batches}.
+__global__ void __launch_bounds__(kMixThreads) k_mix_plan(const int32_t* __restrict__ accepted, int64_t n_batches,
+                                                          double f, uint64_t seed, int64_t n_samples,
+                                                          int32_t* __restrict__ pool, int32_t* __restrict__ source,
+                                                          int64_t* __restrict__ counts) {
+  __shared__ int sh[32];
+  int64_t n_acc = 0;
+  for (int64_t base = 0; base < n_batches; base += blockDim.x) {
+    const int64_t b = base + threadIdx.x;
+    const int v = (b < n_batches && accepted[b] >= 0) ? 1 : 0;
+    int tot;
+    const int pre = block_exclusive_scan(v, sh, tot);
+    if (v) pool[n_acc + pre] = int32_t(b);
+    n_acc += tot;
+  }
+  __syncthreads();
+  int64_t n_ex = 0;
+  for (int64_t base = 0; base < n_samples; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    int v = 0;
+    if (i < n_samples) {
+      uint64_t x = seed + uint64_t(i) * kStreamStep;
+      const double u = double(splitmix64(x) >> 11) * 0x1.0p-53;
+      v = u < f ? 1 : 0;
+    }
+    int tot;
+    const int pre = block_exclusive_scan(v, sh, tot);
+    if (i < n_samples) {
+      const int64_t k = n_ex + pre;
+      source[i] = v ? (k < n_acc ? pool[k] : -2) : -1;
+    }
+    n_ex += tot;
+  }
+  if (threadIdx.x == 0) {
+    counts[0] = n_ex;
+    counts[1] = n_acc;
+  }
+}
+
+// One thread per sample writes its n_qubits bytes.
+__global__ void k_mix_write(const uint8_t* __restrict__ batch_bits, const int32_t* __restrict__ accepted,
+                            const int32_t* __restrict__ source, const __grid_constant__ MixTile tile,
+                            int n_qubits, uint64_t seed, int64_t n_samples, uint8_t* __restrict__ out) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n_samples) return;
+  const int32_t b = source[i];
+  uint8_t* o = out + i * n_qubits;
+  if (b >= 0) {
+    const uint8_t* src = batch_bits + int64_t(b) * n_qubits;
+    for (int q = 0; q < n_qubits; ++q) o[q] = src[q];
+    const int j = accepted[b];
+    for (int t = 0; t < tile.n; ++t) o[tile.q[t]] = uint8_t((j >> (tile.n - 1 - t)) & 1);
+  } else if (b == -1) {
+    uint64_t x = seed + uint64_t(i) * kStreamStep;
+    splitmix64(x);                         // the exact-or-uniform draw
+    uint64_t w = 0;
+    for (int q = 0; q < n_qubits; ++q) {
+      if ((q & 63) == 0) w = splitmix64(x);
+      o[q] = uint8_t((w >> (63 - (q & 63))) & 1);
+    }
+  } else {
+    for (int q = 0; q < n_qubits; ++q) o[q] = 0;
+  }
+}
+
 // Largest |re|, |im|, |re + im| of a complex64 array (the three parts of the
 // 3M product), as float bits, for the power-of-two scale of fp16 operands.
 __global__ void k_absmax(const float2* __restrict__ in, int64_t n, unsigned* __restrict__ out) {
@@ -124,6 +234,22 @@ cudaError_t launch_frugal(const double* amps, int64_t n_batches, int n_c, double
   if (n_c < 1 || n_c > kMaxBatch) return cudaErrorInvalidValue;
   if (n_batches <= 0) return cudaSuccess;
   k_frugal<<<unsigned((n_batches + 127) / 128), 128, 0, s>>>(amps, n_batches, n_c, scale, seed, accepted);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fidelity_mix(const uint8_t* batch_bits, const int32_t* accepted, int64_t n_batches,
+                               const int32_t* tile, int n_tile, int n_qubits, double f, uint64_t seed,
+                               int64_t n_samples, int32_t* pool, int32_t* source, int64_t* counts,
+                               uint8_t* out, cudaStream_t s) {
+  if (n_tile < 0 || n_tile > kMaxMixTile || n_samples < 0 || n_batches < 0) return cudaErrorInvalidValue;
+  MixTile t{};
+  for (int i = 0; i < n_tile; ++i) t.q[i] = tile[i];
+  t.n = n_tile;
+  k_mix_plan<<<1, kMixThreads, 0, s>>>(accepted, n_batches, f, seed, n_samples, pool, source, counts);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || n_samples == 0) return e;
+  k_mix_write<<<unsigned((n_samples + 255) / 256), 256, 0, s>>>(batch_bits, accepted, source, t, n_qubits, seed,
+                                                                 n_samples, out);
   return cudaGetLastError();
 }
 

@@ -149,3 +149,23 @@ def test_iswap_validation(Plan):
     deep = random_circuit(grid_lattice(2, 2), 88, 0, two_qubit="ISWAP")
     with pytest.raises(QFlexError, match="PLAN"):
         Plan(Problem(deep, [], [], None), "fp32", device=-1)
+
+
+def test_fidelity_samples_argument_checks():
+    """qflex_fidelity_samples validates on the host before any device work."""
+    import ctypes as C
+    from paper_1811_09599_gb300 import _lib
+    lib = _lib.load()
+    n_exact = C.c_int64(-1)
+    tile = (C.c_int32 * 2)(3, 3)
+    # repeated tile qubit, fidelity outside [0, 1], too many tile qubits
+    assert lib.qflex_fidelity_samples(None, None, 0, tile, 2, 8, 0.5, 1, 4, None, None,
+                                      C.byref(n_exact), None) == 1
+    tile = (C.c_int32 * 2)(3, 4)
+    assert lib.qflex_fidelity_samples(None, None, 0, tile, 2, 8, 1.5, 1, 4, None, None,
+                                      C.byref(n_exact), None) == 1
+    assert lib.qflex_fidelity_samples(None, None, 0, tile, 31, 40, 0.5, 1, 4, None, None,
+                                      C.byref(n_exact), None) == 1
+    # no draws: nothing to do
+    assert lib.qflex_fidelity_samples(None, None, 0, tile, 2, 8, 0.5, 1, 0, None, None,
+                                      C.byref(n_exact), None) == 0 and n_exact.value == 0
