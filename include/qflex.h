@@ -134,6 +134,19 @@ typedef struct {
   double largest_gemm_cmacs; /* M*N*K of the largest GEMM */
 } qflex_cost;
 
+/* One step of the plan's schedule (introspection; no counterpart in the
+ * paper beyond its pairwise contraction steps, Methods "Matrix
+ * multiplications"). */
+typedef struct {
+  int32_t dst, src;          /* tensor ids of the ordering step (result keeps dst) */
+  int64_t M, N, K;           /* C[M][N] = sum_k A[M][k] B[N][k] */
+  int32_t kernel;            /* 0 FP32 tiled, 1 FP32 thin (N <= 16), 2 FP32 thin (N <= 32),
+                                3 FP32 warp per row, 4 tensor cores */
+  int32_t bn;                /* tensor-core tile width (kernel 4) */
+  int32_t a_direct, b_direct;/* operand read in place, without a permutation */
+  int64_t runs;              /* executions in one call over n_bs bitstrings and the slices */
+} qflex_step_info;
+
 int32_t qflex_abi_version(void);
 const char* qflex_last_error(void);
 
@@ -160,6 +173,11 @@ qflex_status qflex_plan_cost(qflex_plan plan, int64_t n_bs, const int64_t* slice
  * n_f = max(1, floor(f P + 1/2)) capped at P, the first n_f entries of a
  * Fisher-Yates shuffle of 0..P-1 driven by SplitMix64(seed), sorted.
  * slice_ids: host, capacity >= n_f. */
+/* The schedule's steps for a call over n_bs bitstrings and `slice_ids` (host,
+ * NULL = all): out[i] for i < min(cap, n_steps); *n_steps = number of steps. */
+qflex_status qflex_plan_steps(qflex_plan plan, int64_t n_bs, const int64_t* slice_ids, int64_t n_slice_ids,
+                              qflex_step_info* out, int32_t cap, int32_t* n_steps);
+
 qflex_status qflex_select_slices(qflex_plan plan, double fidelity, uint64_t seed,
                                  int64_t* slice_ids, int64_t capacity, int64_t* n_selected);
 

@@ -57,6 +57,12 @@ class Cost(C.Structure):
                 ("steps_executed", C.c_int64), ("largest_gemm_cmacs", C.c_double)]
 
 
+class StepInfo(C.Structure):
+    _fields_ = [("dst", C.c_int32), ("src", C.c_int32), ("M", C.c_int64), ("N", C.c_int64),
+                ("K", C.c_int64), ("kernel", C.c_int32), ("bn", C.c_int32), ("a_direct", C.c_int32),
+                ("b_direct", C.c_int32), ("runs", C.c_int64)]
+
+
 class Profile(C.Structure):
     _fields_ = [("launches", C.c_int64 * 5), ("ms", C.c_double * 5), ("flops", C.c_double * 5),
                 ("mma_flops", C.c_double * 5), ("bytes", C.c_double * 5)]
@@ -99,6 +105,8 @@ SIGNATURES = [
     ("qflex_fidelity_samples", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int32,
                                          C.c_int32, C.c_double, C.c_uint64, C.c_int64, C.c_void_p,
                                          C.c_void_p, C.POINTER(C.c_int64), C.c_void_p]),
+    ("qflex_plan_steps", C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_int64,
+                                   C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
     ("qflex_device_status", C.c_int, [C.c_int, C.POINTER(C.c_int32)]),
     ("qflex_cgemm_noalloc", C.c_int, [C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p]),

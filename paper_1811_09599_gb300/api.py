@@ -87,6 +87,24 @@ class Plan:
         check(self.lib.qflex_plan_cost(self.handle, n_bs, ptr, n, C.byref(c)))
         return {k: getattr(c, k) for k, _ in c._fields_}
 
+    KERNELS = ("fp32_tiled", "fp32_thin16", "fp32_thin32", "fp32_rowwarp", "tensor_cores")
+
+    def steps(self, n_bs: int = 1, slice_ids: Optional[Sequence[int]] = None) -> list:
+        """qflex_plan_steps: per step dst, src, M, N, K, kernel, bn, direct
+        operands and executions in one call over n_bs bitstrings."""
+        arr, n = _i64_array(slice_ids)
+        ptr = arr.ctypes.data_as(C.POINTER(C.c_int64)) if arr is not None else None
+        cnt = C.c_int32()
+        check(self.lib.qflex_plan_steps(self.handle, n_bs, ptr, n, None, 0, C.byref(cnt)))
+        buf = (_lib.StepInfo * max(1, cnt.value))()
+        check(self.lib.qflex_plan_steps(self.handle, n_bs, ptr, n, buf, cnt.value, C.byref(cnt)))
+        out = []
+        for s in buf[: cnt.value]:
+            d = {k: getattr(s, k) for k, _ in s._fields_}
+            d["kernel"] = self.KERNELS[d["kernel"]]
+            out.append(d)
+        return out
+
     def select_slices(self, fidelity: float, seed: int) -> np.ndarray:
         P = self.n_slices
         out = np.zeros(P, dtype=np.int64)

@@ -1031,6 +1031,42 @@ qflex_status qflex_plan_cost(qflex_plan p, int64_t n_bs, const int64_t* ids, int
   return QFLEX_OK;
 }
 
+qflex_status qflex_plan_steps(qflex_plan p, int64_t n_bs, const int64_t* ids, int64_t n_ids, qflex_step_info* out,
+                              int32_t cap, int32_t* n_steps) {
+  if (!p || !n_steps || n_bs < 0 || cap < 0 || (cap > 0 && !out)) return fail(QFLEX_ERR_ARG, "bad argument");
+  if (qflex_status st = check_slices(*p, ids, n_ids)) return st;
+  std::vector<int64_t> runs(p->steps.size(), 0);
+  qflex_status st = walk(*p, n_bs, ids, n_ids, [&](int i, int64_t, const std::vector<int64_t>&) {
+    if (i >= 0) ++runs[size_t(i)];
+    return QFLEX_OK;
+  });
+  if (st) return st;
+  *n_steps = int32_t(p->steps.size());
+  for (int i = 0; i < int(p->steps.size()) && i < cap; ++i) {
+    const Step& s = p->steps[size_t(i)];
+    qflex_step_info& o = out[i];
+    o.dst = s.dst;
+    o.src = s.src;
+    o.M = s.M;
+    o.N = s.N;
+    o.K = s.K;
+    if (s.tc) {
+      o.kernel = 4;
+    } else if (s.fp32_kernel == 1 || (s.fp32_kernel == 0 && s.N <= 32)) {
+      // same rule as launch_cgemm_thin
+      const int64_t cgs = (s.N + 15) / 16;
+      o.kernel = (s.K >= 64 && ((s.M + 255) / 256) * cgs < 256) ? 3 : (s.N <= 16 ? 1 : 2);
+    } else {
+      o.kernel = 0;
+    }
+    o.bn = s.bn;
+    o.a_direct = s.A.direct;
+    o.b_direct = s.B.direct;
+    o.runs = runs[size_t(i)];
+  }
+  return QFLEX_OK;
+}
+
 qflex_status qflex_select_slices(qflex_plan p, double f, uint64_t seed, int64_t* ids, int64_t cap, int64_t* n_sel) {
   if (!p || !ids || !n_sel || !(f > 0.0)) return fail(QFLEX_ERR_ARG, "bad argument");
   if (p->P > (int64_t(1) << 32)) return fail(QFLEX_ERR_UNSUPPORTED, "too many slices to shuffle");

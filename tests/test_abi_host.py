@@ -169,3 +169,22 @@ def test_fidelity_samples_argument_checks():
     # no draws: nothing to do
     assert lib.qflex_fidelity_samples(None, None, 0, tile, 2, 8, 0.5, 1, 0, None, None,
                                       C.byref(n_exact), None) == 0 and n_exact.value == 0
+
+
+def test_plan_steps_agree_with_cost(Plan):
+    """qflex_plan_steps: per-step shapes and executions add up to the
+    host cost replay, and the execution counts follow SI A's reuse (the
+    4096^3 ABD product once per slice, AB once per right-cut value)."""
+    p = Plan(c2_problem(0), "bf16x3", device=-1)
+    for n_bs, ids in ((1, None), (3, [5, 6, 200])):
+        steps = p.steps(n_bs, ids)
+        c = p.cost(n_bs, ids)
+        assert len(steps) == p.info()["n_steps"]
+        assert sum(s["runs"] for s in steps) == c["steps_executed"]
+        assert sum(s["M"] * s["N"] * s["K"] * s["runs"] for s in steps) == c["cmacs"]
+        assert sum(s["M"] * s["N"] * s["K"] * s["runs"] for s in steps
+                   if s["kernel"] == "tensor_cores") == c["tc_cmacs"]
+    big = [s for s in p.steps(1) if (s["M"], s["N"], s["K"]) == (4096, 4096, 4096)]
+    assert sorted(s["runs"] for s in big) == [16, 256]
+    assert all(s["kernel"] == "tensor_cores" for s in big)
+    assert all(s["kernel"] != "tensor_cores" for s in Plan(c2_problem(0), "fp32", device=-1).steps(1))
