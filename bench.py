@@ -186,27 +186,95 @@ def traffic_from_profiles(precision):
     return e.get("dram_bytes_per_launch")
 
 
+def _time_permute(api, torch, x, perm, reps=5):
+    for _ in range(3):
+        y = api.permute(x, perm)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        y = api.permute(x, perm)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, _permute_exact(torch, x, y, perm)
+
+
+def _permute_exact(torch, x, y, perm, n_samples=1 << 20):
+    """Bit-exact check: the whole tensor against torch's permute where torch
+    takes the rank (<= 25 axes), else 2^20 random output positions against
+    the input entries their index arithmetic names."""
+    if x.dim() <= 25:
+        return bool(torch.equal(y, x.permute(*perm).contiguous()))
+    dims = list(x.shape)
+    in_stride = [1] * len(dims)
+    for a in range(len(dims) - 2, -1, -1):
+        in_stride[a] = in_stride[a + 1] * dims[a + 1]
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1)
+    j = torch.randint(0, y.numel(), (n_samples,), device="cuda", generator=g)
+    rem, idx = j.clone(), torch.zeros_like(j)
+    for a in range(len(perm) - 1, -1, -1):
+        d = dims[perm[a]]
+        idx += (rem % d) * in_stride[perm[a]]
+        rem //= d
+    return bool(torch.equal(y.reshape(-1)[j], x.reshape(-1)[idx]))
+
+
 def permute_sweep(api, torch, peaks):
-    out = []
+    """Complex64 tensors of 2^m entries, m = 20..30: (i) m binary axes, 8
+    seeded random permutations each; (ii) axes of dimension 16 (plus one of
+    2^(m mod 4)), 2 random permutations; (iii) at m = 25 binary axes (the
+    paper's permutation benchmark): an arbitrary permutation, left moves L5 /
+    L10 (last 5 / 10 axes fixed), right moves R5 / R10 (only the last 5 / 10
+    axes reordered), identity and full reversal.  GB/s = 16 x entries / time
+    (8 B read + 8 B written per entry); every result is checked bit for bit
+    (_permute_exact)."""
     rng = np.random.default_rng(7)
-    for m in (24, 26, 28):
-        x = torch.randn(1 << m, dtype=torch.complex64, device="cuda").view((2,) * m)
-        perm = list(rng.permutation(m))
-        for _ in range(3):
-            y = api.permute(x, perm)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 5
-        e0.record()
-        for _ in range(reps):
-            y = api.permute(x, perm)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        gbs = 16.0 * (1 << m) / (ms * 1e-3) / 1e9
-        out.append({"elements": 1 << m, "ms": round(ms, 4), "gbs": round(gbs, 1),
-                    "frac": round(gbs / peaks["hbm_gbs"], 3)})
-        del x, y
-    return out
+    hbm = peaks["hbm_gbs"]
+    sizes = []
+    exact_all = True
+    for m in range(20, 31):
+        x = torch.randn(1 << m, dtype=torch.complex64, device="cuda")
+        row = {"m": m}
+        for kind in ("binary", "dim16"):
+            if kind == "binary":
+                dims, n_perm = [2] * m, 8
+            else:
+                dims = [16] * (m // 4) + ([1 << (m % 4)] if m % 4 else [])
+                n_perm = 2
+            xv = x.view(*dims)
+            gbs = []
+            for _ in range(n_perm):
+                perm = [int(a) for a in rng.permutation(len(dims))]
+                ms, exact = _time_permute(api, torch, xv, perm)
+                exact_all &= exact
+                gbs.append(16.0 * (1 << m) / (ms * 1e-3) / 1e9)
+            row[kind] = {"perms": n_perm, "gbs_median": round(float(np.median(gbs)), 1),
+                         "gbs_min": round(float(np.min(gbs)), 1),
+                         "frac_median": round(float(np.median(gbs)) / hbm, 3)}
+        sizes.append(row)
+        del x
+        torch.cuda.empty_cache()
+    m = 25
+    x = torch.randn(1 << m, dtype=torch.complex64, device="cuda").view(*([2] * m))
+    specials = {
+        "arbitrary": [int(a) for a in rng.permutation(m)],
+        "L5": [int(a) for a in rng.permutation(m - 5)] + list(range(m - 5, m)),
+        "L10": [int(a) for a in rng.permutation(m - 10)] + list(range(m - 10, m)),
+        "R5": list(range(m - 5)) + [m - 5 + int(a) for a in rng.permutation(5)],
+        "R10": list(range(m - 10)) + [m - 10 + int(a) for a in rng.permutation(10)],
+        "identity": list(range(m)),
+        "reversal": list(range(m - 1, -1, -1)),
+    }
+    spec = {}
+    for name, perm in specials.items():
+        ms, exact = _time_permute(api, torch, x, perm)
+        exact_all &= exact
+        g = 16.0 * (1 << m) / (ms * 1e-3) / 1e9
+        spec[name] = {"ms": round(ms, 4), "gbs": round(g, 1), "frac": round(g / hbm, 3)}
+    del x
+    torch.cuda.empty_cache()
+    return {"sizes": sizes, "m25_binary": spec, "bit_exact": exact_all,
+            "peak": "measured hbm_gbs"}
 
 
 def rotation_batch_run(api, torch, precision, local):
@@ -280,9 +348,11 @@ def c4_subset(api, torch, precision, local):
     prob = c4_problem(0)
     bits = torch.from_numpy(random_bitstrings(prob.n, 1, 2000)).cuda()
     subset = [0, 1]
-    out = {"subset": "1 bitstring x slices 0,1 of 1024 (one AB, two ABD of 2^15 x 2^15 x 2^15)"}
+    out = {"subset": "1 bitstring x slices 0,1 of 1024 (one AB, two ABD of 2^15 x 2^15 x 2^15)",
+           "note": "plain bf16 (one product, 8-bit operands) is reported, not gated"}
     res = {}
-    for prec in (precision, "fp32"):
+    modes = [precision] + [m for m in ("fp16x3", "tf32x3", "bf16") if m != precision] + ["fp32"]
+    for prec in modes:
         plan = api.Plan(prob, prec, device=local)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -299,7 +369,37 @@ def c4_subset(api, torch, precision, local):
         del plan
         torch.cuda.empty_cache()
     out["speedup"] = out["fp32_ms"] / out[f"{precision}_ms"]
-    out[f"{precision}_err_vs_fp32"] = amp_error(res[precision], res["fp32"], prob.n, 2.0 / 1024)
+    for prec in modes[:-1]:
+        out[f"{prec}_err_vs_fp32"] = amp_error(res[prec], res["fp32"], prob.n, 2.0 / 1024)
+    return out
+
+
+def iswap_run(api, torch, precision, local):
+    """7x7 iSWAP circuit of depth 1+16+1 (2 bond bits per iSWAP: bond
+    dimension 16) against the CZ circuit of depth 1+32+1 with the same cuts
+    and ordering, 1 bitstring x 16 slices each: the paper's statement that
+    the iSWAP circuit costs what the CZ circuit of twice its depth costs,
+    measured."""
+    out = {"subset": "1 bitstring x slices 0..15 of 256"}
+    subset = list(range(16))
+    for name, prob in (("iswap_d16", c2_problem(0, t=16, two_qubit="ISWAP")), ("cz_d32", c2_problem(0))):
+        plan = api.Plan(prob, precision, device=local)
+        bits = torch.from_numpy(random_bitstrings(prob.n, 1, 4000)).cuda()
+        plan.amplitudes(bits, None, subset)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.amplitudes(bits, None, subset)
+        e1.record()
+        torch.cuda.synchronize()
+        plan.sync()
+        ms = e0.elapsed_time(e1)
+        cost = plan.cost(1, subset)
+        out[name] = {"ms": round(ms, 3), "cmacs": cost["cmacs"],
+                     "tflops_cgemm": round(cost["cmacs"] * 8 / (ms * 1e-3) / 1e12, 1)}
+        plan.close()
+    out["time_ratio"] = round(out["iswap_d16"]["ms"] / out["cz_d32"]["ms"], 3)
+    out["same_cmacs"] = out["iswap_d16"]["cmacs"] == out["cz_d32"]["cmacs"]
     return out
 
 
@@ -459,6 +559,7 @@ def run_ours(args):
         extras["permute"] = permute_sweep(api, torch, peaks)
         extras["rotation_batch"] = rotation_batch_run(api, torch, args.precision, local)
         extras["bris70_f001"] = bris70_run(api, torch, args.precision, local)
+        extras["grid7x7_iswap"] = iswap_run(api, torch, args.precision, local)
         if not args.no_c4:
             extras["grid7x7_d40"] = c4_subset(api, torch, args.precision, local)
         line.update(extras)

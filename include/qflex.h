@@ -145,6 +145,9 @@ typedef struct {
   int32_t bn;                /* tensor-core tile width (kernel 4) */
   int32_t a_direct, b_direct;/* operand read in place, without a permutation */
   int64_t runs;              /* executions in one call over n_bs bitstrings and the slices */
+  int32_t a_cached, b_cached;/* operand kept in its own buffer and permuted only when its
+                                source changes (it depends on fewer cuts than the step) */
+  int64_t a_builds, b_builds;/* operand permutations run in that call */
 } qflex_step_info;
 
 int32_t qflex_abi_version(void);

@@ -80,6 +80,7 @@ struct Ref {
 struct Operand {
   Ref ref;
   bool direct = false;      // consumed in place by the GEMM (FP32 path, already in matrix form)
+  int cache = -1;           // index of a dedicated operand buffer kept across executions, or -1
   bool pow2 = true;
   PermTile tile{};
   GatherDesc gather{};
@@ -152,10 +153,20 @@ struct qflex_plan_s {
   char* d_arena = nullptr;
   void* d_opA = nullptr;
   void* d_opB = nullptr;
+  // Operand caches: a permuted operand whose source depends on fewer cuts
+  // than its step keeps a dedicated buffer and is rebuilt only when its
+  // source changes (a new bitstring or a new value of one of its cuts);
+  // the state is reset at the start of every call.
+  struct OpCache { size_t off = 0; uint64_t dep = 0; };
+  std::vector<OpCache> opcache;
+  size_t opcache_bytes = 0;
+  char* d_opcache = nullptr;
+  std::vector<int64_t> oc_b;
+  std::vector<std::vector<int64_t>> oc_v;
   GridQubitMeta* d_gmeta = nullptr;
   int2* d_gops = nullptr;
   int32_t* d_status = nullptr;
-  unsigned* d_smax = nullptr;                  // fp16 operand scales: [0] A, [1] B
+  unsigned* d_smax = nullptr;                  // fp16 operand scales: [0] A, [1] B, [2 + c] cache c
   cudaStream_t last_stream = nullptr;
   // profiling: event pairs around launches
   // gradients (qflex_plan_enable_gradients)
@@ -204,6 +215,34 @@ namespace {
 size_t operand_bytes(const qflex_plan_s& p, bool tc, int64_t elems) {
   if (!tc) return size_t(elems) * 8;
   return size_t(elems) * 3 * p.nsplit * (p.tc_kind == 0 ? 4 : 2);
+}
+
+constexpr int kMaxOpCache = 32;                 // fp16 scale slots 2..33 of 64
+constexpr size_t kOpCacheMinBytes = size_t(16) << 20;
+
+// Buffer an operand is produced into (its cache, else the shared scratch).
+void* op_buf(const qflex_plan_s& p, const Operand& op, bool is_a) {
+  if (op.cache >= 0) return p.d_opcache + p.opcache[size_t(op.cache)].off;
+  return is_a ? p.d_opA : p.d_opB;
+}
+int op_slot(const Operand& op, bool is_a) { return op.cache >= 0 ? 2 + op.cache : (is_a ? 0 : 1); }
+
+// True when cache c already holds the operand for bitstring b and cut values
+// vals (same bitstring and same values of the cuts its source depends on);
+// otherwise records the new key and returns false.
+bool oc_hit(std::vector<int64_t>& ob, std::vector<std::vector<int64_t>>& ov, uint64_t dep, int c, int64_t b,
+            const std::vector<int64_t>& vals) {
+  bool same = ob[size_t(c)] == b;
+  for (size_t k = 0; same && k < vals.size(); ++k)
+    if (((dep >> k) & 1) && ov[size_t(c)][k] != vals[k]) same = false;
+  if (same) return true;
+  ob[size_t(c)] = b;
+  ov[size_t(c)] = vals;
+  return false;
+}
+void oc_reset(const qflex_plan_s& p, std::vector<int64_t>& ob, std::vector<std::vector<int64_t>>& ov) {
+  ob.assign(p.opcache.size(), -1);
+  ov.assign(p.opcache.size(), {});
 }
 
 // Permutation descriptors taking `r` to the row-major order `target`.
@@ -534,12 +573,26 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
     p.arena_bytes = std::max(p.arena_bytes, cur + need);
   }
   p.arena_bytes = std::max(p.arena_bytes, arena);
-  for (const Step& s : p.steps) {
-    if (!s.A.direct) p.opA_bytes = std::max(p.opA_bytes, operand_bytes(p, s.tc, s.M * s.K));
-    if (!s.B.direct) p.opB_bytes = std::max(p.opB_bytes, operand_bytes(p, s.tc, s.N * s.K));
+  for (Step& s : p.steps) {
+    for (int w = 0; w < 2; ++w) {
+      Operand& X = w == 0 ? s.A : s.B;
+      if (X.direct) continue;
+      const size_t bytes = operand_bytes(p, s.tc, (w == 0 ? s.M : s.N) * s.K);
+      const uint64_t d = X.ref.dep;
+      if ((d & ~s.dep) == 0 && d != s.dep && bytes >= kOpCacheMinBytes && int(p.opcache.size()) < kMaxOpCache) {
+        X.cache = int(p.opcache.size());
+        p.opcache.push_back({p.opcache_bytes, d});
+        p.opcache_bytes += align256(bytes);
+      } else if (w == 0) {
+        p.opA_bytes = std::max(p.opA_bytes, bytes);
+      } else {
+        p.opB_bytes = std::max(p.opB_bytes, bytes);
+      }
+    }
   }
   p.grid_bytes = align256(size_t(p.grid_elems) * 8);
   p.total_bytes = p.grid_bytes + align256(p.arena_bytes) + align256(p.opA_bytes) + align256(p.opB_bytes) +
+                  align256(p.opcache_bytes) +
                   align256(sizeof(GridQubitMeta) * n) + align256(sizeof(int2) * std::max<size_t>(1, p.gops.size())) +
                   512;
   return QFLEX_OK;
@@ -561,6 +614,8 @@ qflex_status allocate(qflex_plan_s& p) {
   c += align256(p.opA_bytes);
   p.d_opB = c;
   c += align256(p.opB_bytes);
+  p.d_opcache = c;
+  c += align256(p.opcache_bytes);
   p.d_gmeta = reinterpret_cast<GridQubitMeta*>(c);
   c += align256(sizeof(GridQubitMeta) * p.n);
   p.d_gops = reinterpret_cast<int2*>(c);
@@ -573,7 +628,8 @@ qflex_status allocate(qflex_plan_s& p) {
   QF_CUDA(cudaMemset(p.d_status, 0, sizeof(int32_t)));
   for (Step& s : p.steps) {
     if (!s.tc) continue;
-    if (!tc_encode_maps(p.tc_kind, p.nsplit, s.bn, p.d_opA, s.M, p.d_opB, s.N, s.K, &s.maps))
+    if (!tc_encode_maps(p.tc_kind, p.nsplit, s.bn, op_buf(p, s.A, true), s.M, op_buf(p, s.B, false), s.N, s.K,
+                        &s.maps))
       return fail(QFLEX_ERR_CUDA, "tensor map encoding failed (driver entry point missing?)");
   }
   return QFLEX_OK;
@@ -644,7 +700,7 @@ cudaError_t timed(qflex_plan_s& p, int cls, double flops, double mma, double byt
   return cudaEventRecord(p.ev_pool[i + 1], s);
 }
 
-cudaError_t run_step(qflex_plan_s& p, const Step& st, const std::vector<int64_t>& vals,
+cudaError_t run_step(qflex_plan_s& p, const Step& st, int64_t b, const std::vector<int64_t>& vals,
                      cudaStream_t s) {
   cudaError_t e;
   const double out_per = st.tc ? 3.0 * p.nsplit * (p.tc_kind == 0 ? 4 : 2) : 8.0;
@@ -653,18 +709,24 @@ cudaError_t run_step(qflex_plan_s& p, const Step& st, const std::vector<int64_t>
   if (st.A.direct) {
     A = ref_ptr(p, st.A.ref);
   } else {
-    if ((e = timed(p, 1, 0, 0, double(st.M) * st.K * (8.0 + out_per), s,
-                   [&] { return produce(p, st.A, st.tc, st.M, st.K, vals, p.d_opA, s, 0); })) != cudaSuccess)
+    void* buf = op_buf(p, st.A, true);
+    const bool hit = st.A.cache >= 0 && oc_hit(p.oc_b, p.oc_v, p.opcache[size_t(st.A.cache)].dep, st.A.cache, b, vals);
+    if (!hit && (e = timed(p, 1, 0, 0, double(st.M) * st.K * (8.0 + out_per), s, [&] {
+                   return produce(p, st.A, st.tc, st.M, st.K, vals, buf, s, op_slot(st.A, true));
+                 })) != cudaSuccess)
       return e;
-    A = static_cast<const float2*>(p.d_opA);
+    A = static_cast<const float2*>(buf);
   }
   if (st.B.direct) {
     B = ref_ptr(p, st.B.ref);
   } else {
-    if ((e = timed(p, 1, 0, 0, double(st.N) * st.K * (8.0 + out_per), s,
-                   [&] { return produce(p, st.B, st.tc, st.N, st.K, vals, p.d_opB, s, 1); })) != cudaSuccess)
+    void* buf = op_buf(p, st.B, false);
+    const bool hit = st.B.cache >= 0 && oc_hit(p.oc_b, p.oc_v, p.opcache[size_t(st.B.cache)].dep, st.B.cache, b, vals);
+    if (!hit && (e = timed(p, 1, 0, 0, double(st.N) * st.K * (8.0 + out_per), s, [&] {
+                   return produce(p, st.B, st.tc, st.N, st.K, vals, buf, s, op_slot(st.B, false));
+                 })) != cudaSuccess)
       return e;
-    B = static_cast<const float2*>(p.d_opB);
+    B = static_cast<const float2*>(buf);
   }
   float2* C = reinterpret_cast<float2*>(buf_ptr(p, st.out_buf));
   const double mnk = double(st.M) * double(st.N) * double(st.K);
@@ -673,7 +735,8 @@ cudaError_t run_step(qflex_plan_s& p, const Step& st, const std::vector<int64_t>
   if (st.tc)
     return timed(p, 3, 8.0 * mnk, mma, gbytes, s, [&] {
       return launch_cgemm_tc(p.tc_kind, p.nsplit, st.bn, st.maps, st.M, st.N, st.K, C, p.d_status, s,
-                             p.tc_kind == 2 ? p.d_smax : nullptr, p.tc_kind == 2 ? p.d_smax + 1 : nullptr);
+                             p.tc_kind == 2 ? p.d_smax + op_slot(st.A, true) : nullptr,
+                             p.tc_kind == 2 ? p.d_smax + op_slot(st.B, false) : nullptr);
     });
   const bool thin = st.fp32_kernel == 1 || (st.fp32_kernel == 0 && st.N <= 32);
   return timed(p, 2, 8.0 * mnk, 0, gbytes, s, [&] {
@@ -1007,7 +1070,10 @@ qflex_status qflex_plan_cost(qflex_plan p, int64_t n_bs, const int64_t* ids, int
   if (qflex_status st = check_slices(*p, ids, n_ids)) return st;
   qflex_cost c{};
   const double prods = p->nsplit == 2 ? 3.0 : 1.0;
-  qflex_status st = walk(*p, n_bs, ids, n_ids, [&](int i, int64_t, const std::vector<int64_t>&) {
+  std::vector<int64_t> ob;
+  std::vector<std::vector<int64_t>> ov;
+  oc_reset(*p, ob, ov);
+  qflex_status st = walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) {
     if (i < 0) {
       ++c.launches;
       return QFLEX_OK;
@@ -1020,9 +1086,15 @@ qflex_status qflex_plan_cost(qflex_plan p, int64_t n_bs, const int64_t* ids, int
       c.tc_cmacs += mnk;
       c.tc_mma_flops += mnk * 3.0 * prods * 2.0;
     }
-    if (!s.A.direct) c.permute_bytes += 16.0 * double(s.M) * double(s.K);
-    if (!s.B.direct) c.permute_bytes += 16.0 * double(s.N) * double(s.K);
-    c.launches += 1 + !s.A.direct + !s.B.direct + (s.tc && p->tc_kind == 2 ? 2 : 0);
+    // operand producers that run (not in place, not a cache hit): one
+    // permutation each, plus the absmax of an fp16 operand
+    const bool runA = !s.A.direct && !(s.A.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.A.cache)].dep,
+                                                                 s.A.cache, b, vals));
+    const bool runB = !s.B.direct && !(s.B.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.B.cache)].dep,
+                                                                 s.B.cache, b, vals));
+    if (runA) c.permute_bytes += 16.0 * double(s.M) * double(s.K);
+    if (runB) c.permute_bytes += 16.0 * double(s.N) * double(s.K);
+    c.launches += 1 + runA + runB + (s.tc && p->tc_kind == 2 ? int(runA) + int(runB) : 0);
     ++c.steps_executed;
     return QFLEX_OK;
   });
@@ -1035,9 +1107,18 @@ qflex_status qflex_plan_steps(qflex_plan p, int64_t n_bs, const int64_t* ids, in
                               int32_t cap, int32_t* n_steps) {
   if (!p || !n_steps || n_bs < 0 || cap < 0 || (cap > 0 && !out)) return fail(QFLEX_ERR_ARG, "bad argument");
   if (qflex_status st = check_slices(*p, ids, n_ids)) return st;
-  std::vector<int64_t> runs(p->steps.size(), 0);
-  qflex_status st = walk(*p, n_bs, ids, n_ids, [&](int i, int64_t, const std::vector<int64_t>&) {
-    if (i >= 0) ++runs[size_t(i)];
+  std::vector<int64_t> runs(p->steps.size(), 0), ab(p->steps.size(), 0), bb(p->steps.size(), 0);
+  std::vector<int64_t> ob;
+  std::vector<std::vector<int64_t>> ov;
+  oc_reset(*p, ob, ov);
+  qflex_status st = walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) {
+    if (i < 0) return QFLEX_OK;
+    const Step& s = p->steps[size_t(i)];
+    ++runs[size_t(i)];
+    ab[size_t(i)] += !s.A.direct && !(s.A.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.A.cache)].dep,
+                                                                 s.A.cache, b, vals));
+    bb[size_t(i)] += !s.B.direct && !(s.B.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.B.cache)].dep,
+                                                                 s.B.cache, b, vals));
     return QFLEX_OK;
   });
   if (st) return st;
@@ -1063,6 +1144,10 @@ qflex_status qflex_plan_steps(qflex_plan p, int64_t n_bs, const int64_t* ids, in
     o.a_direct = s.A.direct;
     o.b_direct = s.B.direct;
     o.runs = runs[size_t(i)];
+    o.a_cached = s.A.cache >= 0;
+    o.b_cached = s.B.cache >= 0;
+    o.a_builds = ab[size_t(i)];
+    o.b_builds = bb[size_t(i)];
   }
   return QFLEX_OK;
 }
@@ -1114,6 +1199,7 @@ qflex_status qflex_amplitudes(qflex_plan p, const double* angles, const uint8_t*
   if (ids) key.ids.assign(ids, ids + n_ids);
   return with_graph(*p, key, s, [&]() -> qflex_status {
     QF_CUDA(cudaMemsetAsync(amps, 0, size_t(n_bs) * T * 2 * sizeof(double), s));
+    oc_reset(*p, p->oc_b, p->oc_v);
     return walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) -> qflex_status {
       cudaError_t e;
       if (i == -2) {
@@ -1126,7 +1212,7 @@ qflex_status qflex_amplitudes(qflex_plan p, const double* angles, const uint8_t*
           return launch_slicesum(src, p->final_strides.data(), int(p->tile.size()), amps + b * T * 2, s);
         });
       } else {
-        e = run_step(*p, p->steps[i], vals, s);
+        e = run_step(*p, p->steps[i], b, vals, s);
       }
       if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
       return QFLEX_OK;
@@ -1176,6 +1262,7 @@ qflex_status qflex_amplitudes_grad(qflex_plan p, const double* angles, const uin
   qflex_status res = with_graph(*p, key, s, [&]() -> qflex_status {
   QF_CUDA(cudaMemsetAsync(amps, 0, size_t(n_bs) * T * 2 * sizeof(double), s));
   if (p->n_params > 0) QF_CUDA(cudaMemsetAsync(grad, 0, size_t(p->n_params) * sizeof(double), s));
+  oc_reset(*p, p->oc_b, p->oc_v);
   qflex_status res = walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) -> qflex_status {
     cudaError_t e = cudaSuccess;
     if (i == -2) {
@@ -1197,7 +1284,7 @@ qflex_status qflex_amplitudes_grad(qflex_plan p, const double* angles, const uin
         if (e == cudaSuccess) e = run_bwd(*p, p->steps[k], p->sg[k].gb, vals, s);
       }
     } else {
-      e = run_step(*p, p->steps[i], vals, s);
+      e = run_step(*p, p->steps[i], b, vals, s);
     }
     if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
     return QFLEX_OK;
@@ -1249,18 +1336,20 @@ qflex_status qflex_plan_autotune(qflex_plan p, int32_t reps, int32_t* n_shapes, 
     float best = 1e30f, first = 0.f;
     int best_c = -1;
     for (size_t c = 0; c < cands.size(); ++c) {
-      if (key.tc && !tc_encode_maps(p->tc_kind, p->nsplit, cands[c], p->d_opA, st.M, p->d_opB, st.N, st.K, &maps[c])) {
+      if (key.tc && !tc_encode_maps(p->tc_kind, p->nsplit, cands[c], op_buf(*p, st.A, true), st.M,
+                                    op_buf(*p, st.B, false), st.N, st.K, &maps[c])) {
         res = fail(QFLEX_ERR_CUDA, "tensor map encoding failed");
         break;
       }
       auto launch = [&]() -> cudaError_t {
         if (key.tc)
           return launch_cgemm_tc(p->tc_kind, p->nsplit, cands[c], maps[c], st.M, st.N, st.K, C, p->d_status, s,
-                                 p->tc_kind == 2 ? p->d_smax : nullptr, p->tc_kind == 2 ? p->d_smax + 1 : nullptr);
+                                 p->tc_kind == 2 ? p->d_smax + op_slot(st.A, true) : nullptr,
+                                 p->tc_kind == 2 ? p->d_smax + op_slot(st.B, false) : nullptr);
         // operands as the step reads them: in place when consumed directly
-        // (the scratch is only sized for produced operands), else the scratch
-        const float2* A = st.A.direct ? ref_ptr(*p, st.A.ref) : static_cast<const float2*>(p->d_opA);
-        const float2* B = st.B.direct ? ref_ptr(*p, st.B.ref) : static_cast<const float2*>(p->d_opB);
+        // (the scratch is only sized for produced operands), else their buffer
+        const float2* A = st.A.direct ? ref_ptr(*p, st.A.ref) : static_cast<const float2*>(op_buf(*p, st.A, true));
+        const float2* B = st.B.direct ? ref_ptr(*p, st.B.ref) : static_cast<const float2*>(op_buf(*p, st.B, false));
         return cands[c] == 1 ? launch_cgemm_thin(st.M, st.N, st.K, A, B, C, s)
                              : launch_cgemm_simt(st.M, st.N, st.K, A, B, C, s);
       };
@@ -1288,8 +1377,13 @@ qflex_status qflex_plan_autotune(qflex_plan p, int32_t reps, int32_t* n_shapes, 
     for (size_t i : idx) {
       Step& t = p->steps[i];
       if (key.tc) {
+        // steps of one shape may read different operand buffers (caches)
         t.bn = cands[best_c];
-        t.maps = maps[best_c];
+        if (!tc_encode_maps(p->tc_kind, p->nsplit, t.bn, op_buf(*p, t.A, true), t.M, op_buf(*p, t.B, false), t.N,
+                            t.K, &t.maps)) {
+          res = fail(QFLEX_ERR_CUDA, "tensor map encoding failed");
+          break;
+        }
       } else {
         t.fp32_kernel = cands[best_c];
       }

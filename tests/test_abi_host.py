@@ -184,7 +184,13 @@ def test_plan_steps_agree_with_cost(Plan):
         assert sum(s["M"] * s["N"] * s["K"] * s["runs"] for s in steps) == c["cmacs"]
         assert sum(s["M"] * s["N"] * s["K"] * s["runs"] for s in steps
                    if s["kernel"] == "tensor_cores") == c["tc_cmacs"]
+        assert sum(16 * (s["a_builds"] * s["M"] + s["b_builds"] * s["N"]) * s["K"]
+                   for s in steps) == c["permute_bytes"]
     big = [s for s in p.steps(1) if (s["M"], s["N"], s["K"]) == (4096, 4096, 4096)]
     assert sorted(s["runs"] for s in big) == [16, 256]
     assert all(s["kernel"] == "tensor_cores" for s in big)
+    # AB (changes once per right-cut value) feeds the per-slice ABD product:
+    # its operand planes are kept and rebuilt 16 times, not 256
+    abd = [s for s in big if s["runs"] == 256][0]
+    assert abd["a_cached"] and abd["a_builds"] == 16 and abd["b_builds"] == 256
     assert all(s["kernel"] != "tensor_cores" for s in Plan(c2_problem(0), "fp32", device=-1).steps(1))
