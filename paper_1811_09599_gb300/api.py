@@ -217,13 +217,16 @@ class QFlexAmplitudes(torch.autograd.Function):
 
 
 # ---------------------------------------------------------------------- kernels
-def permute(x: torch.Tensor, perm: Sequence[int], stream=None) -> torch.Tensor:
+def permute(x: torch.Tensor, perm: Sequence[int], stream=None, out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """qflex_permute: out axis i = in axis perm[i] (complex64, bit-exact)."""
     lib = _lib.load()
     assert x.dtype == torch.complex64 and x.is_cuda and x.is_contiguous()
     dims = np.asarray(x.shape, dtype=np.int64)
     p = np.asarray(perm, dtype=np.int32)
-    out = torch.empty([x.shape[i] for i in perm], dtype=x.dtype, device=x.device)
+    shape = [x.shape[i] for i in perm]
+    if out is None:
+        out = torch.empty(shape, dtype=x.dtype, device=x.device)
+    assert out.dtype == x.dtype and out.is_contiguous() and list(out.shape) == shape
     check(lib.qflex_permute(C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), x.dim(),
                             dims.ctypes.data_as(C.POINTER(C.c_int64)),
                             p.ctypes.data_as(C.POINTER(C.c_int32)), _stream_handle(stream)))

@@ -267,11 +267,23 @@ __global__ void k_permute_gather(const float2* __restrict__ in, int64_t in_base,
   }
 }
 
+// Grid of a grid-stride kernel: every block resident at once (SMs x the
+// kernel's occupancy at 256 threads), so the loop shares the work evenly
+// instead of leaving a partial second wave; fewer blocks for small inputs.
+template <auto Kern>
 int grid_for(int64_t work_units) {
+  static const int occ = [] {
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, Kern, 256, 0) != cudaSuccess || v < 1) {
+      cudaGetLastError();
+      v = 1;
+    }
+    return v;
+  }();
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t cap = int64_t(sms) * 8;
+  const int64_t cap = int64_t(sms) * occ;
   return int(std::max<int64_t>(1, std::min<int64_t>(cap, work_units)));
 }
 
@@ -280,28 +292,32 @@ int grid_for(int64_t work_units) {
 cudaError_t launch_permute_tiled(const float2* in, int64_t in_base, const PermTile& t, int fmt,
                                  int nsplit, void* out, int64_t plane, cudaStream_t s,
                                  const unsigned* smax) {
-  const int blocks = grid_for(t.n_tiles);
+#define QF_TILED(F) k_permute_tiled<F><<<grid_for<k_permute_tiled<F>>(t.n_tiles), 256, 0, s>>>( \
+    in, in_base, t, out, nsplit, plane, smax)
   switch (fmt) {
-    case kFmtC64: k_permute_tiled<kFmtC64><<<blocks, 256, 0, s>>>(in, in_base, t, out, nsplit, plane, smax); break;
-    case kFmtTF32: k_permute_tiled<kFmtTF32><<<blocks, 256, 0, s>>>(in, in_base, t, out, nsplit, plane, smax); break;
-    case kFmtAccC128: k_permute_tiled<kFmtAccC128><<<blocks, 256, 0, s>>>(in, in_base, t, out, nsplit, plane, smax); break;
-    case kFmtFP16: k_permute_tiled<kFmtFP16><<<blocks, 256, 0, s>>>(in, in_base, t, out, nsplit, plane, smax); break;
-    default: k_permute_tiled<kFmtBF16><<<blocks, 256, 0, s>>>(in, in_base, t, out, nsplit, plane, smax); break;
+    case kFmtC64: QF_TILED(kFmtC64); break;
+    case kFmtTF32: QF_TILED(kFmtTF32); break;
+    case kFmtAccC128: QF_TILED(kFmtAccC128); break;
+    case kFmtFP16: QF_TILED(kFmtFP16); break;
+    default: QF_TILED(kFmtBF16); break;
   }
+#undef QF_TILED
   return cudaGetLastError();
 }
 
 cudaError_t launch_permute_gather(const float2* in, int64_t in_base, const GatherDesc& d, int fmt,
                                   int nsplit, void* out, int64_t plane, cudaStream_t s,
                                   const unsigned* smax) {
-  const int blocks = grid_for((d.total + 255) / 256);
+#define QF_GATHER(F) k_permute_gather<F><<<grid_for<k_permute_gather<F>>((d.total + 255) / 256), 256, 0, s>>>( \
+    in, in_base, d, out, nsplit, plane, smax)
   switch (fmt) {
-    case kFmtC64: k_permute_gather<kFmtC64><<<blocks, 256, 0, s>>>(in, in_base, d, out, nsplit, plane, smax); break;
-    case kFmtTF32: k_permute_gather<kFmtTF32><<<blocks, 256, 0, s>>>(in, in_base, d, out, nsplit, plane, smax); break;
-    case kFmtAccC128: k_permute_gather<kFmtAccC128><<<blocks, 256, 0, s>>>(in, in_base, d, out, nsplit, plane, smax); break;
-    case kFmtFP16: k_permute_gather<kFmtFP16><<<blocks, 256, 0, s>>>(in, in_base, d, out, nsplit, plane, smax); break;
-    default: k_permute_gather<kFmtBF16><<<blocks, 256, 0, s>>>(in, in_base, d, out, nsplit, plane, smax); break;
+    case kFmtC64: QF_GATHER(kFmtC64); break;
+    case kFmtTF32: QF_GATHER(kFmtTF32); break;
+    case kFmtAccC128: QF_GATHER(kFmtAccC128); break;
+    case kFmtFP16: QF_GATHER(kFmtFP16); break;
+    default: QF_GATHER(kFmtBF16); break;
   }
+#undef QF_GATHER
   return cudaGetLastError();
 }
 
