@@ -104,7 +104,8 @@ typedef struct {
 
 typedef struct {
   const qflex_circuit* circuit;
-  const qflex_ordering* ordering; /* NULL: absorb every qubit into qubit 0 in id order */
+  const qflex_ordering* ordering; /* NULL: qflex_search_ordering for these cuts, no cuts
+                                     added, 32 trials, seed 0, limit 2^28 entries */
   const int32_t* cut_edges;       /* host, indices into circuit->edges; first = most
                                      significant digit of the slice id */
   int32_t n_cuts;
@@ -180,6 +181,35 @@ qflex_status qflex_plan_cost(qflex_plan plan, int64_t n_bs, const int64_t* slice
  * NULL = all): out[i] for i < min(cap, n_steps); *n_steps = number of steps. */
 qflex_status qflex_plan_steps(qflex_plan plan, int64_t n_bs, const int64_t* slice_ids, int64_t n_slice_ids,
                               qflex_step_info* out, int32_t cap, int32_t* n_steps);
+
+/* Automated cut and ordering search (the paper picks both by hand per
+ * lattice: Methods "Cutting indexes", "Contraction of the 3D tensor network";
+ * SI A).  Ordering: randomized greedy over the per-slice network (cut bonds
+ * removed), best of `trials` passes: each step contracts the pair of live
+ * tensors sharing a bond with the smallest log2(result) - alpha log2(larger
+ * input) + tau * Gumbel noise (pass 0: alpha = 1, tau = 0; the others draw
+ * alpha in [0, 1.5], tau in [0, 1] from SplitMix64(seed)); the larger tensor
+ * keeps its id; passes rank by the excess of their largest tensor over the
+ * limit, then by work.  Cuts: starting from `cut_edges` (kept, in order), up to
+ * `max_new_cuts` bonds are appended, each the one whose cut gives the
+ * smallest largest tensor (ties: least work per bitstring), until the largest
+ * tensor has at most max_tensor_elems entries.  Work counts each step as
+ * often as the executor runs it (once per change of the cuts it depends on).
+ * circuit/open_tile/cut_edges: host, as in qflex_problem.  cuts_out: host,
+ * capacity n_cuts + max_new_cuts; steps_out: host, capacity 2 (n_qubits - 1)
+ * (dst, src) pairs, usable as a qflex_ordering.  Returns QFLEX_ERR_PLAN (with
+ * the best result written) when the limit is not met. */
+typedef struct {
+  double log2_max_tensor;      /* log2 entries of the largest tensor */
+  double cmacs_per_bitstring;  /* complex MACs of one bitstring over all slices, with reuse */
+  double n_slices;
+  int32_t n_cuts;
+  int32_t n_steps;
+} qflex_search_result;
+qflex_status qflex_search_ordering(const qflex_circuit* circuit, const int32_t* open_tile, int32_t n_open,
+                                   const int32_t* cut_edges, int32_t n_cuts, int32_t max_new_cuts,
+                                   int64_t max_tensor_elems, int32_t trials, uint64_t seed, int32_t* cuts_out,
+                                   int32_t* steps_out, qflex_search_result* out);
 
 qflex_status qflex_select_slices(qflex_plan plan, double fidelity, uint64_t seed,
                                  int64_t* slice_ids, int64_t capacity, int64_t* n_selected);

@@ -64,6 +64,11 @@ class StepInfo(C.Structure):
                 ("b_cached", C.c_int32), ("a_builds", C.c_int64), ("b_builds", C.c_int64)]
 
 
+class SearchResult(C.Structure):
+    _fields_ = [("log2_max_tensor", C.c_double), ("cmacs_per_bitstring", C.c_double),
+                ("n_slices", C.c_double), ("n_cuts", C.c_int32), ("n_steps", C.c_int32)]
+
+
 class Profile(C.Structure):
     _fields_ = [("launches", C.c_int64 * 5), ("ms", C.c_double * 5), ("flops", C.c_double * 5),
                 ("mma_flops", C.c_double * 5), ("bytes", C.c_double * 5)]
@@ -108,6 +113,9 @@ SIGNATURES = [
                                          C.c_void_p, C.POINTER(C.c_int64), C.c_void_p]),
     ("qflex_plan_steps", C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_int64,
                                    C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
+    ("qflex_search_ordering", C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32),
+                                        C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.c_uint64,
+                                        C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_void_p]),
     ("qflex_device_status", C.c_int, [C.c_int, C.POINTER(C.c_int32)]),
     ("qflex_cgemm_noalloc", C.c_int, [C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p]),

@@ -28,6 +28,45 @@ def _i64_array(values):
     return arr, int(arr.size)
 
 
+def _circuit_struct(circ, keep: list):
+    edges = np.ascontiguousarray(circ.edge_array().reshape(-1), dtype=np.int32)
+    garr = circ.gate_array()
+    gates = (_lib.Gate * max(1, len(garr)))()
+    for i, row in enumerate(garr):
+        gates[i] = _lib.Gate(*[int(v) for v in row])
+    keep += [edges, gates]
+    return _lib.Circuit(circ.n, edges.ctypes.data_as(C.POINTER(C.c_int32)), len(circ.edges), gates, len(garr),
+                        circ.n_params)
+
+
+def search_ordering(problem, max_tensor_elems: int, max_new_cuts: int = 0, trials: int = 32,
+                    seed: int = 0) -> dict:
+    """qflex_search_ordering: greedy ordering (and up to max_new_cuts extra
+    cuts after problem.cut_edges) whose largest tensor has at most
+    max_tensor_elems entries.  Returns cuts, ordering ((dst, src) pairs),
+    log2_max_tensor, cmacs_per_bitstring, n_slices and `fits`."""
+    lib = _lib.load()
+    keep: list = []
+    circ = _circuit_struct(problem.circuit, keep)
+    tile = np.ascontiguousarray(np.asarray(problem.open_tile, dtype=np.int32).reshape(-1))
+    cuts = np.ascontiguousarray(np.asarray(problem.cut_edges, dtype=np.int32).reshape(-1))
+    cuts_out = np.zeros(max(1, cuts.size + max_new_cuts), dtype=np.int32)
+    steps = np.zeros(max(1, 2 * (problem.circuit.n - 1)), dtype=np.int32)
+    res = _lib.SearchResult()
+    st = lib.qflex_search_ordering(C.byref(circ), tile.ctypes.data_as(C.POINTER(C.c_int32)), int(tile.size),
+                                   cuts.ctypes.data_as(C.POINTER(C.c_int32)), int(cuts.size), int(max_new_cuts),
+                                   int(max_tensor_elems), int(trials), C.c_uint64(seed),
+                                   cuts_out.ctypes.data_as(C.POINTER(C.c_int32)),
+                                   steps.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(res))
+    if st not in (0, 3):                       # QFLEX_ERR_PLAN: best result written, limit not met
+        check(st)
+    n = problem.circuit.n
+    return {"cuts": [int(v) for v in cuts_out[: res.n_cuts]],
+            "ordering": [(int(steps[2 * i]), int(steps[2 * i + 1])) for i in range(n - 1)],
+            "log2_max_tensor": res.log2_max_tensor, "cmacs_per_bitstring": res.cmacs_per_bitstring,
+            "n_slices": res.n_slices, "fits": st == 0}
+
+
 class Plan:
     """qflex_plan for one problem (circuit, ordering, cuts, open tile).
 
@@ -43,14 +82,8 @@ class Plan:
         self.n_params = circ.n_params
         self.precision = precision
         self.device = device
-        edges = np.ascontiguousarray(circ.edge_array().reshape(-1), dtype=np.int32)
-        garr = circ.gate_array()
-        gates = (_lib.Gate * max(1, len(garr)))()
-        for i, row in enumerate(garr):
-            gates[i] = _lib.Gate(*[int(v) for v in row])
-        self._keep = [edges, gates]
-        self._circ = _lib.Circuit(circ.n, edges.ctypes.data_as(C.POINTER(C.c_int32)),
-                                  len(circ.edges), gates, len(garr), circ.n_params)
+        self._keep = []
+        self._circ = _circuit_struct(circ, self._keep)
         ordering = None
         if problem.ordering is not None:
             st = np.ascontiguousarray(np.asarray(problem.ordering, dtype=np.int32).reshape(-1))

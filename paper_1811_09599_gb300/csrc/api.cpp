@@ -32,6 +32,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "search.h"
 
 using namespace qflex;
 
@@ -447,10 +448,15 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
     steps = pr->ordering->steps;
     ns = pr->ordering->n_steps;
   } else {
-    for (int q = 1; q < n; ++q) {
-      def.push_back(0);
-      def.push_back(q);
-    }
+    SearchNet net;
+    net.n = n;
+    for (int e = 0; e < E; ++e) net.edges.push_back(ed[size_t(e)]);
+    net.bits = p.K;
+    net.open.assign(size_t(n), 0);
+    for (int q : p.tile) net.open[size_t(q)] = 1;
+    SearchResult sr;
+    if (!search_greedy_order(net, p.cuts, &sr, 32, 28.0, 0)) return fail(QFLEX_ERR_PLAN, "ordering search failed");
+    def = sr.steps;
     steps = def.data();
     ns = n - 1;
   }
@@ -1149,6 +1155,62 @@ qflex_status qflex_plan_steps(qflex_plan p, int64_t n_bs, const int64_t* ids, in
     o.a_builds = ab[size_t(i)];
     o.b_builds = bb[size_t(i)];
   }
+  return QFLEX_OK;
+}
+
+qflex_status qflex_search_ordering(const qflex_circuit* c, const int32_t* tile, int32_t n_open, const int32_t* cut_edges,
+                                   int32_t n_cuts, int32_t max_new_cuts, int64_t max_tensor_elems, int32_t trials,
+                                   uint64_t seed, int32_t* cuts_out, int32_t* steps_out, qflex_search_result* out) {
+  if (!c || !out || !steps_out || n_open < 0 || n_cuts < 0 || max_new_cuts < 0 || max_tensor_elems < 1 ||
+      trials < 1 || trials > 4096 ||
+      (n_open > 0 && !tile) || (n_cuts > 0 && !cut_edges) || (n_cuts + max_new_cuts > 0 && !cuts_out) ||
+      n_cuts + max_new_cuts > 64)
+    return fail(QFLEX_ERR_ARG, "bad search arguments");
+  const int n = c->n_qubits, E = c->n_edges;
+  if (n < 1 || E < 0 || (E > 0 && !c->edges) || c->n_gates < 0 || (c->n_gates > 0 && !c->gates))
+    return fail(QFLEX_ERR_CIRCUIT, "bad circuit");
+  SearchNet net;
+  net.n = n;
+  std::map<std::pair<int, int>, int> index;
+  for (int e = 0; e < E; ++e) {
+    const int a = c->edges[2 * e], b = c->edges[2 * e + 1];
+    if (a < 0 || b < 0 || a >= n || b >= n || a == b) return fail(QFLEX_ERR_CIRCUIT, "bad edge");
+    const auto key = std::make_pair(std::min(a, b), std::max(a, b));
+    if (index.count(key)) return fail(QFLEX_ERR_CIRCUIT, "repeated edge");
+    index[key] = e;
+    net.edges.push_back(key);
+  }
+  net.bits.assign(size_t(E), 0);
+  for (int64_t i = 0; i < c->n_gates; ++i) {
+    const qflex_gate& g = c->gates[i];
+    if (g.kind != QFLEX_GATE_CZ && g.kind != QFLEX_GATE_ISWAP) continue;
+    auto it = index.find(std::make_pair(std::min(g.q0, g.q1), std::max(g.q0, g.q1)));
+    if (it == index.end()) return fail(QFLEX_ERR_CIRCUIT, "two-qubit gate on a pair that is not a lattice edge");
+    net.bits[size_t(it->second)] += g.kind == QFLEX_GATE_ISWAP ? 2 : 1;
+  }
+  net.open.assign(size_t(n), 0);
+  for (int t = 0; t < n_open; ++t) {
+    if (tile[t] < 0 || tile[t] >= n || net.open[size_t(tile[t])]) return fail(QFLEX_ERR_ARG, "bad tile qubit");
+    net.open[size_t(tile[t])] = 1;
+  }
+  std::vector<int> cuts(cut_edges, cut_edges + n_cuts);
+  for (int e : cuts)
+    if (e < 0 || e >= E || std::count(cuts.begin(), cuts.end(), e) > 1) return fail(QFLEX_ERR_ARG, "bad cut edge");
+  std::vector<int> found;
+  SearchResult r;
+  const bool fits = search_cuts(net, cuts, max_new_cuts, std::log2(double(max_tensor_elems)), &found, &r, trials,
+                                seed);
+  if (r.steps.size() != size_t(2 * (n - 1))) return fail(QFLEX_ERR_PLAN, "search failed");
+  std::copy(found.begin(), found.end(), cuts_out);
+  std::copy(r.steps.begin(), r.steps.end(), steps_out);
+  out->log2_max_tensor = r.log2_max;
+  out->cmacs_per_bitstring = r.cmacs;
+  out->n_slices = r.n_slices;
+  out->n_cuts = int32_t(found.size());
+  out->n_steps = n - 1;
+  if (!fits)
+    return fail(QFLEX_ERR_PLAN, "no ordering with at most " + std::to_string(max_tensor_elems) +
+                                    " entries per tensor within " + std::to_string(max_new_cuts) + " new cuts");
   return QFLEX_OK;
 }
 

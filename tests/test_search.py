@@ -1,0 +1,141 @@
+"""Automated cut and ordering search (qflex_search_ordering), on the host.
+
+The paper picks cuts and contraction orders by hand (Methods, "Cutting
+indexes"; SI A).  The search must (a) return valid orderings that the
+planner accepts, (b) estimate the work exactly as the executor counts it
+(steps rerun only when a cut they depend on changes), (c) reach the exact
+optimum of its move set on networks small enough for brute force, and
+(d) find, for the 7x7 depth 1+32+1 grid, a configuration of the paper's
+size class: two cuts (256 paths) and tensors of at most 2^24 entries.
+"""
+import functools
+import math
+
+import pytest
+
+from qflex_inputs import c2_problem, diamond_problem, grid_lattice, grid_problem, random_circuit
+from qflex_inputs.circuits import two_qubit_counts
+from qflex_inputs.problems import Problem
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1811_09599_gb300 import api
+    return api
+
+
+def _bits(circ):
+    """Bond bits per edge: 1 per CZ, 2 per iSWAP."""
+    bits = [0] * len(circ.edges)
+    idx = circ.lattice.edge_index
+    for g in circ.gates:
+        if g.kind in ("CZ", "ISWAP"):
+            bits[idx[(min(g.q0, g.q1), max(g.q0, g.q1))]] += 1 if g.kind == "CZ" else 2
+    return bits
+
+
+def brute_force_min_work(circ, tile, cuts):
+    """Least work over every sequence of contractions of tensors sharing a
+    bond, with each step weighted by how often the executor runs it (once per
+    change of the cuts it depends on, first cut most significant)."""
+    bits = _bits(circ)
+    n, E = circ.n, len(circ.edges)
+    radix = [2 ** bits[e] for e in cuts]
+
+    def legs_of(group):
+        legs = {}
+        for e, (a, b) in enumerate(circ.edges):
+            if bits[e] == 0 or e in cuts:
+                continue
+            ina, inb = a in group, b in group
+            if ina != inb:
+                legs[e] = bits[e]
+        for q in group:
+            if q in tile:
+                legs[E + q] = 1
+        return legs
+
+    def runs(group):
+        dep = [i for i, e in enumerate(cuts) if circ.edges[e][0] in group or circ.edges[e][1] in group]
+        return math.prod(radix[: max(dep) + 1]) if dep else 1
+
+    @functools.lru_cache(maxsize=None)
+    def best(state):
+        groups = list(state)
+        if len(groups) == 1:
+            return 0.0
+        out = math.inf
+        for i in range(len(groups)):
+            for j in range(i + 1, len(groups)):
+                la, lb = legs_of(groups[i]), legs_of(groups[j])
+                s = sum(v for k, v in la.items() if k in lb)
+                if s == 0:
+                    continue
+                merged = groups[i] | groups[j]
+                work = runs(merged) * 2.0 ** (sum(la.values()) + sum(lb.values()) - s)
+                rest = frozenset(g for k, g in enumerate(groups) if k not in (i, j)) | {merged}
+                out = min(out, work + best(rest))
+        return out
+
+    return best(frozenset(frozenset([q]) for q in range(n)))
+
+
+@pytest.mark.parametrize("rows,cols,t,tile,ncut", [(2, 3, 16, [5], 0), (3, 3, 16, [8], 1), (2, 4, 24, [6, 7], 1)])
+def test_search_reaches_brute_force_optimum(api, rows, cols, t, tile, ncut):
+    circ = random_circuit(grid_lattice(rows, cols), t, 3)
+    cuts = [len(circ.edges) // 2] if ncut else []
+    opt = brute_force_min_work(circ, tile, cuts)
+    r = api.search_ordering(Problem(circ, cuts, tile, None), 1 << 40, 0, trials=256, seed=1)
+    assert r["fits"]
+    assert r["cmacs_per_bitstring"] == pytest.approx(opt, rel=1e-12)
+
+
+def test_search_work_model_matches_planner(api):
+    """The search's work per bitstring equals the planner's cost replay of
+    the same cuts and ordering (same reuse rule)."""
+    from paper_1811_09599_gb300.api import Plan
+    p = grid_problem(4, 5, 24, 3, r0=2, c0=2, cuts=True, tile_rows=2, tile_cols=2)
+    r = api.search_ordering(Problem(p.circuit, p.cut_edges, p.open_tile, None), 1 << 20, 0, trials=16)
+    plan = Plan(Problem(p.circuit, r["cuts"], p.open_tile, r["ordering"]), "bf16x3", device=-1)
+    assert plan.cost(1)["cmacs"] == pytest.approx(r["cmacs_per_bitstring"], rel=1e-12)
+    assert math.log2(plan.info()["max_tensor_elems"]) <= r["log2_max_tensor"]
+
+
+def test_search_7x7_finds_two_cut_plan(api):
+    """7x7, 1+32+1, no cuts given, limit 2^24 entries: two cuts (256 paths)
+    suffice, as in the paper's hand plan, at no more than 1.25x its work."""
+    from paper_1811_09599_gb300.api import Plan
+    p = c2_problem(0)
+    r = api.search_ordering(Problem(p.circuit, [], p.open_tile, None), 1 << 24, 4, trials=32, seed=0)
+    assert r["fits"] and len(r["cuts"]) == 2 and r["n_slices"] == 256
+    assert r["log2_max_tensor"] <= 24
+    hand = Plan(p, "bf16x3", device=-1).cost(1)["cmacs"]
+    found = Plan(Problem(p.circuit, r["cuts"], p.open_tile, r["ordering"]), "bf16x3", device=-1)
+    assert found.info()["max_tensor_elems"] <= 1 << 24
+    assert found.cost(1)["cmacs"] <= 1.25 * hand
+    # deterministic for a given seed
+    again = api.search_ordering(Problem(p.circuit, [], p.open_tile, None), 1 << 24, 4, trials=32, seed=0)
+    assert again["cuts"] == r["cuts"] and again["ordering"] == r["ordering"]
+
+
+def test_search_bristlecone_70(api):
+    """Bris-70, 1+32+1, limit 2^28 entries: four cuts (2^16 paths) suffice,
+    the configuration the paper states for this lattice."""
+    d = diamond_problem(32, 0)
+    r = api.search_ordering(Problem(d.circuit, [], d.open_tile, None), 1 << 28, 5, trials=8, seed=0)
+    assert r["fits"] and len(r["cuts"]) == 4 and r["n_slices"] == 65536
+
+
+def test_search_limits_and_defaults(api):
+    from paper_1811_09599_gb300 import QFlexError
+    from paper_1811_09599_gb300.api import Plan
+    p = grid_problem(4, 4, 16, 1, r0=2, c0=2, cuts=False, tile_rows=1, tile_cols=2)
+    # an unreachable limit without new cuts: best effort returned, fits False
+    r = api.search_ordering(Problem(p.circuit, [], p.open_tile, None), 1 << 4, 0)
+    assert not r["fits"] and len(r["ordering"]) == p.n - 1
+    # the planner's default (ordering = None) is a valid greedy ordering
+    plan = Plan(Problem(p.circuit, [], p.open_tile, None), "fp32", device=-1)
+    assert plan.info()["n_steps"] == p.n - 1
+    with pytest.raises(QFlexError, match="ARG"):
+        api.search_ordering(Problem(p.circuit, [3, 3], p.open_tile, None), 1 << 20, 0)
+    assert sum(two_qubit_counts(p.circuit)) > 0
