@@ -419,6 +419,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
     from paper_1811_09599_gb300 import api
+    from paper_1811_09599_gb300.shard import bitstring_seed, max_over_ranks
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -429,7 +430,7 @@ def run_ours(args):
     api._lib.load(build_if_missing=True)
     peaks = load_peaks()
     prob = c2_problem(0)
-    bits = random_bitstrings(prob.n, N_BS, 1000 + rank)
+    bits = random_bitstrings(prob.n, N_BS, bitstring_seed(1000, rank))   # weak scaling: own bitstrings
     plan = api.Plan(prob, args.precision, device=local)
     tune = plan.autotune(3)
     P = plan.n_slices
@@ -464,10 +465,7 @@ def run_ours(args):
     prof = plan.profile_stop()
     plan.sync()
     ms = e0.elapsed_time(e1) / args.steps
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(ms, device="cuda")
     value = world * n_amps / (ms_max * 1e-3)
 
     # ---------------- end to end through the public API with host buffers
@@ -485,10 +483,8 @@ def run_ours(args):
     barrier()
     e2e_wall = (time.perf_counter() - t0) / args.steps
     e2e_ms = max(f0.elapsed_time(f1) / args.steps, 0.0)
-    e2e_t = torch.tensor([max(e2e_ms, e2e_wall * 1e3)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * n_amps / (float(e2e_t.item()) * 1e-3)
+    e2e_max = max_over_ranks(max(e2e_ms, e2e_wall * 1e3), device="cuda")
+    e2e_value = world * n_amps / (e2e_max * 1e-3)
 
     tc = prof["gemm_tc"] if args.precision != "fp32" else prof["gemm_fp32"]
     bf16_peak = peaks["bf16_tflops_sustained"]
