@@ -218,6 +218,16 @@ size_t operand_bytes(const qflex_plan_s& p, bool tc, int64_t elems) {
   return size_t(elems) * 3 * p.nsplit * (p.tc_kind == 0 ? 4 : 2);
 }
 
+// Tensor cores for contractions with enough work per output; thin
+// absorptions of a small tensor (N < 32, or N = 32 with a short K) run on
+// the CUDA cores.  Measured (7x7 workload shapes, bf16x3 incl. the operand
+// split vs FP32): 2^20 x 16 x 16: 530 vs 121 us; 65536 x 16 x 256: 134 vs
+// 87 us; 2^19 x 32 x 32: 195 vs 197 us; 65536 x 32 x 256: 132 vs 189 us.
+bool tc_route(int64_t M, int64_t N, int64_t K) {
+  return M >= 128 && N >= 32 && K >= 16 && K % 8 == 0 && double(M) * N * K >= double(1 << 24) &&
+         !(N <= 32 && K <= 64);
+}
+
 constexpr int kMaxOpCache = 32;                 // fp16 scale slots 2..33 of 64
 constexpr size_t kOpCacheMinBytes = size_t(16) << 20;
 
@@ -483,11 +493,7 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
     s.K = leg_product(shared, p.leg_dim);
     if (s.M * s.N > (int64_t(1) << 34) || s.M * s.K > (int64_t(1) << 34) || s.N * s.K > (int64_t(1) << 34))
       return fail(QFLEX_ERR_PLAN, "intermediate tensor larger than 2^34 entries at step " + std::to_string(i));
-    // Tensor cores for contractions with enough work per output; thin
-    // absorptions of a small tensor (N <= 32 with a short K) are HBM-bound
-    // and run on the CUDA cores.
-    s.tc = tc_prec && s.M >= 128 && s.N >= 32 && s.K >= 16 && s.K % 8 == 0 &&
-           double(s.M) * s.N * s.K >= double(1 << 24) && !(s.N <= 32 && s.K <= 64);
+    s.tc = tc_prec && tc_route(s.M, s.N, s.K);
     s.bn = s.N >= 128 ? 128 : 64;
     s.ml = ml;
     s.nl = nl;
@@ -753,8 +759,7 @@ cudaError_t run_step(qflex_plan_s& p, const Step& st, int64_t b, const std::vect
 
 // ------------------------------------------------------------------ reverse pass
 int route_of(const qflex_plan_s& p, int64_t M, int64_t N, int64_t K) {
-  const bool tc = p.prec != QFLEX_FP32_SIMT && M >= 128 && N >= 32 && K >= 16 && K % 8 == 0 &&
-                  double(M) * N * K >= double(1 << 24) && !(N <= 32 && K <= 64);
+  const bool tc = p.prec != QFLEX_FP32_SIMT && tc_route(M, N, K);
   return tc ? 2 : (N <= 32 ? 1 : 0);
 }
 
