@@ -12,6 +12,8 @@
 // loop reads contiguous rows).
 #include "internal.h"
 
+#include <algorithm>
+
 namespace qflex {
 namespace {
 
@@ -222,6 +224,130 @@ __global__ void __launch_bounds__(256) k_cgemm_rowwarp(int64_t M, int64_t N, int
   }
 }
 
+// Pipelined row-tile form for N <= 16 (absorbing a tensor with few free
+// entries into a large one: HBM-bound).  Persistent blocks walk 64-row
+// tiles; A streams through a 4-stage cp.async pipeline in k-chunks of KC
+// (zero-filled past M and K), B sits transposed in shared memory for the
+// whole kernel.  Thread t owns row t / 4 and output columns 4 (t % 4) ..
+// +3, accumulating P = sum a.x b and Q = sum a.y b in k order with scalar
+// FMAs (the same per-lane roundings as the packed form of k_cgemm_thin,
+// whose register-pair moves made it issue-bound here), so every output is
+// summed exactly as there.  Rows of a stage are padded by 16 B: the 8 rows
+// a warp reads fall in distinct banks.
+constexpr int T2_RT = 64, T2_NST = 4;
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+template <int KC>
+__global__ void __launch_bounds__(256) k_cgemm_thin2(int64_t M, int N, int K, const float2* __restrict__ A,
+                                                    const float2* __restrict__ B, float2* __restrict__ C) {
+  extern __shared__ __align__(16) float2 sm2[];
+  constexpr int LD = KC + 2;                      // padded row (float2), 16-byte multiple
+  float2* Bt = sm2;                               // [K][16]
+  float2* As = sm2 + size_t(K) * 16;              // [T2_NST][T2_RT][LD]
+  const int t = threadIdx.x;
+  for (int e = t; e < K * 16; e += 256) {
+    const int k = e >> 4, n = e & 15;
+    Bt[e] = n < N ? B[int64_t(n) * K + k] : make_float2(0.f, 0.f);
+  }
+  const int64_t n_tiles = (M + T2_RT - 1) / T2_RT;
+  const int nch = (K + KC - 1) / KC;
+  // units of this block: (tile i, chunk c), i over blockIdx.x + j * gridDim.x
+  const int64_t my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t n_units = my_tiles * nch;
+  auto issue = [&](int64_t u) {
+    if (u < n_units) {
+      const int64_t tile = blockIdx.x + (u / nch) * gridDim.x;
+      const int c = int(u % nch);
+      const int64_t m0 = tile * T2_RT;
+      float2* dst = As + size_t(u % T2_NST) * T2_RT * LD;
+#pragma unroll
+      for (int j = 0; j < (T2_RT * KC / 2) / 256; ++j) {
+        const int e2 = t + j * 256;               // pair of complex entries (16 bytes)
+        const int r = e2 / (KC / 2), kp = e2 % (KC / 2);
+        const int64_t gm = m0 + r;
+        const int gk = c * KC + 2 * kp;
+        const bool in = gm < M && gk < K;
+        const float2* src = in ? A + gm * K + gk : A;
+        cp_async16(uint32_t(__cvta_generic_to_shared(dst + r * LD + 2 * kp)), src, in ? 16 : 0);
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  for (int u = 0; u < T2_NST - 1; ++u) issue(u);
+  const int row = t >> 2, cq = t & 3;
+  float2 P[4], Q[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) P[j] = Q[j] = make_float2(0.f, 0.f);
+  for (int64_t u = 0; u < n_units; ++u) {
+    asm volatile("cp.async.wait_group %0;" ::"n"(T2_NST - 2) : "memory");
+    __syncthreads();                              // stage u landed; stage u - 1 fully consumed
+    issue(u + T2_NST - 1);
+    const int c = int(u % nch);
+    const float2* a_row = As + size_t(u % T2_NST) * T2_RT * LD + row * LD;
+    const float2* b_col = Bt + size_t(c) * KC * 16 + cq * 4;
+    const int kn = min(KC, K - c * KC);
+#pragma unroll 4
+    for (int kk = 0; kk < kn; ++kk) {
+      const float2 a = a_row[kk];
+      const float4 b01 = *reinterpret_cast<const float4*>(b_col + kk * 16);
+      const float4 b23 = *reinterpret_cast<const float4*>(b_col + kk * 16 + 2);
+      const float2 b[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w), make_float2(b23.x, b23.y),
+                           make_float2(b23.z, b23.w)};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        P[j].x = fmaf(a.x, b[j].x, P[j].x);
+        P[j].y = fmaf(a.x, b[j].y, P[j].y);
+        Q[j].x = fmaf(a.y, b[j].x, Q[j].x);
+        Q[j].y = fmaf(a.y, b[j].y, Q[j].y);
+      }
+    }
+    if (c == nch - 1) {
+      const int64_t gm = (blockIdx.x + (u / nch) * gridDim.x) * T2_RT + row;
+      if (gm < M) {
+        float2 o[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o[j] = make_float2(P[j].x - Q[j].y, P[j].y + Q[j].x);
+        float2* crow = C + gm * N + cq * 4;
+        if (N == 16 && (reinterpret_cast<uintptr_t>(crow) & 15) == 0) {
+          reinterpret_cast<float4*>(crow)[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+          reinterpret_cast<float4*>(crow)[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (cq * 4 + j < N) crow[j] = o[j];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) P[j] = Q[j] = make_float2(0.f, 0.f);
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+template <int KC>
+cudaError_t launch_thin2(int64_t M, int64_t N, int64_t K, const float2* A, const float2* B, float2* C,
+                         cudaStream_t s) {
+  const size_t smem = size_t(K) * 16 * sizeof(float2) + size_t(T2_NST) * T2_RT * (KC + 2) * sizeof(float2);
+  // at most 512 x 16 x 8 + 4 x 64 x 34 x 8 bytes (K <= 512): opt in once
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(k_cgemm_thin2<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (attr != cudaSuccess) return attr;
+  int dev = 0, sms = 148, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgemm_thin2<KC>, 256, smem) != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  const int64_t tiles = (M + T2_RT - 1) / T2_RT;
+  const int blocks = int(std::min<int64_t>(tiles, int64_t(sms) * occ));
+  k_cgemm_thin2<KC><<<blocks, 256, smem, s>>>(M, int(N), int(K), A, B, C);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_cgemm_thin(int64_t M, int64_t N, int64_t K, const float2* A, const float2* B,
@@ -232,6 +358,9 @@ cudaError_t launch_cgemm_thin(int64_t M, int64_t N, int64_t K, const float2* A, 
     const int64_t warps = M * cgs;
     k_cgemm_rowwarp<<<unsigned((warps + 7) / 8), 256, 0, s>>>(M, N, K, A, B, C);
     return cudaGetLastError();
+  }
+  if (N <= 16 && K % 2 == 0 && K <= 512 && (reinterpret_cast<uintptr_t>(A) & 15) == 0) {
+    return K <= 16 ? launch_thin2<16>(M, N, K, A, B, C, s) : launch_thin2<32>(M, N, K, A, B, C, s);
   }
   if (N <= 16) {
     dim3 grid(unsigned((M + 255) / 256), unsigned((N + 15) / 16));

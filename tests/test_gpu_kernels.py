@@ -77,7 +77,10 @@ def _gemm_case(K, prec, M, N, Kd, seed):
 
 SHAPES = [(128, 128, 64), (256, 128, 128), (300, 200, 72), (128, 64, 8), (1024, 512, 256),
           (4096, 256, 256), (130, 33, 40), (7, 5, 3), (65536, 16, 16), (20000, 32, 256),
-          (4096, 17, 16), (2048, 256, 16)]
+          (4096, 17, 16), (2048, 256, 16),
+          # pipelined thin form (N <= 16, even K <= 512): ragged rows, a K
+          # tail chunk, K = 2, odd N, the largest K, and K = 514 (older form)
+          (1000, 5, 6), (777, 16, 40), (3000, 13, 512), (129, 16, 2), (65, 1, 200), (300, 16, 514)]
 
 
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-5)])
