@@ -149,6 +149,10 @@ typedef struct {
   int32_t a_cached, b_cached;/* operand kept in its own buffer and permuted only when its
                                 source changes (it depends on fewer cuts than the step) */
   int64_t a_builds, b_builds;/* operand permutations run in that call */
+  int32_t a_fused, b_fused;  /* operand planes written by the producing step's epilogue
+                                (no permutation; not in gradient calls) */
+  int32_t out_fused;         /* this step's epilogue writes its consumer's operand planes:
+                                1 stores along its columns, 2 along its rows; 0 not fused */
 } qflex_step_info;
 
 int32_t qflex_abi_version(void);

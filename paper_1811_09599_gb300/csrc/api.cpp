@@ -82,6 +82,7 @@ struct Operand {
   Ref ref;
   bool direct = false;      // consumed in place by the GEMM (FP32 path, already in matrix form)
   int cache = -1;           // index of a dedicated operand buffer kept across executions, or -1
+  bool fused = false;       // written as planes by its producer's epilogue (tensor cores)
   bool pow2 = true;
   PermTile tile{};
   GatherDesc gather{};
@@ -92,6 +93,9 @@ struct Step {
   Operand A, B;
   int64_t M = 1, N = 1, K = 1;
   bool tc = false;
+  bool fuse_out = false;    // epilogue writes the consumer's operand planes (po) instead of C
+  TcPlaneOut po{};
+  TcGemmMaps maps_plain{};  // maps on the operand scratch (used when fusion is off: gradients)
   int bn = 128;
   int fp32_kernel = 0;   // CUDA-core form: 0 = by shape, 1 = thin, 2 = tiled
   int out_buf = -1;
@@ -119,6 +123,7 @@ struct StepGrad {
 
 struct Buf {
   int64_t elems = 0;
+  int bytes_per = 8;        // 8 (complex64) or the operand-plane bytes of a fused output
   int producer = -1, consumer = -1;
   bool persistent = false;
   size_t offset = 0;
@@ -238,6 +243,27 @@ void* op_buf(const qflex_plan_s& p, const Operand& op, bool is_a) {
 }
 int op_slot(const Operand& op, bool is_a) { return op.cache >= 0 ? 2 + op.cache : (is_a ? 0 : 1); }
 
+// Planes a tensor-core step reads for operand X: its producer's fused output
+// (fusion on), else its own buffer.
+void* x_buf(const qflex_plan_s& p, const Operand& X, bool is_a, bool fused_mode) {
+  if (X.fused && fused_mode) return p.d_arena + p.bufs[size_t(X.ref.id)].offset;
+  return op_buf(p, X, is_a);
+}
+
+// Tensor maps of a tensor-core step: fused operands (maps) and, when the step
+// has any, the same on the operand scratch for the unfused gradient forward.
+bool encode_step(qflex_plan_s& p, Step& s) {
+  if (!tc_encode_maps(p.tc_kind, p.nsplit, s.bn, x_buf(p, s.A, true, true), s.M, x_buf(p, s.B, false, true), s.N,
+                      s.K, &s.maps))
+    return false;
+  if (!s.A.fused && !s.B.fused) {
+    s.maps_plain = s.maps;
+    return true;
+  }
+  return tc_encode_maps(p.tc_kind, p.nsplit, s.bn, op_buf(p, s.A, true), s.M, op_buf(p, s.B, false), s.N, s.K,
+                        &s.maps_plain);
+}
+
 // True when cache c already holds the operand for bitstring b and cut values
 // vals (same bitstring and same values of the cuts its source depends on);
 // otherwise records the new key and returns false.
@@ -292,6 +318,70 @@ int64_t leg_product(const std::vector<int>& legs, const std::vector<int64_t>& di
   int64_t v = 1;
   for (int l : legs) v *= dim[l];
   return v;
+}
+
+// Epilogue fusion: a tensor-core step whose result is an operand of a later
+// tensor-core step writes that operand's 3M planes itself (bit-permuted
+// into the consumer's [rows][K] layout) instead of complex64, and the
+// consumer skips its permutation.  Needs power-of-two legs, an output whose
+// lowest row or column bit lands at stride 1 of the operand (so that the
+// scatter stays coalesced), and a split format without a whole-operand scale
+// (not fp16).
+void plan_fusion(qflex_plan_s& p) {
+  if (p.prec == QFLEX_FP32_SIMT || p.tc_kind == 2) return;
+  const int bytes = 3 * p.nsplit * (p.tc_kind == 0 ? 4 : 2);
+  for (Step& k : p.steps) {
+    if (!k.tc) continue;
+    for (int w = 0; w < 2; ++w) {
+      Operand& X = w == 0 ? k.A : k.B;
+      if (X.ref.grid || X.direct || !X.pow2) continue;
+      const int i = p.bufs[size_t(X.ref.id)].producer;
+      Step& pi = p.steps[size_t(i)];
+      if (!pi.tc || pi.fuse_out) continue;
+      // the operand's layout: target legs row-major
+      std::vector<int> target = w == 0 ? k.ml : k.nl;
+      target.insert(target.end(), k.sh.begin(), k.sh.end());
+      std::vector<int64_t> stride(target.size());
+      int64_t st = 1;
+      bool pow2 = true;
+      for (int a = int(target.size()) - 1; a >= 0; --a) {
+        stride[size_t(a)] = st;
+        st *= p.leg_dim[size_t(target[size_t(a)])];
+        pow2 = pow2 && is_pow2(p.leg_dim[size_t(target[size_t(a)])]);
+      }
+      auto weights = [&](const std::vector<int>& legs, std::vector<int64_t>* out) {
+        for (int a = int(legs.size()) - 1; a >= 0; --a) {
+          auto it = std::find(target.begin(), target.end(), legs[size_t(a)]);
+          if (it == target.end() || !is_pow2(p.leg_dim[size_t(legs[size_t(a)])])) return false;
+          for (int b = 0; b < ilog2(p.leg_dim[size_t(legs[size_t(a)])]); ++b)
+            out->push_back(stride[size_t(it - target.begin())] << b);
+        }
+        return true;
+      };
+      std::vector<int64_t> wm, wn;
+      if (!pow2 || !weights(pi.ml, &wm) || !weights(pi.nl, &wn)) continue;
+      if (wm.size() > size_t(kMaxOutBits) || wn.size() > size_t(kMaxOutBits)) continue;
+      const bool n_fast = !wn.empty() && wn[0] == 1, m_fast = !wm.empty() && wm[0] == 1;
+      if (!n_fast && !m_fast) continue;
+      TcPlaneOut& po = pi.po;
+      po.plane = pi.M * pi.N;
+      po.mbits = int32_t(wm.size());
+      po.nbits = int32_t(wn.size());
+      for (size_t b = 0; b < wm.size(); ++b) po.wm[b] = wm[b];
+      for (size_t b = 0; b < wn.size(); ++b) po.wn[b] = wn[b];
+      po.n_fast = n_fast ? 1 : 0;
+      po.vec = 1;
+      if (n_fast) {   // widest vector of columns at destination strides 1, 2, 4, ...
+        const int vmax = p.tc_kind == 0 ? 4 : 8;
+        while (po.vec < vmax && wn.size() > size_t(ilog2(po.vec)) &&
+               wn[size_t(ilog2(po.vec))] == int64_t(po.vec))
+          po.vec *= 2;
+      }
+      pi.fuse_out = true;
+      X.fused = true;
+      p.bufs[size_t(pi.out_buf)].bytes_per = bytes;
+    }
+  }
 }
 
 qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
@@ -470,6 +560,39 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
     steps = def.data();
     ns = n - 1;
   }
+  // Legs each step's result shares with the step that consumes it (a dry
+  // run over leg sets): those legs go last in the result, so the consumer's
+  // contracted index is the fastest in memory (and, when the producer's
+  // epilogue writes the consumer's operand, its stores run along the
+  // lowest bits of one of its own indexes).
+  std::vector<std::vector<int>> next_shared(size_t(std::max(ns, 0)));
+  {
+    std::vector<std::vector<int>> legs(static_cast<size_t>(n));
+    std::vector<int> last_step(size_t(n), -1);   // step that produced the live tensor of this id
+    for (int q = 0; q < n; ++q) legs[size_t(q)] = p.grid_ref[size_t(q)].legs;
+    for (int i = 0; i < ns; ++i) {
+      const int dst = steps[2 * i], src = steps[2 * i + 1];
+      if (dst < 0 || src < 0 || dst >= n || src >= n || dst == src) break;   // reported below
+      const std::vector<int>& la = legs[size_t(dst)];
+      const std::vector<int>& lb = legs[size_t(src)];
+      for (int side = 0; side < 2; ++side) {
+        const int id = side == 0 ? dst : src;
+        const int prod = last_step[size_t(id)];
+        if (prod < 0) continue;
+        const std::vector<int>& mine = side == 0 ? la : lb;
+        const std::vector<int>& other = side == 0 ? lb : la;
+        for (int l : mine)
+          if (std::find(other.begin(), other.end(), l) != other.end()) next_shared[size_t(prod)].push_back(l);
+      }
+      std::vector<int> r;
+      for (int l : la)
+        if (std::find(lb.begin(), lb.end(), l) == lb.end()) r.push_back(l);
+      for (int l : lb)
+        if (std::find(la.begin(), la.end(), l) == la.end()) r.push_back(l);
+      legs[size_t(dst)] = r;
+      last_step[size_t(dst)] = i;
+    }
+  }
   std::vector<Ref> live(n);
   std::vector<char> alive(n, 1);
   for (int q = 0; q < n; ++q) live[q] = p.grid_ref[q];
@@ -488,6 +611,12 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
       (std::find(rb.legs.begin(), rb.legs.end(), l) != rb.legs.end() ? shared : ml).push_back(l);
     for (int l : rb.legs)
       if (std::find(shared.begin(), shared.end(), l) == shared.end()) nl.push_back(l);
+    {
+      const std::vector<int>& kn = next_shared[size_t(i)];
+      auto later = [&](int l) { return std::find(kn.begin(), kn.end(), l) == kn.end(); };
+      std::stable_partition(ml.begin(), ml.end(), later);
+      std::stable_partition(nl.begin(), nl.end(), later);
+    }
     s.M = leg_product(ml, p.leg_dim);
     s.N = leg_product(nl, p.leg_dim);
     s.K = leg_product(shared, p.leg_dim);
@@ -555,6 +684,7 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
   }
   const uint64_t all_cuts = p.cuts.size() >= 64 ? ~uint64_t(0) : ((uint64_t(1) << p.cuts.size()) - 1);
   if (!p.final_ref.grid) p.bufs[p.final_ref.id].consumer = ns;   // read by the slice sum
+  plan_fusion(p);
   // buffers: reused across slices -> dedicated; others share by liveness
   for (Buf& b : p.bufs) {
     const uint64_t cdep = b.consumer >= ns ? all_cuts : p.steps[b.consumer].dep;
@@ -564,7 +694,7 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
   for (Buf& b : p.bufs)
     if (b.persistent) {
       b.offset = arena;
-      arena += align256(size_t(b.elems) * 8);
+      arena += align256(size_t(b.elems) * size_t(b.bytes_per));
       ++p.n_persistent;
     }
   struct Live { size_t off, size; int end; };
@@ -574,7 +704,7 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
     used.erase(std::remove_if(used.begin(), used.end(), [&](const Live& l) { return l.end < b.producer; }),
                used.end());
     std::sort(used.begin(), used.end(), [](const Live& x, const Live& y) { return x.off < y.off; });
-    const size_t need = align256(size_t(b.elems) * 8);
+    const size_t need = align256(size_t(b.elems) * size_t(b.bytes_per));
     size_t cur = arena;   // transient region starts after the persistent ones
     for (const Live& l : used) {
       if (l.off >= cur + need) break;
@@ -591,7 +721,8 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
       if (X.direct) continue;
       const size_t bytes = operand_bytes(p, s.tc, (w == 0 ? s.M : s.N) * s.K);
       const uint64_t d = X.ref.dep;
-      if ((d & ~s.dep) == 0 && d != s.dep && bytes >= kOpCacheMinBytes && int(p.opcache.size()) < kMaxOpCache) {
+      if (!X.fused && (d & ~s.dep) == 0 && d != s.dep && bytes >= kOpCacheMinBytes &&
+          int(p.opcache.size()) < kMaxOpCache) {
         X.cache = int(p.opcache.size());
         p.opcache.push_back({p.opcache_bytes, d});
         p.opcache_bytes += align256(bytes);
@@ -639,10 +770,9 @@ qflex_status allocate(qflex_plan_s& p) {
     QF_CUDA(cudaMemcpy(p.d_gops, p.gops.data(), sizeof(int2) * p.gops.size(), cudaMemcpyHostToDevice));
   QF_CUDA(cudaMemset(p.d_status, 0, sizeof(int32_t)));
   for (Step& s : p.steps) {
+    if (s.fuse_out) s.po.base = p.d_arena + p.bufs[size_t(s.out_buf)].offset;
     if (!s.tc) continue;
-    if (!tc_encode_maps(p.tc_kind, p.nsplit, s.bn, op_buf(p, s.A, true), s.M, op_buf(p, s.B, false), s.N, s.K,
-                        &s.maps))
-      return fail(QFLEX_ERR_CUDA, "tensor map encoding failed (driver entry point missing?)");
+    if (!encode_step(p, s)) return fail(QFLEX_ERR_CUDA, "tensor map encoding failed (driver entry point missing?)");
   }
   return QFLEX_OK;
 }
@@ -718,8 +848,11 @@ cudaError_t run_step(qflex_plan_s& p, const Step& st, int64_t b, const std::vect
   const double out_per = st.tc ? 3.0 * p.nsplit * (p.tc_kind == 0 ? 4 : 2) : 8.0;
   const float2* A = nullptr;
   const float2* B = nullptr;
+  const bool fused_mode = !p.grad_active;
   if (st.A.direct) {
     A = ref_ptr(p, st.A.ref);
+  } else if (st.A.fused && fused_mode) {
+    // planes written by the producing step's epilogue
   } else {
     void* buf = op_buf(p, st.A, true);
     const bool hit = st.A.cache >= 0 && oc_hit(p.oc_b, p.oc_v, p.opcache[size_t(st.A.cache)].dep, st.A.cache, b, vals);
@@ -731,6 +864,8 @@ cudaError_t run_step(qflex_plan_s& p, const Step& st, int64_t b, const std::vect
   }
   if (st.B.direct) {
     B = ref_ptr(p, st.B.ref);
+  } else if (st.B.fused && fused_mode) {
+    // planes written by the producing step's epilogue
   } else {
     void* buf = op_buf(p, st.B, false);
     const bool hit = st.B.cache >= 0 && oc_hit(p.oc_b, p.oc_v, p.opcache[size_t(st.B.cache)].dep, st.B.cache, b, vals);
@@ -746,9 +881,10 @@ cudaError_t run_step(qflex_plan_s& p, const Step& st, int64_t b, const std::vect
   const double gbytes = 8.0 * (double(st.M) * st.K + double(st.N) * st.K + double(st.M) * st.N);
   if (st.tc)
     return timed(p, 3, 8.0 * mnk, mma, gbytes, s, [&] {
-      return launch_cgemm_tc(p.tc_kind, p.nsplit, st.bn, st.maps, st.M, st.N, st.K, C, p.d_status, s,
-                             p.tc_kind == 2 ? p.d_smax + op_slot(st.A, true) : nullptr,
-                             p.tc_kind == 2 ? p.d_smax + op_slot(st.B, false) : nullptr);
+      return launch_cgemm_tc(p.tc_kind, p.nsplit, st.bn, fused_mode ? st.maps : st.maps_plain, st.M, st.N, st.K, C,
+                             p.d_status, s, p.tc_kind == 2 ? p.d_smax + op_slot(st.A, true) : nullptr,
+                             p.tc_kind == 2 ? p.d_smax + op_slot(st.B, false) : nullptr,
+                             st.fuse_out && fused_mode ? &st.po : nullptr);
     });
   const bool thin = st.fp32_kernel == 1 || (st.fp32_kernel == 0 && st.N <= 32);
   return timed(p, 2, 8.0 * mnk, 0, gbytes, s, [&] {
@@ -1099,10 +1235,10 @@ qflex_status qflex_plan_cost(qflex_plan p, int64_t n_bs, const int64_t* ids, int
     }
     // operand producers that run (not in place, not a cache hit): one
     // permutation each, plus the absmax of an fp16 operand
-    const bool runA = !s.A.direct && !(s.A.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.A.cache)].dep,
-                                                                 s.A.cache, b, vals));
-    const bool runB = !s.B.direct && !(s.B.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.B.cache)].dep,
-                                                                 s.B.cache, b, vals));
+    const bool runA = !s.A.direct && !s.A.fused &&
+                      !(s.A.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.A.cache)].dep, s.A.cache, b, vals));
+    const bool runB = !s.B.direct && !s.B.fused &&
+                      !(s.B.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.B.cache)].dep, s.B.cache, b, vals));
     if (runA) c.permute_bytes += 16.0 * double(s.M) * double(s.K);
     if (runB) c.permute_bytes += 16.0 * double(s.N) * double(s.K);
     c.launches += 1 + runA + runB + (s.tc && p->tc_kind == 2 ? int(runA) + int(runB) : 0);
@@ -1126,10 +1262,10 @@ qflex_status qflex_plan_steps(qflex_plan p, int64_t n_bs, const int64_t* ids, in
     if (i < 0) return QFLEX_OK;
     const Step& s = p->steps[size_t(i)];
     ++runs[size_t(i)];
-    ab[size_t(i)] += !s.A.direct && !(s.A.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.A.cache)].dep,
-                                                                 s.A.cache, b, vals));
-    bb[size_t(i)] += !s.B.direct && !(s.B.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.B.cache)].dep,
-                                                                 s.B.cache, b, vals));
+    ab[size_t(i)] += !s.A.direct && !s.A.fused &&
+                     !(s.A.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.A.cache)].dep, s.A.cache, b, vals));
+    bb[size_t(i)] += !s.B.direct && !s.B.fused &&
+                     !(s.B.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.B.cache)].dep, s.B.cache, b, vals));
     return QFLEX_OK;
   });
   if (st) return st;
@@ -1159,6 +1295,9 @@ qflex_status qflex_plan_steps(qflex_plan p, int64_t n_bs, const int64_t* ids, in
     o.b_cached = s.B.cache >= 0;
     o.a_builds = ab[size_t(i)];
     o.b_builds = bb[size_t(i)];
+    o.a_fused = s.A.fused;
+    o.b_fused = s.B.fused;
+    o.out_fused = s.fuse_out ? (s.po.n_fast ? 1 : 2) : 0;
   }
   return QFLEX_OK;
 }
@@ -1403,8 +1542,8 @@ qflex_status qflex_plan_autotune(qflex_plan p, int32_t reps, int32_t* n_shapes, 
     float best = 1e30f, first = 0.f;
     int best_c = -1;
     for (size_t c = 0; c < cands.size(); ++c) {
-      if (key.tc && !tc_encode_maps(p->tc_kind, p->nsplit, cands[c], op_buf(*p, st.A, true), st.M,
-                                    op_buf(*p, st.B, false), st.N, st.K, &maps[c])) {
+      if (key.tc && !tc_encode_maps(p->tc_kind, p->nsplit, cands[c], x_buf(*p, st.A, true, true), st.M,
+                                    x_buf(*p, st.B, false, true), st.N, st.K, &maps[c])) {
         res = fail(QFLEX_ERR_CUDA, "tensor map encoding failed");
         break;
       }
@@ -1412,7 +1551,8 @@ qflex_status qflex_plan_autotune(qflex_plan p, int32_t reps, int32_t* n_shapes, 
         if (key.tc)
           return launch_cgemm_tc(p->tc_kind, p->nsplit, cands[c], maps[c], st.M, st.N, st.K, C, p->d_status, s,
                                  p->tc_kind == 2 ? p->d_smax + op_slot(st.A, true) : nullptr,
-                                 p->tc_kind == 2 ? p->d_smax + op_slot(st.B, false) : nullptr);
+                                 p->tc_kind == 2 ? p->d_smax + op_slot(st.B, false) : nullptr,
+                                 st.fuse_out ? &st.po : nullptr);
         // operands as the step reads them: in place when consumed directly
         // (the scratch is only sized for produced operands), else their buffer
         const float2* A = st.A.direct ? ref_ptr(*p, st.A.ref) : static_cast<const float2*>(op_buf(*p, st.A, true));
@@ -1446,8 +1586,7 @@ qflex_status qflex_plan_autotune(qflex_plan p, int32_t reps, int32_t* n_shapes, 
       if (key.tc) {
         // steps of one shape may read different operand buffers (caches)
         t.bn = cands[best_c];
-        if (!tc_encode_maps(p->tc_kind, p->nsplit, t.bn, op_buf(*p, t.A, true), t.M, op_buf(*p, t.B, false), t.N,
-                            t.K, &t.maps)) {
+        if (!encode_step(*p, t)) {
           res = fail(QFLEX_ERR_CUDA, "tensor map encoding failed");
           break;
         }

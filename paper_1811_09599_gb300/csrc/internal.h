@@ -11,9 +11,13 @@ namespace qflex {
 // ------------------------------------------------------------------ status
 // Device-side status bits, OR-ed into a device word by kernels whose bounded
 // waits ran out (they then skip their remaining work and return).
-enum : int32_t { kDevTimeout = 1 };
+enum : int32_t { kDevTimeout = 1, kDevBadIndex = 2 };
 
 #ifdef __CUDACC__
+}  // namespace qflex
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+namespace qflex {
 __device__ __forceinline__ float fp16_scale_of(unsigned max_bits) {
   const float m = __uint_as_float(max_bits);
   if (!(m > 0.f) || !(m < 3.0e38f)) return 1.f;
@@ -129,6 +133,100 @@ enum PermFormat : int {
   kFmtFP16 = 4        // 3M planes in fp16 hi (+ lo), scaled by a power of two
 };
 
+#ifdef __CUDACC__
+template <int BYTES>
+__device__ __forceinline__ void store_bytes(void* dst, const void* src) {
+  if constexpr (BYTES == 16) {
+    *static_cast<uint4*>(dst) = *static_cast<const uint4*>(src);
+  } else if constexpr (BYTES == 8) {
+    *static_cast<uint2*>(dst) = *static_cast<const uint2*>(src);
+  } else if constexpr (BYTES == 4) {
+    *static_cast<uint32_t*>(dst) = *static_cast<const uint32_t*>(src);
+  } else {
+    *static_cast<uint16_t*>(dst) = *static_cast<const uint16_t*>(src);
+  }
+}
+__device__ __forceinline__ uint32_t tf32_rna(float x);
+// V consecutive entries (positions o .. o + V - 1 of every plane) written
+// as the 3M planes of put_entry, one vector store per plane; o is a
+// multiple of V.  Same arithmetic as put_entry, entry by entry.
+template <int FMT, int V>
+__device__ __forceinline__ void put_planes_vec(void* out, int64_t o, const float2* v, int nsplit, int64_t plane) {
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    float x[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) x[j] = p == 0 ? v[j].x : (p == 1 ? v[j].y : v[j].x + v[j].y);
+    if constexpr (FMT == kFmtTF32) {
+      uint32_t hi[V], lo[V];
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        hi[j] = tf32_rna(x[j]);
+        lo[j] = tf32_rna(x[j] - __uint_as_float(hi[j]));
+      }
+      uint32_t* q = static_cast<uint32_t*>(out);
+      store_bytes<4 * V>(q + int64_t(p * nsplit) * plane + o, hi);
+      if (nsplit == 2) store_bytes<4 * V>(q + int64_t(p * 2 + 1) * plane + o, lo);
+    } else {
+      __nv_bfloat16 hi[V], lo[V];
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        hi[j] = __float2bfloat16_rn(x[j]);
+        lo[j] = __float2bfloat16_rn(x[j] - __bfloat162float(hi[j]));
+      }
+      __nv_bfloat16* q = static_cast<__nv_bfloat16*>(out);
+      store_bytes<2 * V>(q + int64_t(p * nsplit) * plane + o, hi);
+      if (nsplit == 2) store_bytes<2 * V>(q + int64_t(p * 2 + 1) * plane + o, lo);
+    }
+  }
+}
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// Write one complex entry at linear output position o in the requested
+// format: complex64, FP64 accumulate, or the 3M operand planes
+// [part][split][plane] (part re, im, re + im; split hi, lo = the rounding of
+// x - hi) -- shared by the permutation kernels and the GEMM epilogue that
+// writes the next step's operand, so both produce identical planes.
+template <int FMT>
+__device__ __forceinline__ void put_entry(void* out, int64_t o, float2 v, int nsplit, int64_t plane,
+                                    float scale = 1.f) {
+  if constexpr (FMT == kFmtC64) {
+    static_cast<float2*>(out)[o] = v;
+  } else if constexpr (FMT == kFmtAccC128) {
+    double2* q = static_cast<double2*>(out) + o;
+    const double2 c = *q;
+    *q = make_double2(c.x + double(v.x), c.y + double(v.y));
+  } else {
+    const float part[3] = {v.x, v.y, v.x + v.y};
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      if constexpr (FMT == kFmtFP16) {
+        __half* q = static_cast<__half*>(out);
+        const float x = part[p] * scale;   // exact: scale is a power of two
+        const __half hi = __float2half_rn(x);
+        q[int64_t(p * nsplit) * plane + o] = hi;
+        if (nsplit == 2) q[int64_t(p * 2 + 1) * plane + o] = __float2half_rn(x - __half2float(hi));
+      } else if constexpr (FMT == kFmtTF32) {
+        uint32_t* q = static_cast<uint32_t*>(out);
+        const uint32_t hi = tf32_rna(part[p]);
+        q[int64_t(p * nsplit) * plane + o] = hi;
+        if (nsplit == 2) q[int64_t(p * 2 + 1) * plane + o] = tf32_rna(part[p] - __uint_as_float(hi));
+      } else {
+        __nv_bfloat16* q = static_cast<__nv_bfloat16*>(out);
+        const __nv_bfloat16 hi = __float2bfloat16_rn(part[p]);
+        q[int64_t(p * nsplit) * plane + o] = hi;
+        if (nsplit == 2)
+          q[int64_t(p * 2 + 1) * plane + o] = __float2bfloat16_rn(part[p] - __bfloat162float(hi));
+      }
+    }
+  }
+}
+#endif
+
 // Power-of-two scaling of fp16 operands: `smax` points to the bits of the
 // largest |re|, |im|, |re+im| of the operand (written by launch_absmax);
 // scale = 2^(14 - e) with smax = f 2^e, f in [0.5, 1), so scaled parts stay
@@ -180,12 +278,28 @@ struct TcGemmMaps {
   CUtensorMap a;
   CUtensorMap b;
 };
+// Epilogue output as the next step's 3M operand planes instead of C: entry
+// (m, n) of the product goes to position sum_b bit_b(m) wm[b] + sum_b
+// bit_b(n) wn[b] of each plane [part][split] (M and N powers of two; the map
+// is a bijection onto [0, plane)).  n_fast: the lowest destination bits come
+// from the column index (writes go along rows of the staged tile), else from
+// the row index (writes go along columns).
+constexpr int kMaxOutBits = 40;
+struct TcPlaneOut {
+  void* base = nullptr;      // planes [3 * nsplit][plane] (nullptr: write C)
+  int64_t plane = 0;         // entries per plane (M * N)
+  int64_t wm[kMaxOutBits] = {};
+  int64_t wn[kMaxOutBits] = {};
+  int32_t mbits = 0, nbits = 0;
+  int32_t n_fast = 1;
+  int32_t vec = 1;           // n_fast: columns per store (wn[b] = 2^b for 2^b < vec)
+};
 bool tc_encode_maps(int kind, int nsplit, int bn, const void* a_planes, int64_t M,
                     const void* b_planes, int64_t N, int64_t K, TcGemmMaps* maps);
 cudaError_t launch_cgemm_tc(int kind, int nsplit, int bn, const TcGemmMaps& maps, int64_t M,
                             int64_t N, int64_t K, float2* C, int32_t* d_status,
                             cudaStream_t s, const unsigned* smax_a = nullptr,
-                            const unsigned* smax_b = nullptr);
+                            const unsigned* smax_b = nullptr, const TcPlaneOut* planes = nullptr);
 bool tc_available();   // driver entry point for tensor-map encoding found
 
 // ------------------------------------------------------------------ small kernels

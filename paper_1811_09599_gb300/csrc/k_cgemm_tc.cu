@@ -151,12 +151,42 @@ struct Cfg {
   static constexpr int TMEM_COLS = 3 * BN <= 256 ? 256 : 512;
   static constexpr int HALF = BN / 2;                        // columns per epilogue warp
   static constexpr int STAGING = 8 * 32 * 16 * 8;            // 8 warps x 32 rows x 16 complex
-  static constexpr int SMEM = NSTAGE * STAGE + STAGING + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int DN_TABLE = BN * 8;                     // column offsets of a plane output
+  static constexpr int SMEM = NSTAGE * STAGE + STAGING + 1024 /*align*/ + 256 /*barriers*/ + DN_TABLE;
   static_assert(NSTAGE >= 2, "pipeline needs at least two stages");
   static_assert(SMEM <= 232448, "shared memory per CTA");
 };
 constexpr int KB_CHUNK = 4;      // k-blocks accumulated in TMEM before promotion to registers
 constexpr int EPI_WARPS = 8;
+
+// Column-mode plane output of one staged 32 x 16 sub-block: V consecutive
+// columns per lane (their destinations are consecutive), 16 / V lanes per
+// row; returns whether a destination fell outside the planes.
+template <int FMT, int NSPLIT, int V>
+__device__ __forceinline__ bool write_sub_columns(const TcPlaneOut& po, const float2* st, int lane, int64_t drow,
+                                                  int64_t row0, int64_t M, int64_t gn0, int64_t N, int64_t dn_hi,
+                                                  const int64_t* s_dn, int colb) {
+  constexpr int LPR = 16 / V, RPI = 32 / LPR;
+  const int c = (lane % LPR) * V, rl = lane / LPR;
+  bool bad = false;
+#pragma unroll
+  for (int r0 = 0; r0 < 32; r0 += RPI) {
+    const int r = r0 + rl;
+    const int64_t dr = __shfl_sync(0xffffffffu, drow, r);
+    if (row0 + r < M && gn0 + c < N) {
+      const int64_t d = dr + dn_hi + s_dn[colb + c];
+      if (d >= 0 && d + V <= po.plane) {
+        float2 v[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) v[j] = st[r * 16 + ((c + j) ^ (r & 15))];
+        put_planes_vec<FMT, V>(po.base, d, v, NSPLIT, po.plane);
+      } else {
+        bad = true;
+      }
+    }
+  }
+  return bad;
+}
 
 // Persistent: one CTA per SM walks the output tiles (tile += gridDim.x, N
 // fastest).  Block: warp 0 = TMA producer, warp 1 = TMEM owner + MMA issuer,
@@ -174,11 +204,11 @@ constexpr int EPI_WARPS = 8;
 // warps load it and add it with round-to-nearest FP32 adds into register
 // accumulators Re += T1 - T2, Im += T3 - T1 - T2, while the tensor core
 // already works on the next part.
-template <int KIND, int BN, int NSPLIT>
+template <int KIND, int BN, int NSPLIT, bool PO>
 __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
     k_cgemm_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                int64_t M, int64_t N, int64_t K, float2* __restrict__ C, int32_t* status,
-               const unsigned* smax_a, const unsigned* smax_b) {
+               const unsigned* smax_a, const unsigned* smax_b, const __grid_constant__ TcPlaneOut po) {
   using G = Cfg<BN, NSPLIT>;
   constexpr int ELEM = KIND == 0 ? 4 : 2;
   constexpr uint32_t FMT_AB = KIND == 0 ? 2u : (KIND == 1 ? 1u : 0u);   // tf32 / bf16 / f16
@@ -199,6 +229,16 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
   uint64_t* acc_empty = acc_full + 3;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + 3);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  int64_t* s_dn = reinterpret_cast<int64_t*>(smem + G::NSTAGE * G::STAGE + G::STAGING + 256);
+  constexpr int BN_LOG = BN == 128 ? 7 : 6;
+  if (PO) {   // destination offset of each column within a BN-wide tile
+    for (int j = threadIdx.x; j < BN; j += blockDim.x) {
+      int64_t d = 0;
+      for (int b = 0; b < BN_LOG && b < po.nbits; ++b)
+        if ((j >> b) & 1) d += po.wn[b];
+      s_dn[j] = d;
+    }
+  }
 
   // A CTA of an earlier launch gave up on a wait: skip the work (the status
   // word stays set until the host reads and clears it).
@@ -372,6 +412,56 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
         }
       }
       if (!ok || *abort_flag) break;
+      if constexpr (PO) {
+        // the next step's operand planes: each entry goes to its bit-permuted
+        // position in every [part][split] plane
+        constexpr int FMT = KIND == 0 ? kFmtTF32 : (KIND == 1 ? kFmtBF16 : kFmtFP16);
+        const int64_t gm_own = m0 + q * 32 + lane;
+        int64_t drow = 0;
+        for (int b = 0; b < po.mbits; ++b)
+          if ((gm_own >> b) & 1) drow += po.wm[b];
+        int64_t dn_hi = 0;
+        for (int b = BN_LOG; b < po.nbits; ++b)
+          if ((n0 >> b) & 1) dn_hi += po.wn[b];
+        bool bad = false;
+#pragma unroll
+        for (int sub = 0; sub < G::HALF / 16; ++sub) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            st[lane * 16 + (j ^ (lane & 15))] = make_float2(re[sub * 16 + j], im[sub * 16 + j]);
+          __syncwarp();
+          if (po.n_fast) {
+            const int colb = col0 + sub * 16;
+            const int64_t row0 = m0 + q * 32, gn0 = n0 + colb;
+            if (KIND != 0 && po.vec == 8)
+              bad |= write_sub_columns<FMT, NSPLIT, (KIND != 0 ? 8 : 4)>(po, st, lane, drow, row0, M, gn0, N, dn_hi,
+                                                                         s_dn, colb);
+            else if (po.vec >= 4)
+              bad |= write_sub_columns<FMT, NSPLIT, 4>(po, st, lane, drow, row0, M, gn0, N, dn_hi, s_dn, colb);
+            else if (po.vec == 2)
+              bad |= write_sub_columns<FMT, NSPLIT, 2>(po, st, lane, drow, row0, M, gn0, N, dn_hi, s_dn, colb);
+            else
+              bad |= write_sub_columns<FMT, NSPLIT, 1>(po, st, lane, drow, row0, M, gn0, N, dn_hi, s_dn, colb);
+          } else if (gm_own < M) {
+            // each lane its own row, column by column: consecutive lanes are
+            // consecutive rows
+#pragma unroll 4
+            for (int c = 0; c < 16; ++c) {
+              const int col = col0 + sub * 16 + c;
+              if (n0 + col < N) {
+                const int64_t d = drow + dn_hi + s_dn[col];
+                if (d >= 0 && d < po.plane)
+                  put_entry<FMT>(po.base, d, st[lane * 16 + (c ^ (lane & 15))], NSPLIT, po.plane);
+                else
+                  bad = true;
+              }
+            }
+          }
+          __syncwarp();
+        }
+        if (bad && status) atomicOr(status, kDevBadIndex);
+        continue;
+      }
       // final store: 16 columns at a time through this warp's staging area
       // (row = lane, column slot XOR-swizzled by the row: conflict-free in
       // both directions), then two 128-byte row segments per instruction.
@@ -434,11 +524,12 @@ bool encode(int kind, const void* ptr, int64_t rows, int64_t K, int box_rows, CU
   return r == CUDA_SUCCESS;
 }
 
-template <int KIND, int BN, int NSPLIT>
+template <int KIND, int BN, int NSPLIT, bool PO>
 cudaError_t launch_t(const TcGemmMaps& maps, int64_t M, int64_t N, int64_t K, float2* C,
-                     int32_t* status, cudaStream_t s, const unsigned* sa, const unsigned* sb) {
+                     int32_t* status, cudaStream_t s, const unsigned* sa, const unsigned* sb,
+                     const TcPlaneOut& po) {
   using G = Cfg<BN, NSPLIT>;
-  auto kern = k_cgemm_tc<KIND, BN, NSPLIT>;
+  auto kern = k_cgemm_tc<KIND, BN, NSPLIT, PO>;
   static int configured_dev = -1;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -451,7 +542,7 @@ cudaError_t launch_t(const TcGemmMaps& maps, int64_t M, int64_t N, int64_t K, fl
   if (sms == 0) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
   const unsigned grid = unsigned(tiles < sms ? tiles : sms);
-  kern<<<grid, 64 + 32 * EPI_WARPS, G::SMEM, s>>>(maps.a, maps.b, M, N, K, C, status, sa, sb);
+  kern<<<grid, 64 + 32 * EPI_WARPS, G::SMEM, s>>>(maps.a, maps.b, M, N, K, C, status, sa, sb, po);
   return cudaGetLastError();
 }
 
@@ -469,14 +560,25 @@ bool tc_encode_maps(int kind, int nsplit, int bn, const void* a_planes, int64_t 
 
 cudaError_t launch_cgemm_tc(int kind, int nsplit, int bn, const TcGemmMaps& maps, int64_t M,
                             int64_t N, int64_t K, float2* C, int32_t* status, cudaStream_t s,
-                            const unsigned* smax_a, const unsigned* smax_b) {
+                            const unsigned* smax_a, const unsigned* smax_b, const TcPlaneOut* planes) {
   if (3 * nsplit * M > INT32_MAX || 3 * nsplit * N > INT32_MAX) return cudaErrorInvalidValue;
-#define QF_TC(KD, B, S) \
-  if (kind == KD && bn == B && nsplit == S) return launch_t<KD, B, S>(maps, M, N, K, C, status, s, smax_a, smax_b);
+  static const TcPlaneOut none{};
+  const TcPlaneOut& po = planes ? *planes : none;
+  if (po.base && (kind == 2 || po.mbits > kMaxOutBits || po.nbits > kMaxOutBits ||
+                  (int64_t(1) << po.mbits) != M || (int64_t(1) << po.nbits) != N))
+    return cudaErrorInvalidValue;
+#define QF_TC(KD, B, S)                                                                                  \
+  if (kind == KD && bn == B && nsplit == S)                                                              \
+    return po.base ? launch_t<KD, B, S, true>(maps, M, N, K, C, status, s, smax_a, smax_b, po)            \
+                   : launch_t<KD, B, S, false>(maps, M, N, K, C, status, s, smax_a, smax_b, po);
+#define QF_TC16(B)                                                                                       \
+  if (kind == 2 && bn == B && nsplit == 2)                                                               \
+    return launch_t<2, B, 2, false>(maps, M, N, K, C, status, s, smax_a, smax_b, po);
   QF_TC(0, 64, 1) QF_TC(0, 64, 2) QF_TC(0, 128, 1) QF_TC(0, 128, 2)
   QF_TC(1, 64, 1) QF_TC(1, 64, 2) QF_TC(1, 128, 1) QF_TC(1, 128, 2)
-  QF_TC(2, 64, 2) QF_TC(2, 128, 2)
+  QF_TC16(64) QF_TC16(128)
 #undef QF_TC
+#undef QF_TC16
   return cudaErrorInvalidValue;
 }
 

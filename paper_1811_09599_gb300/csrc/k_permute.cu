@@ -125,48 +125,6 @@ bool build_perm_tile(int nbits, const int64_t* w, PermTile* t, const int64_t* w_
 
 namespace {
 
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-
-// Write one complex entry at linear output position o in the requested format.
-template <int FMT>
-__device__ __forceinline__ void put(void* out, int64_t o, float2 v, int nsplit, int64_t plane,
-                                    float scale = 1.f) {
-  if constexpr (FMT == kFmtC64) {
-    static_cast<float2*>(out)[o] = v;
-  } else if constexpr (FMT == kFmtAccC128) {
-    double2* q = static_cast<double2*>(out) + o;
-    const double2 c = *q;
-    *q = make_double2(c.x + double(v.x), c.y + double(v.y));
-  } else {
-    const float part[3] = {v.x, v.y, v.x + v.y};
-#pragma unroll
-    for (int p = 0; p < 3; ++p) {
-      if constexpr (FMT == kFmtFP16) {
-        __half* q = static_cast<__half*>(out);
-        const float x = part[p] * scale;   // exact: scale is a power of two
-        const __half hi = __float2half_rn(x);
-        q[int64_t(p * nsplit) * plane + o] = hi;
-        if (nsplit == 2) q[int64_t(p * 2 + 1) * plane + o] = __float2half_rn(x - __half2float(hi));
-      } else if constexpr (FMT == kFmtTF32) {
-        uint32_t* q = static_cast<uint32_t*>(out);
-        const uint32_t hi = tf32_rna(part[p]);
-        q[int64_t(p * nsplit) * plane + o] = hi;
-        if (nsplit == 2) q[int64_t(p * 2 + 1) * plane + o] = tf32_rna(part[p] - __uint_as_float(hi));
-      } else {
-        __nv_bfloat16* q = static_cast<__nv_bfloat16*>(out);
-        const __nv_bfloat16 hi = __float2bfloat16_rn(part[p]);
-        q[int64_t(p * nsplit) * plane + o] = hi;
-        if (nsplit == 2)
-          q[int64_t(p * 2 + 1) * plane + o] = __float2bfloat16_rn(part[p] - __bfloat162float(hi));
-      }
-    }
-  }
-}
-
 template <int FMT>
 __global__ void __launch_bounds__(256, 6) k_permute_tiled(const float2* __restrict__ in, int64_t in_base,
                                                        const __grid_constant__ PermTile t, void* out,
@@ -243,7 +201,7 @@ __global__ void __launch_bounds__(256, 6) k_permute_tiled(const float2* __restri
     for (int k = 0; k < kPer; ++k) {
       const int h = wid + 8 * k;
       if (h * 32 + lane < n)
-        put<FMT>(out, cur_ob + out_lo + s_out_hi[h], tile[st_lo ^ s_st_hi[h]], nsplit, plane, scale);
+        put_entry<FMT>(out, cur_ob + out_lo + s_out_hi[h], tile[st_lo ^ s_st_hi[h]], nsplit, plane, scale);
     }
     __syncthreads();
   }
@@ -263,7 +221,7 @@ __global__ void k_permute_gather(const float2* __restrict__ in, int64_t in_base,
       rem /= d.dims[a];
       off += i * d.in_strides[a];
     }
-    put<FMT>(out, o, in[off], nsplit, plane, scale);
+    put_entry<FMT>(out, o, in[off], nsplit, plane, scale);
   }
 }
 

@@ -189,8 +189,17 @@ def test_plan_steps_agree_with_cost(Plan):
     big = [s for s in p.steps(1) if (s["M"], s["N"], s["K"]) == (4096, 4096, 4096)]
     assert sorted(s["runs"] for s in big) == [16, 256]
     assert all(s["kernel"] == "tensor_cores" for s in big)
-    # AB (changes once per right-cut value) feeds the per-slice ABD product:
-    # its operand planes are kept and rebuilt 16 times, not 256
+    # both ABD operands are written by their producers' epilogues (fusion)
     abd = [s for s in big if s["runs"] == 256][0]
-    assert abd["a_cached"] and abd["a_builds"] == 16 and abd["b_builds"] == 256
+    assert abd["a_fused"] and abd["b_fused"] and abd["a_builds"] == 0 and abd["b_builds"] == 0
+    # without fusion (plain FP32 plan): AB's output order is already ABD's
+    # operand layout (legs the consumer contracts go last), so it is read in
+    # place; pD (changes once per right-cut value) keeps its permuted operand
+    # for the first D-column absorb: built 16 times, not 256
+    f = Plan(c2_problem(0), "fp32", device=-1)
+    st32 = f.steps(1)
+    abd32 = [s for s in st32 if (s["M"], s["N"], s["K"], s["runs"]) == (4096, 4096, 4096, 256)][0]
+    assert abd32["a_direct"] and abd32["b_builds"] == 256
+    d0 = [s for s in st32 if (s["M"], s["N"], s["K"]) == (1 << 20, 16, 16)][0]
+    assert d0["a_cached"] and d0["a_builds"] == 16 and d0["runs"] == 256
     assert all(s["kernel"] != "tensor_cores" for s in Plan(c2_problem(0), "fp32", device=-1).steps(1))
