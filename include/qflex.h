@@ -291,7 +291,9 @@ typedef struct {
 qflex_status qflex_plan_profile(qflex_plan plan, int32_t mode, qflex_profile* out);
 
 /* Synchronize the plan's last stream and report its device status word
- * (QFLEX_ERR_DEVICE_TIMEOUT if a bounded wait ran out); the word is cleared. */
+ * (QFLEX_ERR_DEVICE_TIMEOUT if a bounded wait ran out; QFLEX_ERR_PLAN if a
+ * fused epilogue computed a destination outside its operand planes, which
+ * the kernel skipped); the word is cleared. */
 qflex_status qflex_plan_sync(qflex_plan plan);
 
 /* ---------------- standalone hot-path kernels (same kernels the plan runs) ---------------- */

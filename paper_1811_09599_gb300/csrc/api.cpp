@@ -1669,7 +1669,8 @@ qflex_status qflex_plan_sync(qflex_plan p) {
   QF_CUDA(cudaMemcpy(&w, p->d_status, sizeof(w), cudaMemcpyDeviceToHost));
   if (w) {
     QF_CUDA(cudaMemset(p->d_status, 0, sizeof(int32_t)));
-    return fail(QFLEX_ERR_DEVICE_TIMEOUT, "a bounded device-side wait ran out");
+    if (w & kDevTimeout) return fail(QFLEX_ERR_DEVICE_TIMEOUT, "a bounded device-side wait ran out");
+    return fail(QFLEX_ERR_PLAN, "internal: a fused epilogue destination fell outside its operand planes");
   }
   return QFLEX_OK;
 }
