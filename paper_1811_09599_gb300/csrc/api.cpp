@@ -349,7 +349,10 @@ void plan_fusion(qflex_plan_s& p) {
       if (X.ref.grid || X.direct || !X.pow2) continue;
       const int i = p.bufs[size_t(X.ref.id)].producer;
       Step& pi = p.steps[size_t(i)];
-      if (!pi.tc || pi.fuse_out) continue;
+      // producers: tensor-core steps, and CUDA-core steps that take the
+      // pipelined thin form (it has a plane-output variant)
+      const bool thin_prod = !pi.tc && pi.fp32_kernel != 2 && thin_pipelined(pi.M, pi.N, pi.K);
+      if ((!pi.tc && !thin_prod) || pi.fuse_out) continue;
       // the operand's layout: target legs row-major
       std::vector<int> target = w == 0 ? k.ml : k.nl;
       target.insert(target.end(), k.sh.begin(), k.sh.end());
@@ -382,6 +385,9 @@ void plan_fusion(qflex_plan_s& p) {
       for (size_t b = 0; b < wm.size(); ++b) po.wm[b] = wm[b];
       for (size_t b = 0; b < wn.size(); ++b) po.wn[b] = wn[b];
       po.n_fast = n_fast ? 1 : 0;
+      po.fmt = p.tc_kind == 0 ? kFmtTF32 : kFmtBF16;
+      po.nsplit = p.nsplit;
+      if (thin_prod) pi.fp32_kernel = 1;   // keep the form that writes planes
       po.vec = 1;
       if (n_fast) {   // widest vector of columns at destination strides 1, 2, 4, ...
         const int vmax = p.tc_kind == 0 ? 4 : 8;
@@ -900,6 +906,7 @@ cudaError_t run_step(qflex_plan_s& p, const Step& st, int64_t b, const std::vect
     });
   const bool thin = st.fp32_kernel == 1 || (st.fp32_kernel == 0 && st.N <= 32);
   return timed(p, 2, 8.0 * mnk, 0, gbytes, s, [&] {
+    if (st.fuse_out && fused_mode) return launch_cgemm_thin_planes(st.M, st.N, st.K, A, B, st.po, s);
     return thin ? launch_cgemm_thin(st.M, st.N, st.K, A, B, C, s) : launch_cgemm_simt(st.M, st.N, st.K, A, B, C, s);
   });
 }
@@ -1547,8 +1554,10 @@ qflex_status qflex_plan_autotune(qflex_plan p, int32_t reps, int32_t* n_shapes, 
     Step& st = p->steps[idx.front()];
     float2* C = reinterpret_cast<float2*>(p->d_arena + p->bufs[st.out_buf].offset);
     std::vector<int> cands;
+    bool fused_fp32 = false;   // CUDA-core producers writing planes keep their form
+    for (size_t i : idx) fused_fp32 = fused_fp32 || (!p->steps[i].tc && p->steps[i].fuse_out);
     if (key.tc) cands = {128, 64};
-    else if (key.N <= 32) cands = {1, 2};
+    else if (key.N <= 32 && !fused_fp32) cands = {1, 2};
     else continue;
     std::vector<TcGemmMaps> maps(cands.size());
     float best = 1e30f, first = 0.f;

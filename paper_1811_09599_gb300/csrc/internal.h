@@ -293,7 +293,14 @@ struct TcPlaneOut {
   int32_t mbits = 0, nbits = 0;
   int32_t n_fast = 1;
   int32_t vec = 1;           // n_fast: columns per store (wn[b] = 2^b for 2^b < vec)
+  int32_t fmt = 0;           // plane format for the CUDA-core producer: kFmtTF32 or kFmtBF16
+  int32_t nsplit = 2;        // splits per part, same use
 };
+// The pipelined thin product (launch_cgemm_thin's form for this shape) with
+// its result written as operand planes (po) instead of C.
+bool thin_pipelined(int64_t M, int64_t N, int64_t K);
+cudaError_t launch_cgemm_thin_planes(int64_t M, int64_t N, int64_t K, const float2* A, const float2* B,
+                                     const TcPlaneOut& po, cudaStream_t s);
 bool tc_encode_maps(int kind, int nsplit, int bn, const void* a_planes, int64_t M,
                     const void* b_planes, int64_t N, int64_t K, TcGemmMaps* maps);
 cudaError_t launch_cgemm_tc(int kind, int nsplit, int bn, const TcGemmMaps& maps, int64_t M,

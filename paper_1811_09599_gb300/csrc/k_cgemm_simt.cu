@@ -240,9 +240,10 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int sr
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
 
-template <int KC>
+template <int KC, bool PO>
 __global__ void __launch_bounds__(256) k_cgemm_thin2(int64_t M, int N, int K, const float2* __restrict__ A,
-                                                    const float2* __restrict__ B, float2* __restrict__ C) {
+                                                    const float2* __restrict__ B, float2* __restrict__ C,
+                                                    const __grid_constant__ TcPlaneOut po) {
   extern __shared__ __align__(16) float2 sm2[];
   constexpr int LD = KC + 2;                      // padded row (float2), 16-byte multiple
   float2* Bt = sm2;                               // [K][16]
@@ -306,6 +307,44 @@ __global__ void __launch_bounds__(256) k_cgemm_thin2(int64_t M, int N, int K, co
     }
     if (c == nch - 1) {
       const int64_t gm = (blockIdx.x + (u / nch) * gridDim.x) * T2_RT + row;
+      if constexpr (PO) {
+        // the next step's operand planes at the bit-permuted positions
+        if (gm < M) {
+          float2 o[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) o[j] = make_float2(P[j].x - Q[j].y, P[j].y + Q[j].x);
+          int64_t d0 = 0;
+          for (int b = 0; b < po.mbits; ++b)
+            if ((gm >> b) & 1) d0 += po.wm[b];
+          int64_t dn[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            dn[j] = 0;
+            for (int b = 0; b < po.nbits; ++b)
+              if (((cq * 4 + j) >> b) & 1) dn[j] += po.wn[b];
+          }
+          if (po.n_fast && po.vec >= 4 && cq * 4 + 3 < N && d0 + dn[0] + 4 <= po.plane) {
+            if (po.fmt == kFmtTF32)
+              put_planes_vec<kFmtTF32, 4>(po.base, d0 + dn[0], o, po.nsplit, po.plane);
+            else
+              put_planes_vec<kFmtBF16, 4>(po.base, d0 + dn[0], o, po.nsplit, po.plane);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int64_t d = d0 + dn[j];
+              if (cq * 4 + j < N && d >= 0 && d < po.plane) {
+                if (po.fmt == kFmtTF32)
+                  put_entry<kFmtTF32>(po.base, d, o[j], po.nsplit, po.plane);
+                else
+                  put_entry<kFmtBF16>(po.base, d, o[j], po.nsplit, po.plane);
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) P[j] = Q[j] = make_float2(0.f, 0.f);
+        continue;
+      }
       if (gm < M) {
         float2 o[4];
 #pragma unroll
@@ -327,28 +366,44 @@ __global__ void __launch_bounds__(256) k_cgemm_thin2(int64_t M, int N, int K, co
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
-template <int KC>
+template <int KC, bool PO>
 cudaError_t launch_thin2(int64_t M, int64_t N, int64_t K, const float2* A, const float2* B, float2* C,
-                         cudaStream_t s) {
+                         const TcPlaneOut& po, cudaStream_t s) {
   const size_t smem = size_t(K) * 16 * sizeof(float2) + size_t(T2_NST) * T2_RT * (KC + 2) * sizeof(float2);
   // at most 512 x 16 x 8 + 4 x 64 x 34 x 8 bytes (K <= 512): opt in once
   static const cudaError_t attr =
-      cudaFuncSetAttribute(k_cgemm_thin2<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      cudaFuncSetAttribute(k_cgemm_thin2<KC, PO>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (attr != cudaSuccess) return attr;
   int dev = 0, sms = 148, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgemm_thin2<KC>, 256, smem) != cudaSuccess || occ < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgemm_thin2<KC, PO>, 256, smem) != cudaSuccess ||
+      occ < 1) {
     cudaGetLastError();
     occ = 1;
   }
   const int64_t tiles = (M + T2_RT - 1) / T2_RT;
   const int blocks = int(std::min<int64_t>(tiles, int64_t(sms) * occ));
-  k_cgemm_thin2<KC><<<blocks, 256, smem, s>>>(M, int(N), int(K), A, B, C);
+  k_cgemm_thin2<KC, PO><<<blocks, 256, smem, s>>>(M, int(N), int(K), A, B, C, po);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+bool thin_pipelined(int64_t M, int64_t N, int64_t K) {
+  const bool rowwarp = K >= 64 && ((M + 255) / 256) * ((N + 15) / 16) < 256;
+  return !rowwarp && N <= 16 && K % 2 == 0 && K <= 512;
+}
+
+cudaError_t launch_cgemm_thin_planes(int64_t M, int64_t N, int64_t K, const float2* A, const float2* B,
+                                     const TcPlaneOut& po, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (!thin_pipelined(M, N, K) || (reinterpret_cast<uintptr_t>(A) & 15) != 0 || !po.base ||
+      (po.fmt != kFmtTF32 && po.fmt != kFmtBF16))
+    return cudaErrorInvalidValue;
+  return K <= 16 ? launch_thin2<16, true>(M, N, K, A, B, nullptr, po, s)
+                 : launch_thin2<32, true>(M, N, K, A, B, nullptr, po, s);
+}
 
 cudaError_t launch_cgemm_thin(int64_t M, int64_t N, int64_t K, const float2* A, const float2* B,
                               float2* C, cudaStream_t s) {
@@ -359,8 +414,10 @@ cudaError_t launch_cgemm_thin(int64_t M, int64_t N, int64_t K, const float2* A, 
     k_cgemm_rowwarp<<<unsigned((warps + 7) / 8), 256, 0, s>>>(M, N, K, A, B, C);
     return cudaGetLastError();
   }
-  if (N <= 16 && K % 2 == 0 && K <= 512 && (reinterpret_cast<uintptr_t>(A) & 15) == 0) {
-    return K <= 16 ? launch_thin2<16>(M, N, K, A, B, C, s) : launch_thin2<32>(M, N, K, A, B, C, s);
+  if (thin_pipelined(M, N, K) && (reinterpret_cast<uintptr_t>(A) & 15) == 0) {
+    static const TcPlaneOut none{};
+    return K <= 16 ? launch_thin2<16, false>(M, N, K, A, B, C, none, s)
+                   : launch_thin2<32, false>(M, N, K, A, B, C, none, s);
   }
   if (N <= 16) {
     dim3 grid(unsigned((M + 255) / 256), unsigned((N + 15) / 16));
