@@ -172,7 +172,7 @@ struct qflex_plan_s {
   GridQubitMeta* d_gmeta = nullptr;
   int2* d_gops = nullptr;
   int32_t* d_status = nullptr;
-  unsigned* d_smax = nullptr;                  // fp16 operand scales: [0] A, [1] B, [2 + c] cache c
+  unsigned* d_smax = nullptr;                  // fp16 operand scales: [0] A, [1] B, [2 + c] cache c (192 slots)
   cudaStream_t last_stream = nullptr;
   // profiling: event pairs around launches
   // gradients (qflex_plan_enable_gradients)
@@ -233,8 +233,8 @@ bool tc_route(int64_t M, int64_t N, int64_t K) {
          !(N <= 32 && K <= 64);
 }
 
-constexpr int kMaxOpCache = 32;                 // fp16 scale slots 2..33 of 64
-constexpr size_t kOpCacheMinBytes = size_t(16) << 20;
+constexpr int kMaxOpCache = 128;                // fp16 scale slots 2..129 of 192
+constexpr size_t kOpCacheMinBytes = 0;           // small operands too: each saves a launch per execution
 
 // Buffer an operand is produced into (its cache, else the shared scratch).
 void* op_buf(const qflex_plan_s& p, const Operand& op, bool is_a) {
@@ -755,7 +755,8 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
   p.total_bytes = p.grid_bytes + align256(p.arena_bytes) + align256(p.opA_bytes) + align256(p.opB_bytes) +
                   align256(p.opcache_bytes) +
                   align256(sizeof(GridQubitMeta) * n) + align256(sizeof(int2) * std::max<size_t>(1, p.gops.size())) +
-                  512;
+                  256 /* status word */ + 768 /* fp16 scale slots: A, B, one per cache */;
+  static_assert((2 + kMaxOpCache) * sizeof(unsigned) <= 768, "fp16 scale slots");
   return QFLEX_OK;
 }
 
