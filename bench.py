@@ -231,6 +231,35 @@ def _permute_exact(torch, x, y, perm, n_samples=1 << 20):
     return bool(torch.equal(y.reshape(-1)[j], x.reshape(-1)[idx]))
 
 
+def per_step_roofline(plan, n_bs, precision, peak_tflops, peak_gbs, measured_ms_per_call):
+    """Per-step roofline of the tensor-core kernel over one call's schedule:
+    each tensor-core step is bound by max(MMA flops / tensor peak,
+    algorithmic bytes / HBM peak), with bytes = its operand planes read
+    (A: M K, B: N K entries) plus its output written (M N entries, as operand
+    planes when its epilogue is fused, else complex64).  frac = the sum of
+    those bounds over the measured device time of the kernel."""
+    nsplit = 1 if precision in ("bf16", "tf32") else 2
+    plane_b = 3 * nsplit * (4 if precision.startswith("tf32") else 2)
+    mma_per_cmac = 3 * nsplit * 2 if nsplit == 1 else 18
+    t_tensor = t_hbm = 0.0
+    for s in plan.steps(n_bs):
+        if s["kernel"] != "tensor_cores":
+            continue
+        M, N, K, r = s["M"], s["N"], s["K"], s["runs"]
+        flops = M * N * K * mma_per_cmac
+        byts = (M * K + N * K) * plane_b + M * N * (plane_b if s["out_fused"] else 8)
+        tf, tb = flops / (peak_tflops * 1e12), byts / (peak_gbs * 1e9)
+        if tf >= tb:
+            t_tensor += r * tf
+        else:
+            t_hbm += r * tb
+    bound_ms = (t_tensor + t_hbm) * 1e3
+    return {"roofline_ms_per_call": round(bound_ms, 3), "measured_ms_per_call": round(measured_ms_per_call, 3),
+            "frac": round(bound_ms / measured_ms_per_call, 4) if measured_ms_per_call > 0 else None,
+            "tensor_bound_share": round(t_tensor / max(t_tensor + t_hbm, 1e-30), 4),
+            "peaks": "measured bf16 sustained (tensor), measured copy (HBM)"}
+
+
 def permute_sweep(api, torch, peaks):
     """Complex64 tensors of 2^m entries, m = 20..30: (i) m binary axes, 8
     seeded random permutations each; (ii) axes of dimension 16 (plus one of
@@ -502,7 +531,9 @@ def run_ours(args):
                 "share_of_step": round(tc["ms"] / (ms * args.steps), 4),
                 "peak_source": f"{peaks['source']} bf16_tflops_sustained"
                                + (" x 1.1/2.25 (nominal tf32/bf16 ratio)" if tf_scale != 1.0 else ""),
-                "flops_convention": "executed tensor-core flops: 3M x (hi.hi+hi.lo+lo.hi) = 18 per complex MAC"}
+                "flops_convention": "executed tensor-core flops: 3M x (hi.hi+hi.lo+lo.hi) = 18 per complex MAC",
+                "per_step": per_step_roofline(plan, N_BS, args.precision, peak, peaks["hbm_gbs"],
+                                              tc["ms"] / args.steps)}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
