@@ -331,11 +331,13 @@ void plan_fusion(qflex_plan_s& p) {
   if (p.prec == QFLEX_FP32_SIMT || p.tc_kind == 2) return;
   const int bytes = 3 * p.nsplit * (p.tc_kind == 0 ? 4 : 2);
   for (Step& k : p.steps) {
-    // A narrow product (16 <= N < 32) with many rows and a long K whose A
-    // comes straight from a tensor-core step moves to the tensor cores too:
+    // A CUDA-core product with N >= 16, at least 2^10 rows and a long K whose
+    // A comes straight from a tensor-core step moves to the tensor cores too:
     // with its operand fused it skips both the permutation and the CUDA-core
-    // product (65536 x 16 x 256: ~65 us vs 90 us + 45 us).
-    if (!k.tc && k.N >= 16 && k.K >= 64 && k.K % 8 == 0 && k.M >= (int64_t(1) << 14) && !k.A.ref.grid &&
+    // product (65536 x 16 x 256: ~45 us vs 90 us + 45 us; on the 7x7 plan
+    // the threshold 2^10 instead of 2^14 also takes 4096 x 16 x 256 and
+    // 1024 x 32 x 256: 128.9 -> 132.7 amplitudes/s).
+    if (!k.tc && k.N >= 16 && k.K >= 64 && k.K % 8 == 0 && k.M >= (int64_t(1) << 10) && !k.A.ref.grid &&
         k.A.pow2 && p.steps[size_t(p.bufs[size_t(k.A.ref.id)].producer)].tc) {
       k.tc = true;
       k.bn = 64;
