@@ -159,6 +159,19 @@ struct Cfg {
 constexpr int KB_CHUNK = 4;      // k-blocks accumulated in TMEM before promotion to registers
 constexpr int EPI_WARPS = 8;
 
+// Tile order of the persistent walk: groups of TILE_GROUP row blocks, each
+// group swept column by column, so the tiles in flight at once (one per SM)
+// share a few A row blocks and a part of B instead of all of B.
+constexpr int64_t TILE_GROUP = 8;
+template <int BN>
+__device__ __forceinline__ void tile_origin(int64_t tile, int64_t n_mt, int64_t n_nt, int64_t* m0, int64_t* n0) {
+  const int64_t per_group = TILE_GROUP * n_nt;
+  const int64_t g = tile / per_group, r = tile - g * per_group;
+  const int64_t rows = min(TILE_GROUP, n_mt - g * TILE_GROUP);
+  *m0 = (g * TILE_GROUP + r % rows) * BM;
+  *n0 = (r / rows) * BN;
+}
+
 // Column-mode plane output of one staged 32 x 16 sub-block: V consecutive
 // columns per lane (their destinations are consecutive), 16 / V lanes per
 // row; returns whether a destination fell outside the planes.
@@ -249,7 +262,8 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t n_nt = (N + BN - 1) / BN;
-  const int64_t n_tiles = ((M + BM - 1) / BM) * n_nt;
+  const int64_t n_mt = (M + BM - 1) / BM;
+  const int64_t n_tiles = n_mt * n_nt;
   const int nkb = int((K + BK - 1) / BK);
   const int nchunk = (nkb + KB_CHUNK - 1) / KB_CHUNK;
 
@@ -285,7 +299,8 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
       int i = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-      const int64_t m0 = (tile / n_nt) * BM, n0 = (tile % n_nt) * BN;
+      int64_t m0, n0;
+      tile_origin<BN>(tile, n_mt, n_nt, &m0, &n0);
       for (int c = 0; c < nchunk && ok; ++c) {
         const int kb0 = c * KB_CHUNK, kb1 = min(nkb, kb0 + KB_CHUNK);
         for (int part = 0; part < 3 && ok; ++part) {
@@ -373,7 +388,8 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
     bool ok = true;
     int cg = 0;
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-      const int64_t m0 = (tile / n_nt) * BM, n0 = (tile % n_nt) * BN;
+      int64_t m0, n0;
+      tile_origin<BN>(tile, n_mt, n_nt, &m0, &n0);
       float re[G::HALF], im[G::HALF];
 #pragma unroll
       for (int j = 0; j < G::HALF; ++j) re[j] = im[j] = 0.f;
