@@ -253,6 +253,13 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
     }
   }
 
+  // Launched with programmatic stream serialization: the launch itself can
+  // be staged while the previous kernel on the stream runs; wait here for
+  // its completion (and the visibility of its writes) before anything else,
+  // then let the next such launch stage itself.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+
   // A CTA of an earlier launch gave up on a wait: skip the work (the status
   // word stays set until the host reads and clears it).
   __shared__ int s_skip;
@@ -558,8 +565,17 @@ cudaError_t launch_t(const TcGemmMaps& maps, int64_t M, int64_t N, int64_t K, fl
   if (sms == 0) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
   const unsigned grid = unsigned(tiles < sms ? tiles : sms);
-  kern<<<grid, 64 + 32 * EPI_WARPS, G::SMEM, s>>>(maps.a, maps.b, M, N, K, C, status, sa, sb, po);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(64 + 32 * EPI_WARPS);
+  cfg.dynamicSmemBytes = G::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, maps.a, maps.b, M, N, K, C, status, sa, sb, po);
 }
 
 }  // namespace
