@@ -134,6 +134,30 @@ enum PermFormat : int {
 };
 
 #ifdef __CUDACC__
+// Programmatic dependent launch: a kernel launched with launch_pdl may start
+// while the previous kernel on its stream is still running; it must call
+// pdl_wait() before reading anything that kernel wrote (the wait returns once
+// the previous kernel has completed and its writes are visible).  It then
+// allows the next such launch to stage itself early.
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<Args&&>(args)...);
+}
 template <int BYTES>
 __device__ __forceinline__ void store_bytes(void* dst, const void* src) {
   if constexpr (BYTES == 16) {

@@ -23,6 +23,7 @@ __global__ void __launch_bounds__(256) k_cgemm_simt(int64_t M, int64_t N, int64_
                                                     const float2* __restrict__ A,
                                                     const float2* __restrict__ B,
                                                     float2* __restrict__ C) {
+  pdl_wait();
   __shared__ __align__(16) float2 As[BK][BM + PAD];
   __shared__ __align__(16) float2 Bs[BK][BN + PAD];
   const int tid = threadIdx.x;
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(256, 2) k_cgemm_thin(int64_t M, int64_t N, int
                                                       const float2* __restrict__ A,
                                                       const float2* __restrict__ B,
                                                       float2* __restrict__ C) {
+  pdl_wait();
   constexpr int CG = TBN / 16;            // column groups per row
   constexpr int RB = 256 / CG;            // rows per block
   __shared__ __align__(16) float2 As[RB][TBK + 1];
@@ -190,6 +192,7 @@ __global__ void __launch_bounds__(256) k_cgemm_rowwarp(int64_t M, int64_t N, int
                                                       const float2* __restrict__ A,
                                                       const float2* __restrict__ B,
                                                       float2* __restrict__ C) {
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int64_t cgs = (N + 15) / 16;
   const int64_t w = int64_t(blockIdx.x) * 8 + (threadIdx.x >> 5);
@@ -244,6 +247,7 @@ template <int KC, bool PO>
 __global__ void __launch_bounds__(256) k_cgemm_thin2(int64_t M, int N, int K, const float2* __restrict__ A,
                                                     const float2* __restrict__ B, float2* __restrict__ C,
                                                     const __grid_constant__ TcPlaneOut po) {
+  pdl_wait();
   extern __shared__ __align__(16) float2 sm2[];
   constexpr int LD = KC + 2;                      // padded row (float2), 16-byte multiple
   float2* Bt = sm2;                               // [K][16]
@@ -384,8 +388,7 @@ cudaError_t launch_thin2(int64_t M, int64_t N, int64_t K, const float2* A, const
   }
   const int64_t tiles = (M + T2_RT - 1) / T2_RT;
   const int blocks = int(std::min<int64_t>(tiles, int64_t(sms) * occ));
-  k_cgemm_thin2<KC, PO><<<blocks, 256, smem, s>>>(M, int(N), int(K), A, B, C, po);
-  return cudaGetLastError();
+  return launch_pdl(k_cgemm_thin2<KC, PO>, dim3(blocks), dim3(256), smem, s, M, int(N), int(K), A, B, C, po);
 }
 
 }  // namespace
@@ -411,8 +414,7 @@ cudaError_t launch_cgemm_thin(int64_t M, int64_t N, int64_t K, const float2* A, 
   const int64_t cgs = (N + 15) / 16;
   if (K >= 64 && ((M + 255) / 256) * cgs < 256) {   // few rows, long K: warp per row
     const int64_t warps = M * cgs;
-    k_cgemm_rowwarp<<<unsigned((warps + 7) / 8), 256, 0, s>>>(M, N, K, A, B, C);
-    return cudaGetLastError();
+    return launch_pdl(k_cgemm_rowwarp, dim3(unsigned((warps + 7) / 8)), dim3(256), 0, s, M, N, K, A, B, C);
   }
   if (thin_pipelined(M, N, K) && (reinterpret_cast<uintptr_t>(A) & 15) == 0) {
     static const TcPlaneOut none{};
@@ -421,12 +423,11 @@ cudaError_t launch_cgemm_thin(int64_t M, int64_t N, int64_t K, const float2* A, 
   }
   if (N <= 16) {
     dim3 grid(unsigned((M + 255) / 256), unsigned((N + 15) / 16));
-    k_cgemm_thin<16><<<grid, 256, 0, s>>>(M, N, K, A, B, C);
+    return launch_pdl(k_cgemm_thin<16>, grid, dim3(256), 0, s, M, N, K, A, B, C);
   } else {
     dim3 grid(unsigned((M + 127) / 128), unsigned((N + 31) / 32));
-    k_cgemm_thin<32><<<grid, 256, 0, s>>>(M, N, K, A, B, C);
+    return launch_pdl(k_cgemm_thin<32>, grid, dim3(256), 0, s, M, N, K, A, B, C);
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_cgemm_simt(int64_t M, int64_t N, int64_t K, const float2* A, const float2* B,
@@ -434,8 +435,7 @@ cudaError_t launch_cgemm_simt(int64_t M, int64_t N, int64_t K, const float2* A, 
   if (M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid(unsigned((N + BN - 1) / BN), unsigned((M + BM - 1) / BM));
   if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
-  k_cgemm_simt<<<grid, 256, 0, s>>>(M, N, K, A, B, C);
-  return cudaGetLastError();
+  return launch_pdl(k_cgemm_simt, grid, dim3(256), 0, s, M, N, K, A, B, C);
 }
 
 }  // namespace qflex

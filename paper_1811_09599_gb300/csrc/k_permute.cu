@@ -129,6 +129,7 @@ template <int FMT>
 __global__ void __launch_bounds__(256, 6) k_permute_tiled(const float2* __restrict__ in, int64_t in_base,
                                                        const __grid_constant__ PermTile t, void* out,
                                                        int nsplit, int64_t plane, const unsigned* smax) {
+  pdl_wait();
   static_assert((1 << kPermTileBits) % 256 == 0, "tile must be a multiple of the block");
   __shared__ float2 tile[1 << kPermTileBits];
   __shared__ int64_t s_in_lo[32], s_in_hi[64], s_out_lo[32], s_out_hi[64];
@@ -211,6 +212,7 @@ template <int FMT>
 __global__ void k_permute_gather(const float2* __restrict__ in, int64_t in_base,
                                  const __grid_constant__ GatherDesc d, void* out, int nsplit,
                                  int64_t plane, const unsigned* smax) {
+  pdl_wait();
   float scale = 1.f;
   if constexpr (FMT == kFmtFP16) scale = smax ? fp16_scale_of(*smax) : 1.f;
   for (int64_t o = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; o < d.total;
@@ -250,8 +252,9 @@ int grid_for(int64_t work_units) {
 cudaError_t launch_permute_tiled(const float2* in, int64_t in_base, const PermTile& t, int fmt,
                                  int nsplit, void* out, int64_t plane, cudaStream_t s,
                                  const unsigned* smax) {
-#define QF_TILED(F) k_permute_tiled<F><<<grid_for<k_permute_tiled<F>>(t.n_tiles), 256, 0, s>>>( \
+#define QF_TILED(F) e = launch_pdl(k_permute_tiled<F>, dim3(grid_for<k_permute_tiled<F>>(t.n_tiles)), dim3(256), 0, s, \
     in, in_base, t, out, nsplit, plane, smax)
+  cudaError_t e;
   switch (fmt) {
     case kFmtC64: QF_TILED(kFmtC64); break;
     case kFmtTF32: QF_TILED(kFmtTF32); break;
@@ -260,14 +263,15 @@ cudaError_t launch_permute_tiled(const float2* in, int64_t in_base, const PermTi
     default: QF_TILED(kFmtBF16); break;
   }
 #undef QF_TILED
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_permute_gather(const float2* in, int64_t in_base, const GatherDesc& d, int fmt,
                                   int nsplit, void* out, int64_t plane, cudaStream_t s,
                                   const unsigned* smax) {
-#define QF_GATHER(F) k_permute_gather<F><<<grid_for<k_permute_gather<F>>((d.total + 255) / 256), 256, 0, s>>>( \
-    in, in_base, d, out, nsplit, plane, smax)
+#define QF_GATHER(F) e = launch_pdl(k_permute_gather<F>, dim3(grid_for<k_permute_gather<F>>((d.total + 255) / 256)), \
+    dim3(256), 0, s, in, in_base, d, out, nsplit, plane, smax)
+  cudaError_t e;
   switch (fmt) {
     case kFmtC64: QF_GATHER(kFmtC64); break;
     case kFmtTF32: QF_GATHER(kFmtTF32); break;
@@ -276,7 +280,7 @@ cudaError_t launch_permute_gather(const float2* in, int64_t in_base, const Gathe
     default: QF_GATHER(kFmtBF16); break;
   }
 #undef QF_GATHER
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace qflex

@@ -20,6 +20,7 @@ struct SliceSumArgs {
 
 __global__ void k_slicesum(const float2* __restrict__ src, const __grid_constant__ SliceSumArgs a,
                            double* __restrict__ amps) {
+  pdl_wait();
   const int64_t count = int64_t(1) << a.n_open;
   for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < count;
        j += int64_t(gridDim.x) * blockDim.x) {
@@ -261,8 +262,7 @@ cudaError_t launch_slicesum(const float2* src, const int64_t* strides, int n_ope
   a.n_open = n_open;
   const int64_t count = int64_t(1) << n_open;
   const int blocks = int(count < 256 ? 1 : (count + 255) / 256 > 4096 ? 4096 : (count + 255) / 256);
-  k_slicesum<<<blocks, 256, 0, s>>>(src, a, amps);
-  return cudaGetLastError();
+  return launch_pdl(k_slicesum, dim3(blocks), dim3(256), 0, s, src, a, amps);
 }
 
 cudaError_t launch_norm(const double* amps, int64_t n, double* out, cudaStream_t s) {
