@@ -13,6 +13,8 @@
 #include "internal.h"
 
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 namespace qflex {
 namespace {
@@ -374,12 +376,21 @@ template <int KC, bool PO>
 cudaError_t launch_thin2(int64_t M, int64_t N, int64_t K, const float2* A, const float2* B, float2* C,
                          const TcPlaneOut& po, cudaStream_t s) {
   const size_t smem = size_t(K) * 16 * sizeof(float2) + size_t(T2_NST) * T2_RT * (KC + 2) * sizeof(float2);
-  // at most 512 x 16 x 8 + 4 x 64 x 34 x 8 bytes (K <= 512): opt in once
-  static const cudaError_t attr =
-      cudaFuncSetAttribute(k_cgemm_thin2<KC, PO>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  if (attr != cudaSuccess) return attr;
+  // at most 512 x 16 x 8 + 4 x 64 x 34 x 8 bytes (K <= 512): opt in once per device
   int dev = 0, sms = 148, occ = 0;
   cudaGetDevice(&dev);
+  static std::mutex mu;
+  static std::vector<char> opted;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (int(opted.size()) <= dev) opted.resize(size_t(dev) + 1, 0);
+    if (!opted[size_t(dev)]) {
+      const cudaError_t e =
+          cudaFuncSetAttribute(k_cgemm_thin2<KC, PO>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      if (e != cudaSuccess) return e;
+      opted[size_t(dev)] = 1;
+    }
+  }
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgemm_thin2<KC, PO>, 256, smem) != cudaSuccess ||
       occ < 1) {
