@@ -318,36 +318,69 @@ def permute_sweep(api, torch, peaks):
             "peak": "measured hbm_gbs"}
 
 
-def rotation_batch_run(api, torch, precision, local):
+def rotation_batch_run(api, torch, precision, local, chunk=32, n_streams=8):
     """256 uneven rotation circuits (4x4..6x6 grids, depth 1+16..32+1), one
-    amplitude and the gradient w.r.t. every angle each.  Each circuit gets its
-    own plan (created, run, destroyed in turn); GPU time is the sum of CUDA
-    event intervals around the amplitude+gradient calls, wall time includes
-    planning and workspace allocation."""
+    amplitude and the gradient w.r.t. every angle each.
+    sequential: each circuit's plan is created, run and destroyed in turn;
+    GPU time = the sum of CUDA-event intervals around its amplitude+gradient
+    call.  concurrent: circuits are taken `chunk` at a time -- their plans
+    and gradient buffers created first (allocation synchronizes), then the
+    calls issued round-robin on `n_streams` streams -- and the GPU time is
+    the sum over chunks of the interval from the first launch to the last
+    stream's completion.  Wall times include planning and allocation."""
     from qflex_inputs import rotation_batch
     batch = rotation_batch(256, 0)
     g = torch.ones((1, 1), dtype=torch.complex128, device="cuda")
-    gpu_ms = 0.0
-    n_params = 0
+    inputs = [(torch.from_numpy(random_bitstrings(p.n, 1, 5000 + i)).cuda(),
+               torch.from_numpy(p.circuit.angles).cuda()) for i, p in enumerate(batch)]
+    n_params = sum(p.circuit.n_params for p in batch)
+    seq_ms = 0.0
     t0 = time.perf_counter()
     for i, prob in enumerate(batch):
         plan = api.Plan(prob, precision, device=local)
         plan.enable_gradients()
-        bits = torch.from_numpy(random_bitstrings(prob.n, 1, 5000 + i)).cuda()
-        th = torch.from_numpy(prob.circuit.angles).cuda()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        plan.amplitudes_grad(bits, th, g)
+        plan.amplitudes_grad(inputs[i][0], inputs[i][1], g)
         e1.record()
         torch.cuda.synchronize()
-        gpu_ms += e0.elapsed_time(e1)
-        n_params += prob.circuit.n_params
+        seq_ms += e0.elapsed_time(e1)
         plan.close()
-    wall = time.perf_counter() - t0
-    return {"circuits": len(batch), "angles": n_params, "gpu_ms": gpu_ms, "wall_s": wall,
-            "amplitudes_per_s_gpu": len(batch) / (gpu_ms * 1e-3),
-            "gradient_entries_per_s_gpu": n_params / (gpu_ms * 1e-3),
-            "note": "one plan per circuit, created/run/destroyed in turn; not a single persistent launch"}
+    seq_wall = time.perf_counter() - t0
+    streams = [torch.cuda.Stream() for _ in range(n_streams)]
+    conc_ms = 0.0
+    t0 = time.perf_counter()
+    for c0 in range(0, len(batch), chunk):
+        plans = [api.Plan(p, precision, device=local) for p in batch[c0:c0 + chunk]]
+        for pl in plans:
+            pl.enable_gradients()
+        torch.cuda.synchronize()
+        main = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(main)
+        for j, pl in enumerate(plans):
+            st = streams[j % n_streams]
+            st.wait_event(e0)
+            with torch.cuda.stream(st):
+                pl.amplitudes_grad(inputs[c0 + j][0], inputs[c0 + j][1], g, stream=st)
+        for st in streams:
+            main.wait_stream(st)
+        e1.record(main)
+        torch.cuda.synchronize()
+        conc_ms += e0.elapsed_time(e1)
+        for pl in plans:
+            pl.sync()
+            pl.close()
+    conc_wall = time.perf_counter() - t0
+    return {"circuits": len(batch), "angles": n_params,
+            "sequential": {"gpu_ms": round(seq_ms, 2), "wall_s": round(seq_wall, 3),
+                           "amplitudes_per_s_gpu": round(len(batch) / (seq_ms * 1e-3), 1),
+                           "gradient_entries_per_s_gpu": round(n_params / (seq_ms * 1e-3), 1)},
+            "concurrent": {"chunk": chunk, "streams": n_streams, "gpu_ms": round(conc_ms, 2),
+                           "wall_s": round(conc_wall, 3),
+                           "amplitudes_per_s_gpu": round(len(batch) / (conc_ms * 1e-3), 1),
+                           "gradient_entries_per_s_gpu": round(n_params / (conc_ms * 1e-3), 1)},
+            "note": "one plan per circuit; concurrent = independent circuits on several streams"}
 
 
 def bris70_run(api, torch, precision, local):

@@ -84,3 +84,35 @@ def test_batch_split_precision_members(api):
         ref = NW.slice_amplitudes(prob, bs[0], 0)
         assert amp_error(amps, ref, prob.n) < 1e-4
         assert np.all(np.isfinite(grad))
+
+
+def test_batch_concurrent_streams_match_sequential(api):
+    """Independent circuits of the batch run concurrently on several streams
+    (as bench.py times them) give exactly the sequential amplitudes and
+    gradients: each plan owns its workspace and status word."""
+    members = BATCH[:12]
+    g = torch.ones((1, 1), dtype=torch.complex128, device="cuda")
+    inputs = [(torch.from_numpy(random_bitstrings(p.n, 1, 900 + i)).cuda(),
+               torch.from_numpy(p.circuit.angles).cuda()) for i, p in enumerate(members)]
+    seq = []
+    for p, (b, th) in zip(members, inputs):
+        plan = api.Plan(p, "bf16x3", device=0)
+        a, gr = plan.amplitudes_grad(b, th, g)
+        plan.sync()
+        seq.append((a.cpu().numpy(), gr.cpu().numpy()))
+        plan.close()
+    plans = [api.Plan(p, "bf16x3", device=0) for p in members]
+    for pl in plans:
+        pl.enable_gradients()
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    outs = []
+    for j, pl in enumerate(plans):
+        st = streams[j % 4]
+        st.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(st):
+            outs.append(pl.amplitudes_grad(inputs[j][0], inputs[j][1], g, stream=st))
+    torch.cuda.synchronize()
+    for pl, (a, gr), (sa, sg) in zip(plans, outs, seq):
+        pl.sync()
+        assert np.array_equal(a.cpu().numpy(), sa) and np.array_equal(gr.cpu().numpy(), sg)
