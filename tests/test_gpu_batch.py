@@ -88,8 +88,10 @@ def test_batch_split_precision_members(api):
 
 def test_batch_concurrent_streams_match_sequential(api):
     """Independent circuits of the batch run concurrently on several streams
-    (as bench.py times them) give exactly the sequential amplitudes and
-    gradients: each plan owns its workspace and status word."""
+    (as bench.py times them) give exactly the sequential amplitudes, and the
+    same gradients up to the order of their FP64 atomic accumulation (each
+    angle's gradient is summed with atomicAdd over grid-tensor entries):
+    each plan owns its workspace and status word."""
     members = BATCH[:12]
     g = torch.ones((1, 1), dtype=torch.complex128, device="cuda")
     inputs = [(torch.from_numpy(random_bitstrings(p.n, 1, 900 + i)).cuda(),
@@ -115,4 +117,6 @@ def test_batch_concurrent_streams_match_sequential(api):
     torch.cuda.synchronize()
     for pl, (a, gr), (sa, sg) in zip(plans, outs, seq):
         pl.sync()
-        assert np.array_equal(a.cpu().numpy(), sa) and np.array_equal(gr.cpu().numpy(), sg)
+        assert np.array_equal(a.cpu().numpy(), sa)
+        gc = gr.cpu().numpy()
+        assert np.max(np.abs(gc - sg)) <= 1e-12 * np.max(np.abs(sg)) + 1e-300
