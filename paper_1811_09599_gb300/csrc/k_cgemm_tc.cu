@@ -156,7 +156,7 @@ struct Cfg {
   static_assert(NSTAGE >= 2, "pipeline needs at least two stages");
   static_assert(SMEM <= 232448, "shared memory per CTA");
 };
-constexpr int KB_CHUNK = 4;      // k-blocks accumulated in TMEM before promotion to registers
+constexpr int KB_CHUNK = 8;      // k-blocks accumulated in TMEM before promotion to registers
 constexpr int EPI_WARPS = 8;
 
 // Tile order of the persistent walk: groups of TILE_GROUP row blocks, each
