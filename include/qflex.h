@@ -20,10 +20,13 @@
  *    caller owns every input and output buffer.
  *  - A plan owns one device workspace allocated in qflex_plan_create (the
  *    paper preallocates scratch space once, Methods "Implementation of the
- *    simulator"); no call allocates device memory afterwards.
+ *    simulator"); afterwards only qflex_plan_enable_gradients (the reverse
+ *    pass's buffers, once) and qflex_fidelity_samples (stream-ordered
+ *    scratch) allocate device memory.
  *  - Calls that take a stream enqueue work on it and return at once; the
  *    returned status covers argument checks and launches.  Errors detected on
- *    the device (a bounded wait that ran out) set a status word that
+ *    the device (a bounded wait that ran out; a fused store whose computed
+ *    position fell outside its planes, skipped) set a status word that
  *    qflex_plan_sync / qflex_device_status report.
  *  - Nothing throws across the ABI; on failure the call returns a nonzero
  *    qflex_status and qflex_last_error() describes it (thread-local string).
