@@ -9,17 +9,22 @@
 //  * ordering: randomized greedy over the per-slice network (cut bonds
 //    removed), best of several trials.  Each step contracts the pair of live
 //    tensors sharing a bond with the smallest key
-//      r - alpha * max(a, b) + tau * gumbel     (log2 sizes: result r,
-//                                                inputs a, b)
-//    ties broken by the work 2^(a + b - s); the larger tensor keeps its id
-//    (dst).  Tensors sharing no bond are joined only when no connected pair
-//    is left.  Trial 0 is deterministic (alpha = 1, tau = 0: least growth of
-//    the larger operand); the others draw alpha in [0, 1.5] and tau in
-//    [0, 1] from a SplitMix64 stream.  The best trial has the smallest
-//    excess of its largest tensor over the limit, then the least work.
-//  * cuts: while the largest tensor of the greedy ordering exceeds the
-//    limit, add the bond whose cut gives the smallest largest tensor, ties
-//    broken by the total work of one bitstring.
+//      r - alpha * max(a, b) + beta * log2 runs(D) + tau * gumbel
+//    (log2 sizes: result r, inputs a, b; D the cuts the result depends on,
+//    runs(D) how often the step reruns per bitstring, below), plus a large
+//    penalty when r exceeds the size limit, so that such a step is taken only
+//    when nothing else is left; ties are broken by the work 2^(a + b - s) and
+//    the larger tensor keeps its id (dst).  Tensors sharing no bond are
+//    joined only when no connected pair is left.  Trial 0 is deterministic
+//    (alpha = 1, beta = tau = 0: least growth of the larger operand); the
+//    others draw alpha in [0, 1.5] and tau in [0, 1], and every odd one beta
+//    in [0, 2] (steps that rerun per path are put off), from a SplitMix64
+//    stream.  The best trial has the smallest excess of its largest tensor
+//    over the limit, then the least work.
+//  * cuts: beam search.  While the best cut set's ordering exceeds the
+//    limit, every set of the beam is extended by every bond not yet cut and
+//    the kCutBeam best distinct sets (same ranking) carry on.  The chosen set
+//    then gets an ordering search with four times the trials.
 //  * work model: a step depending on cuts D runs once per change of those
 //    cuts in mixed-radix slice order (first cut most significant), i.e.
 //    prod_{c <= max D} 2^{K_c} times per bitstring, 2^(a + b - s) complex
@@ -77,9 +82,10 @@ uint64_t splitmix(uint64_t& x) {
 }
 double uniform01(uint64_t& x) { return (double(splitmix(x) >> 11) + 0.5) * 0x1.0p-53; }
 
-// One greedy pass with parameters (alpha, tau) and noise stream `rng`.
-bool greedy_pass(const SearchNet& net, const std::vector<int>& cuts, double alpha, double tau, uint64_t rng,
-                 SearchResult* out) {
+// One greedy pass with parameters (alpha, beta, tau) and noise stream `rng`;
+// results above 2^log2_limit entries are taken only when nothing else is left.
+bool greedy_pass(const SearchNet& net, const std::vector<int>& cuts, double alpha, double beta, double tau,
+                 double log2_limit, uint64_t rng, SearchResult* out) {
   const int n = net.n, E = int(net.edges.size());
   if (n < 1) return false;
   std::vector<int> cut_idx(size_t(E), -1);
@@ -135,6 +141,8 @@ bool greedy_pass(const SearchNet& net, const std::vector<int>& cuts, double alph
         const int ra = t[size_t(a)].bits, rb = t[size_t(b)].bits;
         const int rr = ra + rb - 2 * s;
         double key = double(rr) - alpha * double(std::max(ra, rb));
+        if (beta > 0) key += beta * std::log2(runs_of(t[size_t(a)].dep | t[size_t(b)].dep));
+        if (double(rr) > log2_limit) key += 1e6;
         if (tau > 0) key -= tau * std::log(-std::log(uniform01(rng)));
         const double work = std::ldexp(1.0, ra + rb - s);
         const bool better = best_a < 0 || (conn && !best_conn) || key < best_key ||
@@ -165,6 +173,8 @@ bool greedy_pass(const SearchNet& net, const std::vector<int>& cuts, double alph
   return true;
 }
 
+constexpr int kCutBeam = 3;   // cut sets kept per level of the cut search
+
 bool better_result(const SearchResult& x, const SearchResult& y, double log2_limit) {
   const double ox = std::max(0.0, x.log2_max - log2_limit), oy = std::max(0.0, y.log2_max - log2_limit);
   return ox < oy || (ox == oy && x.cmacs < y.cmacs);
@@ -180,8 +190,9 @@ bool search_greedy_order(const SearchNet& net, const std::vector<int>& cuts, Sea
   for (int i = 0; i < std::max(1, trials); ++i) {
     const double alpha = i == 0 ? 1.0 : 1.5 * uniform01(x);
     const double tau = i == 0 ? 0.0 : uniform01(x);
+    const double beta = (i % 2 == 1) ? 2.0 * uniform01(x) : 0.0;   // odd passes weigh reuse
     SearchResult r;
-    if (!greedy_pass(net, cuts, alpha, tau, splitmix(x), &r)) return false;
+    if (!greedy_pass(net, cuts, alpha, beta, tau, log2_limit, splitmix(x), &r)) return false;
     if (!have || better_result(r, best, log2_limit)) {
       best = std::move(r);
       have = true;
@@ -193,29 +204,52 @@ bool search_greedy_order(const SearchNet& net, const std::vector<int>& cuts, Sea
 
 bool search_cuts(const SearchNet& net, std::vector<int> cuts, int max_new, double log2_limit,
                  std::vector<int>* cuts_out, SearchResult* out, int trials, uint64_t seed) {
-  SearchResult cur;
-  if (!search_greedy_order(net, cuts, &cur, trials, log2_limit, seed)) return false;
-  for (int added = 0; cur.log2_max > log2_limit && added < max_new; ++added) {
-    int best_e = -1;
-    SearchResult best;
-    for (int e = 0; e < int(net.edges.size()); ++e) {
-      if (net.bits[size_t(e)] == 0 || std::find(cuts.begin(), cuts.end(), e) != cuts.end()) continue;
-      std::vector<int> trial = cuts;
-      trial.push_back(e);
-      SearchResult r;
-      if (!search_greedy_order(net, trial, &r, trials, log2_limit, seed)) continue;
-      if (best_e < 0 || better_result(r, best, log2_limit)) {
-        best_e = e;
-        best = std::move(r);
+  struct State {
+    std::vector<int> cuts;
+    SearchResult r;
+  };
+  std::vector<State> beam(1);
+  beam[0].cuts = cuts;
+  if (!search_greedy_order(net, cuts, &beam[0].r, trials, log2_limit, seed)) return false;
+  for (int added = 0; beam[0].r.log2_max > log2_limit && added < max_new; ++added) {
+    // every state of the beam, extended by every bond not yet cut; the
+    // kCutBeam best distinct cut sets carry on to the next level
+    std::vector<State> next;
+    for (const State& st : beam) {
+      for (int e = 0; e < int(net.edges.size()); ++e) {
+        if (net.bits[size_t(e)] == 0 || std::find(st.cuts.begin(), st.cuts.end(), e) != st.cuts.end()) continue;
+        State c;
+        c.cuts = st.cuts;
+        c.cuts.push_back(e);
+        std::vector<int> key_c(c.cuts.begin() + long(cuts.size()), c.cuts.end());
+        std::sort(key_c.begin(), key_c.end());
+        bool dup = false;
+        for (const State& o : next) {
+          std::vector<int> key_o(o.cuts.begin() + long(cuts.size()), o.cuts.end());
+          std::sort(key_o.begin(), key_o.end());
+          if (key_o == key_c) {
+            dup = true;
+            break;
+          }
+        }
+        if (dup || !search_greedy_order(net, c.cuts, &c.r, trials, log2_limit, seed)) continue;
+        next.push_back(std::move(c));
       }
     }
-    if (best_e < 0) break;
-    cuts.push_back(best_e);
-    cur = std::move(best);
+    if (next.empty()) break;
+    std::stable_sort(next.begin(), next.end(),
+                     [&](const State& x, const State& y) { return better_result(x.r, y.r, log2_limit); });
+    if (next.size() > size_t(kCutBeam)) next.resize(size_t(kCutBeam));
+    beam = std::move(next);
   }
-  const bool fits = cur.log2_max <= log2_limit;
-  *cuts_out = cuts;
-  *out = std::move(cur);
+  // the chosen cut set gets a longer ordering search of its own
+  SearchResult polished;
+  if (search_greedy_order(net, beam[0].cuts, &polished, 4 * std::max(1, trials), log2_limit, seed ^ 0x5851F42D4C957F2Dull) &&
+      better_result(polished, beam[0].r, log2_limit))
+    beam[0].r = std::move(polished);
+  const bool fits = beam[0].r.log2_max <= log2_limit;
+  *cuts_out = beam[0].cuts;
+  *out = std::move(beam[0].r);
   return fits;
 }
 

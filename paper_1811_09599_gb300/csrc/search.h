@@ -27,7 +27,7 @@ struct SearchResult {
 bool search_greedy_order(const SearchNet& net, const std::vector<int>& cuts, SearchResult* out, int trials = 1,
                          double log2_limit = 1e300, uint64_t seed = 0);
 
-// Adds up to max_new cuts to `cuts` until the ordering's largest tensor has
+// Adds up to max_new cuts to `cuts` (beam search) until the ordering's largest tensor has
 // at most 2^log2_limit entries; returns whether it fits.
 bool search_cuts(const SearchNet& net, std::vector<int> cuts, int max_new, double log2_limit,
                  std::vector<int>* cuts_out, SearchResult* out, int trials = 1, uint64_t seed = 0);

@@ -103,7 +103,7 @@ def test_search_work_model_matches_planner(api):
 
 def test_search_7x7_finds_two_cut_plan(api):
     """7x7, 1+32+1, no cuts given, limit 2^24 entries: two cuts (256 paths)
-    suffice, as in the paper's hand plan, at no more than 1.25x its work."""
+    suffice, as in the paper's hand plan, at no more than 1.15x its work."""
     from paper_1811_09599_gb300.api import Plan
     p = c2_problem(0)
     r = api.search_ordering(Problem(p.circuit, [], p.open_tile, None), 1 << 24, 4, trials=32, seed=0)
@@ -112,7 +112,7 @@ def test_search_7x7_finds_two_cut_plan(api):
     hand = Plan(p, "bf16x3", device=-1).cost(1)["cmacs"]
     found = Plan(Problem(p.circuit, r["cuts"], p.open_tile, r["ordering"]), "bf16x3", device=-1)
     assert found.info()["max_tensor_elems"] <= 1 << 24
-    assert found.cost(1)["cmacs"] <= 1.25 * hand
+    assert found.cost(1)["cmacs"] <= 1.15 * hand
     # deterministic for a given seed
     again = api.search_ordering(Problem(p.circuit, [], p.open_tile, None), 1 << 24, 4, trials=32, seed=0)
     assert again["cuts"] == r["cuts"] and again["ordering"] == r["ordering"]
@@ -120,10 +120,16 @@ def test_search_7x7_finds_two_cut_plan(api):
 
 def test_search_bristlecone_70(api):
     """Bris-70, 1+32+1, limit 2^28 entries: four cuts (2^16 paths) suffice,
-    the configuration the paper states for this lattice."""
+    the configuration the paper states for this lattice, with no more work
+    than the hand plan's cuts and ordering."""
+    from paper_1811_09599_gb300.api import Plan
     d = diamond_problem(32, 0)
     r = api.search_ordering(Problem(d.circuit, [], d.open_tile, None), 1 << 28, 5, trials=8, seed=0)
     assert r["fits"] and len(r["cuts"]) == 4 and r["n_slices"] == 65536
+    hand = Plan(d, "bf16x3", device=-1).cost(1)["cmacs"]
+    found = Plan(Problem(d.circuit, r["cuts"], d.open_tile, r["ordering"]), "bf16x3", device=-1)
+    assert found.info()["max_tensor_elems"] <= 1 << 28
+    assert found.cost(1)["cmacs"] <= hand
 
 
 def test_search_limits_and_defaults(api):
