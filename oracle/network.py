@@ -21,6 +21,8 @@ Follows the paper's construction step by step, in plain NumPy:
   stay open, so one contraction gives 2^{|tile|} amplitudes.
 * Fraction-f sums (Methods, "Summing a fraction of the paths"): summing a
   subset of slices, with no rescaling.
+* Paths that vanish identically (projector_runs): CZ projector halves on
+  one qubit with only diagonal gates between them must agree.
 """
 from __future__ import annotations
 
@@ -104,6 +106,70 @@ def slice_values(circ, cut_edges: Sequence[int], s: int) -> Dict[int, int]:
         vals[e] = s % r
         s //= r
     return vals
+
+
+# Gates whose matrix is diagonal for every angle (the Z half of a CZ and its
+# projector half are diagonal too; iSWAP halves are not).
+_DIAGONAL_1Q = ("T", "RZ")
+
+
+def projector_runs(circ, cut_edges: Sequence[int]) -> Tuple[List[List[Tuple[int, int]]], List[bool]]:
+    """Per qubit, the maximal stretches of its time line free of non-diagonal
+    gates, each reduced to the CZ projector halves |k><k| it holds on cut
+    edges, as (edge, bit position in the edge's value) pairs; and whether
+    the stretch is the first one (it then acts on the input |0>).
+
+    Projectors multiply through diagonal gates: |j><j| D |k><k| = 0 unless
+    j = k, and |k><k| |0> = 0 unless k = 0.  So a path whose cut values give
+    two different bits inside one stretch, or a 1 inside a first stretch, is
+    zero for every bitstring and every angle (Methods, "Cutting indexes": a
+    path is the network with the cut bonds fixed)."""
+    K = bond_exponents(circ)
+    cut = set(int(e) for e in cut_edges)
+    runs: List[List[Tuple[int, int]]] = []
+    first: List[bool] = []
+    for q in range(circ.n):
+        used: Dict[int, int] = {}
+        cur: List[Tuple[int, int]] = []
+        is_first = True
+        for g in sorted((g for g in circ.gates if q in (g.q0, g.q1)), key=lambda g: g.cycle):
+            if g.kind in ("CZ", "ISWAP"):
+                e = circ.lattice.edge_index[(min(g.q0, g.q1), max(g.q0, g.q1))]
+                j = used.get(e, 0)
+                used[e] = j + _GATE_BITS[g.kind]
+                if g.kind == "CZ":
+                    other = g.q1 if g.q0 == q else g.q0
+                    if q < other and e in cut:
+                        cur.append((e, int(K[e]) - 1 - j))   # first bit in time = most significant
+                    continue
+            elif g.kind in _DIAGONAL_1Q:
+                continue
+            # a non-diagonal gate closes the stretch
+            runs.append(cur)
+            first.append(is_first)
+            cur, is_first = [], False
+        runs.append(cur)
+        first.append(is_first)
+    return runs, first
+
+
+def structurally_zero(circ, cut_edges: Sequence[int], s: int, runs=None) -> bool:
+    """Whether path s vanishes identically by the projector rule of
+    projector_runs (the last stretch of a qubit meets the bitstring's <x_q|
+    and is not used: the rule holds for every bitstring)."""
+    runs, first = projector_runs(circ, cut_edges) if runs is None else runs
+    vals = slice_values(circ, cut_edges, s)
+    for members, is_first in zip(runs, first):
+        bits = {(vals[e] >> b) & 1 for e, b in members}
+        if len(bits) > 1 or (is_first and 1 in bits):
+            return True
+    return False
+
+
+def nonzero_slices(circ, cut_edges: Sequence[int]) -> List[int]:
+    """Ascending ids of the paths that projector_runs does not rule out."""
+    runs = projector_runs(circ, cut_edges)
+    return [s for s in range(n_slices(circ, cut_edges)) if not structurally_zero(circ, cut_edges, s, runs)]
 
 
 def _fix(arr: np.ndarray, legs: List[tuple], fixed: Dict[tuple, int]):

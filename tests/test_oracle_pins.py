@@ -22,6 +22,7 @@ from oracle import selection as SEL
 from oracle import statevector as SV
 from qflex_inputs import (c1_problem, grid_lattice, grid_problem,
                           random_bitstrings, random_circuit)
+from qflex_inputs.circuits import Circuit, Gate
 
 
 # ---------------------------------------------------------------- gates
@@ -212,6 +213,83 @@ def test_mixed_radix_first_cut_most_significant():
     e0, e1 = p.cut_edges
     assert NW.slice_values(p.circuit, p.cut_edges, 1) == {e0: 0, e1: 1}
     assert NW.slice_values(p.circuit, p.cut_edges, 4) == {e0: 1, e1: 0}
+
+
+def _circuit_2x2(body):
+    """2x2 grid (edges (0,1), (0,2), (1,3), (2,3)) with the given gates."""
+    lat = grid_lattice(2, 2)
+    return Circuit(lat, 4, list(body), np.zeros(0)), lat.edge_index
+
+
+def _assert_zero_rule_against_statevector(circ, cuts):
+    """Every path the projector rule rules out is the zero vector under the
+    state-vector substitution of its cut values; every other path is not;
+    the kept paths sum to the uncut state."""
+    nz = set(NW.nonzero_slices(circ, cuts))
+    total = np.zeros((2,) * circ.n, dtype=np.complex128)
+    for s in range(NW.n_slices(circ, cuts)):
+        psi = SV.final_state(circ, cut_values=NW.slice_values(circ, cuts, s))
+        if s in nz:
+            assert np.linalg.norm(psi) > 1e-6, s
+            total += psi
+        else:
+            assert np.max(np.abs(psi)) == 0.0, s
+    assert np.max(np.abs(total - SV.final_state(circ))) < 1e-14
+    return nz
+
+
+def test_structurally_zero_paths_closed_forms():
+    """Closed forms of the projector rule (P_j P_k = delta_jk P_k through
+    diagonal gates; P_k |0> = delta_k0 |0>) on hand-made 2x2 circuits."""
+    H = lambda c, qs=range(4): [Gate(c, "H", q) for q in qs]
+    # qubit 0 is the projector side of (0,1) and (0,2); only T between them
+    circ, ei = _circuit_2x2(H(0) + [Gate(1, "CZ", 0, 1), Gate(2, "T", 0), Gate(3, "CZ", 0, 2)] + H(4))
+    cuts = [ei[(0, 1)], ei[(0, 2)]]
+    assert _assert_zero_rule_against_statevector(circ, cuts) == {0, 3}
+    # a non-diagonal gate between them: no constraint
+    circ, ei = _circuit_2x2(H(0) + [Gate(1, "CZ", 0, 1), Gate(2, "SX", 0), Gate(3, "CZ", 0, 2)] + H(4))
+    assert _assert_zero_rule_against_statevector(circ, cuts) == {0, 1, 2, 3}
+    # qubit 3 is the Z side of (1,3) and (2,3): Z halves never vanish
+    circ, ei = _circuit_2x2(H(0) + [Gate(1, "CZ", 1, 3), Gate(2, "RZ", 3, param=0), Gate(3, "CZ", 2, 3)] + H(4))
+    circ = circ.with_angles(np.array([0.7]))
+    assert _assert_zero_rule_against_statevector(circ, [ei[(1, 3)], ei[(2, 3)]]) == {0, 1, 2, 3}
+    # a projector before qubit 0's first non-diagonal gate acts on |0>
+    circ, ei = _circuit_2x2(H(0, (1, 2, 3)) + [Gate(1, "CZ", 0, 1), Gate(2, "H", 0)] + H(3))
+    assert _assert_zero_rule_against_statevector(circ, [ei[(0, 1)]]) == {0}
+    # two CZs on one edge with RZ between: its two bits agree (values 00, 11)
+    circ, ei = _circuit_2x2(H(0) + [Gate(1, "CZ", 0, 1), Gate(2, "RZ", 0, param=0), Gate(3, "CZ", 0, 1)] + H(4))
+    circ = circ.with_angles(np.array([1.3]))
+    assert _assert_zero_rule_against_statevector(circ, [ei[(0, 1)]]) == {0, 3}
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_structurally_zero_paths_random_circuits(seed):
+    """3x3, 1+16+1, cuts on the two bonds whose projector side is the centre
+    qubit and one more: the rule removes some paths, and the state vector
+    confirms each removed path vanishes and the rest sum to the state."""
+    circ = random_circuit(grid_lattice(3, 3), 16, seed)
+    ei = circ.lattice.edge_index
+    cuts = [ei[(4, 5)], ei[(4, 7)], ei[(1, 2)]]
+    nz = _assert_zero_rule_against_statevector(circ, cuts)
+    assert len(nz) < NW.n_slices(circ, cuts)
+
+
+def test_structurally_zero_planted_mistakes_fail(monkeypatch):
+    """A rule that also treats X^1/2 and Y^1/2 as diagonal, or that forgets
+    the input |0>, disagrees with the state vector."""
+    circ = random_circuit(grid_lattice(3, 3), 16, 0)
+    ei = circ.lattice.edge_index
+    cuts = [ei[(4, 5)], ei[(4, 7)], ei[(1, 2)]]
+    monkeypatch.setattr(NW, "_DIAGONAL_1Q", ("T", "RZ", "SX", "SY"))
+    with pytest.raises(AssertionError):
+        _assert_zero_rule_against_statevector(circ, cuts)
+    monkeypatch.setattr(NW, "_DIAGONAL_1Q", ("T", "RZ"))
+    H = lambda c, qs=range(4): [Gate(c, "H", q) for q in qs]
+    circ, ei = _circuit_2x2(H(0, (1, 2, 3)) + [Gate(1, "CZ", 0, 1), Gate(2, "H", 0)] + H(3))
+    orig = NW.projector_runs
+    monkeypatch.setattr(NW, "projector_runs", lambda c, cu: (orig(c, cu)[0], [False] * len(orig(c, cu)[1])))
+    with pytest.raises(AssertionError):
+        _assert_zero_rule_against_statevector(circ, [ei[(0, 1)]])
 
 
 def test_planted_mistakes_fail_a_pin(monkeypatch):
