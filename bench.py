@@ -383,15 +383,28 @@ def rotation_batch_run(api, torch, precision, local, chunk=32, n_streams=8):
             "note": "one plan per circuit; concurrent = independent circuits on several streams"}
 
 
-def bris70_run(api, torch, precision, local):
+def bris70_run(api, torch, precision, local, searched=False):
     """70-qubit Bristlecone-like diamond, depth 1+32+1, four cuts (2^16 paths,
-    2^28-entry intermediates), fidelity f = 0.01 (655 paths chosen by the
-    seeded Fisher-Yates rule), 8-qubit open tile: 256 amplitudes of one
-    bitstring, with the FP64 norm estimate 2^n <|a|^2> (~f expected)."""
+    2^28-entry intermediates), fidelity f = 0.01 (a fraction f of the paths
+    that do not vanish identically, chosen by the seeded Fisher-Yates rule:
+    655 of 65536 with the region cuts), 8-qubit open tile: 256 amplitudes of
+    one bitstring, with the FP64 norm estimate 2^n <|a|^2> (~f expected).
+    searched: cuts and ordering from the automated search (no cuts given,
+    up to four added, 2^28-entry limit, 8 passes, seed 0) instead of the
+    region plan."""
     from qflex_inputs import diamond_problem
+    from qflex_inputs.problems import Problem
     prob = diamond_problem(32, 0)
+    info = {}
+    if searched:
+        t0 = time.perf_counter()
+        r = api.search_ordering(Problem(prob.circuit, [], prob.open_tile, None), 1 << 28, 4, trials=8, seed=0)
+        info = {"search_s": round(time.perf_counter() - t0, 2), "cuts": r["cuts"]}
+        if not r["fits"] or r["n_slices"] != 65536:
+            raise RuntimeError(f"search did not reach four cuts within 2^28 entries: {r}")
+        prob = Problem(prob.circuit, r["cuts"], prob.open_tile, r["ordering"])
     plan = api.Plan(prob, precision, device=local)
-    sel = plan.select_slices(0.01, 2026)
+    sel = plan.select_slices(0.01, 2026, nonzero=True)
     bits = torch.from_numpy(random_bitstrings(prob.n, 1, 3000)).cuda()
     plan.amplitudes(bits, None, sel[:4])                 # warm (plans, tensor maps)
     torch.cuda.synchronize()
@@ -404,12 +417,14 @@ def bris70_run(api, torch, precision, local):
     ms = e0.elapsed_time(e1)
     cost = plan.cost(1, sel)
     nrm = api.norm(amps).item()
+    n_nonzero, n_slices = int(plan.info()["n_nonzero_slices"]), int(plan.n_slices)
     plan.close()
-    return {"paths": int(len(sel)), "of": 65536, "amplitudes": int(amps.numel()), "ms": ms,
+    return {"paths": int(len(sel)), "of": n_nonzero, "n_slices": n_slices,
+            "amplitudes": int(amps.numel()), "ms": ms,
             "amplitudes_per_s": amps.numel() / (ms * 1e-3),
             "tflops_cgemm": cost["cmacs"] * 8 / (ms * 1e-3) / 1e12,
             "norm_estimate": nrm * 2.0 ** prob.n / amps.numel(),
-            "max_tensor_entries": 2 ** 28}
+            "max_tensor_entries": 2 ** 28, **info}
 
 
 def c4_subset(api, torch, precision, local):
@@ -631,6 +646,7 @@ def run_ours(args):
         extras["permute"] = permute_sweep(api, torch, peaks)
         extras["rotation_batch"] = rotation_batch_run(api, torch, args.precision, local)
         extras["bris70_f001"] = bris70_run(api, torch, args.precision, local)
+        extras["bris70_f001_searched"] = bris70_run(api, torch, args.precision, local, searched=True)
         extras["grid7x7_iswap"] = iswap_run(api, torch, args.precision, local)
         if not args.no_c4:
             extras["grid7x7_d40"] = c4_subset(api, torch, args.precision, local)

@@ -124,6 +124,7 @@ typedef struct {
   size_t workspace_bytes;    /* device bytes owned by the plan */
   int32_t n_tc_steps;        /* steps whose GEMM runs on the tensor cores */
   int32_t n_persistent_buffers;
+  int64_t n_nonzero_slices;  /* paths that do not vanish identically (qflex_nonzero_slices) */
 } qflex_plan_info;
 
 /* Work of one qflex_amplitudes call, counted by replaying the schedule on the
@@ -180,10 +181,6 @@ qflex_status qflex_plan_get_info(qflex_plan plan, qflex_plan_info* info);
 qflex_status qflex_plan_cost(qflex_plan plan, int64_t n_bs, const int64_t* slice_ids,
                              int64_t n_slice_ids, qflex_cost* out);
 
-/* Fraction-f path choice (Methods, "Summing a fraction of the paths"):
- * n_f = max(1, floor(f P + 1/2)) capped at P, the first n_f entries of a
- * Fisher-Yates shuffle of 0..P-1 driven by SplitMix64(seed), sorted.
- * slice_ids: host, capacity >= n_f. */
 /* The schedule's steps for a call over n_bs bitstrings and `slice_ids` (host,
  * NULL = all): out[i] for i < min(cap, n_steps); *n_steps = number of steps. */
 qflex_status qflex_plan_steps(qflex_plan plan, int64_t n_bs, const int64_t* slice_ids, int64_t n_slice_ids,
@@ -194,14 +191,18 @@ qflex_status qflex_plan_steps(qflex_plan plan, int64_t n_bs, const int64_t* slic
  * SI A).  Ordering: randomized greedy over the per-slice network (cut bonds
  * removed), best of `trials` passes: each step contracts the pair of live
  * tensors sharing a bond with the smallest log2(result) - alpha log2(larger
- * input) + tau * Gumbel noise (pass 0: alpha = 1, tau = 0; the others draw
- * alpha in [0, 1.5], tau in [0, 1] from SplitMix64(seed)); the larger tensor
- * keeps its id; passes rank by the excess of their largest tensor over the
- * limit, then by work.  Cuts: starting from `cut_edges` (kept, in order), up to
- * `max_new_cuts` bonds are appended, each the one whose cut gives the
- * smallest largest tensor (ties: least work per bitstring), until the largest
- * tensor has at most max_tensor_elems entries.  Work counts each step as
- * often as the executor runs it (once per change of the cuts it depends on).
+ * input) + beta log2(runs of the result) + tau * Gumbel noise, steps whose
+ * result exceeds the limit last (pass 0: alpha = 1, beta = tau = 0; the
+ * others draw alpha in [0, 1.5], tau in [0, 1] and, every second pass,
+ * beta in [0, 2] from SplitMix64(seed)); the larger tensor keeps its id;
+ * passes rank by the excess of their largest tensor over the limit, then by
+ * work.  Cuts: starting from `cut_edges` (kept, in order), up to
+ * `max_new_cuts` bonds are appended by a beam search (three cut sets per
+ * level, each extended by every bond, same ranking) until the largest
+ * tensor has at most max_tensor_elems entries; the chosen set gets an
+ * ordering search with 4 x trials.  Work counts each step as often as the
+ * executor runs it: once per change of the cuts it depends on, over the
+ * paths that do not vanish identically (qflex_nonzero_slices).
  * circuit/open_tile/cut_edges: host, as in qflex_problem.  cuts_out: host,
  * capacity n_cuts + max_new_cuts; steps_out: host, capacity 2 (n_qubits - 1)
  * (dst, src) pairs, usable as a qflex_ordering.  Returns QFLEX_ERR_PLAN (with
@@ -209,7 +210,8 @@ qflex_status qflex_plan_steps(qflex_plan plan, int64_t n_bs, const int64_t* slic
 typedef struct {
   double log2_max_tensor;      /* log2 entries of the largest tensor */
   double cmacs_per_bitstring;  /* complex MACs of one bitstring over all slices, with reuse */
-  double n_slices;
+  double n_slices;             /* P of the cuts found */
+  double n_nonzero_slices;     /* of which do not vanish identically */
   int32_t n_cuts;
   int32_t n_steps;
 } qflex_search_result;
@@ -218,8 +220,33 @@ qflex_status qflex_search_ordering(const qflex_circuit* circuit, const int32_t* 
                                    int64_t max_tensor_elems, int32_t trials, uint64_t seed, int32_t* cuts_out,
                                    int32_t* steps_out, qflex_search_result* out);
 
+/* Fraction-f path choice (Methods, "Summing a fraction of the paths"):
+ * n_f = max(1, floor(f P + 1/2)) capped at P, the first n_f entries of a
+ * Fisher-Yates shuffle of 0..P-1 driven by SplitMix64(seed), sorted.
+ * slice_ids: host, capacity >= n_f. */
 qflex_status qflex_select_slices(qflex_plan plan, double fidelity, uint64_t seed,
                                  int64_t* slice_ids, int64_t capacity, int64_t* n_selected);
+
+/* Paths that vanish identically.  A path fixes the cut bonds (Methods,
+ * "Cutting indexes").  On one qubit, the CZ projector halves |k><k| (lower-
+ * index qubit of each CZ) multiply through diagonal gates (T, R_Z, Z halves)
+ * to zero unless their bits agree, and one met before the qubit's first
+ * non-diagonal gate acts on |0> and needs k = 0.  A path that breaks this
+ * contributes exactly zero for every bitstring and angle; qflex_amplitudes,
+ * qflex_amplitudes_grad and qflex_plan_cost skip such paths, in `slice_ids`
+ * lists as well.  qflex_nonzero_slices writes the other paths' ids in
+ * ascending order.
+ * slice_ids: host, capacity entries (may be NULL when capacity is 0).
+ * *n_nonzero: their number, also set when capacity is too small
+ * (QFLEX_ERR_ARG).  QFLEX_ERR_UNSUPPORTED above 2^32 paths. */
+qflex_status qflex_nonzero_slices(qflex_plan plan, int64_t* slice_ids, int64_t capacity, int64_t* n_nonzero);
+
+/* Fraction-f path choice among the paths that do not vanish identically:
+ * qflex_select_slices' rule over the P' entries of qflex_nonzero_slices'
+ * list (n_f = max(1, floor(f P' + 1/2)) capped at P'), mapped to slice ids,
+ * ascending.  slice_ids: host, capacity >= n_f. */
+qflex_status qflex_select_nonzero_slices(qflex_plan plan, double fidelity, uint64_t seed,
+                                         int64_t* slice_ids, int64_t capacity, int64_t* n_selected);
 
 /* Amplitudes of n_bs bitstrings, each with the open tile enumerated:
  *   amps_out[b][j] = sum_{s in slice_ids} amp_s(x_b with tile bits j)

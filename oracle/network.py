@@ -153,12 +153,7 @@ def projector_runs(circ, cut_edges: Sequence[int]) -> Tuple[List[List[Tuple[int,
     return runs, first
 
 
-def structurally_zero(circ, cut_edges: Sequence[int], s: int, runs=None) -> bool:
-    """Whether path s vanishes identically by the projector rule of
-    projector_runs (the last stretch of a qubit meets the bitstring's <x_q|
-    and is not used: the rule holds for every bitstring)."""
-    runs, first = projector_runs(circ, cut_edges) if runs is None else runs
-    vals = slice_values(circ, cut_edges, s)
+def _zero_by_runs(runs, first, vals: Dict[int, int]) -> bool:
     for members, is_first in zip(runs, first):
         bits = {(vals[e] >> b) & 1 for e, b in members}
         if len(bits) > 1 or (is_first and 1 in bits):
@@ -166,10 +161,27 @@ def structurally_zero(circ, cut_edges: Sequence[int], s: int, runs=None) -> bool
     return False
 
 
+def structurally_zero(circ, cut_edges: Sequence[int], s: int) -> bool:
+    """Whether path s vanishes identically by the projector rule of
+    projector_runs.  (The bitstring's <x_q| after a qubit's last stretch
+    would fix that stretch's bits too; it is left out, so the rule holds for
+    every bitstring.)"""
+    return _zero_by_runs(*projector_runs(circ, cut_edges), slice_values(circ, cut_edges, s))
+
+
 def nonzero_slices(circ, cut_edges: Sequence[int]) -> List[int]:
     """Ascending ids of the paths that projector_runs does not rule out."""
-    runs = projector_runs(circ, cut_edges)
-    return [s for s in range(n_slices(circ, cut_edges)) if not structurally_zero(circ, cut_edges, s, runs)]
+    runs, first = projector_runs(circ, cut_edges)
+    K = bond_exponents(circ)
+    out = []
+    for s in range(n_slices(circ, cut_edges)):
+        vals, rest = {}, s                       # mixed radix, as slice_values
+        for e in reversed(list(cut_edges)):
+            vals[e] = rest % (1 << int(K[e]))
+            rest //= 1 << int(K[e])
+        if not _zero_by_runs(runs, first, vals):
+            out.append(s)
+    return out
 
 
 def _fix(arr: np.ndarray, legs: List[tuple], fixed: Dict[tuple, int]):

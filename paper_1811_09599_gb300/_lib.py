@@ -48,7 +48,7 @@ class PlanInfo(C.Structure):
     _fields_ = [("n_slices", C.c_int64), ("n_qubits", C.c_int32), ("n_params", C.c_int32),
                 ("n_open", C.c_int32), ("n_steps", C.c_int32), ("max_tensor_elems", C.c_int64),
                 ("workspace_bytes", C.c_size_t), ("n_tc_steps", C.c_int32),
-                ("n_persistent_buffers", C.c_int32)]
+                ("n_persistent_buffers", C.c_int32), ("n_nonzero_slices", C.c_int64)]
 
 
 class Cost(C.Structure):
@@ -67,7 +67,8 @@ class StepInfo(C.Structure):
 
 class SearchResult(C.Structure):
     _fields_ = [("log2_max_tensor", C.c_double), ("cmacs_per_bitstring", C.c_double),
-                ("n_slices", C.c_double), ("n_cuts", C.c_int32), ("n_steps", C.c_int32)]
+                ("n_slices", C.c_double), ("n_nonzero_slices", C.c_double), ("n_cuts", C.c_int32),
+                ("n_steps", C.c_int32)]
 
 
 class Profile(C.Structure):
@@ -89,6 +90,9 @@ SIGNATURES = [
                                   C.POINTER(Cost)]),
     ("qflex_select_slices", C.c_int, [C.c_void_p, C.c_double, C.c_uint64, C.POINTER(C.c_int64),
                                       C.c_int64, C.POINTER(C.c_int64)]),
+    ("qflex_nonzero_slices", C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_int64, C.POINTER(C.c_int64)]),
+    ("qflex_select_nonzero_slices", C.c_int, [C.c_void_p, C.c_double, C.c_uint64, C.POINTER(C.c_int64),
+                                              C.c_int64, C.POINTER(C.c_int64)]),
     ("qflex_amplitudes", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                    C.POINTER(C.c_int64), C.c_int64, C.c_void_p, C.c_void_p]),
     ("qflex_amplitudes_grad", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,

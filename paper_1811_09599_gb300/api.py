@@ -44,7 +44,8 @@ def search_ordering(problem, max_tensor_elems: int, max_new_cuts: int = 0, trial
     """qflex_search_ordering: greedy ordering (and up to max_new_cuts extra
     cuts after problem.cut_edges) whose largest tensor has at most
     max_tensor_elems entries.  Returns cuts, ordering ((dst, src) pairs),
-    log2_max_tensor, cmacs_per_bitstring, n_slices and `fits`."""
+    log2_max_tensor, cmacs_per_bitstring, n_slices, n_nonzero_slices (paths
+    that do not vanish identically) and `fits`."""
     lib = _lib.load()
     keep: list = []
     circ = _circuit_struct(problem.circuit, keep)
@@ -64,7 +65,7 @@ def search_ordering(problem, max_tensor_elems: int, max_new_cuts: int = 0, trial
     return {"cuts": [int(v) for v in cuts_out[: res.n_cuts]],
             "ordering": [(int(steps[2 * i]), int(steps[2 * i + 1])) for i in range(n - 1)],
             "log2_max_tensor": res.log2_max_tensor, "cmacs_per_bitstring": res.cmacs_per_bitstring,
-            "n_slices": res.n_slices, "fits": st == 0}
+            "n_slices": res.n_slices, "n_nonzero_slices": res.n_nonzero_slices, "fits": st == 0}
 
 
 class Plan:
@@ -138,12 +139,24 @@ class Plan:
             out.append(d)
         return out
 
-    def select_slices(self, fidelity: float, seed: int) -> np.ndarray:
-        P = self.n_slices
+    def select_slices(self, fidelity: float, seed: int, nonzero: bool = False) -> np.ndarray:
+        """Fraction-f path choice; nonzero=True chooses among the paths that
+        do not vanish identically (qflex_select_nonzero_slices)."""
+        P = self.info()["n_nonzero_slices"] if nonzero else self.n_slices
         out = np.zeros(P, dtype=np.int64)
         n = C.c_int64()
-        check(self.lib.qflex_select_slices(self.handle, float(fidelity), C.c_uint64(seed),
-                                           out.ctypes.data_as(C.POINTER(C.c_int64)), P, C.byref(n)))
+        fn = self.lib.qflex_select_nonzero_slices if nonzero else self.lib.qflex_select_slices
+        check(fn(self.handle, float(fidelity), C.c_uint64(seed), out.ctypes.data_as(C.POINTER(C.c_int64)), P,
+                 C.byref(n)))
+        return out[: n.value].copy()
+
+    def nonzero_slices(self) -> np.ndarray:
+        """Ascending ids of the paths that do not vanish identically."""
+        n = C.c_int64()
+        cnt = self.info()["n_nonzero_slices"]
+        out = np.zeros(cnt, dtype=np.int64)
+        check(self.lib.qflex_nonzero_slices(self.handle, out.ctypes.data_as(C.POINTER(C.c_int64)), cnt,
+                                            C.byref(n)))
         return out[: n.value].copy()
 
     # ------------------------------------------------------------------ compute

@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libqflex_gb300.so")
-SOURCES = ["api.cpp", "search.cpp", "k_gridtensor.cu", "k_permute.cu", "k_cgemm_simt.cu",
+SOURCES = ["api.cpp", "search.cpp", "slices.cpp", "k_gridtensor.cu", "k_permute.cu", "k_cgemm_simt.cu",
            "k_cgemm_tc.cu", "k_small.cu", "k_noalloc.cu", "k_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

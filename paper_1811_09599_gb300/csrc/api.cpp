@@ -33,6 +33,7 @@
 
 #include "internal.h"
 #include "search.h"
+#include "slices.h"
 
 using namespace qflex;
 
@@ -51,6 +52,29 @@ qflex_status fail(qflex_status st, const std::string& msg) {
     if (e_ != cudaSuccess)                                                         \
       return fail(QFLEX_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
+
+// Projector lines (slices.h) of a circuit: `order` = gate indices in time
+// order, gate_edge = edge of each two-qubit gate, K = bond bits per edge.
+ProjLines proj_lines(const qflex_circuit* c, const std::vector<int64_t>& order, const std::vector<int>& gate_edge,
+                     const std::vector<int>& K) {
+  ProjLines lines(size_t(c->n_qubits));
+  std::vector<int> used(K.size(), 0);
+  for (int64_t gi : order) {
+    const qflex_gate& g = c->gates[gi];
+    if (g.kind == QFLEX_GATE_CZ) {
+      const int e = gate_edge[size_t(gi)];
+      lines[size_t(std::min(g.q0, g.q1))].push_back({e, K[size_t(e)] - 1 - used[size_t(e)]});
+      used[size_t(e)] += 1;
+    } else if (g.kind == QFLEX_GATE_ISWAP) {
+      used[size_t(gate_edge[size_t(gi)])] += 2;
+      lines[size_t(g.q0)].push_back({-1, 0});
+      lines[size_t(g.q1)].push_back({-1, 0});
+    } else if (g.kind != QFLEX_GATE_T && g.kind != QFLEX_GATE_RZ) {
+      lines[size_t(g.q0)].push_back({-1, 0});
+    }
+  }
+  return lines;
+}
 
 int tc_kind_of(int prec) {
   return (prec == QFLEX_TF32X3 || prec == QFLEX_TF32_PLAIN) ? 0 : (prec == QFLEX_FP16X3 ? 2 : 1);
@@ -140,6 +164,7 @@ struct qflex_plan_s {
   std::vector<std::vector<int>> inc;           // per qubit: incident edges by neighbour id
   std::vector<int> cuts, cut_of_edge, tile, tile_pos;
   int64_t P = 1;
+  SliceZeros zeros;                            // paths that vanish identically (skipped)
   std::vector<int64_t> leg_dim;                // E bond legs then n output legs
   std::vector<GridQubitMeta> gmeta;
   std::vector<int2> gops;
@@ -453,6 +478,7 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
                    [&](int64_t x, int64_t y) { return c->gates[x].cycle < c->gates[y].cycle; });
   p.K.assign(E, 0);
   std::vector<std::vector<std::pair<int64_t, int>>> line(n);   // (gate index, edge or -1)
+  std::vector<int> gate_edge(size_t(c->n_gates), -1);
   for (int64_t gi : order) {
     const qflex_gate& g = c->gates[gi];
     if (g.kind < 0 || g.kind > 8) return fail(QFLEX_ERR_CIRCUIT, "unknown gate kind");
@@ -463,6 +489,7 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
       if (e < 0) return fail(QFLEX_ERR_CIRCUIT, "two-qubit gate on a pair that is not a lattice edge");
       p.K[e] += g.kind == QFLEX_GATE_ISWAP ? 2 : 1;
       if (p.K[e] > 20) return fail(QFLEX_ERR_PLAN, "bond with more than 20 bits");
+      gate_edge[size_t(gi)] = e;
       line[g.q0].push_back({gi, e});
       line[g.q1].push_back({gi, e});
     } else {
@@ -487,6 +514,8 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
     if (p.P > (int64_t(1) << 50) >> p.K[e]) return fail(QFLEX_ERR_PLAN, "too many slices");
     p.P <<= p.K[e];
   }
+  const ProjLines plines = proj_lines(c, order, gate_edge, p.K);
+  p.zeros = SliceZeros(plines, p.K, p.cuts);
   p.tile_pos.assign(n, -1);
   if (pr->n_open < 0 || pr->n_open > 30 || (pr->n_open > 0 && !pr->open_tile))
     return fail(QFLEX_ERR_ARG, "bad open tile");
@@ -574,6 +603,7 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
     net.bits = p.K;
     net.open.assign(size_t(n), 0);
     for (int q : p.tile) net.open[size_t(q)] = 1;
+    net.lines = plines;
     SearchResult sr;
     if (!search_greedy_order(net, p.cuts, &sr, 32, 28.0, 0)) return fail(QFLEX_ERR_PLAN, "ordering search failed");
     def = sr.steps;
@@ -1111,6 +1141,7 @@ qflex_status walk(const qflex_plan_s& p, int64_t n_bs, const int64_t* ids, int64
     for (int64_t k = 0; k < cnt; ++k) {
       const int64_t s = ids ? ids[k] : k;
       decode_slice(p, s, vals);
+      if (p.zeros.any() && p.zeros.zero(vals)) continue;   // contributes exactly zero
       uint64_t changed = 0;
       for (size_t c = 0; c < vals.size(); ++c)
         if (first || vals[c] != prev[c]) changed |= uint64_t(1) << c;
@@ -1231,6 +1262,7 @@ qflex_status qflex_plan_get_info(qflex_plan p, qflex_plan_info* info) {
   info->workspace_bytes = p->total_bytes;
   info->n_tc_steps = p->n_tc;
   info->n_persistent_buffers = p->n_persistent;
+  info->n_nonzero_slices = int64_t(p->zeros.n_nonzero());
   return QFLEX_OK;
 }
 
@@ -1347,13 +1379,22 @@ qflex_status qflex_search_ordering(const qflex_circuit* c, const int32_t* tile, 
     net.edges.push_back(key);
   }
   net.bits.assign(size_t(E), 0);
+  std::vector<int> gate_edge(size_t(c->n_gates), -1);
   for (int64_t i = 0; i < c->n_gates; ++i) {
     const qflex_gate& g = c->gates[i];
+    if (g.kind < 0 || g.kind > QFLEX_GATE_ISWAP || g.q0 < 0 || g.q0 >= n)
+      return fail(QFLEX_ERR_CIRCUIT, "bad gate kind or qubit");
     if (g.kind != QFLEX_GATE_CZ && g.kind != QFLEX_GATE_ISWAP) continue;
     auto it = index.find(std::make_pair(std::min(g.q0, g.q1), std::max(g.q0, g.q1)));
     if (it == index.end()) return fail(QFLEX_ERR_CIRCUIT, "two-qubit gate on a pair that is not a lattice edge");
     net.bits[size_t(it->second)] += g.kind == QFLEX_GATE_ISWAP ? 2 : 1;
+    gate_edge[size_t(i)] = it->second;
   }
+  std::vector<int64_t> order(size_t(c->n_gates));
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int64_t x, int64_t y) { return c->gates[x].cycle < c->gates[y].cycle; });
+  net.lines = proj_lines(c, order, gate_edge, net.bits);
   net.open.assign(size_t(n), 0);
   for (int t = 0; t < n_open; ++t) {
     if (tile[t] < 0 || tile[t] >= n || net.open[size_t(tile[t])]) return fail(QFLEX_ERR_ARG, "bad tile qubit");
@@ -1372,6 +1413,7 @@ qflex_status qflex_search_ordering(const qflex_circuit* c, const int32_t* tile, 
   out->log2_max_tensor = r.log2_max;
   out->cmacs_per_bitstring = r.cmacs;
   out->n_slices = r.n_slices;
+  out->n_nonzero_slices = r.n_nonzero;
   out->n_cuts = int32_t(found.size());
   out->n_steps = n - 1;
   if (!fits)
@@ -1380,13 +1422,16 @@ qflex_status qflex_search_ordering(const qflex_circuit* c, const int32_t* tile, 
   return QFLEX_OK;
 }
 
-qflex_status qflex_select_slices(qflex_plan p, double f, uint64_t seed, int64_t* ids, int64_t cap, int64_t* n_sel) {
-  if (!p || !ids || !n_sel || !(f > 0.0)) return fail(QFLEX_ERR_ARG, "bad argument");
-  if (p->P > (int64_t(1) << 32)) return fail(QFLEX_ERR_UNSUPPORTED, "too many slices to shuffle");
-  int64_t nf = int64_t(std::floor(f * double(p->P) + 0.5));
-  nf = std::max<int64_t>(1, std::min<int64_t>(p->P, nf));
+namespace {
+
+// The first n_f of a Fisher-Yates shuffle of 0..P-1 (SplitMix64 stream),
+// n_f = max(1, floor(f P + 1/2)) capped at P, sorted.
+qflex_status shuffle_select(int64_t P, double f, uint64_t seed, int64_t cap, std::vector<int64_t>* out) {
+  if (P > (int64_t(1) << 32)) return fail(QFLEX_ERR_UNSUPPORTED, "too many slices to shuffle");
+  int64_t nf = int64_t(std::floor(f * double(P) + 0.5));
+  nf = std::max<int64_t>(1, std::min<int64_t>(P, nf));
   if (cap < nf) return fail(QFLEX_ERR_ARG, "slice_ids capacity too small");
-  std::vector<int64_t> a(size_t(p->P));
+  std::vector<int64_t> a(static_cast<size_t>(P));
   std::iota(a.begin(), a.end(), 0);
   uint64_t x = seed;
   auto next = [&]() {   // SplitMix64 (Steele, Lea, Flood 2014)
@@ -1396,13 +1441,50 @@ qflex_status qflex_select_slices(qflex_plan p, double f, uint64_t seed, int64_t*
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
   };
-  for (int64_t i = p->P - 1; i > 0; --i) {
+  for (int64_t i = P - 1; i > 0; --i) {
     const int64_t j = int64_t(next() % uint64_t(i + 1));
-    std::swap(a[i], a[j]);
+    std::swap(a[size_t(i)], a[size_t(j)]);
   }
-  std::sort(a.begin(), a.begin() + nf);
-  std::copy(a.begin(), a.begin() + nf, ids);
-  *n_sel = nf;
+  a.resize(size_t(nf));
+  std::sort(a.begin(), a.end());
+  *out = std::move(a);
+  return QFLEX_OK;
+}
+
+constexpr int64_t kMaxListedSlices = int64_t(1) << 32;
+
+}  // namespace
+
+qflex_status qflex_select_slices(qflex_plan p, double f, uint64_t seed, int64_t* ids, int64_t cap, int64_t* n_sel) {
+  if (!p || !ids || !n_sel || !(f > 0.0)) return fail(QFLEX_ERR_ARG, "bad argument");
+  std::vector<int64_t> a;
+  if (qflex_status st = shuffle_select(p->P, f, seed, cap, &a)) return st;
+  std::copy(a.begin(), a.end(), ids);
+  *n_sel = int64_t(a.size());
+  return QFLEX_OK;
+}
+
+qflex_status qflex_nonzero_slices(qflex_plan p, int64_t* ids, int64_t cap, int64_t* n_nonzero) {
+  if (!p || !n_nonzero || cap < 0 || (cap > 0 && !ids)) return fail(QFLEX_ERR_ARG, "bad argument");
+  const double count = p->zeros.n_nonzero();
+  if (count > double(kMaxListedSlices)) return fail(QFLEX_ERR_UNSUPPORTED, "too many paths to list");
+  *n_nonzero = int64_t(count);
+  if (cap < *n_nonzero) return fail(QFLEX_ERR_ARG, "slice_ids capacity too small");
+  std::vector<int64_t> all;
+  if (!p->zeros.list(&all, kMaxListedSlices)) return fail(QFLEX_ERR_UNSUPPORTED, "too many paths to list");
+  std::copy(all.begin(), all.end(), ids);
+  return QFLEX_OK;
+}
+
+qflex_status qflex_select_nonzero_slices(qflex_plan p, double f, uint64_t seed, int64_t* ids, int64_t cap,
+                                         int64_t* n_sel) {
+  if (!p || !ids || !n_sel || !(f > 0.0)) return fail(QFLEX_ERR_ARG, "bad argument");
+  std::vector<int64_t> all;
+  if (!p->zeros.list(&all, kMaxListedSlices)) return fail(QFLEX_ERR_UNSUPPORTED, "too many paths to list");
+  std::vector<int64_t> a;
+  if (qflex_status st = shuffle_select(int64_t(all.size()), f, seed, cap, &a)) return st;
+  for (size_t k = 0; k < a.size(); ++k) ids[k] = all[size_t(a[k])];
+  *n_sel = int64_t(a.size());
   return QFLEX_OK;
 }
 

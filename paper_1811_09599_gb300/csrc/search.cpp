@@ -26,13 +26,16 @@
 //    the kCutBeam best distinct sets (same ranking) carry on.  The chosen set
 //    then gets an ordering search with four times the trials.
 //  * work model: a step depending on cuts D runs once per change of those
-//    cuts in mixed-radix slice order (first cut most significant), i.e.
-//    prod_{c <= max D} 2^{K_c} times per bitstring, 2^(a + b - s) complex
-//    MACs each -- the executor's reuse rule.
+//    cuts along the executor's path order (ascending slice ids, first cut
+//    most significant, paths that vanish identically skipped), 2^(a + b - s)
+//    complex MACs each -- the executor's reuse rule.  With every path kept
+//    that is prod_{c <= max D} 2^{K_c} runs per bitstring; otherwise the
+//    changes are counted along the listed nonzero paths.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <iterator>
+#include <map>
 #include <utility>
 #include <vector>
 
@@ -73,6 +76,70 @@ Tensor merge(const Tensor& a, const Tensor& b, const std::vector<int>& leg_bits)
   return r;
 }
 
+bool valid_cuts(const SearchNet& net, const std::vector<int>& cuts) {
+  if (cuts.size() > 64) return false;
+  std::vector<char> seen(net.edges.size(), 0);
+  for (int e : cuts) {
+    if (e < 0 || e >= int(net.edges.size()) || seen[size_t(e)]) return false;
+    seen[size_t(e)] = 1;
+  }
+  return true;
+}
+
+// Runs of a step per bitstring by the cuts it depends on (work model above).
+class RunModel {
+ public:
+  RunModel(const SearchNet& net, const std::vector<int>& cuts) : prefix_(cuts.size() + 1, 1.0) {
+    for (size_t c = 0; c < cuts.size(); ++c)
+      prefix_[c + 1] = prefix_[c] * std::ldexp(1.0, net.bits[size_t(cuts[c])]);
+    n_slices = prefix_.back();
+    n_nonzero = n_slices;
+    const SliceZeros zeros(net.lines, net.bits, cuts);
+    if (!zeros.any()) return;
+    n_nonzero = zeros.n_nonzero();
+    std::vector<int64_t> ids;
+    if (!zeros.list(&ids, kMaxListed)) return;   // too many: count as if all were kept
+    vals_.resize(ids.size());
+    for (size_t k = 0; k < ids.size(); ++k) {
+      int64_t v = ids[k];
+      vals_[k].resize(cuts.size());
+      for (size_t c = cuts.size(); c-- > 0;) {
+        const int bits = net.bits[size_t(cuts[c])];
+        vals_[k][c] = v & ((int64_t(1) << bits) - 1);
+        v >>= bits;
+      }
+    }
+  }
+
+  double runs(uint64_t dep) {
+    if (!dep) return 1.0;
+    if (vals_.empty()) {
+      int hi = 63;
+      while (!((dep >> hi) & 1)) --hi;
+      return prefix_[size_t(hi) + 1];
+    }
+    auto it = memo_.find(dep);
+    if (it != memo_.end()) return it->second;
+    double r = 0;
+    for (size_t k = 0; k < vals_.size(); ++k) {
+      bool changed = k == 0;
+      for (size_t c = 0; !changed && c < vals_[k].size(); ++c)
+        changed = ((dep >> c) & 1) && vals_[k][c] != vals_[k - 1][c];
+      r += changed ? 1.0 : 0.0;
+    }
+    memo_[dep] = r;
+    return r;
+  }
+
+  double n_slices = 1, n_nonzero = 1;
+
+ private:
+  static constexpr int64_t kMaxListed = int64_t(1) << 18;
+  std::vector<double> prefix_;
+  std::vector<std::vector<int64_t>> vals_;   // listed nonzero paths, value per cut
+  std::map<uint64_t, double> memo_;
+};
+
 uint64_t splitmix(uint64_t& x) {
   x += 0x9E3779B97F4A7C15ull;
   uint64_t z = x;
@@ -84,28 +151,15 @@ double uniform01(uint64_t& x) { return (double(splitmix(x) >> 11) + 0.5) * 0x1.0
 
 // One greedy pass with parameters (alpha, beta, tau) and noise stream `rng`;
 // results above 2^log2_limit entries are taken only when nothing else is left.
-bool greedy_pass(const SearchNet& net, const std::vector<int>& cuts, double alpha, double beta, double tau,
-                 double log2_limit, uint64_t rng, SearchResult* out) {
+bool greedy_pass(const SearchNet& net, const std::vector<int>& cuts, RunModel& model, double alpha, double beta,
+                 double tau, double log2_limit, uint64_t rng, SearchResult* out) {
   const int n = net.n, E = int(net.edges.size());
   if (n < 1) return false;
   std::vector<int> cut_idx(size_t(E), -1);
-  for (size_t c = 0; c < cuts.size(); ++c) {
-    if (cuts[c] < 0 || cuts[c] >= E || cut_idx[size_t(cuts[c])] >= 0 || c >= 64) return false;
-    cut_idx[size_t(cuts[c])] = int(c);
-  }
+  for (size_t c = 0; c < cuts.size(); ++c) cut_idx[size_t(cuts[c])] = int(c);
   std::vector<int> leg_bits(size_t(E + n), 1);
   for (int e = 0; e < E; ++e) leg_bits[size_t(e)] = net.bits[size_t(e)];
-  // runs of a step by its dependence mask: the product of the radices of all
-  // cuts down to the least significant one it depends on
-  std::vector<double> prefix_runs(cuts.size() + 1, 1.0);
-  for (size_t c = 0; c < cuts.size(); ++c)
-    prefix_runs[c + 1] = prefix_runs[c] * std::ldexp(1.0, net.bits[size_t(cuts[c])]);
-  auto runs_of = [&](uint64_t dep) {
-    if (!dep) return 1.0;
-    int hi = 63;
-    while (!((dep >> hi) & 1)) --hi;
-    return prefix_runs[size_t(hi) + 1];
-  };
+  auto runs_of = [&](uint64_t dep) { return model.runs(dep); };
   std::vector<Tensor> t(static_cast<size_t>(n));
   std::vector<char> alive(size_t(n), 1);
   SearchResult r;
@@ -168,7 +222,8 @@ bool greedy_pass(const SearchNet& net, const std::vector<int>& cuts, double alph
     r.steps.push_back(dst);
     r.steps.push_back(src);
   }
-  r.n_slices = prefix_runs.back();
+  r.n_slices = model.n_slices;
+  r.n_nonzero = model.n_nonzero;
   *out = std::move(r);
   return true;
 }
@@ -184,6 +239,8 @@ bool better_result(const SearchResult& x, const SearchResult& y, double log2_lim
 
 bool search_greedy_order(const SearchNet& net, const std::vector<int>& cuts, SearchResult* out, int trials,
                          double log2_limit, uint64_t seed) {
+  if (!valid_cuts(net, cuts)) return false;
+  RunModel model(net, cuts);
   SearchResult best;
   bool have = false;
   uint64_t x = seed;
@@ -192,7 +249,7 @@ bool search_greedy_order(const SearchNet& net, const std::vector<int>& cuts, Sea
     const double tau = i == 0 ? 0.0 : uniform01(x);
     const double beta = (i % 2 == 1) ? 2.0 * uniform01(x) : 0.0;   // odd passes weigh reuse
     SearchResult r;
-    if (!greedy_pass(net, cuts, alpha, beta, tau, log2_limit, splitmix(x), &r)) return false;
+    if (!greedy_pass(net, cuts, model, alpha, beta, tau, log2_limit, splitmix(x), &r)) return false;
     if (!have || better_result(r, best, log2_limit)) {
       best = std::move(r);
       have = true;

@@ -5,6 +5,8 @@
 #include <utility>
 #include <vector>
 
+#include "slices.h"
+
 namespace qflex {
 
 struct SearchNet {
@@ -12,6 +14,8 @@ struct SearchNet {
   std::vector<std::pair<int, int>> edges;    // lattice bonds (qubit pairs)
   std::vector<int> bits;                     // bond bits per edge (0: no gate on it)
   std::vector<char> open;                    // per qubit: output leg kept open (tile)
+  ProjLines lines;                           // per qubit: CZ projector halves (slices.h);
+                                             // empty: every path is counted
 };
 
 struct SearchResult {
@@ -19,6 +23,7 @@ struct SearchResult {
   double log2_max = 0;          // log2 entries of the largest tensor (inputs included)
   double cmacs = 0;             // complex MACs of one bitstring over all slices, with reuse
   double n_slices = 1;
+  double n_nonzero = 1;         // paths that do not vanish identically
 };
 
 // Best of `trials` randomized greedy orderings of the network with `cuts`

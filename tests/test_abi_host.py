@@ -203,3 +203,53 @@ def test_plan_steps_agree_with_cost(Plan):
     d0 = [s for s in st32 if (s["M"], s["N"], s["K"]) == (1 << 20, 16, 16)][0]
     assert d0["a_cached"] and d0["a_builds"] == 16 and d0["runs"] == 256
     assert all(s["kernel"] != "tensor_cores" for s in Plan(c2_problem(0), "fp32", device=-1).steps(1))
+
+
+def _constrained_problems():
+    """Problems whose cuts leave paths that vanish identically (projector
+    halves in one diagonal stretch), and one where none do."""
+    from qflex_inputs import diamond_problem
+    rot = grid_problem(4, 5, 24, 3, r0=2, c0=2, cuts=True, tile_rows=2, tile_cols=2, rotations=True)
+    circ = random_circuit(grid_lattice(3, 3), 16, 0)
+    ei = circ.lattice.edge_index
+    corr = Problem(circ, [ei[(4, 5)], ei[(4, 7)], ei[(1, 2)]], [8], None)
+    d = diamond_problem(32, 0)
+    bris = Problem(d.circuit, [101, 100, 11, 22], d.open_tile, None)   # two bonds of qubit 56
+    return [rot, corr, bris, c2_problem(0)]
+
+
+def test_nonzero_slices_match_oracle(Plan):
+    """qflex_nonzero_slices / qflex_select_nonzero_slices against the
+    oracle's projector rule, and the plan info count."""
+    from paper_1811_09599_gb300 import QFlexError
+    for prob in _constrained_problems():
+        p = Plan(prob, "bf16x3", device=-1)
+        ref = NW.nonzero_slices(prob.circuit, prob.cut_edges)
+        assert list(p.nonzero_slices()) == ref
+        assert p.info()["n_nonzero_slices"] == len(ref)
+        for f, seed in ((0.01, 2026), (0.3, 5), (1.0, 1)):
+            want = sorted(ref[i] for i in SEL.select_slices(len(ref), f, seed))
+            assert list(p.select_slices(f, seed, nonzero=True)) == want
+    import ctypes as C
+    p = Plan(_constrained_problems()[1], "fp32", device=-1)
+    n = C.c_int64()
+    assert p.lib.qflex_nonzero_slices(p.handle, None, 0, C.byref(n)) != 0   # capacity too small
+    assert n.value == p.info()["n_nonzero_slices"] < p.n_slices
+    with pytest.raises(QFlexError, match="ARG"):
+        from paper_1811_09599_gb300._lib import check
+        check(p.lib.qflex_nonzero_slices(p.handle, None, 0, None))
+
+
+def test_vanishing_paths_are_skipped_in_the_schedule(Plan):
+    """The cost replay (the executor's schedule) runs nothing for a path that
+    vanishes identically: all paths cost what the nonzero ones cost, and a
+    list of vanishing paths only builds the grid tensors."""
+    prob = _constrained_problems()[0]
+    p = Plan(prob, "bf16x3", device=-1)
+    nz = list(p.nonzero_slices())
+    zero = sorted(set(range(p.n_slices)) - set(nz))
+    assert len(zero) > 0
+    assert p.cost(2) == p.cost(2, nz)
+    c0 = p.cost(1, zero[:5])
+    assert c0["cmacs"] == 0 and c0["steps_executed"] == 0
+    assert p.cost(1, sorted(nz[:3] + zero[:3])) == p.cost(1, nz[:3])

@@ -90,6 +90,32 @@ def test_rotation_circuit_with_angles(api, prec):
     assert amp_error(got, ref, prob.n) < TOL[prec]
 
 
+def test_vanishing_paths_skipped(api):
+    """3x4, 1+20+1 rotations, two cuts: R_Z between CZ projector halves makes
+    half the paths vanish identically.  The sum over all paths, which skips
+    them, equals the sum over the oracle's list of the others bit for bit
+    (the same kernels run), a list of vanishing paths gives exact zeros,
+    and the total matches the state vector."""
+    prob = grid_problem(3, 4, 20, 8, r0=2, c0=2, cuts=True, tile_rows=1, tile_cols=2, rotations=True)
+    nz = NW.nonzero_slices(prob.circuit, prob.cut_edges)
+    P = NW.n_slices(prob.circuit, prob.cut_edges)
+    zero = sorted(set(range(P)) - set(nz))
+    assert len(zero) > 0
+    bs = random_bitstrings(prob.n, 2, 12)
+    plan = api.Plan(prob, "bf16x3", device=0)
+    b = torch.from_numpy(bs).cuda()
+    th = torch.from_numpy(prob.circuit.angles).cuda()
+    assert list(plan.nonzero_slices()) == nz
+    full = plan.amplitudes(b, th)
+    part = plan.amplitudes(b, th, nz)
+    assert torch.equal(full, part)
+    assert torch.count_nonzero(plan.amplitudes(b, th, zero)).item() == 0
+    assert np.max(np.abs(NW.amplitudes(prob, bs, zero))) == 0.0
+    ref = SV.amplitudes(prob.circuit, bs, prob.open_tile)
+    assert amp_error(full.cpu().numpy(), ref, prob.n) < TOL["bf16x3"]
+    plan.sync()
+
+
 def test_slice_order_and_repeats_are_consistent(api):
     """Slice lists in any order give the same sum (memoised reuse must not
     leak values across bitstrings or slice orders)."""

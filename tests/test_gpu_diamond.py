@@ -75,3 +75,32 @@ def test_bris70_full_size_path(api):
         plan.close()
     for prec, e in errs.items():
         assert e < BRIS70_TOL[prec], (prec, errs)
+
+
+def test_bris70_searched_path(api):
+    """The cuts and ordering the automated search finds for the 70-qubit
+    diamond (no cuts given, up to four added, 2^28-entry limit): one path
+    that does not vanish identically against the oracle's contraction of
+    the same path with the same cuts and ordering; a path that vanishes
+    identically gives exact zeros."""
+    from qflex_inputs.problems import Problem
+    d = diamond_problem(32, 0)
+    r = api.search_ordering(Problem(d.circuit, [], d.open_tile, None), 1 << 28, 4, trials=8, seed=0)
+    assert r["fits"] and r["n_slices"] == 65536
+    prob = Problem(d.circuit, r["cuts"], d.open_tile, r["ordering"])
+    bs = random_bitstrings(prob.n, 1, 78)
+    nz = NW.nonzero_slices(prob.circuit, prob.cut_edges)      # paths that do not vanish identically
+    s = nz[int(np.random.default_rng(4321).integers(len(nz)))]
+    ref = NW.slice_amplitudes(prob, bs[0], s)
+    plan = api.Plan(prob, "bf16x3", device=0)
+    got = plan.amplitudes(torch.from_numpy(bs).cuda(), None, [s])
+    plan.sync()
+    nrm = api.norm(got).item()
+    assert abs(nrm - float(np.sum(np.abs(ref) ** 2))) < 1e-3 * nrm
+    assert amp_error(got.cpu().numpy(), ref, prob.n, 1.0 / 65536) < BRIS70_TOL["bf16x3"]
+    assert list(plan.nonzero_slices()) == nz
+    if len(nz) < 65536:
+        z = min(set(range(65536)) - set(nz))
+        assert NW.structurally_zero(prob.circuit, prob.cut_edges, z)
+        assert torch.count_nonzero(plan.amplitudes(torch.from_numpy(bs).cuda(), None, [z])).item() == 0
+    plan.close()

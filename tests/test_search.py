@@ -90,15 +90,20 @@ def test_search_reaches_brute_force_optimum(api, rows, cols, t, tile, ncut):
     assert r["cmacs_per_bitstring"] == pytest.approx(opt, rel=1e-12)
 
 
-def test_search_work_model_matches_planner(api):
+@pytest.mark.parametrize("rotations", [False, True])
+def test_search_work_model_matches_planner(api, rotations):
     """The search's work per bitstring equals the planner's cost replay of
-    the same cuts and ordering (same reuse rule)."""
+    the same cuts and ordering (same reuse rule); with rotation gates the
+    cuts leave paths that vanish identically (R_Z is diagonal), which both
+    skip."""
     from paper_1811_09599_gb300.api import Plan
-    p = grid_problem(4, 5, 24, 3, r0=2, c0=2, cuts=True, tile_rows=2, tile_cols=2)
+    p = grid_problem(4, 5, 24, 3, r0=2, c0=2, cuts=True, tile_rows=2, tile_cols=2, rotations=rotations)
     r = api.search_ordering(Problem(p.circuit, p.cut_edges, p.open_tile, None), 1 << 20, 0, trials=16)
     plan = Plan(Problem(p.circuit, r["cuts"], p.open_tile, r["ordering"]), "bf16x3", device=-1)
     assert plan.cost(1)["cmacs"] == pytest.approx(r["cmacs_per_bitstring"], rel=1e-12)
     assert math.log2(plan.info()["max_tensor_elems"]) <= r["log2_max_tensor"]
+    assert r["n_nonzero_slices"] == plan.info()["n_nonzero_slices"]
+    assert (r["n_nonzero_slices"] < r["n_slices"]) == rotations
 
 
 def test_search_7x7_finds_two_cut_plan(api):
@@ -126,6 +131,7 @@ def test_search_bristlecone_70(api):
     d = diamond_problem(32, 0)
     r = api.search_ordering(Problem(d.circuit, [], d.open_tile, None), 1 << 28, 5, trials=8, seed=0)
     assert r["fits"] and len(r["cuts"]) == 4 and r["n_slices"] == 65536
+    assert r["n_nonzero_slices"] <= r["n_slices"]
     hand = Plan(d, "bf16x3", device=-1).cost(1)["cmacs"]
     found = Plan(Problem(d.circuit, r["cuts"], d.open_tile, r["ordering"]), "bf16x3", device=-1)
     assert found.info()["max_tensor_elems"] <= 1 << 28
