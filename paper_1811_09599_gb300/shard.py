@@ -6,8 +6,9 @@ independent, and so are bitstrings.  Two partitions follow:
 * by bitstrings (weak scaling): every rank contracts its own bitstrings
   with all paths; nothing is exchanged on the data path, only the timing
   is reduced (max over ranks).
-* by slices (strong scaling of one batch): the slice range is split into
-  contiguous shards; each rank sums its shard's contributions and one
+* by slices (strong scaling of one batch): the slice range (or a list of
+  slice ids, such as the paths that do not vanish identically) is split
+  into contiguous shards; each rank sums its shard's contributions and one
   collective, an FP64 sum over ranks of the n_bs x 2^|tile| partial
   amplitudes, completes the batch (the sum over paths is exact up to the
   order of FP64 additions).
@@ -16,7 +17,7 @@ The collectives go through torch.distributed (NCCL on GPUs, gloo on CPU).
 """
 from __future__ import annotations
 
-from typing import Callable, Sequence, Tuple
+from typing import Callable, Sequence, Tuple, Union
 
 import torch
 import torch.distributed as dist
@@ -46,15 +47,20 @@ def max_over_ranks(value: float, device=None, group=None) -> float:
     return float(t.item())
 
 
-def slice_sharded_amplitudes(compute: Callable[[Sequence[int]], torch.Tensor], n_slices: int,
-                             group=None) -> torch.Tensor:
-    """Sum over all slices, split across ranks: compute(slice_ids) returns
+def slice_sharded_amplitudes(compute: Callable[[Sequence[int]], torch.Tensor],
+                             slices: Union[int, Sequence[int]], group=None) -> torch.Tensor:
+    """Sum over paths, split across ranks: `slices` is the number of slices
+    (all ids 0..P-1) or a list of slice ids, e.g. the paths that do not
+    vanish identically (Plan.nonzero_slices), so that every rank gets an
+    equal share of the paths that cost work.  compute(slice_ids) returns
     this rank's partial complex128 amplitudes (zeros for an empty list); the
-    partial sums are added over ranks in FP64 and every rank gets the total."""
+    partial sums are added over ranks in FP64 and every rank gets the
+    total."""
     rank = dist.get_rank(group) if dist.is_initialized() else 0
     world = dist.get_world_size(group) if dist.is_initialized() else 1
-    lo, hi = shard(n_slices, rank, world)
-    part = compute(list(range(lo, hi)))
+    ids = list(range(slices)) if isinstance(slices, int) else [int(s) for s in slices]
+    lo, hi = shard(len(ids), rank, world)
+    part = compute(ids[lo:hi])
     if part.dtype != torch.complex128:
         raise TypeError("partial amplitudes must be complex128")
     if world > 1:

@@ -57,6 +57,22 @@ def _worker(rank, world, port, out_dir):
         total = slice_sharded_amplitudes(compute, P).numpy()
         t = max_over_ranks(1.0 + rank)
         np.save(os.path.join(out_dir, f"r{rank}.npy"), total)
+        # a list of ids: the paths of a rotation circuit that do not vanish
+        rot = grid_problem(3, 4, 16, 2, r0=2, c0=2, cuts=True, tile_rows=1, tile_cols=2, rotations=True)
+        rt = NW.all_grid_tensors(rot.circuit)
+        nz = NW.nonzero_slices(rot.circuit, rot.cut_edges)
+        seen = []
+
+        def compute_rot(ids):
+            seen.extend(ids)
+            out = np.zeros((len(bs), 1 << len(rot.open_tile)), dtype=np.complex128)
+            for i, b in enumerate(bs):
+                for s in ids:
+                    out[i] += NW.slice_amplitudes(rot, b, s, tensors=rt)
+            return torch.from_numpy(out)
+
+        np.save(os.path.join(out_dir, f"rot{rank}.npy"), slice_sharded_amplitudes(compute_rot, nz).numpy())
+        np.save(os.path.join(out_dir, f"rotids{rank}.npy"), np.array(seen, dtype=np.int64))
         with open(os.path.join(out_dir, f"r{rank}.txt"), "w") as f:
             f.write(f"{t} {calls[0][0] if calls[0] else -1} {len(calls[0])} {P}\n")
     finally:
@@ -78,4 +94,12 @@ def test_slice_partition_gloo_world2(tmp_path):
     P = int(info[0][3])
     assert float(info[0][0]) == float(info[1][0]) == 2.0          # max over ranks
     assert int(info[0][1]) == 0 and int(info[1][1]) == P // 2     # contiguous halves
+    rot = grid_problem(3, 4, 16, 2, r0=2, c0=2, cuts=True, tile_rows=1, tile_cols=2, rotations=True)
+    nz = NW.nonzero_slices(rot.circuit, rot.cut_edges)
+    assert len(nz) < NW.n_slices(rot.circuit, rot.cut_edges)
+    ids = [list(np.load(tmp_path / f"rotids{r}.npy")) for r in (0, 1)]
+    assert ids[0] + ids[1] == nz and abs(len(ids[0]) - len(ids[1])) <= 1
+    got = np.load(tmp_path / "rot0.npy")
+    assert np.array_equal(got, np.load(tmp_path / "rot1.npy"))
+    assert np.max(np.abs(got - NW.amplitudes(rot, bs))) < 1e-15     # vanishing paths add nothing
     assert int(info[0][2]) + int(info[1][2]) == P
