@@ -30,6 +30,7 @@
  *    qflex_plan_sync / qflex_device_status report.
  *  - Nothing throws across the ABI; on failure the call returns a nonzero
  *    qflex_status and qflex_last_error() describes it (thread-local string).
+ *    A failed host allocation inside a call returns QFLEX_ERR_OOM.
  *  - Complex numbers are interleaved (re, im): complex64 = 2 x float,
  *    complex128 = 2 x double.  Tensors are row-major.
  */

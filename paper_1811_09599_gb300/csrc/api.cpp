@@ -28,6 +28,7 @@
 #include <tuple>
 #include <memory>
 #include <numeric>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -44,6 +45,28 @@ thread_local std::string g_err;
 qflex_status fail(qflex_status st, const std::string& msg) {
   g_err = msg;
   return st;
+}
+
+// Runs an entry point's body; no C++ exception crosses the C ABI (a failed
+// host allocation becomes QFLEX_ERR_OOM, anything else QFLEX_ERR_UNSUPPORTED
+// with its message).
+template <class F>
+qflex_status guarded(F&& body) noexcept {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    return fail(QFLEX_ERR_OOM, "host allocation failed");
+  } catch (const std::length_error&) {
+    return fail(QFLEX_ERR_OOM, "host allocation too large");
+  } catch (const std::exception& e) {
+    try {
+      return fail(QFLEX_ERR_UNSUPPORTED, std::string("internal error: ") + e.what());
+    } catch (...) {
+      return QFLEX_ERR_UNSUPPORTED;
+    }
+  } catch (...) {
+    return QFLEX_ERR_UNSUPPORTED;
+  }
 }
 
 #define QF_CUDA(call)                                                              \
@@ -1215,28 +1238,30 @@ const char* qflex_last_error(void) { return g_err.c_str(); }
 
 qflex_status qflex_plan_create(const qflex_problem* problem, qflex_precision prec, size_t ws_max, int device,
                                qflex_plan* out) {
-  if (!problem || !out) return fail(QFLEX_ERR_ARG, "null problem or output");
-  *out = nullptr;
-  if (prec < QFLEX_FP32_SIMT || prec > QFLEX_FP16X3) return fail(QFLEX_ERR_ARG, "unknown precision");
-  auto p = std::make_unique<qflex_plan_s>();
-  p->prec = prec;
-  p->device = device;
-  p->tc_kind = tc_kind_of(prec);
-  p->nsplit = nsplit_of(prec);
-  if (qflex_status st = build_plan(problem, *p)) return st;
-  if (ws_max > 0 && p->total_bytes > ws_max)
-    return fail(QFLEX_ERR_PLAN, "plan needs " + std::to_string(p->total_bytes) + " bytes, budget " +
-                                    std::to_string(ws_max));
-  if (device >= 0) {
-    if (prec != QFLEX_FP32_SIMT && !tc_available())
-      return fail(QFLEX_ERR_UNSUPPORTED, "tensor-map encoder unavailable in this driver");
-    if (qflex_status st = allocate(*p)) {
-      if (p->d_ws) cudaFree(p->d_ws);
-      return st;
+  return guarded([&]() -> qflex_status {
+    if (!problem || !out) return fail(QFLEX_ERR_ARG, "null problem or output");
+    *out = nullptr;
+    if (prec < QFLEX_FP32_SIMT || prec > QFLEX_FP16X3) return fail(QFLEX_ERR_ARG, "unknown precision");
+    auto p = std::make_unique<qflex_plan_s>();
+    p->prec = prec;
+    p->device = device;
+    p->tc_kind = tc_kind_of(prec);
+    p->nsplit = nsplit_of(prec);
+    if (qflex_status st = build_plan(problem, *p)) return st;
+    if (ws_max > 0 && p->total_bytes > ws_max)
+      return fail(QFLEX_ERR_PLAN, "plan needs " + std::to_string(p->total_bytes) + " bytes, budget " +
+                                      std::to_string(ws_max));
+    if (device >= 0) {
+      if (prec != QFLEX_FP32_SIMT && !tc_available())
+        return fail(QFLEX_ERR_UNSUPPORTED, "tensor-map encoder unavailable in this driver");
+      if (qflex_status st = allocate(*p)) {
+        if (p->d_ws) cudaFree(p->d_ws);
+        return st;
+      }
     }
-  }
-  *out = p.release();
-  return QFLEX_OK;
+    *out = p.release();
+    return QFLEX_OK;
+  });
 }
 
 void qflex_plan_destroy(qflex_plan plan) {
@@ -1252,174 +1277,182 @@ void qflex_plan_destroy(qflex_plan plan) {
 }
 
 qflex_status qflex_plan_get_info(qflex_plan p, qflex_plan_info* info) {
-  if (!p || !info) return fail(QFLEX_ERR_ARG, "null argument");
-  info->n_slices = p->P;
-  info->n_qubits = p->n;
-  info->n_params = p->n_params;
-  info->n_open = int(p->tile.size());
-  info->n_steps = int(p->steps.size());
-  info->max_tensor_elems = p->max_tensor;
-  info->workspace_bytes = p->total_bytes;
-  info->n_tc_steps = p->n_tc;
-  info->n_persistent_buffers = p->n_persistent;
-  info->n_nonzero_slices = int64_t(p->zeros.n_nonzero());
-  return QFLEX_OK;
+  return guarded([&]() -> qflex_status {
+    if (!p || !info) return fail(QFLEX_ERR_ARG, "null argument");
+    info->n_slices = p->P;
+    info->n_qubits = p->n;
+    info->n_params = p->n_params;
+    info->n_open = int(p->tile.size());
+    info->n_steps = int(p->steps.size());
+    info->max_tensor_elems = p->max_tensor;
+    info->workspace_bytes = p->total_bytes;
+    info->n_tc_steps = p->n_tc;
+    info->n_persistent_buffers = p->n_persistent;
+    info->n_nonzero_slices = int64_t(p->zeros.n_nonzero());
+    return QFLEX_OK;
+  });
 }
 
 qflex_status qflex_plan_cost(qflex_plan p, int64_t n_bs, const int64_t* ids, int64_t n_ids, qflex_cost* out) {
-  if (!p || !out || n_bs < 0) return fail(QFLEX_ERR_ARG, "bad argument");
-  if (qflex_status st = check_slices(*p, ids, n_ids)) return st;
-  qflex_cost c{};
-  const double prods = p->nsplit == 2 ? 3.0 : 1.0;
-  std::vector<int64_t> ob;
-  std::vector<std::vector<int64_t>> ov;
-  oc_reset(*p, ob, ov);
-  qflex_status st = walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) {
-    if (i < 0) {
-      ++c.launches;
+  return guarded([&]() -> qflex_status {
+    if (!p || !out || n_bs < 0) return fail(QFLEX_ERR_ARG, "bad argument");
+    if (qflex_status st = check_slices(*p, ids, n_ids)) return st;
+    qflex_cost c{};
+    const double prods = p->nsplit == 2 ? 3.0 : 1.0;
+    std::vector<int64_t> ob;
+    std::vector<std::vector<int64_t>> ov;
+    oc_reset(*p, ob, ov);
+    qflex_status st = walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) {
+      if (i < 0) {
+        ++c.launches;
+        return QFLEX_OK;
+      }
+      const Step& s = p->steps[i];
+      const double mnk = double(s.M) * double(s.N) * double(s.K);
+      c.cmacs += mnk;
+      c.largest_gemm_cmacs = std::max(c.largest_gemm_cmacs, mnk);
+      if (s.tc) {
+        c.tc_cmacs += mnk;
+        c.tc_mma_flops += mnk * 3.0 * prods * 2.0;
+      }
+      // operand producers that run (not in place, not a cache hit): one
+      // permutation each, plus the absmax of an fp16 operand
+      const bool runA = !s.A.direct && !s.A.fused &&
+                        !(s.A.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.A.cache)].dep, s.A.cache, b, vals));
+      const bool runB = !s.B.direct && !s.B.fused &&
+                        !(s.B.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.B.cache)].dep, s.B.cache, b, vals));
+      if (runA) c.permute_bytes += 16.0 * double(s.M) * double(s.K);
+      if (runB) c.permute_bytes += 16.0 * double(s.N) * double(s.K);
+      c.launches += 1 + runA + runB + (s.tc && p->tc_kind == 2 ? int(runA) + int(runB) : 0);
+      ++c.steps_executed;
       return QFLEX_OK;
-    }
-    const Step& s = p->steps[i];
-    const double mnk = double(s.M) * double(s.N) * double(s.K);
-    c.cmacs += mnk;
-    c.largest_gemm_cmacs = std::max(c.largest_gemm_cmacs, mnk);
-    if (s.tc) {
-      c.tc_cmacs += mnk;
-      c.tc_mma_flops += mnk * 3.0 * prods * 2.0;
-    }
-    // operand producers that run (not in place, not a cache hit): one
-    // permutation each, plus the absmax of an fp16 operand
-    const bool runA = !s.A.direct && !s.A.fused &&
-                      !(s.A.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.A.cache)].dep, s.A.cache, b, vals));
-    const bool runB = !s.B.direct && !s.B.fused &&
-                      !(s.B.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.B.cache)].dep, s.B.cache, b, vals));
-    if (runA) c.permute_bytes += 16.0 * double(s.M) * double(s.K);
-    if (runB) c.permute_bytes += 16.0 * double(s.N) * double(s.K);
-    c.launches += 1 + runA + runB + (s.tc && p->tc_kind == 2 ? int(runA) + int(runB) : 0);
-    ++c.steps_executed;
+    });
+    if (st) return st;
+    *out = c;
     return QFLEX_OK;
   });
-  if (st) return st;
-  *out = c;
-  return QFLEX_OK;
 }
 
 qflex_status qflex_plan_steps(qflex_plan p, int64_t n_bs, const int64_t* ids, int64_t n_ids, qflex_step_info* out,
                               int32_t cap, int32_t* n_steps) {
-  if (!p || !n_steps || n_bs < 0 || cap < 0 || (cap > 0 && !out)) return fail(QFLEX_ERR_ARG, "bad argument");
-  if (qflex_status st = check_slices(*p, ids, n_ids)) return st;
-  std::vector<int64_t> runs(p->steps.size(), 0), ab(p->steps.size(), 0), bb(p->steps.size(), 0);
-  std::vector<int64_t> ob;
-  std::vector<std::vector<int64_t>> ov;
-  oc_reset(*p, ob, ov);
-  qflex_status st = walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) {
-    if (i < 0) return QFLEX_OK;
-    const Step& s = p->steps[size_t(i)];
-    ++runs[size_t(i)];
-    ab[size_t(i)] += !s.A.direct && !s.A.fused &&
-                     !(s.A.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.A.cache)].dep, s.A.cache, b, vals));
-    bb[size_t(i)] += !s.B.direct && !s.B.fused &&
-                     !(s.B.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.B.cache)].dep, s.B.cache, b, vals));
+  return guarded([&]() -> qflex_status {
+    if (!p || !n_steps || n_bs < 0 || cap < 0 || (cap > 0 && !out)) return fail(QFLEX_ERR_ARG, "bad argument");
+    if (qflex_status st = check_slices(*p, ids, n_ids)) return st;
+    std::vector<int64_t> runs(p->steps.size(), 0), ab(p->steps.size(), 0), bb(p->steps.size(), 0);
+    std::vector<int64_t> ob;
+    std::vector<std::vector<int64_t>> ov;
+    oc_reset(*p, ob, ov);
+    qflex_status st = walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) {
+      if (i < 0) return QFLEX_OK;
+      const Step& s = p->steps[size_t(i)];
+      ++runs[size_t(i)];
+      ab[size_t(i)] += !s.A.direct && !s.A.fused &&
+                       !(s.A.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.A.cache)].dep, s.A.cache, b, vals));
+      bb[size_t(i)] += !s.B.direct && !s.B.fused &&
+                       !(s.B.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.B.cache)].dep, s.B.cache, b, vals));
+      return QFLEX_OK;
+    });
+    if (st) return st;
+    *n_steps = int32_t(p->steps.size());
+    for (int i = 0; i < int(p->steps.size()) && i < cap; ++i) {
+      const Step& s = p->steps[size_t(i)];
+      qflex_step_info& o = out[i];
+      o.dst = s.dst;
+      o.src = s.src;
+      o.M = s.M;
+      o.N = s.N;
+      o.K = s.K;
+      if (s.tc) {
+        o.kernel = 4;
+      } else if (s.fp32_kernel == 1 || (s.fp32_kernel == 0 && s.N <= 32)) {
+        // same rule as launch_cgemm_thin
+        const int64_t cgs = (s.N + 15) / 16;
+        o.kernel = (s.K >= 64 && ((s.M + 255) / 256) * cgs < 256) ? 3 : (s.N <= 16 ? 1 : 2);
+      } else {
+        o.kernel = 0;
+      }
+      o.bn = s.bn;
+      o.a_direct = s.A.direct;
+      o.b_direct = s.B.direct;
+      o.runs = runs[size_t(i)];
+      o.a_cached = s.A.cache >= 0;
+      o.b_cached = s.B.cache >= 0;
+      o.a_builds = ab[size_t(i)];
+      o.b_builds = bb[size_t(i)];
+      o.a_fused = s.A.fused;
+      o.b_fused = s.B.fused;
+      o.out_fused = s.fuse_out ? (s.po.n_fast ? 1 : 2) : 0;
+    }
     return QFLEX_OK;
   });
-  if (st) return st;
-  *n_steps = int32_t(p->steps.size());
-  for (int i = 0; i < int(p->steps.size()) && i < cap; ++i) {
-    const Step& s = p->steps[size_t(i)];
-    qflex_step_info& o = out[i];
-    o.dst = s.dst;
-    o.src = s.src;
-    o.M = s.M;
-    o.N = s.N;
-    o.K = s.K;
-    if (s.tc) {
-      o.kernel = 4;
-    } else if (s.fp32_kernel == 1 || (s.fp32_kernel == 0 && s.N <= 32)) {
-      // same rule as launch_cgemm_thin
-      const int64_t cgs = (s.N + 15) / 16;
-      o.kernel = (s.K >= 64 && ((s.M + 255) / 256) * cgs < 256) ? 3 : (s.N <= 16 ? 1 : 2);
-    } else {
-      o.kernel = 0;
-    }
-    o.bn = s.bn;
-    o.a_direct = s.A.direct;
-    o.b_direct = s.B.direct;
-    o.runs = runs[size_t(i)];
-    o.a_cached = s.A.cache >= 0;
-    o.b_cached = s.B.cache >= 0;
-    o.a_builds = ab[size_t(i)];
-    o.b_builds = bb[size_t(i)];
-    o.a_fused = s.A.fused;
-    o.b_fused = s.B.fused;
-    o.out_fused = s.fuse_out ? (s.po.n_fast ? 1 : 2) : 0;
-  }
-  return QFLEX_OK;
 }
 
 qflex_status qflex_search_ordering(const qflex_circuit* c, const int32_t* tile, int32_t n_open, const int32_t* cut_edges,
                                    int32_t n_cuts, int32_t max_new_cuts, int64_t max_tensor_elems, int32_t trials,
                                    uint64_t seed, int32_t* cuts_out, int32_t* steps_out, qflex_search_result* out) {
-  if (!c || !out || !steps_out || n_open < 0 || n_cuts < 0 || max_new_cuts < 0 || max_tensor_elems < 1 ||
-      trials < 1 || trials > 4096 ||
-      (n_open > 0 && !tile) || (n_cuts > 0 && !cut_edges) || (n_cuts + max_new_cuts > 0 && !cuts_out) ||
-      n_cuts + max_new_cuts > 64)
-    return fail(QFLEX_ERR_ARG, "bad search arguments");
-  const int n = c->n_qubits, E = c->n_edges;
-  if (n < 1 || E < 0 || (E > 0 && !c->edges) || c->n_gates < 0 || (c->n_gates > 0 && !c->gates))
-    return fail(QFLEX_ERR_CIRCUIT, "bad circuit");
-  SearchNet net;
-  net.n = n;
-  std::map<std::pair<int, int>, int> index;
-  for (int e = 0; e < E; ++e) {
-    const int a = c->edges[2 * e], b = c->edges[2 * e + 1];
-    if (a < 0 || b < 0 || a >= n || b >= n || a == b) return fail(QFLEX_ERR_CIRCUIT, "bad edge");
-    const auto key = std::make_pair(std::min(a, b), std::max(a, b));
-    if (index.count(key)) return fail(QFLEX_ERR_CIRCUIT, "repeated edge");
-    index[key] = e;
-    net.edges.push_back(key);
-  }
-  net.bits.assign(size_t(E), 0);
-  std::vector<int> gate_edge(size_t(c->n_gates), -1);
-  for (int64_t i = 0; i < c->n_gates; ++i) {
-    const qflex_gate& g = c->gates[i];
-    if (g.kind < 0 || g.kind > QFLEX_GATE_ISWAP || g.q0 < 0 || g.q0 >= n)
-      return fail(QFLEX_ERR_CIRCUIT, "bad gate kind or qubit");
-    if (g.kind != QFLEX_GATE_CZ && g.kind != QFLEX_GATE_ISWAP) continue;
-    auto it = index.find(std::make_pair(std::min(g.q0, g.q1), std::max(g.q0, g.q1)));
-    if (it == index.end()) return fail(QFLEX_ERR_CIRCUIT, "two-qubit gate on a pair that is not a lattice edge");
-    net.bits[size_t(it->second)] += g.kind == QFLEX_GATE_ISWAP ? 2 : 1;
-    gate_edge[size_t(i)] = it->second;
-  }
-  std::vector<int64_t> order(size_t(c->n_gates));
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int64_t x, int64_t y) { return c->gates[x].cycle < c->gates[y].cycle; });
-  net.lines = proj_lines(c, order, gate_edge, net.bits);
-  net.open.assign(size_t(n), 0);
-  for (int t = 0; t < n_open; ++t) {
-    if (tile[t] < 0 || tile[t] >= n || net.open[size_t(tile[t])]) return fail(QFLEX_ERR_ARG, "bad tile qubit");
-    net.open[size_t(tile[t])] = 1;
-  }
-  std::vector<int> cuts(cut_edges, cut_edges + n_cuts);
-  for (int e : cuts)
-    if (e < 0 || e >= E || std::count(cuts.begin(), cuts.end(), e) > 1) return fail(QFLEX_ERR_ARG, "bad cut edge");
-  std::vector<int> found;
-  SearchResult r;
-  const bool fits = search_cuts(net, cuts, max_new_cuts, std::log2(double(max_tensor_elems)), &found, &r, trials,
-                                seed);
-  if (r.steps.size() != size_t(2 * (n - 1))) return fail(QFLEX_ERR_PLAN, "search failed");
-  std::copy(found.begin(), found.end(), cuts_out);
-  std::copy(r.steps.begin(), r.steps.end(), steps_out);
-  out->log2_max_tensor = r.log2_max;
-  out->cmacs_per_bitstring = r.cmacs;
-  out->n_slices = r.n_slices;
-  out->n_nonzero_slices = r.n_nonzero;
-  out->n_cuts = int32_t(found.size());
-  out->n_steps = n - 1;
-  if (!fits)
-    return fail(QFLEX_ERR_PLAN, "no ordering with at most " + std::to_string(max_tensor_elems) +
-                                    " entries per tensor within " + std::to_string(max_new_cuts) + " new cuts");
-  return QFLEX_OK;
+  return guarded([&]() -> qflex_status {
+    if (!c || !out || !steps_out || n_open < 0 || n_cuts < 0 || max_new_cuts < 0 || max_tensor_elems < 1 ||
+        trials < 1 || trials > 4096 ||
+        (n_open > 0 && !tile) || (n_cuts > 0 && !cut_edges) || (n_cuts + max_new_cuts > 0 && !cuts_out) ||
+        n_cuts + max_new_cuts > 64)
+      return fail(QFLEX_ERR_ARG, "bad search arguments");
+    const int n = c->n_qubits, E = c->n_edges;
+    if (n < 1 || E < 0 || (E > 0 && !c->edges) || c->n_gates < 0 || (c->n_gates > 0 && !c->gates))
+      return fail(QFLEX_ERR_CIRCUIT, "bad circuit");
+    SearchNet net;
+    net.n = n;
+    std::map<std::pair<int, int>, int> index;
+    for (int e = 0; e < E; ++e) {
+      const int a = c->edges[2 * e], b = c->edges[2 * e + 1];
+      if (a < 0 || b < 0 || a >= n || b >= n || a == b) return fail(QFLEX_ERR_CIRCUIT, "bad edge");
+      const auto key = std::make_pair(std::min(a, b), std::max(a, b));
+      if (index.count(key)) return fail(QFLEX_ERR_CIRCUIT, "repeated edge");
+      index[key] = e;
+      net.edges.push_back(key);
+    }
+    net.bits.assign(size_t(E), 0);
+    std::vector<int> gate_edge(size_t(c->n_gates), -1);
+    for (int64_t i = 0; i < c->n_gates; ++i) {
+      const qflex_gate& g = c->gates[i];
+      if (g.kind < 0 || g.kind > QFLEX_GATE_ISWAP || g.q0 < 0 || g.q0 >= n)
+        return fail(QFLEX_ERR_CIRCUIT, "bad gate kind or qubit");
+      if (g.kind != QFLEX_GATE_CZ && g.kind != QFLEX_GATE_ISWAP) continue;
+      auto it = index.find(std::make_pair(std::min(g.q0, g.q1), std::max(g.q0, g.q1)));
+      if (it == index.end()) return fail(QFLEX_ERR_CIRCUIT, "two-qubit gate on a pair that is not a lattice edge");
+      net.bits[size_t(it->second)] += g.kind == QFLEX_GATE_ISWAP ? 2 : 1;
+      gate_edge[size_t(i)] = it->second;
+    }
+    std::vector<int64_t> order(size_t(c->n_gates));
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int64_t x, int64_t y) { return c->gates[x].cycle < c->gates[y].cycle; });
+    net.lines = proj_lines(c, order, gate_edge, net.bits);
+    net.open.assign(size_t(n), 0);
+    for (int t = 0; t < n_open; ++t) {
+      if (tile[t] < 0 || tile[t] >= n || net.open[size_t(tile[t])]) return fail(QFLEX_ERR_ARG, "bad tile qubit");
+      net.open[size_t(tile[t])] = 1;
+    }
+    std::vector<int> cuts(cut_edges, cut_edges + n_cuts);
+    for (int e : cuts)
+      if (e < 0 || e >= E || std::count(cuts.begin(), cuts.end(), e) > 1) return fail(QFLEX_ERR_ARG, "bad cut edge");
+    std::vector<int> found;
+    SearchResult r;
+    const bool fits = search_cuts(net, cuts, max_new_cuts, std::log2(double(max_tensor_elems)), &found, &r, trials,
+                                  seed);
+    if (r.steps.size() != size_t(2 * (n - 1))) return fail(QFLEX_ERR_PLAN, "search failed");
+    std::copy(found.begin(), found.end(), cuts_out);
+    std::copy(r.steps.begin(), r.steps.end(), steps_out);
+    out->log2_max_tensor = r.log2_max;
+    out->cmacs_per_bitstring = r.cmacs;
+    out->n_slices = r.n_slices;
+    out->n_nonzero_slices = r.n_nonzero;
+    out->n_cuts = int32_t(found.size());
+    out->n_steps = n - 1;
+    if (!fits)
+      return fail(QFLEX_ERR_PLAN, "no ordering with at most " + std::to_string(max_tensor_elems) +
+                                      " entries per tensor within " + std::to_string(max_new_cuts) + " new cuts");
+    return QFLEX_OK;
+  });
 }
 
 namespace {
@@ -1456,514 +1489,548 @@ constexpr int64_t kMaxListedSlices = int64_t(1) << 32;
 }  // namespace
 
 qflex_status qflex_select_slices(qflex_plan p, double f, uint64_t seed, int64_t* ids, int64_t cap, int64_t* n_sel) {
-  if (!p || !ids || !n_sel || !(f > 0.0)) return fail(QFLEX_ERR_ARG, "bad argument");
-  std::vector<int64_t> a;
-  if (qflex_status st = shuffle_select(p->P, f, seed, cap, &a)) return st;
-  std::copy(a.begin(), a.end(), ids);
-  *n_sel = int64_t(a.size());
-  return QFLEX_OK;
+  return guarded([&]() -> qflex_status {
+    if (!p || !ids || !n_sel || !(f > 0.0)) return fail(QFLEX_ERR_ARG, "bad argument");
+    std::vector<int64_t> a;
+    if (qflex_status st = shuffle_select(p->P, f, seed, cap, &a)) return st;
+    std::copy(a.begin(), a.end(), ids);
+    *n_sel = int64_t(a.size());
+    return QFLEX_OK;
+  });
 }
 
 qflex_status qflex_nonzero_slices(qflex_plan p, int64_t* ids, int64_t cap, int64_t* n_nonzero) {
-  if (!p || !n_nonzero || cap < 0 || (cap > 0 && !ids)) return fail(QFLEX_ERR_ARG, "bad argument");
-  const double count = p->zeros.n_nonzero();
-  if (count > double(kMaxListedSlices)) return fail(QFLEX_ERR_UNSUPPORTED, "too many paths to list");
-  *n_nonzero = int64_t(count);
-  if (cap < *n_nonzero) return fail(QFLEX_ERR_ARG, "slice_ids capacity too small");
-  std::vector<int64_t> all;
-  if (!p->zeros.list(&all, kMaxListedSlices)) return fail(QFLEX_ERR_UNSUPPORTED, "too many paths to list");
-  std::copy(all.begin(), all.end(), ids);
-  return QFLEX_OK;
+  return guarded([&]() -> qflex_status {
+    if (!p || !n_nonzero || cap < 0 || (cap > 0 && !ids)) return fail(QFLEX_ERR_ARG, "bad argument");
+    const double count = p->zeros.n_nonzero();
+    if (count > double(kMaxListedSlices)) return fail(QFLEX_ERR_UNSUPPORTED, "too many paths to list");
+    *n_nonzero = int64_t(count);
+    if (cap < *n_nonzero) return fail(QFLEX_ERR_ARG, "slice_ids capacity too small");
+    std::vector<int64_t> all;
+    if (!p->zeros.list(&all, kMaxListedSlices)) return fail(QFLEX_ERR_UNSUPPORTED, "too many paths to list");
+    std::copy(all.begin(), all.end(), ids);
+    return QFLEX_OK;
+  });
 }
 
 qflex_status qflex_select_nonzero_slices(qflex_plan p, double f, uint64_t seed, int64_t* ids, int64_t cap,
                                          int64_t* n_sel) {
-  if (!p || !ids || !n_sel || !(f > 0.0)) return fail(QFLEX_ERR_ARG, "bad argument");
-  std::vector<int64_t> all;
-  if (!p->zeros.list(&all, kMaxListedSlices)) return fail(QFLEX_ERR_UNSUPPORTED, "too many paths to list");
-  std::vector<int64_t> a;
-  if (qflex_status st = shuffle_select(int64_t(all.size()), f, seed, cap, &a)) return st;
-  for (size_t k = 0; k < a.size(); ++k) ids[k] = all[size_t(a[k])];
-  *n_sel = int64_t(a.size());
-  return QFLEX_OK;
+  return guarded([&]() -> qflex_status {
+    if (!p || !ids || !n_sel || !(f > 0.0)) return fail(QFLEX_ERR_ARG, "bad argument");
+    std::vector<int64_t> all;
+    if (!p->zeros.list(&all, kMaxListedSlices)) return fail(QFLEX_ERR_UNSUPPORTED, "too many paths to list");
+    std::vector<int64_t> a;
+    if (qflex_status st = shuffle_select(int64_t(all.size()), f, seed, cap, &a)) return st;
+    for (size_t k = 0; k < a.size(); ++k) ids[k] = all[size_t(a[k])];
+    *n_sel = int64_t(a.size());
+    return QFLEX_OK;
+  });
 }
 
 qflex_status qflex_amplitudes(qflex_plan p, const double* angles, const uint8_t* bits, int64_t n_bs,
                               const int64_t* ids, int64_t n_ids, double* amps, void* stream) {
-  if (!p) return fail(QFLEX_ERR_ARG, "null plan");
-  if (p->device < 0) return fail(QFLEX_ERR_UNSUPPORTED, "host-only plan");
-  if (n_bs < 0 || (n_bs > 0 && (!bits || !amps))) return fail(QFLEX_ERR_ARG, "bad bitstrings/output");
-  if (p->n_params > 0 && !angles) return fail(QFLEX_ERR_ARG, "angles required");
-  if (qflex_status st = check_slices(*p, ids, n_ids)) return st;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  QF_CUDA(cudaSetDevice(p->device));
-  p->last_stream = s;
-  const int64_t T = int64_t(1) << p->tile.size();
-  qflex_plan_s::GraphKey key;
-  key.angles = angles;
-  key.bits = bits;
-  key.out = amps;
-  key.n_bs = n_bs;
-  key.kind = 0;
-  key.all = ids == nullptr;
-  if (ids) key.ids.assign(ids, ids + n_ids);
-  return with_graph(*p, key, s, [&]() -> qflex_status {
+  return guarded([&]() -> qflex_status {
+    if (!p) return fail(QFLEX_ERR_ARG, "null plan");
+    if (p->device < 0) return fail(QFLEX_ERR_UNSUPPORTED, "host-only plan");
+    if (n_bs < 0 || (n_bs > 0 && (!bits || !amps))) return fail(QFLEX_ERR_ARG, "bad bitstrings/output");
+    if (p->n_params > 0 && !angles) return fail(QFLEX_ERR_ARG, "angles required");
+    if (qflex_status st = check_slices(*p, ids, n_ids)) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    QF_CUDA(cudaSetDevice(p->device));
+    p->last_stream = s;
+    const int64_t T = int64_t(1) << p->tile.size();
+    qflex_plan_s::GraphKey key;
+    key.angles = angles;
+    key.bits = bits;
+    key.out = amps;
+    key.n_bs = n_bs;
+    key.kind = 0;
+    key.all = ids == nullptr;
+    if (ids) key.ids.assign(ids, ids + n_ids);
+    return with_graph(*p, key, s, [&]() -> qflex_status {
+      QF_CUDA(cudaMemsetAsync(amps, 0, size_t(n_bs) * T * 2 * sizeof(double), s));
+      oc_reset(*p, p->oc_b, p->oc_v);
+      return walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) -> qflex_status {
+        cudaError_t e;
+        if (i == -2) {
+          e = timed(*p, 0, 0, 0, 8.0 * p->grid_elems, s, [&] {
+            return launch_gridtensor(p->d_gmeta, p->n, p->max_bits, p->d_gops, angles, bits + b * p->n, p->d_grid, s);
+          });
+        } else if (i == -1) {
+          const float2* src = ref_ptr(*p, p->final_ref) + ref_base(p->final_ref, vals);
+          e = timed(*p, 4, 0, 0, 40.0 * T, s, [&] {
+            return launch_slicesum(src, p->final_strides.data(), int(p->tile.size()), amps + b * T * 2, s);
+          });
+        } else {
+          e = run_step(*p, p->steps[i], b, vals, s);
+        }
+        if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
+        return QFLEX_OK;
+      });
+    });
+  });
+}
+
+qflex_status qflex_plan_enable_gradients(qflex_plan p) {
+  return guarded([&]() -> qflex_status {
+    if (!p) return fail(QFLEX_ERR_ARG, "null plan");
+    if (p->device < 0) return fail(QFLEX_ERR_UNSUPPORTED, "host-only plan");
+    if (p->grad_ready) return QFLEX_OK;
+    QF_CUDA(cudaSetDevice(p->device));
+    if (qflex_status st = build_grad(*p)) {
+      if (p->d_gws) cudaFree(p->d_gws);
+      p->d_gws = nullptr;
+      return st;
+    }
+    return QFLEX_OK;
+  });
+}
+
+qflex_status qflex_amplitudes_grad(qflex_plan p, const double* angles, const uint8_t* bits, int64_t n_bs,
+                                   const int64_t* ids, int64_t n_ids, const double* g, double* amps,
+                                   double* grad, void* stream) {
+  return guarded([&]() -> qflex_status {
+    if (!p) return fail(QFLEX_ERR_ARG, "null plan");
+    if (p->device < 0) return fail(QFLEX_ERR_UNSUPPORTED, "host-only plan");
+    if (!p->grad_ready) return fail(QFLEX_ERR_UNSUPPORTED, "call qflex_plan_enable_gradients first");
+    if (n_bs < 0 || (n_bs > 0 && (!bits || !amps || !g))) return fail(QFLEX_ERR_ARG, "bad bitstrings/outputs");
+    if (p->n_params > 0 && (!angles || !grad)) return fail(QFLEX_ERR_ARG, "angles and grad_angles required");
+    if (p->steps.empty()) return fail(QFLEX_ERR_UNSUPPORTED, "gradients need at least one contraction step");
+    if (qflex_status st = check_slices(*p, ids, n_ids)) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    QF_CUDA(cudaSetDevice(p->device));
+    p->last_stream = s;
+    const int64_t T = int64_t(1) << p->tile.size();
+    qflex_plan_s::GraphKey key;
+    key.angles = angles;
+    key.bits = bits;
+    key.out = amps;
+    key.grad = grad;
+    key.g = g;
+    key.n_bs = n_bs;
+    key.kind = 1;
+    key.all = ids == nullptr;
+    if (ids) key.ids.assign(ids, ids + n_ids);
+    p->grad_active = true;
+    const int final_buf = p->final_ref.id;
+    qflex_status res = with_graph(*p, key, s, [&]() -> qflex_status {
     QF_CUDA(cudaMemsetAsync(amps, 0, size_t(n_bs) * T * 2 * sizeof(double), s));
+    if (p->n_params > 0) QF_CUDA(cudaMemsetAsync(grad, 0, size_t(p->n_params) * sizeof(double), s));
     oc_reset(*p, p->oc_b, p->oc_v);
-    return walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) -> qflex_status {
-      cudaError_t e;
+    qflex_status res = walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) -> qflex_status {
+      cudaError_t e = cudaSuccess;
       if (i == -2) {
-        e = timed(*p, 0, 0, 0, 8.0 * p->grid_elems, s, [&] {
-          return launch_gridtensor(p->d_gmeta, p->n, p->max_bits, p->d_gops, angles, bits + b * p->n, p->d_grid, s);
-        });
+        if (b > 0 && p->n_params > 0)   // gradient of the previous bitstring
+          e = launch_gridgrad(p->d_gmeta, p->n, p->max_bits, p->d_gops, angles, bits + (b - 1) * p->n,
+                              p->d_wgrid, grad, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p->d_wgrid, 0, size_t(p->grid_elems) * 16, s);
+        if (e == cudaSuccess)
+          e = launch_gridtensor(p->d_gmeta, p->n, p->max_bits, p->d_gops, angles, bits + b * p->n, p->d_grid, s);
       } else if (i == -1) {
-        const float2* src = ref_ptr(*p, p->final_ref) + ref_base(p->final_ref, vals);
-        e = timed(*p, 4, 0, 0, 40.0 * T, s, [&] {
-          return launch_slicesum(src, p->final_strides.data(), int(p->tile.size()), amps + b * T * 2, s);
-        });
+        const float2* src = ref_ptr(*p, p->final_ref);
+        e = launch_slicesum(src, p->final_strides.data(), int(p->tile.size()), amps + b * T * 2, s);
+        // reverse pass of this slice
+        if (e == cudaSuccess)
+          e = launch_init_cotangent(reinterpret_cast<float2*>(p->d_warena + p->w_off[final_buf]),
+                                    p->final_strides.data(), int(p->tile.size()), g + b * T * 2, s);
+        for (int k = int(p->steps.size()) - 1; k >= 0 && e == cudaSuccess; --k) {
+          e = run_bwd(*p, p->steps[k], p->sg[k].ga, vals, s);
+          if (e == cudaSuccess) e = run_bwd(*p, p->steps[k], p->sg[k].gb, vals, s);
+        }
       } else {
         e = run_step(*p, p->steps[i], b, vals, s);
       }
       if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
       return QFLEX_OK;
     });
-  });
-}
-
-qflex_status qflex_plan_enable_gradients(qflex_plan p) {
-  if (!p) return fail(QFLEX_ERR_ARG, "null plan");
-  if (p->device < 0) return fail(QFLEX_ERR_UNSUPPORTED, "host-only plan");
-  if (p->grad_ready) return QFLEX_OK;
-  QF_CUDA(cudaSetDevice(p->device));
-  if (qflex_status st = build_grad(*p)) {
-    if (p->d_gws) cudaFree(p->d_gws);
-    p->d_gws = nullptr;
-    return st;
-  }
-  return QFLEX_OK;
-}
-
-qflex_status qflex_amplitudes_grad(qflex_plan p, const double* angles, const uint8_t* bits, int64_t n_bs,
-                                   const int64_t* ids, int64_t n_ids, const double* g, double* amps,
-                                   double* grad, void* stream) {
-  if (!p) return fail(QFLEX_ERR_ARG, "null plan");
-  if (p->device < 0) return fail(QFLEX_ERR_UNSUPPORTED, "host-only plan");
-  if (!p->grad_ready) return fail(QFLEX_ERR_UNSUPPORTED, "call qflex_plan_enable_gradients first");
-  if (n_bs < 0 || (n_bs > 0 && (!bits || !amps || !g))) return fail(QFLEX_ERR_ARG, "bad bitstrings/outputs");
-  if (p->n_params > 0 && (!angles || !grad)) return fail(QFLEX_ERR_ARG, "angles and grad_angles required");
-  if (p->steps.empty()) return fail(QFLEX_ERR_UNSUPPORTED, "gradients need at least one contraction step");
-  if (qflex_status st = check_slices(*p, ids, n_ids)) return st;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  QF_CUDA(cudaSetDevice(p->device));
-  p->last_stream = s;
-  const int64_t T = int64_t(1) << p->tile.size();
-  qflex_plan_s::GraphKey key;
-  key.angles = angles;
-  key.bits = bits;
-  key.out = amps;
-  key.grad = grad;
-  key.g = g;
-  key.n_bs = n_bs;
-  key.kind = 1;
-  key.all = ids == nullptr;
-  if (ids) key.ids.assign(ids, ids + n_ids);
-  p->grad_active = true;
-  const int final_buf = p->final_ref.id;
-  qflex_status res = with_graph(*p, key, s, [&]() -> qflex_status {
-  QF_CUDA(cudaMemsetAsync(amps, 0, size_t(n_bs) * T * 2 * sizeof(double), s));
-  if (p->n_params > 0) QF_CUDA(cudaMemsetAsync(grad, 0, size_t(p->n_params) * sizeof(double), s));
-  oc_reset(*p, p->oc_b, p->oc_v);
-  qflex_status res = walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) -> qflex_status {
-    cudaError_t e = cudaSuccess;
-    if (i == -2) {
-      if (b > 0 && p->n_params > 0)   // gradient of the previous bitstring
-        e = launch_gridgrad(p->d_gmeta, p->n, p->max_bits, p->d_gops, angles, bits + (b - 1) * p->n,
-                            p->d_wgrid, grad, s);
-      if (e == cudaSuccess) e = cudaMemsetAsync(p->d_wgrid, 0, size_t(p->grid_elems) * 16, s);
-      if (e == cudaSuccess)
-        e = launch_gridtensor(p->d_gmeta, p->n, p->max_bits, p->d_gops, angles, bits + b * p->n, p->d_grid, s);
-    } else if (i == -1) {
-      const float2* src = ref_ptr(*p, p->final_ref);
-      e = launch_slicesum(src, p->final_strides.data(), int(p->tile.size()), amps + b * T * 2, s);
-      // reverse pass of this slice
-      if (e == cudaSuccess)
-        e = launch_init_cotangent(reinterpret_cast<float2*>(p->d_warena + p->w_off[final_buf]),
-                                  p->final_strides.data(), int(p->tile.size()), g + b * T * 2, s);
-      for (int k = int(p->steps.size()) - 1; k >= 0 && e == cudaSuccess; --k) {
-        e = run_bwd(*p, p->steps[k], p->sg[k].ga, vals, s);
-        if (e == cudaSuccess) e = run_bwd(*p, p->steps[k], p->sg[k].gb, vals, s);
-      }
-    } else {
-      e = run_step(*p, p->steps[i], b, vals, s);
+    if (res == QFLEX_OK && n_bs > 0 && p->n_params > 0) {
+      cudaError_t e = launch_gridgrad(p->d_gmeta, p->n, p->max_bits, p->d_gops, angles, bits + (n_bs - 1) * p->n,
+                                      p->d_wgrid, grad, s);
+      if (e != cudaSuccess) res = fail(QFLEX_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
     }
-    if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
-    return QFLEX_OK;
+    return res;
+    });
+    p->grad_active = false;
+    return res;
   });
-  if (res == QFLEX_OK && n_bs > 0 && p->n_params > 0) {
-    cudaError_t e = launch_gridgrad(p->d_gmeta, p->n, p->max_bits, p->d_gops, angles, bits + (n_bs - 1) * p->n,
-                                    p->d_wgrid, grad, s);
-    if (e != cudaSuccess) res = fail(QFLEX_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
-  }
-  return res;
-  });
-  p->grad_active = false;
-  return res;
 }
 
 qflex_status qflex_plan_autotune(qflex_plan p, int32_t reps, int32_t* n_shapes, double* gain_ms) {
-  if (!p) return fail(QFLEX_ERR_ARG, "null plan");
-  if (p->device < 0) return fail(QFLEX_ERR_UNSUPPORTED, "host-only plan");
-  if (reps < 1 || reps > 100) return fail(QFLEX_ERR_ARG, "reps must be in [1, 100]");
-  QF_CUDA(cudaSetDevice(p->device));
-  cudaStream_t s = nullptr;
-  QF_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-  cudaEvent_t e0, e1;
-  QF_CUDA(cudaEventCreate(&e0));
-  QF_CUDA(cudaEventCreate(&e1));
-  struct Key {
-    int64_t M, N, K;
-    bool tc;
-    bool operator<(const Key& o) const {
-      return std::tie(M, N, K, tc) < std::tie(o.M, o.N, o.K, o.tc);
+  return guarded([&]() -> qflex_status {
+    if (!p) return fail(QFLEX_ERR_ARG, "null plan");
+    if (p->device < 0) return fail(QFLEX_ERR_UNSUPPORTED, "host-only plan");
+    if (reps < 1 || reps > 100) return fail(QFLEX_ERR_ARG, "reps must be in [1, 100]");
+    QF_CUDA(cudaSetDevice(p->device));
+    cudaStream_t s = nullptr;
+    QF_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    cudaEvent_t e0, e1;
+    QF_CUDA(cudaEventCreate(&e0));
+    QF_CUDA(cudaEventCreate(&e1));
+    struct Key {
+      int64_t M, N, K;
+      bool tc;
+      bool operator<(const Key& o) const {
+        return std::tie(M, N, K, tc) < std::tie(o.M, o.N, o.K, o.tc);
+      }
+    };
+    std::map<Key, std::vector<size_t>> groups;
+    for (size_t i = 0; i < p->steps.size(); ++i) {
+      const Step& st = p->steps[i];
+      groups[{st.M, st.N, st.K, st.tc}].push_back(i);
     }
-  };
-  std::map<Key, std::vector<size_t>> groups;
-  for (size_t i = 0; i < p->steps.size(); ++i) {
-    const Step& st = p->steps[i];
-    groups[{st.M, st.N, st.K, st.tc}].push_back(i);
-  }
-  int tuned = 0;
-  double gain = 0.0;
-  qflex_status res = QFLEX_OK;
-  for (auto& [key, idx] : groups) {
-    Step& st = p->steps[idx.front()];
-    float2* C = reinterpret_cast<float2*>(p->d_arena + p->bufs[st.out_buf].offset);
-    std::vector<int> cands;
-    bool fused_fp32 = false;   // CUDA-core producers writing planes keep their form
-    for (size_t i : idx) fused_fp32 = fused_fp32 || (!p->steps[i].tc && p->steps[i].fuse_out);
-    if (key.tc) cands = {128, 64};
-    else if (key.N <= 32 && !fused_fp32) cands = {1, 2};
-    else continue;
-    std::vector<TcGemmMaps> maps(cands.size());
-    float best = 1e30f, first = 0.f;
-    int best_c = -1;
-    for (size_t c = 0; c < cands.size(); ++c) {
-      if (key.tc && !tc_encode_maps(p->tc_kind, p->nsplit, cands[c], x_buf(*p, st.A, true, true), st.M,
-                                    x_buf(*p, st.B, false, true), st.N, st.K, &maps[c])) {
-        res = fail(QFLEX_ERR_CUDA, "tensor map encoding failed");
-        break;
-      }
-      auto launch = [&]() -> cudaError_t {
-        if (key.tc)
-          return launch_cgemm_tc(p->tc_kind, p->nsplit, cands[c], maps[c], st.M, st.N, st.K, C, p->d_status, s,
-                                 p->tc_kind == 2 ? p->d_smax + op_slot(st.A, true) : nullptr,
-                                 p->tc_kind == 2 ? p->d_smax + op_slot(st.B, false) : nullptr,
-                                 st.fuse_out ? &st.po : nullptr);
-        // operands as the step reads them: in place when consumed directly
-        // (the scratch is only sized for produced operands), else their buffer
-        const float2* A = st.A.direct ? ref_ptr(*p, st.A.ref) : static_cast<const float2*>(op_buf(*p, st.A, true));
-        const float2* B = st.B.direct ? ref_ptr(*p, st.B.ref) : static_cast<const float2*>(op_buf(*p, st.B, false));
-        return cands[c] == 1 ? launch_cgemm_thin(st.M, st.N, st.K, A, B, C, s)
-                             : launch_cgemm_simt(st.M, st.N, st.K, A, B, C, s);
-      };
-      cudaError_t e = launch();   // warm-up
-      for (int r = 0; r < reps && e == cudaSuccess; ++r) {
-        if (r == 0) e = cudaEventRecord(e0, s);
-        if (e == cudaSuccess) e = launch();
-      }
-      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float ms = 0.f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e != cudaSuccess) {
-        res = fail(QFLEX_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
-        break;
-      }
-      ms /= float(reps);
-      if (c == 0) first = ms;
-      if (ms < best) {
-        best = ms;
-        best_c = int(c);
-      }
-    }
-    if (res != QFLEX_OK) break;
-    for (size_t i : idx) {
-      Step& t = p->steps[i];
-      if (key.tc) {
-        // steps of one shape may read different operand buffers (caches)
-        t.bn = cands[best_c];
-        if (!encode_step(*p, t)) {
+    int tuned = 0;
+    double gain = 0.0;
+    qflex_status res = QFLEX_OK;
+    for (auto& [key, idx] : groups) {
+      Step& st = p->steps[idx.front()];
+      float2* C = reinterpret_cast<float2*>(p->d_arena + p->bufs[st.out_buf].offset);
+      std::vector<int> cands;
+      bool fused_fp32 = false;   // CUDA-core producers writing planes keep their form
+      for (size_t i : idx) fused_fp32 = fused_fp32 || (!p->steps[i].tc && p->steps[i].fuse_out);
+      if (key.tc) cands = {128, 64};
+      else if (key.N <= 32 && !fused_fp32) cands = {1, 2};
+      else continue;
+      std::vector<TcGemmMaps> maps(cands.size());
+      float best = 1e30f, first = 0.f;
+      int best_c = -1;
+      for (size_t c = 0; c < cands.size(); ++c) {
+        if (key.tc && !tc_encode_maps(p->tc_kind, p->nsplit, cands[c], x_buf(*p, st.A, true, true), st.M,
+                                      x_buf(*p, st.B, false, true), st.N, st.K, &maps[c])) {
           res = fail(QFLEX_ERR_CUDA, "tensor map encoding failed");
           break;
         }
-      } else {
-        t.fp32_kernel = cands[best_c];
+        auto launch = [&]() -> cudaError_t {
+          if (key.tc)
+            return launch_cgemm_tc(p->tc_kind, p->nsplit, cands[c], maps[c], st.M, st.N, st.K, C, p->d_status, s,
+                                   p->tc_kind == 2 ? p->d_smax + op_slot(st.A, true) : nullptr,
+                                   p->tc_kind == 2 ? p->d_smax + op_slot(st.B, false) : nullptr,
+                                   st.fuse_out ? &st.po : nullptr);
+          // operands as the step reads them: in place when consumed directly
+          // (the scratch is only sized for produced operands), else their buffer
+          const float2* A = st.A.direct ? ref_ptr(*p, st.A.ref) : static_cast<const float2*>(op_buf(*p, st.A, true));
+          const float2* B = st.B.direct ? ref_ptr(*p, st.B.ref) : static_cast<const float2*>(op_buf(*p, st.B, false));
+          return cands[c] == 1 ? launch_cgemm_thin(st.M, st.N, st.K, A, B, C, s)
+                               : launch_cgemm_simt(st.M, st.N, st.K, A, B, C, s);
+        };
+        cudaError_t e = launch();   // warm-up
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+          if (r == 0) e = cudaEventRecord(e0, s);
+          if (e == cudaSuccess) e = launch();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+          res = fail(QFLEX_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+          break;
+        }
+        ms /= float(reps);
+        if (c == 0) first = ms;
+        if (ms < best) {
+          best = ms;
+          best_c = int(c);
+        }
       }
+      if (res != QFLEX_OK) break;
+      for (size_t i : idx) {
+        Step& t = p->steps[i];
+        if (key.tc) {
+          // steps of one shape may read different operand buffers (caches)
+          t.bn = cands[best_c];
+          if (!encode_step(*p, t)) {
+            res = fail(QFLEX_ERR_CUDA, "tensor map encoding failed");
+            break;
+          }
+        } else {
+          t.fp32_kernel = cands[best_c];
+        }
+      }
+      ++tuned;
+      gain += double(first - best) * double(idx.size());
     }
-    ++tuned;
-    gain += double(first - best) * double(idx.size());
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaStreamDestroy(s);
-  if (res != QFLEX_OK) return res;
-  int32_t w = 0;
-  QF_CUDA(cudaMemcpy(&w, p->d_status, sizeof(w), cudaMemcpyDeviceToHost));
-  if (w) return fail(QFLEX_ERR_DEVICE_TIMEOUT, "a bounded device-side wait ran out during autotuning");
-  if (p->gexec) {   // cached graph holds the old configuration
-    cudaGraphExecDestroy(p->gexec);
-    p->gexec = nullptr;
-    p->gseen = qflex_plan_s::GraphKey{};
-  }
-  if (n_shapes) *n_shapes = tuned;
-  if (gain_ms) *gain_ms = gain;
-  return QFLEX_OK;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    if (res != QFLEX_OK) return res;
+    int32_t w = 0;
+    QF_CUDA(cudaMemcpy(&w, p->d_status, sizeof(w), cudaMemcpyDeviceToHost));
+    if (w) return fail(QFLEX_ERR_DEVICE_TIMEOUT, "a bounded device-side wait ran out during autotuning");
+    if (p->gexec) {   // cached graph holds the old configuration
+      cudaGraphExecDestroy(p->gexec);
+      p->gexec = nullptr;
+      p->gseen = qflex_plan_s::GraphKey{};
+    }
+    if (n_shapes) *n_shapes = tuned;
+    if (gain_ms) *gain_ms = gain;
+    return QFLEX_OK;
+  });
 }
 
 qflex_status qflex_plan_use_graphs(qflex_plan p, int32_t enable) {
-  if (!p) return fail(QFLEX_ERR_ARG, "null plan");
-  p->use_graphs = enable != 0;
-  if (!p->use_graphs && p->gexec) {
-    cudaGraphExecDestroy(p->gexec);
-    p->gexec = nullptr;
-  }
-  return QFLEX_OK;
+  return guarded([&]() -> qflex_status {
+    if (!p) return fail(QFLEX_ERR_ARG, "null plan");
+    p->use_graphs = enable != 0;
+    if (!p->use_graphs && p->gexec) {
+      cudaGraphExecDestroy(p->gexec);
+      p->gexec = nullptr;
+    }
+    return QFLEX_OK;
+  });
 }
 
 qflex_status qflex_plan_profile(qflex_plan p, int32_t mode, qflex_profile* out) {
-  if (!p) return fail(QFLEX_ERR_ARG, "null plan");
-  if (p->device < 0) return fail(QFLEX_ERR_UNSUPPORTED, "host-only plan");
-  QF_CUDA(cudaSetDevice(p->device));
-  auto drain = [&]() -> qflex_status {
-    if (p->recs.empty()) return QFLEX_OK;
-    QF_CUDA(cudaEventSynchronize(p->ev_pool[p->recs.back().e0 + 1]));
-    for (const auto& r : p->recs) {
-      float ms = 0.f;
-      QF_CUDA(cudaEventElapsedTime(&ms, p->ev_pool[r.e0], p->ev_pool[r.e0 + 1]));
-      p->prof.launches[r.cls] += 1;
-      p->prof.ms[r.cls] += ms;
-      p->prof.flops[r.cls] += r.flops;
-      p->prof.mma_flops[r.cls] += r.mma;
-      p->prof.bytes[r.cls] += r.bytes;
+  return guarded([&]() -> qflex_status {
+    if (!p) return fail(QFLEX_ERR_ARG, "null plan");
+    if (p->device < 0) return fail(QFLEX_ERR_UNSUPPORTED, "host-only plan");
+    QF_CUDA(cudaSetDevice(p->device));
+    auto drain = [&]() -> qflex_status {
+      if (p->recs.empty()) return QFLEX_OK;
+      QF_CUDA(cudaEventSynchronize(p->ev_pool[p->recs.back().e0 + 1]));
+      for (const auto& r : p->recs) {
+        float ms = 0.f;
+        QF_CUDA(cudaEventElapsedTime(&ms, p->ev_pool[r.e0], p->ev_pool[r.e0 + 1]));
+        p->prof.launches[r.cls] += 1;
+        p->prof.ms[r.cls] += ms;
+        p->prof.flops[r.cls] += r.flops;
+        p->prof.mma_flops[r.cls] += r.mma;
+        p->prof.bytes[r.cls] += r.bytes;
+      }
+      p->recs.clear();
+      p->ev_used = 0;
+      return QFLEX_OK;
+    };
+    if (mode < 0 || mode > 31) return fail(QFLEX_ERR_ARG, "mode must be a class mask in [0, 31]");
+    if (mode != 0) {
+      if (qflex_status st = drain()) return st;
+      p->prof = qflex_profile{};
+      p->profiling = true;
+      p->prof_mask = mode;
+    } else {
+      p->profiling = false;
     }
-    p->recs.clear();
-    p->ev_used = 0;
+    if (out) {
+      if (qflex_status st = drain()) return st;
+      *out = p->prof;
+    }
     return QFLEX_OK;
-  };
-  if (mode < 0 || mode > 31) return fail(QFLEX_ERR_ARG, "mode must be a class mask in [0, 31]");
-  if (mode != 0) {
-    if (qflex_status st = drain()) return st;
-    p->prof = qflex_profile{};
-    p->profiling = true;
-    p->prof_mask = mode;
-  } else {
-    p->profiling = false;
-  }
-  if (out) {
-    if (qflex_status st = drain()) return st;
-    *out = p->prof;
-  }
-  return QFLEX_OK;
+  });
 }
 
 qflex_status qflex_plan_sync(qflex_plan p) {
-  if (!p) return fail(QFLEX_ERR_ARG, "null plan");
-  if (p->device < 0) return QFLEX_OK;
-  QF_CUDA(cudaSetDevice(p->device));
-  QF_CUDA(cudaStreamSynchronize(p->last_stream));
-  int32_t w = 0;
-  QF_CUDA(cudaMemcpy(&w, p->d_status, sizeof(w), cudaMemcpyDeviceToHost));
-  if (w) {
-    QF_CUDA(cudaMemset(p->d_status, 0, sizeof(int32_t)));
-    if (w & kDevTimeout) return fail(QFLEX_ERR_DEVICE_TIMEOUT, "a bounded device-side wait ran out");
-    return fail(QFLEX_ERR_PLAN, "internal: a fused epilogue destination fell outside its operand planes");
-  }
-  return QFLEX_OK;
+  return guarded([&]() -> qflex_status {
+    if (!p) return fail(QFLEX_ERR_ARG, "null plan");
+    if (p->device < 0) return QFLEX_OK;
+    QF_CUDA(cudaSetDevice(p->device));
+    QF_CUDA(cudaStreamSynchronize(p->last_stream));
+    int32_t w = 0;
+    QF_CUDA(cudaMemcpy(&w, p->d_status, sizeof(w), cudaMemcpyDeviceToHost));
+    if (w) {
+      QF_CUDA(cudaMemset(p->d_status, 0, sizeof(int32_t)));
+      if (w & kDevTimeout) return fail(QFLEX_ERR_DEVICE_TIMEOUT, "a bounded device-side wait ran out");
+      return fail(QFLEX_ERR_PLAN, "internal: a fused epilogue destination fell outside its operand planes");
+    }
+    return QFLEX_OK;
+  });
 }
 
 qflex_status qflex_permute(const void* in, void* out, int32_t rank, const int64_t* dims, const int32_t* perm,
                            void* stream) {
-  if (rank < 0 || rank > 32 || (rank > 0 && (!dims || !perm))) return fail(QFLEX_ERR_ARG, "bad permute arguments");
-  std::vector<int64_t> istr(rank);
-  int64_t total = 1;
-  for (int a = rank - 1; a >= 0; --a) {
-    if (dims[a] < 0) return fail(QFLEX_ERR_ARG, "dims must be non-negative");
-    istr[a] = total;
-    total *= dims[a];
-  }
-  std::vector<int> seen(rank, 0);
-  for (int a = 0; a < rank; ++a) {
-    if (perm[a] < 0 || perm[a] >= rank || seen[perm[a]]++) return fail(QFLEX_ERR_ARG, "perm is not a permutation");
-  }
-  if (total == 0) return QFLEX_OK;
-  if (!in || !out) return fail(QFLEX_ERR_ARG, "null tensor pointer");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  bool pow2 = true;
-  for (int a = 0; a < rank; ++a) pow2 = pow2 && is_pow2(dims[a]);
-  cudaError_t e;
-  if (pow2) {
-    std::vector<int64_t> w;
-    for (int a = rank - 1; a >= 0; --a)
-      for (int b = 0; b < ilog2(dims[perm[a]]); ++b) w.push_back(istr[perm[a]] << b);
-    PermTile t;
-    if (!build_perm_tile(int(w.size()), w.data(), &t)) return fail(QFLEX_ERR_UNSUPPORTED, "tensor too large");
-    e = launch_permute_tiled(static_cast<const float2*>(in), 0, t, kFmtC64, 1, out, total, s);
-  } else {
-    GatherDesc g{};
-    g.rank = rank;
-    g.total = total;
-    for (int a = 0; a < rank; ++a) {
-      g.dims[a] = dims[perm[a]];
-      g.in_strides[a] = istr[perm[a]];
+  return guarded([&]() -> qflex_status {
+    if (rank < 0 || rank > 32 || (rank > 0 && (!dims || !perm))) return fail(QFLEX_ERR_ARG, "bad permute arguments");
+    std::vector<int64_t> istr(rank);
+    int64_t total = 1;
+    for (int a = rank - 1; a >= 0; --a) {
+      if (dims[a] < 0) return fail(QFLEX_ERR_ARG, "dims must be non-negative");
+      istr[a] = total;
+      total *= dims[a];
     }
-    e = launch_permute_gather(static_cast<const float2*>(in), 0, g, kFmtC64, 1, out, total, s);
-  }
-  if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
-  return QFLEX_OK;
+    std::vector<int> seen(rank, 0);
+    for (int a = 0; a < rank; ++a) {
+      if (perm[a] < 0 || perm[a] >= rank || seen[perm[a]]++) return fail(QFLEX_ERR_ARG, "perm is not a permutation");
+    }
+    if (total == 0) return QFLEX_OK;
+    if (!in || !out) return fail(QFLEX_ERR_ARG, "null tensor pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    bool pow2 = true;
+    for (int a = 0; a < rank; ++a) pow2 = pow2 && is_pow2(dims[a]);
+    cudaError_t e;
+    if (pow2) {
+      std::vector<int64_t> w;
+      for (int a = rank - 1; a >= 0; --a)
+        for (int b = 0; b < ilog2(dims[perm[a]]); ++b) w.push_back(istr[perm[a]] << b);
+      PermTile t;
+      if (!build_perm_tile(int(w.size()), w.data(), &t)) return fail(QFLEX_ERR_UNSUPPORTED, "tensor too large");
+      e = launch_permute_tiled(static_cast<const float2*>(in), 0, t, kFmtC64, 1, out, total, s);
+    } else {
+      GatherDesc g{};
+      g.rank = rank;
+      g.total = total;
+      for (int a = 0; a < rank; ++a) {
+        g.dims[a] = dims[perm[a]];
+        g.in_strides[a] = istr[perm[a]];
+      }
+      e = launch_permute_gather(static_cast<const float2*>(in), 0, g, kFmtC64, 1, out, total, s);
+    }
+    if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
+    return QFLEX_OK;
+  });
 }
 
 qflex_status qflex_cgemm_workspace_size(int32_t prec, int64_t M, int64_t N, int64_t K, size_t* bytes) {
-  if (!bytes || M < 0 || N < 0 || K < 0) return fail(QFLEX_ERR_ARG, "bad argument");
-  if (prec == QFLEX_FP32_SIMT) {
-    *bytes = 0;
+  return guarded([&]() -> qflex_status {
+    if (!bytes || M < 0 || N < 0 || K < 0) return fail(QFLEX_ERR_ARG, "bad argument");
+    if (prec == QFLEX_FP32_SIMT) {
+      *bytes = 0;
+      return QFLEX_OK;
+    }
+    if (prec < 0 || prec > QFLEX_FP16X3) return fail(QFLEX_ERR_ARG, "unknown precision");
+    const int kind = tc_kind_of(prec);
+    const int nsplit = nsplit_of(prec);
+    const size_t per = size_t(3) * nsplit * (kind == 0 ? 4 : 2);
+    *bytes = align256(per * size_t(M) * size_t(K)) + align256(per * size_t(N) * size_t(K)) + 256;
     return QFLEX_OK;
-  }
-  if (prec < 0 || prec > QFLEX_FP16X3) return fail(QFLEX_ERR_ARG, "unknown precision");
-  const int kind = tc_kind_of(prec);
-  const int nsplit = nsplit_of(prec);
-  const size_t per = size_t(3) * nsplit * (kind == 0 ? 4 : 2);
-  *bytes = align256(per * size_t(M) * size_t(K)) + align256(per * size_t(N) * size_t(K)) + 256;
-  return QFLEX_OK;
+  });
 }
 
 qflex_status qflex_cgemm(int32_t prec, int64_t M, int64_t N, int64_t K, const void* A, const void* B, void* C,
                          void* ws, size_t ws_bytes, void* stream) {
-  if (M < 0 || N < 0 || K < 0 || (M * N > 0 && (!A || !B || !C))) return fail(QFLEX_ERR_ARG, "bad GEMM arguments");
-  if (M == 0 || N == 0) return QFLEX_OK;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const bool tc = prec != QFLEX_FP32_SIMT && M >= 128 && K % 8 == 0 && K > 0 && N >= 16;
-  if (!tc) {
-    if (K == 0) QF_CUDA(cudaMemsetAsync(C, 0, size_t(M) * N * 8, s));
-    else if (N <= 32)
-      QF_CUDA(launch_cgemm_thin(M, N, K, static_cast<const float2*>(A), static_cast<const float2*>(B),
-                                static_cast<float2*>(C), s));
-    else
-      QF_CUDA(launch_cgemm_simt(M, N, K, static_cast<const float2*>(A), static_cast<const float2*>(B),
-                                static_cast<float2*>(C), s));
+  return guarded([&]() -> qflex_status {
+    if (M < 0 || N < 0 || K < 0 || (M * N > 0 && (!A || !B || !C))) return fail(QFLEX_ERR_ARG, "bad GEMM arguments");
+    if (M == 0 || N == 0) return QFLEX_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool tc = prec != QFLEX_FP32_SIMT && M >= 128 && K % 8 == 0 && K > 0 && N >= 16;
+    if (!tc) {
+      if (K == 0) QF_CUDA(cudaMemsetAsync(C, 0, size_t(M) * N * 8, s));
+      else if (N <= 32)
+        QF_CUDA(launch_cgemm_thin(M, N, K, static_cast<const float2*>(A), static_cast<const float2*>(B),
+                                  static_cast<float2*>(C), s));
+      else
+        QF_CUDA(launch_cgemm_simt(M, N, K, static_cast<const float2*>(A), static_cast<const float2*>(B),
+                                  static_cast<float2*>(C), s));
+      return QFLEX_OK;
+    }
+    size_t need = 0;
+    if (qflex_status st = qflex_cgemm_workspace_size(prec, M, N, K, &need)) return st;
+    if (!ws || ws_bytes < need) return fail(QFLEX_ERR_ARG, "workspace too small");
+    if (!tc_available()) return fail(QFLEX_ERR_UNSUPPORTED, "tensor-map encoder unavailable");
+    const int kind = tc_kind_of(prec);
+    const int nsplit = nsplit_of(prec);
+    const size_t per = size_t(3) * nsplit * (kind == 0 ? 4 : 2);
+    char* pa = static_cast<char*>(ws);
+    char* pb = pa + align256(per * size_t(M) * size_t(K));
+    unsigned* smax = reinterpret_cast<unsigned*>(pb + align256(per * size_t(N) * size_t(K)));
+    const int fmt = plane_fmt(kind);
+    // identity "permutation" of a [rows][K] matrix into operand planes
+    auto planes = [&](const void* src, int64_t rows, void* dst, unsigned* sm) {
+      std::vector<int64_t> w;
+      const int64_t total = rows * K;
+      if (fmt == kFmtFP16) {
+        cudaError_t e = launch_absmax(static_cast<const float2*>(src), total, sm, s);
+        if (e != cudaSuccess) return e;
+      } else {
+        sm = nullptr;
+      }
+      if (is_pow2(total)) {
+        for (int b = 0; b < ilog2(total); ++b) w.push_back(int64_t(1) << b);
+        PermTile t;
+        build_perm_tile(int(w.size()), w.data(), &t);
+        return launch_permute_tiled(static_cast<const float2*>(src), 0, t, fmt, nsplit, dst, total, s, sm);
+      }
+      GatherDesc g{};
+      g.rank = 1;
+      g.total = total;
+      g.dims[0] = total;
+      g.in_strides[0] = 1;
+      return launch_permute_gather(static_cast<const float2*>(src), 0, g, fmt, nsplit, dst, total, s, sm);
+    };
+    QF_CUDA(planes(A, M, pa, smax));
+    QF_CUDA(planes(B, N, pb, smax + 1));
+    TcGemmMaps maps;
+    const int bn = N >= 128 ? 128 : 64;
+    if (!tc_encode_maps(kind, nsplit, bn, pa, M, pb, N, K, &maps)) return fail(QFLEX_ERR_CUDA, "tensor map encoding failed");
+    int dev = 0;
+    QF_CUDA(cudaGetDevice(&dev));
+    QF_CUDA(launch_cgemm_tc(kind, nsplit, bn, maps, M, N, K, static_cast<float2*>(C), device_status_word(dev), s,
+                            kind == 2 ? smax : nullptr, kind == 2 ? smax + 1 : nullptr));
     return QFLEX_OK;
-  }
-  size_t need = 0;
-  if (qflex_status st = qflex_cgemm_workspace_size(prec, M, N, K, &need)) return st;
-  if (!ws || ws_bytes < need) return fail(QFLEX_ERR_ARG, "workspace too small");
-  if (!tc_available()) return fail(QFLEX_ERR_UNSUPPORTED, "tensor-map encoder unavailable");
-  const int kind = tc_kind_of(prec);
-  const int nsplit = nsplit_of(prec);
-  const size_t per = size_t(3) * nsplit * (kind == 0 ? 4 : 2);
-  char* pa = static_cast<char*>(ws);
-  char* pb = pa + align256(per * size_t(M) * size_t(K));
-  unsigned* smax = reinterpret_cast<unsigned*>(pb + align256(per * size_t(N) * size_t(K)));
-  const int fmt = plane_fmt(kind);
-  // identity "permutation" of a [rows][K] matrix into operand planes
-  auto planes = [&](const void* src, int64_t rows, void* dst, unsigned* sm) {
-    std::vector<int64_t> w;
-    const int64_t total = rows * K;
-    if (fmt == kFmtFP16) {
-      cudaError_t e = launch_absmax(static_cast<const float2*>(src), total, sm, s);
-      if (e != cudaSuccess) return e;
-    } else {
-      sm = nullptr;
-    }
-    if (is_pow2(total)) {
-      for (int b = 0; b < ilog2(total); ++b) w.push_back(int64_t(1) << b);
-      PermTile t;
-      build_perm_tile(int(w.size()), w.data(), &t);
-      return launch_permute_tiled(static_cast<const float2*>(src), 0, t, fmt, nsplit, dst, total, s, sm);
-    }
-    GatherDesc g{};
-    g.rank = 1;
-    g.total = total;
-    g.dims[0] = total;
-    g.in_strides[0] = 1;
-    return launch_permute_gather(static_cast<const float2*>(src), 0, g, fmt, nsplit, dst, total, s, sm);
-  };
-  QF_CUDA(planes(A, M, pa, smax));
-  QF_CUDA(planes(B, N, pb, smax + 1));
-  TcGemmMaps maps;
-  const int bn = N >= 128 ? 128 : 64;
-  if (!tc_encode_maps(kind, nsplit, bn, pa, M, pb, N, K, &maps)) return fail(QFLEX_ERR_CUDA, "tensor map encoding failed");
-  int dev = 0;
-  QF_CUDA(cudaGetDevice(&dev));
-  QF_CUDA(launch_cgemm_tc(kind, nsplit, bn, maps, M, N, K, static_cast<float2*>(C), device_status_word(dev), s,
-                          kind == 2 ? smax : nullptr, kind == 2 ? smax + 1 : nullptr));
-  return QFLEX_OK;
+  });
 }
 
 qflex_status qflex_norm(const double* amps, int64_t n, double* out, void* stream) {
-  if (!amps || !out || n < 0) return fail(QFLEX_ERR_ARG, "bad argument");
-  QF_CUDA(launch_norm(amps, n, out, static_cast<cudaStream_t>(stream)));
-  return QFLEX_OK;
+  return guarded([&]() -> qflex_status {
+    if (!amps || !out || n < 0) return fail(QFLEX_ERR_ARG, "bad argument");
+    QF_CUDA(launch_norm(amps, n, out, static_cast<cudaStream_t>(stream)));
+    return QFLEX_OK;
+  });
 }
 
 qflex_status qflex_frugal_sample(const double* amps, int64_t n_batches, int32_t n_c, int32_t n_qubits,
                                  double M, uint64_t seed, int32_t* accepted, void* stream) {
-  if (n_batches < 0 || n_c < 1 || n_c > 4096 || n_qubits < 0 || n_qubits > 1000 || !(M > 0.0))
-    return fail(QFLEX_ERR_ARG, "bad sampling arguments");
-  if (n_batches == 0) return QFLEX_OK;
-  if (!amps || !accepted) return fail(QFLEX_ERR_ARG, "null pointer");
-  const double scale = std::ldexp(1.0, n_qubits) / M;
-  QF_CUDA(launch_frugal(amps, n_batches, n_c, scale, seed, accepted, static_cast<cudaStream_t>(stream)));
-  return QFLEX_OK;
+  return guarded([&]() -> qflex_status {
+    if (n_batches < 0 || n_c < 1 || n_c > 4096 || n_qubits < 0 || n_qubits > 1000 || !(M > 0.0))
+      return fail(QFLEX_ERR_ARG, "bad sampling arguments");
+    if (n_batches == 0) return QFLEX_OK;
+    if (!amps || !accepted) return fail(QFLEX_ERR_ARG, "null pointer");
+    const double scale = std::ldexp(1.0, n_qubits) / M;
+    QF_CUDA(launch_frugal(amps, n_batches, n_c, scale, seed, accepted, static_cast<cudaStream_t>(stream)));
+    return QFLEX_OK;
+  });
 }
 
 qflex_status qflex_fidelity_samples(const uint8_t* batch_bits, const int32_t* accepted, int64_t n_batches,
                                     const int32_t* tile, int32_t n_tile, int32_t n_qubits, double fidelity,
                                     uint64_t seed, int64_t n_samples, uint8_t* samples, int32_t* source,
                                     int64_t* n_exact, void* stream) {
-  if (!n_exact || n_batches < 0 || n_samples < 0 || n_qubits < 1 || n_qubits > 100000 || n_tile < 0 ||
-      n_tile > 30 || n_tile > n_qubits || !(fidelity >= 0.0 && fidelity <= 1.0))
-    return fail(QFLEX_ERR_ARG, "bad fidelity-sampling arguments");
-  if (n_batches > INT32_MAX) return fail(QFLEX_ERR_ARG, "more than 2^31 - 1 batches");
-  std::vector<char> seen(size_t(n_qubits), 0);
-  for (int t = 0; t < n_tile; ++t) {
-    if (!tile || tile[t] < 0 || tile[t] >= n_qubits || seen[tile[t]]) return fail(QFLEX_ERR_ARG, "bad tile qubit");
-    seen[tile[t]] = 1;
-  }
-  *n_exact = 0;
-  if (n_samples == 0) return QFLEX_OK;
-  if (!samples || !source || (n_batches > 0 && (!batch_bits || !accepted))) return fail(QFLEX_ERR_ARG, "null pointer");
-  const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  void* scratch = nullptr;
-  const size_t pool_bytes = (size_t(n_batches) * 4 + 15) / 16 * 16;
-  QF_CUDA(cudaMallocAsync(&scratch, pool_bytes + 16, s));
-  int32_t* pool = static_cast<int32_t*>(scratch);
-  int64_t* counts = reinterpret_cast<int64_t*>(static_cast<char*>(scratch) + pool_bytes);
-  int64_t host_counts[2] = {0, 0};
-  cudaError_t e = launch_fidelity_mix(batch_bits, accepted, n_batches, tile, n_tile, n_qubits, fidelity, seed,
-                                      n_samples, pool, source, counts, samples, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(host_counts, counts, sizeof(host_counts), cudaMemcpyDeviceToHost, s);
-  const cudaError_t ef = cudaFreeAsync(scratch, s);
-  if (e == cudaSuccess) e = ef;
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("fidelity sampling: ") + cudaGetErrorString(e));
-  *n_exact = host_counts[0];
-  if (host_counts[0] > host_counts[1])
-    return fail(QFLEX_ERR_ARG, "fidelity sampling needs " + std::to_string(host_counts[0]) +
-                                   " exact samples but only " + std::to_string(host_counts[1]) +
-                                   " batches were accepted; compute more batches");
-  return QFLEX_OK;
+  return guarded([&]() -> qflex_status {
+    if (!n_exact || n_batches < 0 || n_samples < 0 || n_qubits < 1 || n_qubits > 100000 || n_tile < 0 ||
+        n_tile > 30 || n_tile > n_qubits || !(fidelity >= 0.0 && fidelity <= 1.0))
+      return fail(QFLEX_ERR_ARG, "bad fidelity-sampling arguments");
+    if (n_batches > INT32_MAX) return fail(QFLEX_ERR_ARG, "more than 2^31 - 1 batches");
+    std::vector<char> seen(size_t(n_qubits), 0);
+    for (int t = 0; t < n_tile; ++t) {
+      if (!tile || tile[t] < 0 || tile[t] >= n_qubits || seen[tile[t]]) return fail(QFLEX_ERR_ARG, "bad tile qubit");
+      seen[tile[t]] = 1;
+    }
+    *n_exact = 0;
+    if (n_samples == 0) return QFLEX_OK;
+    if (!samples || !source || (n_batches > 0 && (!batch_bits || !accepted))) return fail(QFLEX_ERR_ARG, "null pointer");
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void* scratch = nullptr;
+    const size_t pool_bytes = (size_t(n_batches) * 4 + 15) / 16 * 16;
+    QF_CUDA(cudaMallocAsync(&scratch, pool_bytes + 16, s));
+    int32_t* pool = static_cast<int32_t*>(scratch);
+    int64_t* counts = reinterpret_cast<int64_t*>(static_cast<char*>(scratch) + pool_bytes);
+    int64_t host_counts[2] = {0, 0};
+    cudaError_t e = launch_fidelity_mix(batch_bits, accepted, n_batches, tile, n_tile, n_qubits, fidelity, seed,
+                                        n_samples, pool, source, counts, samples, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_counts, counts, sizeof(host_counts), cudaMemcpyDeviceToHost, s);
+    const cudaError_t ef = cudaFreeAsync(scratch, s);
+    if (e == cudaSuccess) e = ef;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("fidelity sampling: ") + cudaGetErrorString(e));
+    *n_exact = host_counts[0];
+    if (host_counts[0] > host_counts[1])
+      return fail(QFLEX_ERR_ARG, "fidelity sampling needs " + std::to_string(host_counts[0]) +
+                                     " exact samples but only " + std::to_string(host_counts[1]) +
+                                     " batches were accepted; compute more batches");
+    return QFLEX_OK;
+  });
 }
 
 qflex_status qflex_device_status(int device, int32_t* status) {
-  if (!status || device < 0) return fail(QFLEX_ERR_ARG, "bad argument");
-  QF_CUDA(cudaSetDevice(device));
-  QF_CUDA(cudaDeviceSynchronize());
-  int32_t* w = device_status_word(device);
-  if (!w) return fail(QFLEX_ERR_CUDA, "status word allocation failed");
-  int32_t v = 0;
-  QF_CUDA(cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost));
-  QF_CUDA(cudaMemset(w, 0, sizeof(v)));
-  *status = v ? QFLEX_ERR_DEVICE_TIMEOUT : QFLEX_OK;
-  return QFLEX_OK;
+  return guarded([&]() -> qflex_status {
+    if (!status || device < 0) return fail(QFLEX_ERR_ARG, "bad argument");
+    QF_CUDA(cudaSetDevice(device));
+    QF_CUDA(cudaDeviceSynchronize());
+    int32_t* w = device_status_word(device);
+    if (!w) return fail(QFLEX_ERR_CUDA, "status word allocation failed");
+    int32_t v = 0;
+    QF_CUDA(cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost));
+    QF_CUDA(cudaMemset(w, 0, sizeof(v)));
+    *status = v ? QFLEX_ERR_DEVICE_TIMEOUT : QFLEX_OK;
+    return QFLEX_OK;
+  });
 }
 
 }  // extern "C"

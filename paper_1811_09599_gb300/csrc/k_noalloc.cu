@@ -4,6 +4,7 @@
 // in a fixed array compiled into the library instead of a caller workspace,
 // for callers that cannot allocate device memory (see the header).
 #include <mutex>
+#include <stdexcept>
 #include <string>
 
 #include "internal.h"
@@ -94,45 +95,51 @@ cudaError_t planes(const void* src, int64_t rows, int64_t K, int kind, int nspli
 
 extern "C" qflex_status qflex_cgemm_noalloc(int32_t prec, int64_t M, int64_t N, int64_t K, const void* A,
                                             const void* B, void* C, void* stream) {
-  if (prec < QFLEX_FP32_SIMT || prec > QFLEX_FP16X3) return fail(QFLEX_ERR_ARG, "unknown precision");
-  if (M < 0 || N < 0 || K < 0 || (M * N > 0 && (!A || !B || !C))) return fail(QFLEX_ERR_ARG, "bad GEMM arguments");
-  if (M == 0 || N == 0) return QFLEX_OK;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
-  DeviceScratch d;
-  if (qflex_status st = setup(dev, &d)) return st;
-  const bool tc = prec != QFLEX_FP32_SIMT && M >= 128 && K % 8 == 0 && K > 0 && N >= 16;
-  if (!tc) {
-    if (K == 0) e = cudaMemsetAsync(C, 0, size_t(M) * N * 8, s);
-    else if (N <= 32)
-      e = launch_cgemm_thin(M, N, K, static_cast<const float2*>(A), static_cast<const float2*>(B),
-                            static_cast<float2*>(C), s);
-    else
-      e = launch_cgemm_simt(M, N, K, static_cast<const float2*>(A), static_cast<const float2*>(B),
-                            static_cast<float2*>(C), s);
+  try {
+    if (prec < QFLEX_FP32_SIMT || prec > QFLEX_FP16X3) return fail(QFLEX_ERR_ARG, "unknown precision");
+    if (M < 0 || N < 0 || K < 0 || (M * N > 0 && (!A || !B || !C))) return fail(QFLEX_ERR_ARG, "bad GEMM arguments");
+    if (M == 0 || N == 0) return QFLEX_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
+    DeviceScratch d;
+    if (qflex_status st = setup(dev, &d)) return st;
+    const bool tc = prec != QFLEX_FP32_SIMT && M >= 128 && K % 8 == 0 && K > 0 && N >= 16;
+    if (!tc) {
+      if (K == 0) e = cudaMemsetAsync(C, 0, size_t(M) * N * 8, s);
+      else if (N <= 32)
+        e = launch_cgemm_thin(M, N, K, static_cast<const float2*>(A), static_cast<const float2*>(B),
+                              static_cast<float2*>(C), s);
+      else
+        e = launch_cgemm_simt(M, N, K, static_cast<const float2*>(A), static_cast<const float2*>(B),
+                              static_cast<float2*>(C), s);
+      if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
+      return QFLEX_OK;
+    }
+    const int kind = (prec == QFLEX_TF32X3 || prec == QFLEX_TF32_PLAIN) ? 0 : (prec == QFLEX_FP16X3 ? 2 : 1);
+    const int nsplit = (prec == QFLEX_TF32X3 || prec == QFLEX_BF16X3 || prec == QFLEX_FP16X3) ? 2 : 1;
+    const size_t per = size_t(3) * nsplit * (kind == 0 ? 4 : 2);
+    const size_t a_bytes = round256(per * size_t(M) * size_t(K));
+    const size_t b_bytes = round256(per * size_t(N) * size_t(K));
+    if (a_bytes + b_bytes > QFLEX_NOALLOC_SCRATCH_BYTES)
+      return fail(QFLEX_ERR_ARG, "operand planes need " + std::to_string(a_bytes + b_bytes) +
+                                     " bytes, more than the 64 MiB static scratch of qflex_cgemm_noalloc");
+    if (!tc_available()) return fail(QFLEX_ERR_UNSUPPORTED, "tensor-map encoder unavailable");
+    char* pa = static_cast<char*>(d.scratch);
+    char* pb = pa + a_bytes;
+    if ((e = planes(A, M, K, kind, nsplit, pa, s, d.smax)) != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
+    if ((e = planes(B, N, K, kind, nsplit, pb, s, d.smax + 1)) != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
+    TcGemmMaps maps;
+    const int bn = N >= 128 ? 128 : 64;
+    if (!tc_encode_maps(kind, nsplit, bn, pa, M, pb, N, K, &maps)) return fail(QFLEX_ERR_CUDA, "tensor map encoding failed");
+    e = launch_cgemm_tc(kind, nsplit, bn, maps, M, N, K, static_cast<float2*>(C), d.status, s,
+                        kind == 2 ? d.smax : nullptr, kind == 2 ? d.smax + 1 : nullptr);
     if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
     return QFLEX_OK;
+  } catch (const std::exception&) {   // no C++ exception crosses the C ABI
+    return QFLEX_ERR_OOM;
+  } catch (...) {
+    return QFLEX_ERR_UNSUPPORTED;
   }
-  const int kind = (prec == QFLEX_TF32X3 || prec == QFLEX_TF32_PLAIN) ? 0 : (prec == QFLEX_FP16X3 ? 2 : 1);
-  const int nsplit = (prec == QFLEX_TF32X3 || prec == QFLEX_BF16X3 || prec == QFLEX_FP16X3) ? 2 : 1;
-  const size_t per = size_t(3) * nsplit * (kind == 0 ? 4 : 2);
-  const size_t a_bytes = round256(per * size_t(M) * size_t(K));
-  const size_t b_bytes = round256(per * size_t(N) * size_t(K));
-  if (a_bytes + b_bytes > QFLEX_NOALLOC_SCRATCH_BYTES)
-    return fail(QFLEX_ERR_ARG, "operand planes need " + std::to_string(a_bytes + b_bytes) +
-                                   " bytes, more than the 64 MiB static scratch of qflex_cgemm_noalloc");
-  if (!tc_available()) return fail(QFLEX_ERR_UNSUPPORTED, "tensor-map encoder unavailable");
-  char* pa = static_cast<char*>(d.scratch);
-  char* pb = pa + a_bytes;
-  if ((e = planes(A, M, K, kind, nsplit, pa, s, d.smax)) != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
-  if ((e = planes(B, N, K, kind, nsplit, pb, s, d.smax + 1)) != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
-  TcGemmMaps maps;
-  const int bn = N >= 128 ? 128 : 64;
-  if (!tc_encode_maps(kind, nsplit, bn, pa, M, pb, N, K, &maps)) return fail(QFLEX_ERR_CUDA, "tensor map encoding failed");
-  e = launch_cgemm_tc(kind, nsplit, bn, maps, M, N, K, static_cast<float2*>(C), d.status, s,
-                      kind == 2 ? d.smax : nullptr, kind == 2 ? d.smax + 1 : nullptr);
-  if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, cudaGetErrorString(e));
-  return QFLEX_OK;
 }
