@@ -199,8 +199,10 @@ qflex_status qflex_plan_steps(qflex_plan plan, int64_t n_bs, const int64_t* slic
  * passes rank by the excess of their largest tensor over the limit, then by
  * work.  Cuts: starting from `cut_edges` (kept, in order), up to
  * `max_new_cuts` bonds are appended by a beam search (three cut sets per
- * level, each extended by every bond, same ranking) until the largest
- * tensor has at most max_tensor_elems entries; the chosen set gets an
+ * level, same ranking) until the largest tensor has at most
+ * max_tensor_elems entries; a level extends every set by one bond, or by
+ * two bonds whose CZ projector halves share a diagonal stretch of one
+ * qubit (tied bits: see qflex_nonzero_slices); the chosen set gets an
  * ordering search with 4 x trials.  Work counts each step as often as the
  * executor runs it: once per change of the cuts it depends on, over the
  * paths that do not vanish identically (qflex_nonzero_slices).

@@ -22,8 +22,11 @@
 //    stream.  The best trial has the smallest excess of its largest tensor
 //    over the limit, then the least work.
 //  * cuts: beam search.  While the best cut set's ordering exceeds the
-//    limit, every set of the beam is extended by every bond not yet cut and
-//    the kCutBeam best distinct sets (same ranking) carry on.  The chosen set
+//    limit, every set of the beam is extended by every bond not yet cut, and
+//    by every pair of bonds whose CZ projector halves share a diagonal
+//    stretch of one qubit (their bits are tied: the pair adds the paths of
+//    one cut and removes two bonds, which neither does alone), and the
+//    kCutBeam best distinct sets (same ranking) carry on.  The chosen set
 //    then gets an ordering search with four times the trials.
 //  * work model: a step depending on cuts D runs once per change of those
 //    cuts along the executor's path order (ascending slice ids, first cut
@@ -265,31 +268,57 @@ bool search_cuts(const SearchNet& net, std::vector<int> cuts, int max_new, doubl
     std::vector<int> cuts;
     SearchResult r;
   };
+  // moves: one bond, or two bonds whose CZ projector halves share a diagonal
+  // stretch of a qubit (their bits are tied, so cutting both adds the paths
+  // of one cut while removing two bonds)
+  std::vector<std::vector<int>> moves;
+  for (int e = 0; e < int(net.edges.size()); ++e)
+    if (net.bits[size_t(e)] > 0) moves.push_back({e});
+  {
+    std::vector<std::pair<int, int>> pairs;
+    for (const auto& line : net.lines) {
+      std::vector<int> stretch;
+      auto flush = [&]() {
+        std::sort(stretch.begin(), stretch.end());
+        stretch.erase(std::unique(stretch.begin(), stretch.end()), stretch.end());
+        for (size_t i = 0; i < stretch.size(); ++i)
+          for (size_t j = i + 1; j < stretch.size(); ++j) pairs.push_back({stretch[i], stretch[j]});
+        stretch.clear();
+      };
+      for (const ProjEvent& ev : line) {
+        if (ev.edge < 0)
+          flush();
+        else
+          stretch.push_back(ev.edge);
+      }
+      flush();
+    }
+    std::sort(pairs.begin(), pairs.end());
+    pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
+    for (const auto& [a, b] : pairs) moves.push_back({a, b});
+  }
   std::vector<State> beam(1);
   beam[0].cuts = cuts;
   if (!search_greedy_order(net, cuts, &beam[0].r, trials, log2_limit, seed)) return false;
-  for (int added = 0; beam[0].r.log2_max > log2_limit && added < max_new; ++added) {
-    // every state of the beam, extended by every bond not yet cut; the
-    // kCutBeam best distinct cut sets carry on to the next level
+  while (beam[0].r.log2_max > log2_limit) {
+    // every state of the beam, extended by every move that fits the budget;
+    // the kCutBeam best distinct cut sets carry on to the next level
     std::vector<State> next;
+    std::vector<std::vector<int>> keys;
     for (const State& st : beam) {
-      for (int e = 0; e < int(net.edges.size()); ++e) {
-        if (net.bits[size_t(e)] == 0 || std::find(st.cuts.begin(), st.cuts.end(), e) != st.cuts.end()) continue;
+      for (const std::vector<int>& mv : moves) {
+        if (int(st.cuts.size() + mv.size() - cuts.size()) > max_new) continue;
+        bool taken = false;
+        for (int e : mv) taken = taken || std::find(st.cuts.begin(), st.cuts.end(), e) != st.cuts.end();
+        if (taken) continue;
         State c;
         c.cuts = st.cuts;
-        c.cuts.push_back(e);
-        std::vector<int> key_c(c.cuts.begin() + long(cuts.size()), c.cuts.end());
-        std::sort(key_c.begin(), key_c.end());
-        bool dup = false;
-        for (const State& o : next) {
-          std::vector<int> key_o(o.cuts.begin() + long(cuts.size()), o.cuts.end());
-          std::sort(key_o.begin(), key_o.end());
-          if (key_o == key_c) {
-            dup = true;
-            break;
-          }
-        }
-        if (dup || !search_greedy_order(net, c.cuts, &c.r, trials, log2_limit, seed)) continue;
+        c.cuts.insert(c.cuts.end(), mv.begin(), mv.end());
+        std::vector<int> key(c.cuts.begin() + long(cuts.size()), c.cuts.end());
+        std::sort(key.begin(), key.end());
+        if (std::find(keys.begin(), keys.end(), key) != keys.end()) continue;
+        if (!search_greedy_order(net, c.cuts, &c.r, trials, log2_limit, seed)) continue;
+        keys.push_back(std::move(key));
         next.push_back(std::move(c));
       }
     }

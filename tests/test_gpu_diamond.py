@@ -77,16 +77,20 @@ def test_bris70_full_size_path(api):
         assert e < BRIS70_TOL[prec], (prec, errs)
 
 
-def test_bris70_searched_path(api):
-    """The cuts and ordering the automated search finds for the 70-qubit
-    diamond (no cuts given, up to four added, 2^28-entry limit): one path
-    that does not vanish identically against the oracle's contraction of
-    the same path with the same cuts and ordering; a path that vanishes
-    identically gives exact zeros."""
+def test_bris70_tied_cuts_path(api):
+    """Four cuts of the 70-qubit diamond of which two, (56, 62) and
+    (56, 57), have their CZ projector halves in one diagonal stretch of
+    qubit 56 (their bits are tied: 4,096 of the 2^16 paths are nonzero),
+    with the search's ordering for them (2^28-entry limit): one path that
+    does not vanish identically against the oracle's contraction of the same
+    path with the same cuts and ordering; a path that vanishes identically
+    gives exact zeros."""
     from qflex_inputs.problems import Problem
     d = diamond_problem(32, 0)
-    r = api.search_ordering(Problem(d.circuit, [], d.open_tile, None), 1 << 28, 4, trials=8, seed=0)
-    assert r["fits"] and r["n_slices"] == 65536
+    ei = d.circuit.lattice.edge_index
+    assert ei[(56, 62)] == 101 and ei[(56, 57)] == 100
+    r = api.search_ordering(Problem(d.circuit, [101, 100, 11, 22], d.open_tile, None), 1 << 28, 0, trials=8, seed=0)
+    assert r["fits"] and r["n_slices"] == 65536 and r["n_nonzero_slices"] == 4096
     prob = Problem(d.circuit, r["cuts"], d.open_tile, r["ordering"])
     bs = random_bitstrings(prob.n, 1, 78)
     nz = NW.nonzero_slices(prob.circuit, prob.cut_edges)      # paths that do not vanish identically

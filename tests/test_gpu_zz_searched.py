@@ -1,0 +1,57 @@
+"""GPU parity of the configurations the cut search finds when it may cut two
+bonds whose CZ projector bits are tied (Methods, "Cutting indexes": a path
+fixes the cut bonds; tied bits leave most paths identically zero), at the
+bench's sizes: one path that does not vanish identically against the
+oracle's contraction of the same path, a vanishing path against exact
+zeros, and the FP64 norm of the path."""
+import numpy as np
+import pytest
+
+from oracle import network as NW
+from qflex_inputs import c2_problem, diamond_problem, random_bitstrings
+from qflex_inputs.problems import Problem
+from tests.gpu_util import TOL, amp_error
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# the 70-qubit diamond's long chain: bf16x3 gated at 2e-4 (as for its
+# region plan); the 7x7 grid keeps the split-BF16 bound
+CASES = {
+    "grid7x7_d32": (lambda: c2_problem(0), 24, 4, 32, TOL["bf16x3"], 256),
+    "bris70_d32": (lambda: diamond_problem(32, 0), 28, 4, 8, 2e-4, 256),
+}
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1811_09599_gb300 import api
+    api._lib.load(build_if_missing=True)
+    return api
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_searched_tied_cuts_path(api, case):
+    make, log2_limit, max_new, trials, tol, n_nonzero = CASES[case]
+    base = make()
+    r = api.search_ordering(Problem(base.circuit, [], base.open_tile, None), 1 << log2_limit, max_new,
+                            trials=trials, seed=0)
+    assert r["fits"] and r["n_nonzero_slices"] == n_nonzero < r["n_slices"]
+    prob = Problem(base.circuit, r["cuts"], base.open_tile, r["ordering"])
+    nz = NW.nonzero_slices(prob.circuit, prob.cut_edges)
+    assert len(nz) == n_nonzero
+    s = nz[int(np.random.default_rng(99).integers(len(nz)))]
+    bs = random_bitstrings(prob.n, 1, 80)
+    ref = NW.slice_amplitudes(prob, bs[0], s)
+    plan = api.Plan(prob, "bf16x3", device=0)
+    assert list(plan.nonzero_slices()) == nz
+    b = torch.from_numpy(bs).cuda()
+    got = plan.amplitudes(b, None, [s])
+    plan.sync()
+    nrm = api.norm(got).item()
+    assert abs(nrm - float(np.sum(np.abs(ref) ** 2))) < 1e-3 * nrm
+    # a kept path carries 1/len(nz) of the norm: the floor of the relative error
+    assert amp_error(got.cpu().numpy(), ref, prob.n, 1.0 / len(nz)) < tol
+    z = min(set(range(int(r["n_slices"]))) - set(nz))
+    assert torch.count_nonzero(plan.amplitudes(b, None, [z])).item() == 0
+    plan.close()

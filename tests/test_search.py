@@ -5,14 +5,17 @@ indexes"; SI A).  The search must (a) return valid orderings that the
 planner accepts, (b) estimate the work exactly as the executor counts it
 (steps rerun only when a cut they depend on changes), (c) reach the exact
 optimum of its move set on networks small enough for brute force, and
-(d) find, for the 7x7 depth 1+32+1 grid, a configuration of the paper's
-size class: two cuts (256 paths) and tensors of at most 2^24 entries.
+(d) find, for the 7x7 depth 1+32+1 grid and the 70-qubit diamond,
+configurations of the paper's size class (256 and at most 2^16 nonzero
+paths; tensors of at most 2^24 and 2^28 entries) with less work than the
+region plans.
 """
 import functools
 import math
 
 import pytest
 
+from oracle import network as NW
 from qflex_inputs import c2_problem, diamond_problem, grid_lattice, grid_problem, random_circuit
 from qflex_inputs.circuits import two_qubit_counts
 from qflex_inputs.problems import Problem
@@ -106,36 +109,49 @@ def test_search_work_model_matches_planner(api, rotations):
     assert (r["n_nonzero_slices"] < r["n_slices"]) == rotations
 
 
-def test_search_7x7_finds_two_cut_plan(api):
-    """7x7, 1+32+1, no cuts given, limit 2^24 entries: two cuts (256 paths)
-    suffice, as in the paper's hand plan, at no more than 1.15x its work."""
+def test_search_7x7_finds_tied_cut_plan(api):
+    """7x7, 1+32+1, no cuts given, limit 2^24 entries, up to four new cuts:
+    the search keeps the paper's 256 paths and tensor limit but reaches them
+    with three cuts, two of whose bonds share a diagonal stretch of one
+    qubit's projector halves (their bits are tied, so 256 of the 4,096 paths
+    are nonzero), at under 0.3x the hand plan's work (both counted by the
+    planner's cost replay).  The region ordering with the paper's two cuts
+    is what the search finds when no new cut is allowed, within 1.15x."""
     from paper_1811_09599_gb300.api import Plan
     p = c2_problem(0)
     r = api.search_ordering(Problem(p.circuit, [], p.open_tile, None), 1 << 24, 4, trials=32, seed=0)
-    assert r["fits"] and len(r["cuts"]) == 2 and r["n_slices"] == 256
-    assert r["log2_max_tensor"] <= 24
+    assert r["fits"] and r["n_nonzero_slices"] == 256 and r["log2_max_tensor"] <= 24
+    assert len(r["cuts"]) == 3 and r["n_slices"] == 4096
     hand = Plan(p, "bf16x3", device=-1).cost(1)["cmacs"]
     found = Plan(Problem(p.circuit, r["cuts"], p.open_tile, r["ordering"]), "bf16x3", device=-1)
     assert found.info()["max_tensor_elems"] <= 1 << 24
-    assert found.cost(1)["cmacs"] <= 1.15 * hand
+    assert found.cost(1)["cmacs"] == pytest.approx(r["cmacs_per_bitstring"], rel=1e-12)
+    assert found.cost(1)["cmacs"] <= 0.3 * hand
+    # the two tied bonds: projector halves of one qubit with no non-diagonal gate between
+    runs, _ = NW.projector_runs(p.circuit, r["cuts"])
+    assert any(len({e for e, _ in m}) == 2 for m in runs)
+    # the paper's cuts, ordering searched
+    q = api.search_ordering(Problem(p.circuit, p.cut_edges, p.open_tile, None), 1 << 24, 0, trials=32, seed=0)
+    assert q["fits"] and q["n_slices"] == 256 and q["cmacs_per_bitstring"] <= 1.15 * hand
     # deterministic for a given seed
     again = api.search_ordering(Problem(p.circuit, [], p.open_tile, None), 1 << 24, 4, trials=32, seed=0)
     assert again["cuts"] == r["cuts"] and again["ordering"] == r["ordering"]
 
 
 def test_search_bristlecone_70(api):
-    """Bris-70, 1+32+1, limit 2^28 entries: four cuts (2^16 paths) suffice,
-    the configuration the paper states for this lattice, with no more work
-    than the hand plan's cuts and ordering."""
+    """Bris-70, 1+32+1, limit 2^28 entries: four cuts (2^16 paths), the
+    configuration the paper states for this lattice; the search picks two
+    pairs of bonds with tied projector bits (256 nonzero paths) and needs
+    under 1% of the region plan's work for all paths."""
     from paper_1811_09599_gb300.api import Plan
     d = diamond_problem(32, 0)
     r = api.search_ordering(Problem(d.circuit, [], d.open_tile, None), 1 << 28, 5, trials=8, seed=0)
     assert r["fits"] and len(r["cuts"]) == 4 and r["n_slices"] == 65536
-    assert r["n_nonzero_slices"] <= r["n_slices"]
+    assert r["n_nonzero_slices"] == 256            # two pairs of tied bonds
     hand = Plan(d, "bf16x3", device=-1).cost(1)["cmacs"]
     found = Plan(Problem(d.circuit, r["cuts"], d.open_tile, r["ordering"]), "bf16x3", device=-1)
     assert found.info()["max_tensor_elems"] <= 1 << 28
-    assert found.cost(1)["cmacs"] <= hand
+    assert found.cost(1)["cmacs"] <= 0.01 * hand
 
 
 def test_search_limits_and_defaults(api):
