@@ -215,7 +215,8 @@ def _constrained_problems():
     corr = Problem(circ, [ei[(4, 5)], ei[(4, 7)], ei[(1, 2)]], [8], None)
     d = diamond_problem(32, 0)
     bris = Problem(d.circuit, [101, 100, 11, 22], d.open_tile, None)   # two bonds of qubit 56
-    return [rot, corr, bris, c2_problem(0)]
+    isw = grid_problem(4, 5, 16, 8, r0=2, c0=2, cuts=True, tile_rows=2, tile_cols=2, two_qubit="ISWAP")
+    return [rot, corr, bris, c2_problem(0), isw]
 
 
 def test_nonzero_slices_match_oracle(Plan):
