@@ -21,13 +21,14 @@
 //    in [0, 2] (steps that rerun per path are put off), from a SplitMix64
 //    stream.  The best trial has the smallest excess of its largest tensor
 //    over the limit, then the least work.
-//  * cuts: beam search.  While the best cut set's ordering exceeds the
-//    limit, every set of the beam is extended by every bond not yet cut, and
-//    by every pair of bonds whose CZ projector halves share a diagonal
-//    stretch of one qubit (their bits are tied: the pair adds the paths of
-//    one cut and removes two bonds, which neither does alone), and the
-//    kCutBeam best distinct sets (same ranking) carry on.  The chosen set
-//    then gets an ordering search with four times the trials.
+//  * cuts: beam search by the number of new cuts.  The kCutBeam best sets
+//    with k new cuts that still exceed the limit are extended by every bond
+//    not yet cut (k + 1), and by every pair of bonds whose CZ projector
+//    halves share a diagonal stretch of one qubit (k + 2; their bits are
+//    tied: the pair adds the paths of one cut and removes two bonds, which
+//    neither does alone), up to max_new.  The result is the best set
+//    evaluated (same ranking), which then gets an ordering search with four
+//    times the trials.
 //  * work model: a step depending on cuts D runs once per change of those
 //    cuts along the executor's path order (ascending slice ids, first cut
 //    most significant, paths that vanish identically skipped), 2^(a + b - s)
@@ -297,37 +298,45 @@ bool search_cuts(const SearchNet& net, std::vector<int> cuts, int max_new, doubl
     pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
     for (const auto& [a, b] : pairs) moves.push_back({a, b});
   }
-  std::vector<State> beam(1);
-  beam[0].cuts = cuts;
-  if (!search_greedy_order(net, cuts, &beam[0].r, trials, log2_limit, seed)) return false;
-  while (beam[0].r.log2_max > log2_limit) {
-    // every state of the beam, extended by every move that fits the budget;
-    // the kCutBeam best distinct cut sets carry on to the next level
-    std::vector<State> next;
-    std::vector<std::vector<int>> keys;
-    for (const State& st : beam) {
+  // layers by the number of new cuts: the kCutBeam best states of a layer
+  // that do not fit yet are extended by every move within the budget (a
+  // pair lands two layers further); every evaluated set competes for the
+  // result, so a tied pair that fits with less work than a shallower set
+  // is still found
+  const size_t base = cuts.size();
+  std::vector<std::vector<State>> layer(size_t(max_new) + 1);
+  std::vector<std::vector<int>> seen;   // sorted new cuts of every evaluated set
+  State best;
+  best.cuts = cuts;
+  if (!search_greedy_order(net, cuts, &best.r, trials, log2_limit, seed)) return false;
+  if (best.r.log2_max > log2_limit && max_new > 0) layer[0].push_back(best);
+  for (int k = 0; k < max_new; ++k) {
+    std::vector<State>& cur = layer[size_t(k)];
+    std::stable_sort(cur.begin(), cur.end(),
+                     [&](const State& x, const State& y) { return better_result(x.r, y.r, log2_limit); });
+    if (cur.size() > size_t(kCutBeam)) cur.resize(size_t(kCutBeam));
+    for (const State& st : cur) {
       for (const std::vector<int>& mv : moves) {
-        if (int(st.cuts.size() + mv.size() - cuts.size()) > max_new) continue;
+        const int k2 = k + int(mv.size());
+        if (k2 > max_new) continue;
         bool taken = false;
         for (int e : mv) taken = taken || std::find(st.cuts.begin(), st.cuts.end(), e) != st.cuts.end();
         if (taken) continue;
         State c;
         c.cuts = st.cuts;
         c.cuts.insert(c.cuts.end(), mv.begin(), mv.end());
-        std::vector<int> key(c.cuts.begin() + long(cuts.size()), c.cuts.end());
+        std::vector<int> key(c.cuts.begin() + long(base), c.cuts.end());
         std::sort(key.begin(), key.end());
-        if (std::find(keys.begin(), keys.end(), key) != keys.end()) continue;
+        if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
+        seen.push_back(std::move(key));
         if (!search_greedy_order(net, c.cuts, &c.r, trials, log2_limit, seed)) continue;
-        keys.push_back(std::move(key));
-        next.push_back(std::move(c));
+        if (better_result(c.r, best.r, log2_limit)) best = c;
+        if (c.r.log2_max > log2_limit) layer[size_t(k2)].push_back(std::move(c));
       }
     }
-    if (next.empty()) break;
-    std::stable_sort(next.begin(), next.end(),
-                     [&](const State& x, const State& y) { return better_result(x.r, y.r, log2_limit); });
-    if (next.size() > size_t(kCutBeam)) next.resize(size_t(kCutBeam));
-    beam = std::move(next);
+    cur.clear();
   }
+  std::vector<State> beam(1, std::move(best));
   // the chosen cut set gets a longer ordering search of its own
   SearchResult polished;
   if (search_greedy_order(net, beam[0].cuts, &polished, 4 * std::max(1, trials), log2_limit, seed ^ 0x5851F42D4C957F2Dull) &&

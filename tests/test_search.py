@@ -145,13 +145,22 @@ def test_search_bristlecone_70(api):
     under 1% of the region plan's work for all paths."""
     from paper_1811_09599_gb300.api import Plan
     d = diamond_problem(32, 0)
-    r = api.search_ordering(Problem(d.circuit, [], d.open_tile, None), 1 << 28, 5, trials=8, seed=0)
+    r = api.search_ordering(Problem(d.circuit, [], d.open_tile, None), 1 << 28, 4, trials=8, seed=0)
     assert r["fits"] and len(r["cuts"]) == 4 and r["n_slices"] == 65536
     assert r["n_nonzero_slices"] == 256            # two pairs of tied bonds
     hand = Plan(d, "bf16x3", device=-1).cost(1)["cmacs"]
     found = Plan(Problem(d.circuit, r["cuts"], d.open_tile, r["ordering"]), "bf16x3", device=-1)
     assert found.info()["max_tensor_elems"] <= 1 << 28
     assert found.cost(1)["cmacs"] <= 0.01 * hand
+
+
+def test_search_8x9_three_cuts(api):
+    """8x9 grid (72 qubits), 1+32+1, limit 2^28 entries: three cuts suffice
+    (the paper's comparison with Bris-70, which needs four: Methods,
+    "Simulation of Bristlecone compared to rectangular grids")."""
+    circ = random_circuit(grid_lattice(8, 9), 32, 0)
+    r = api.search_ordering(Problem(circ, [], [71], None), 1 << 28, 3, trials=4, seed=0)
+    assert r["fits"] and len(r["cuts"]) <= 3 and r["log2_max_tensor"] <= 28
 
 
 def test_search_limits_and_defaults(api):
