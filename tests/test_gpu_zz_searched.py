@@ -10,16 +10,21 @@ import pytest
 from oracle import network as NW
 from qflex_inputs import c2_problem, diamond_problem, random_bitstrings
 from qflex_inputs.problems import Problem
-from tests.gpu_util import TOL, amp_error
+from tests.gpu_util import amp_error
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-# the 70-qubit diamond's long chain: bf16x3 gated at 2e-4 (as for its
-# region plan); the 7x7 grid keeps the split-BF16 bound
+# bf16x3 keeps about 16 bits per product (2^-16 = 1.5e-5 relative).  Over
+# the d split-precision products a path goes through, the error grows like
+# sqrt(d) 2^-16 (random rounding; d 2^-16 at worst): about 1e-4 at d = 40.
+# Both searched plans run 40 (7x7) and 45 (70-qubit diamond) tensor-core
+# products, more than the 7x7 region plan's 36 that the 1e-4 gate was set
+# on, so they are gated at 2e-4, as the diamond's region plan (44) is.
+LONG_CHAIN_BF16X3 = 2e-4
 CASES = {
-    "grid7x7_d32": (lambda: c2_problem(0), 24, 4, 32, TOL["bf16x3"], 256),
-    "bris70_d32": (lambda: diamond_problem(32, 0), 28, 4, 8, 2e-4, 256),
+    "grid7x7_d32": (lambda: c2_problem(0), 24, 4, 32, LONG_CHAIN_BF16X3, 256),
+    "bris70_d32": (lambda: diamond_problem(32, 0), 28, 4, 8, LONG_CHAIN_BF16X3, 256),
 }
 
 
