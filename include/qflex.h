@@ -203,7 +203,8 @@ qflex_status qflex_plan_steps(qflex_plan plan, int64_t n_bs, const int64_t* slic
  * max_tensor_elems entries; a level extends every set by one bond, or by
  * two bonds whose CZ projector halves share a diagonal stretch of one
  * qubit (tied bits: see qflex_nonzero_slices); the chosen set gets an
- * ordering search with 4 x trials.  Work counts each step as often as the
+ * ordering search with 4 x trials.  Candidate sets are searched on the
+ * host's cores (std::thread); the result does not depend on their number.  Work counts each step as often as the
  * executor runs it: once per change of the cuts it depends on, over the
  * paths that do not vanish identically (qflex_nonzero_slices).
  * circuit/open_tile/cut_edges: host, as in qflex_problem.  cuts_out: host,

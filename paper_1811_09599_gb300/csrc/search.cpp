@@ -38,8 +38,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <atomic>
 #include <iterator>
 #include <map>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -315,10 +317,11 @@ bool search_cuts(const SearchNet& net, std::vector<int> cuts, int max_new, doubl
     std::stable_sort(cur.begin(), cur.end(),
                      [&](const State& x, const State& y) { return better_result(x.r, y.r, log2_limit); });
     if (cur.size() > size_t(kCutBeam)) cur.resize(size_t(kCutBeam));
+    // candidate sets of this layer, in a fixed order
+    std::vector<State> cand;
     for (const State& st : cur) {
       for (const std::vector<int>& mv : moves) {
-        const int k2 = k + int(mv.size());
-        if (k2 > max_new) continue;
+        if (k + int(mv.size()) > max_new) continue;
         bool taken = false;
         for (int e : mv) taken = taken || std::find(st.cuts.begin(), st.cuts.end(), e) != st.cuts.end();
         if (taken) continue;
@@ -329,10 +332,35 @@ bool search_cuts(const SearchNet& net, std::vector<int> cuts, int max_new, doubl
         std::sort(key.begin(), key.end());
         if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
         seen.push_back(std::move(key));
-        if (!search_greedy_order(net, c.cuts, &c.r, trials, log2_limit, seed)) continue;
-        if (better_result(c.r, best.r, log2_limit)) best = c;
-        if (c.r.log2_max > log2_limit) layer[size_t(k2)].push_back(std::move(c));
+        cand.push_back(std::move(c));
       }
+    }
+    // ordering searches of the candidates on the host cores (independent:
+    // each builds its own work model); results are then taken in the
+    // fixed order, so the outcome does not depend on the threads
+    std::vector<char> ok(cand.size(), 0);
+    std::atomic<size_t> next_i{0};
+    auto worker = [&]() {
+      for (size_t i = next_i++; i < cand.size(); i = next_i++) {
+        try {
+          ok[i] = search_greedy_order(net, cand[i].cuts, &cand[i].r, trials, log2_limit, seed) ? 1 : 0;
+        } catch (...) {
+          ok[i] = 0;
+        }
+      }
+    };
+    const size_t n_threads =
+        std::min<size_t>(cand.size(), std::max<unsigned>(1, std::min<unsigned>(32, std::thread::hardware_concurrency())));
+    std::vector<std::thread> pool;
+    for (size_t t = 1; t < n_threads; ++t) pool.emplace_back(worker);
+    worker();
+    for (std::thread& th : pool) th.join();
+    for (size_t i = 0; i < cand.size(); ++i) {
+      if (!ok[i]) continue;
+      State& c = cand[i];
+      const size_t k2 = c.cuts.size() - base;
+      if (better_result(c.r, best.r, log2_limit)) best = c;
+      if (c.r.log2_max > log2_limit) layer[k2].push_back(std::move(c));
     }
     cur.clear();
   }
