@@ -154,6 +154,23 @@ def test_search_bristlecone_70(api):
     assert found.cost(1)["cmacs"] <= 0.01 * hand
 
 
+def test_searched_tied_cuts_sum_to_the_state_vector(api):
+    """4x5, 1+24+1, limit 2^12: the search cuts tied pairs of bonds, most
+    paths vanish identically, and the oracle's sum over the others, with
+    the searched cuts and ordering, is the state-vector amplitude."""
+    from oracle import statevector as SV
+    from qflex_inputs import random_bitstrings
+    p = grid_problem(4, 5, 24, 7, r0=2, c0=2, cuts=False, tile_rows=2, tile_cols=2)
+    r = api.search_ordering(Problem(p.circuit, [], p.open_tile, None), 1 << 12, 4, trials=16)
+    assert r["fits"] and r["n_nonzero_slices"] < r["n_slices"]
+    prob = Problem(p.circuit, r["cuts"], p.open_tile, r["ordering"])
+    nz = NW.nonzero_slices(prob.circuit, prob.cut_edges)
+    assert len(nz) == r["n_nonzero_slices"]
+    bs = random_bitstrings(p.n, 1, 5)
+    got = NW.amplitudes(prob, bs, nz)
+    assert abs(got - SV.amplitudes(p.circuit, bs, p.open_tile)).max() < 1e-14
+
+
 def test_search_8x9_three_cuts(api):
     """8x9 grid (72 qubits), 1+32+1, limit 2^28 entries: three cuts suffice
     (the paper's comparison with Bris-70, which needs four: Methods,
