@@ -13,6 +13,9 @@ a warm launch) and prints "<case> ok".  Cases:
   path    the 7x7 depth 1+32+1 workload for one bitstring and one right-cut
           value (slices 0..15, 1/16 of one bitstring with the same mix of
           launches as a full bench step)
+  searched  the same workload planned by the cut search (tied cut pairs;
+          2^24-entry limit, up to four new cuts, 32 passes): one bitstring,
+          the first 16 nonzero paths
 """
 from __future__ import annotations
 
@@ -51,6 +54,17 @@ def main(case: str) -> None:
         bits = torch.from_numpy(random_bitstrings(prob.n, 1, 1000)).cuda()
         for _ in range(3):
             plan.amplitudes(bits, None, list(range(16)))
+        plan.sync()
+    elif case == "searched":
+        from qflex_inputs import c2_problem, random_bitstrings
+        from qflex_inputs.problems import Problem
+        base = c2_problem(0)
+        r = api.search_ordering(Problem(base.circuit, [], base.open_tile, None), 1 << 24, 4, trials=32, seed=0)
+        plan = api.Plan(Problem(base.circuit, r["cuts"], base.open_tile, r["ordering"]), "bf16x3", device=0)
+        bits = torch.from_numpy(random_bitstrings(base.n, 1, 1000)).cuda()
+        paths = list(plan.nonzero_slices()[:16])
+        for _ in range(3):
+            plan.amplitudes(bits, None, paths)
         plan.sync()
     else:
         raise SystemExit(f"unknown case {case}")
