@@ -402,6 +402,15 @@ qflex_status qflex_fidelity_samples(const uint8_t* batch_bits, const int32_t* ac
  * used by the standalone kernels.  *status = QFLEX_OK or QFLEX_ERR_DEVICE_TIMEOUT. */
 qflex_status qflex_device_status(int device, int32_t* status);
 
+/* Self-test of failure detection (no counterpart in the paper): one CTA
+ * waits, by the bounded-wait pattern of the tensor-core GEMM, on an mbarrier
+ * that no one arrives at; after limit_ns (1e3 .. 1e9 ns) the wait gives up,
+ * sets the timeout bit of the library's device status word and the kernel
+ * returns.  Synchronizes `device`, clears the status word before and after;
+ * *status = QFLEX_ERR_DEVICE_TIMEOUT when the wait ran out (the expected
+ * outcome), QFLEX_OK otherwise.  The context stays usable. */
+qflex_status qflex_device_selftest_timeout(int device, uint64_t limit_ns, int32_t* status);
+
 /* ---------------- allocation-free complex GEMM ----------------
  * The paper has no counterpart to this call; it exists for callers that cannot
  * allocate device memory.  qflex_cgemm needs a workspace, and obtaining one

@@ -122,6 +122,7 @@ SIGNATURES = [
                                         C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.c_uint64,
                                         C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_void_p]),
     ("qflex_device_status", C.c_int, [C.c_int, C.POINTER(C.c_int32)]),
+    ("qflex_device_selftest_timeout", C.c_int, [C.c_int, C.c_uint64, C.POINTER(C.c_int32)]),
     ("qflex_cgemm_noalloc", C.c_int, [C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p]),
 ]

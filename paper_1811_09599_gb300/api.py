@@ -353,3 +353,13 @@ def device_status(device: int = 0) -> int:
     v = C.c_int32()
     check(lib.qflex_device_status(device, C.byref(v)))
     return v.value
+
+
+def device_selftest_timeout(device: int = 0, limit_ns: int = 10_000_000) -> int:
+    """qflex_device_selftest_timeout: a bounded device wait that nothing
+    completes runs out after limit_ns; returns the status it reports
+    (QFLEX_ERR_DEVICE_TIMEOUT = 6 expected)."""
+    lib = _lib.load()
+    v = C.c_int32()
+    check(lib.qflex_device_selftest_timeout(int(device), C.c_uint64(limit_ns), C.byref(v)))
+    return v.value

@@ -2033,6 +2033,25 @@ qflex_status qflex_device_status(int device, int32_t* status) {
   });
 }
 
+qflex_status qflex_device_selftest_timeout(int device, uint64_t limit_ns, int32_t* status) {
+  return guarded([&]() -> qflex_status {
+    if (!status || device < 0 || limit_ns < 1000 || limit_ns > 1000000000ull)
+      return fail(QFLEX_ERR_ARG, "bad argument (limit_ns must be in [1e3, 1e9])");
+    QF_CUDA(cudaSetDevice(device));
+    int32_t* w = device_status_word(device);
+    if (!w) return fail(QFLEX_ERR_CUDA, "status word allocation failed");
+    QF_CUDA(cudaDeviceSynchronize());
+    QF_CUDA(cudaMemset(w, 0, sizeof(int32_t)));
+    QF_CUDA(launch_wait_selftest(limit_ns, w, nullptr));
+    QF_CUDA(cudaDeviceSynchronize());
+    int32_t v = 0;
+    QF_CUDA(cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost));
+    QF_CUDA(cudaMemset(w, 0, sizeof(v)));
+    *status = (v & kDevTimeout) ? QFLEX_ERR_DEVICE_TIMEOUT : QFLEX_OK;
+    return QFLEX_OK;
+  });
+}
+
 }  // extern "C"
 
 void qflex::set_last_error(const char* msg) { g_err = msg; }

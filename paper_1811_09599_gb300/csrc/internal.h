@@ -338,6 +338,9 @@ bool tc_available();   // driver entry point for tensor-map encoding found
 cudaError_t launch_slicesum(const float2* src, const int64_t* strides, int n_open,
                             double* amps, cudaStream_t s);
 cudaError_t launch_norm(const double* amps, int64_t n, double* out, cudaStream_t s);
+// One CTA whose bounded wait on an mbarrier that no one arrives at runs out
+// after limit_ns and sets kDevTimeout in *status (failure-detection test).
+cudaError_t launch_wait_selftest(uint64_t limit_ns, int32_t* status, cudaStream_t s);
 // Frugal rejection sampling, one accepted tile index (or -1) per batch;
 // scale = N / M.  n_c <= 4096.
 cudaError_t launch_frugal(const double* amps, int64_t n_batches, int n_c, double scale, uint64_t seed,

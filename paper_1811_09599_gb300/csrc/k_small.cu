@@ -216,7 +216,48 @@ __global__ void k_absmax(const float2* __restrict__ in, int64_t n, unsigned* __r
   if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, __float_as_uint(m));
 }
 
+// Self-test of failure detection: thread 0 waits, by the same bounded
+// pattern as the tensor-core GEMM's mbarrier waits (mbarrier.try_wait in a
+// loop, %globaltimer checked every 256 tries), on an mbarrier that no one
+// arrives at.  After limit_ns the wait gives up, sets kDevTimeout in the
+// status word and the kernel returns; nothing faults and the context stays
+// usable.
+__global__ void k_wait_selftest(uint64_t limit_ns, int32_t* status) {
+  __shared__ alignas(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  const uint32_t b = static_cast<uint32_t>(__cvta_generic_to_shared(&bar));
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(1u) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(b), "r"(0u)
+        : "memory");
+    if (done) return;   // not reached: phase 0 never completes
+    if ((it & 255u) == 255u) {
+      uint64_t now;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+      if (t0 == 0) {
+        t0 = now;
+      } else if (now - t0 > limit_ns) {
+        atomicOr(status, kDevTimeout);
+        return;
+      }
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(uint64_t limit_ns, int32_t* status, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(limit_ns, status);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_absmax(const float2* in, int64_t n, unsigned* smax, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(smax, 0, sizeof(unsigned), s);

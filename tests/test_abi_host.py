@@ -254,3 +254,14 @@ def test_vanishing_paths_are_skipped_in_the_schedule(Plan):
     c0 = p.cost(1, zero[:5])
     assert c0["cmacs"] == 0 and c0["steps_executed"] == 0
     assert p.cost(1, sorted(nz[:3] + zero[:3])) == p.cost(1, nz[:3])
+
+
+def test_selftest_timeout_argument_checks(lib):
+    """qflex_device_selftest_timeout rejects a bad device or limit before
+    touching a GPU."""
+    import ctypes as C
+    v = C.c_int32()
+    assert lib.qflex_device_selftest_timeout(-1, C.c_uint64(10_000_000), C.byref(v)) == 1
+    assert lib.qflex_device_selftest_timeout(0, C.c_uint64(10), C.byref(v)) == 1
+    assert lib.qflex_device_selftest_timeout(0, C.c_uint64(10 ** 10), C.byref(v)) == 1
+    assert lib.qflex_device_selftest_timeout(0, C.c_uint64(10_000_000), None) == 1
