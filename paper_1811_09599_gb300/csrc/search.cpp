@@ -352,7 +352,14 @@ bool search_cuts(const SearchNet& net, std::vector<int> cuts, int max_new, doubl
     const size_t n_threads =
         std::min<size_t>(cand.size(), std::max<unsigned>(1, std::min<unsigned>(32, std::thread::hardware_concurrency())));
     std::vector<std::thread> pool;
-    for (size_t t = 1; t < n_threads; ++t) pool.emplace_back(worker);
+    pool.reserve(n_threads);
+    for (size_t t = 1; t < n_threads; ++t) {
+      try {
+        pool.emplace_back(worker);
+      } catch (...) {   // no more threads: the ones started (and this one) finish the work
+        break;
+      }
+    }
     worker();
     for (std::thread& th : pool) th.join();
     for (size_t i = 0; i < cand.size(); ++i) {
