@@ -38,6 +38,12 @@ def Plan():
     return Plan
 
 
+@pytest.fixture
+def api_mod():
+    from paper_1811_09599_gb300 import api
+    return api
+
+
 def test_host_plan_7x7_d40_sizes(Plan):
     """SI A: 7x7x(1+40+1) with two cuts has 2^(2x5) paths and regions of 2^(6x5)."""
     p = Plan(c4_problem(0), "bf16x3", device=-1)
@@ -265,3 +271,60 @@ def test_selftest_timeout_argument_checks(lib):
     assert lib.qflex_device_selftest_timeout(0, C.c_uint64(10), C.byref(v)) == 1
     assert lib.qflex_device_selftest_timeout(0, C.c_uint64(10 ** 10), C.byref(v)) == 1
     assert lib.qflex_device_selftest_timeout(0, C.c_uint64(10_000_000), None) == 1
+
+
+def _plain_work(prob):
+    """Complex MACs of one bitstring, counted from the definition: each
+    ordering step multiplies 2^(a + b - s) (a, b: index bits of the two
+    groups' tensors, s: bits they share) and runs once per change of the
+    values of the cuts touching its group along the ascending list of
+    paths that do not vanish identically (the oracle's list)."""
+    circ = prob.circuit
+    K = NW.bond_exponents(circ)
+    cut = list(prob.cut_edges)
+    nz = NW.nonzero_slices(circ, cut)
+    vals = [NW.slice_values(circ, cut, s) for s in nz]
+
+    def bits_of(group):
+        legs = {}
+        for e, (a, b) in enumerate(circ.edges):
+            if K[e] and e not in cut and ((a in group) != (b in group)):
+                legs[("e", e)] = int(K[e])
+        for q in group:
+            if q in prob.open_tile:
+                legs[("o", q)] = 1
+        return legs
+
+    def runs(group):
+        dep = [e for e in cut if circ.edges[e][0] in group or circ.edges[e][1] in group]
+        count, prev = 0, None
+        for v in vals:
+            key = tuple(v[e] for e in dep)
+            if key != prev:
+                count += 1
+            prev = key
+        return count
+
+    groups = {q: {q} for q in range(circ.n)}
+    total = 0
+    for dst, src in prob.ordering:
+        la, lb = bits_of(groups[dst]), bits_of(groups[src])
+        s = sum(v for k, v in la.items() if k in lb)
+        merged = groups[dst] | groups.pop(src)
+        total += runs(merged) * 2 ** (sum(la.values()) + sum(lb.values()) - s)
+        groups[dst] = merged
+    return total
+
+
+def test_cost_replay_matches_the_plain_count(Plan, api_mod):
+    """qflex_plan_cost's complex MACs (bench.py's TFLOP/s numerator) equal
+    the count from the definition, with reuse across paths and vanishing
+    paths skipped: the 7x7 region plan, a rotation circuit whose cuts leave
+    vanishing paths, and a searched plan with tied cut pairs."""
+    rot = grid_problem(4, 5, 24, 3, r0=2, c0=2, cuts=True, tile_rows=2, tile_cols=2, rotations=True)
+    small = grid_problem(4, 5, 24, 7, r0=2, c0=2, cuts=False, tile_rows=2, tile_cols=2)
+    r = api_mod.search_ordering(Problem(small.circuit, [], small.open_tile, None), 1 << 12, 4, trials=16)
+    searched = Problem(small.circuit, r["cuts"], small.open_tile, r["ordering"])
+    for prob in (c2_problem(0), rot, searched):
+        p = Plan(prob, "bf16x3", device=-1)
+        assert p.cost(1)["cmacs"] == _plain_work(prob)
