@@ -143,11 +143,12 @@ class Plan:
         """Fraction-f path choice; nonzero=True chooses among the paths that
         do not vanish identically (qflex_select_nonzero_slices)."""
         P = self.info()["n_nonzero_slices"] if nonzero else self.n_slices
-        out = np.zeros(P, dtype=np.int64)
+        cap = int(min(P, max(1, int(np.floor(float(fidelity) * P + 0.5)))))   # n_f of the rule
+        out = np.zeros(max(cap, 1), dtype=np.int64)
         n = C.c_int64()
         fn = self.lib.qflex_select_nonzero_slices if nonzero else self.lib.qflex_select_slices
-        check(fn(self.handle, float(fidelity), C.c_uint64(seed), out.ctypes.data_as(C.POINTER(C.c_int64)), P,
-                 C.byref(n)))
+        check(fn(self.handle, float(fidelity), C.c_uint64(seed), out.ctypes.data_as(C.POINTER(C.c_int64)),
+                 out.size, C.byref(n)))
         return out[: n.value].copy()
 
     def nonzero_slices(self) -> np.ndarray:
