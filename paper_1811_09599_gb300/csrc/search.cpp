@@ -371,15 +371,15 @@ bool search_cuts(const SearchNet& net, std::vector<int> cuts, int max_new, doubl
     }
     cur.clear();
   }
-  std::vector<State> beam(1, std::move(best));
   // the chosen cut set gets a longer ordering search of its own
   SearchResult polished;
-  if (search_greedy_order(net, beam[0].cuts, &polished, 4 * std::max(1, trials), log2_limit, seed ^ 0x5851F42D4C957F2Dull) &&
-      better_result(polished, beam[0].r, log2_limit))
-    beam[0].r = std::move(polished);
-  const bool fits = beam[0].r.log2_max <= log2_limit;
-  *cuts_out = beam[0].cuts;
-  *out = std::move(beam[0].r);
+  if (search_greedy_order(net, best.cuts, &polished, 4 * std::max(1, trials), log2_limit,
+                          seed ^ 0x5851F42D4C957F2Dull) &&
+      better_result(polished, best.r, log2_limit))
+    best.r = std::move(polished);
+  const bool fits = best.r.log2_max <= log2_limit;
+  *cuts_out = best.cuts;
+  *out = std::move(best.r);
   return fits;
 }
 
