@@ -32,7 +32,9 @@ def nvcc() -> str:
 
 
 def _flags():
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3",
+    # host code: no FMA contraction, so the cut search's floating-point keys
+    # (and its result) are the same on x86-64 and aarch64 hosts
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3,-ffp-contract=off",
                    "-I" + INCLUDE, "-I" + CSRC, "--expt-relaxed-constexpr"]
 
 

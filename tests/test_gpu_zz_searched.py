@@ -23,8 +23,8 @@ pytestmark = pytest.mark.gpu
 # on, so they are gated at 2e-4, as the diamond's region plan (44) is.
 LONG_CHAIN_BF16X3 = 2e-4
 CASES = {
-    "grid7x7_d32": (lambda: c2_problem(0), 24, 4, 32, LONG_CHAIN_BF16X3, 256),
-    "bris70_d32": (lambda: diamond_problem(32, 0), 28, 4, 8, LONG_CHAIN_BF16X3, 256),
+    "grid7x7_d32": (lambda: c2_problem(0), 24, 4, 32, LONG_CHAIN_BF16X3, 1024),
+    "bris70_d32": (lambda: diamond_problem(32, 0), 28, 4, 8, LONG_CHAIN_BF16X3, 4096),
 }
 
 
@@ -37,14 +37,16 @@ def api():
 
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_searched_tied_cuts_path(api, case):
-    make, log2_limit, max_new, trials, tol, n_nonzero = CASES[case]
+    make, log2_limit, max_new, trials, tol, n_nonzero_max = CASES[case]
     base = make()
     r = api.search_ordering(Problem(base.circuit, [], base.open_tile, None), 1 << log2_limit, max_new,
                             trials=trials, seed=0)
-    assert r["fits"] and r["n_nonzero_slices"] == n_nonzero < r["n_slices"]
+    # the host tests pin the search's exact choice (256 nonzero paths on
+    # either lattice); here any tied-cut result it returns is contracted
+    assert r["fits"] and r["n_nonzero_slices"] <= n_nonzero_max and r["n_nonzero_slices"] < r["n_slices"]
     prob = Problem(base.circuit, r["cuts"], base.open_tile, r["ordering"])
     nz = NW.nonzero_slices(prob.circuit, prob.cut_edges)
-    assert len(nz) == n_nonzero
+    assert len(nz) == r["n_nonzero_slices"]
     s = nz[int(np.random.default_rng(99).integers(len(nz)))]
     bs = random_bitstrings(prob.n, 1, 80)
     ref = NW.slice_amplitudes(prob, bs[0], s)
