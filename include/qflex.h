@@ -399,7 +399,11 @@ qflex_status qflex_fidelity_samples(const uint8_t* batch_bits, const int32_t* ac
                                     int64_t* n_exact, void* stream);
 
 /* Synchronize `device` and read (and clear) the library's device status word
- * used by the standalone kernels.  *status = QFLEX_OK or QFLEX_ERR_DEVICE_TIMEOUT. */
+ * used by the standalone kernels, together with the status and report words
+ * of qflex_cgemm_noalloc on that device.  *status = QFLEX_ERR_DEVICE_TIMEOUT
+ * if a bounded wait ran out, else QFLEX_ERR_PLAN if a fused store fell
+ * outside its planes (the bits as qflex_plan_sync decodes them), else
+ * QFLEX_OK. */
 qflex_status qflex_device_status(int device, int32_t* status);
 
 /* Self-test of failure detection (no counterpart in the paper): one CTA
@@ -408,7 +412,11 @@ qflex_status qflex_device_status(int device, int32_t* status);
  * sets the timeout bit of the library's device status word and the kernel
  * returns.  Synchronizes `device`, clears the status word before and after;
  * *status = QFLEX_ERR_DEVICE_TIMEOUT when the wait ran out (the expected
- * outcome), QFLEX_OK otherwise.  The context stays usable. */
+ * outcome), QFLEX_OK otherwise.  The context stays usable.  The same wait
+ * then runs out once more on the private status word of qflex_cgemm_noalloc
+ * (set up on `device` if needed) and leaves its bit there, as a call of that
+ * entry point whose wait ran out would: its next call still computes C, and
+ * qflex_device_status reports QFLEX_ERR_DEVICE_TIMEOUT once for it. */
 qflex_status qflex_device_selftest_timeout(int device, uint64_t limit_ns, int32_t* status);
 
 /* ---------------- allocation-free complex GEMM ----------------
@@ -437,8 +445,16 @@ qflex_status qflex_device_selftest_timeout(int device, uint64_t limit_ns, int32_
  *    call, so leftover contents of an earlier call do not matter.
  *  - No cudaMalloc, cudaFree or allocating library routine is called.
  *  - A bounded device-side wait that runs out (a fault, not a normal
- *    condition) is recorded in a status word private to this entry point and
- *    not reported by its return value.
+ *    condition) is recorded in a status word private to this entry point;
+ *    the return value does not report it (that would need a host read and
+ *    a stream synchronization per call).  Every tensor-core call starts
+ *    with one stream-ordered thread that moves what earlier calls left in
+ *    that word into a report word and clears it, so one timed-out call never
+ *    makes later calls skip their work; qflex_device_status(device) reads
+ *    and clears both words and returns QFLEX_ERR_DEVICE_TIMEOUT if any call
+ *    since its last read timed out.
+ *  - Sizes are checked before their products are formed: M or N above
+ *    64 MiB / (plane bytes per entry x K) return QFLEX_ERR_ARG.
  * Arguments are those of qflex_cgemm without the workspace. */
 #define QFLEX_NOALLOC_SCRATCH_BYTES (64ull << 20)
 qflex_status qflex_cgemm_noalloc(int32_t prec, int64_t M, int64_t N, int64_t K, const void* A,

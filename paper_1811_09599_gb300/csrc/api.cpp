@@ -1888,6 +1888,10 @@ qflex_status qflex_cgemm_workspace_size(int32_t prec, int64_t M, int64_t N, int6
     const int kind = tc_kind_of(prec);
     const int nsplit = nsplit_of(prec);
     const size_t per = size_t(3) * nsplit * (kind == 0 ? 4 : 2);
+    // planes of at most 2^62 bytes each, checked before multiplying out
+    const uint64_t lim = uint64_t(1) << 62;
+    if (K > 0 && (uint64_t(M) > lim / (per * uint64_t(K)) || uint64_t(N) > lim / (per * uint64_t(K))))
+      return fail(QFLEX_ERR_ARG, "GEMM too large");
     *bytes = align256(per * size_t(M) * size_t(K)) + align256(per * size_t(N) * size_t(K)) + 256;
     return QFLEX_OK;
   });
@@ -2025,10 +2029,13 @@ qflex_status qflex_device_status(int device, int32_t* status) {
     QF_CUDA(cudaDeviceSynchronize());
     int32_t* w = device_status_word(device);
     if (!w) return fail(QFLEX_ERR_CUDA, "status word allocation failed");
-    int32_t v = 0;
+    int32_t v = 0, na = 0;
     QF_CUDA(cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost));
     QF_CUDA(cudaMemset(w, 0, sizeof(v)));
-    *status = v ? QFLEX_ERR_DEVICE_TIMEOUT : QFLEX_OK;
+    QF_CUDA(noalloc_take_status(device, &na));
+    v |= na;
+    // the bits as qflex_plan_sync decodes them
+    *status = (v & kDevTimeout) ? QFLEX_ERR_DEVICE_TIMEOUT : (v & kDevBadIndex) ? QFLEX_ERR_PLAN : QFLEX_OK;
     return QFLEX_OK;
   });
 }
@@ -2047,6 +2054,9 @@ qflex_status qflex_device_selftest_timeout(int device, uint64_t limit_ns, int32_
     int32_t v = 0;
     QF_CUDA(cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost));
     QF_CUDA(cudaMemset(w, 0, sizeof(v)));
+    // the same bounded wait on the allocation-free GEMM's private word, whose
+    // bit stays set for that entry point's next call to clear and report
+    QF_CUDA(noalloc_selftest(device, limit_ns));
     *status = (v & kDevTimeout) ? QFLEX_ERR_DEVICE_TIMEOUT : QFLEX_OK;
     return QFLEX_OK;
   });

@@ -356,6 +356,11 @@ cudaError_t launch_gridgrad(const GridQubitMeta* d_meta, int n_qubits, int max_b
                             double* d_grad, cudaStream_t s);
 
 int32_t* device_status_word(int device);   // library-wide status word for standalone calls
+// Allocation-free GEMM (k_noalloc.cu): read and clear its status and report
+// words on `dev` (synchronized by the caller); and its failure-detection
+// self-test, which leaves the timeout bit in its status word.
+cudaError_t noalloc_take_status(int dev, int32_t* bits);
+cudaError_t noalloc_selftest(int dev, uint64_t limit_ns);
 
 void set_last_error(const char* msg);      // text returned by qflex_last_error()
 
