@@ -59,3 +59,25 @@ def test_golden_bris70_plan_sizes():
     info = Plan(prob, "bf16x3", device=-1).info()
     assert info["n_slices"] == 2 ** (g["n_cuts"] * g["K"])
     assert info["max_tensor_elems"] == 2 ** (g["cut_rank"] * g["K"])
+
+
+def test_region_split_contraction_matches_oracle():
+    """The golden writer of the 7x7 depth 1+40+1 paths (tests/golden/
+    make_c4_golden.py) cuts two more bonds itself and sums over them where
+    they close; on the same lattice and region cuts at depths 1+8+1 and
+    1+16+1 its per-path amplitudes equal oracle.network.slice_amplitudes."""
+    import importlib.util
+    from oracle import network as NW
+    from qflex_inputs import random_bitstrings
+    spec = importlib.util.spec_from_file_location(
+        "make_c4_golden", os.path.join(os.path.dirname(__file__), "golden", "make_c4_golden.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    for t in (8, 16):
+        prob = c2_problem(3, t=t)
+        bits = random_bitstrings(prob.n, 1, 17)[0]
+        P = NW.n_slices(prob.circuit, prob.cut_edges)
+        for s in (0, 1, P - 1):
+            got = mod.region_split_amplitudes(prob, bits, s, log=None)
+            ref = NW.slice_amplitudes(prob, bits, s)
+            assert np.allclose(got, ref, rtol=1e-10, atol=1e-13 * np.max(np.abs(ref))), (t, s)
