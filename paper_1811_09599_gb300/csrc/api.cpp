@@ -221,6 +221,12 @@ struct qflex_plan_s {
   int2* d_gops = nullptr;
   int32_t* d_status = nullptr;
   unsigned* d_smax = nullptr;                  // fp16 operand scales: [0] A, [1] B, [2 + c] cache c (192 slots)
+  // fp16 planes written by a producer's epilogue (fused operands), per
+  // buffer: the bound whose scale the planes carry, and the largest part
+  // written (reset at the start of every call; only grows within a call)
+  unsigned* d_bscale = nullptr;
+  unsigned* d_bmax = nullptr;
+  bool fp16_fused = false;
   cudaStream_t last_stream = nullptr;
   // profiling: event pairs around launches
   // gradients (qflex_plan_enable_gradients)
@@ -290,6 +296,15 @@ void* op_buf(const qflex_plan_s& p, const Operand& op, bool is_a) {
   return is_a ? p.d_opA : p.d_opB;
 }
 int op_slot(const Operand& op, bool is_a) { return op.cache >= 0 ? 2 + op.cache : (is_a ? 0 : 1); }
+
+// Word whose fp16_scale_of gives the scale of operand X's fp16 planes: the
+// producer's bound for planes written by its epilogue (fusion on), else the
+// measured maximum of the permuted source (launch_absmax).
+const unsigned* scale_word(const qflex_plan_s& p, const Operand& X, bool is_a, bool fused_mode) {
+  if (p.tc_kind != 2) return nullptr;
+  if (X.fused && fused_mode) return p.d_bscale + X.ref.id;
+  return p.d_smax + op_slot(X, is_a);
+}
 
 // Planes a tensor-core step reads for operand X: its producer's fused output
 // (fusion on), else its own buffer.
@@ -371,12 +386,15 @@ int64_t leg_product(const std::vector<int>& legs, const std::vector<int64_t>& di
 // Epilogue fusion: a tensor-core step whose result is an operand of a later
 // tensor-core step writes that operand's 3M planes itself (bit-permuted
 // into the consumer's [rows][K] layout) instead of complex64, and the
-// consumer skips its permutation.  Needs power-of-two legs, an output whose
-// lowest row or column bit lands at stride 1 of the operand (so that the
-// scatter stays coalesced), and a split format without a whole-operand scale
-// (not fp16).
+// consumer skips its permutation.  Needs power-of-two legs and an output
+// whose lowest row or column bit lands at stride 1 of the operand (so that
+// the scatter stays coalesced).  fp16 planes need a power-of-two scale
+// before the first entry is written, so the producer takes it from a bound
+// of its output's entries (3 K max_a max_b, TcPlaneOut) instead of their
+// measured maximum; only tensor-core producers track the maxima these bounds
+// use, so CUDA-core producers do not write fp16 planes.
 void plan_fusion(qflex_plan_s& p) {
-  if (p.prec == QFLEX_FP32_SIMT || p.tc_kind == 2) return;
+  if (p.prec == QFLEX_FP32_SIMT) return;
   const int bytes = 3 * p.nsplit * (p.tc_kind == 0 ? 4 : 2);
   for (Step& k : p.steps) {
     // A CUDA-core product with N >= 16, at least 2^10 rows and a long K whose
@@ -401,7 +419,7 @@ void plan_fusion(qflex_plan_s& p) {
       Step& pi = p.steps[size_t(i)];
       // producers: tensor-core steps, and CUDA-core steps that take the
       // pipelined thin form (it has a plane-output variant)
-      const bool thin_prod = !pi.tc && pi.fp32_kernel != 2 && thin_pipelined(pi.M, pi.N, pi.K);
+      const bool thin_prod = !pi.tc && pi.fp32_kernel != 2 && thin_pipelined(pi.M, pi.N, pi.K) && p.tc_kind != 2;
       if ((!pi.tc && !thin_prod) || pi.fuse_out) continue;
       // the operand's layout: target legs row-major
       std::vector<int> target = w == 0 ? k.ml : k.nl;
@@ -435,7 +453,7 @@ void plan_fusion(qflex_plan_s& p) {
       for (size_t b = 0; b < wm.size(); ++b) po.wm[b] = wm[b];
       for (size_t b = 0; b < wn.size(); ++b) po.wn[b] = wn[b];
       po.n_fast = n_fast ? 1 : 0;
-      po.fmt = p.tc_kind == 0 ? kFmtTF32 : kFmtBF16;
+      po.fmt = plane_fmt(p.tc_kind);
       po.nsplit = p.nsplit;
       if (thin_prod) pi.fp32_kernel = 1;   // keep the form that writes planes
       po.vec = 1;
@@ -448,6 +466,7 @@ void plan_fusion(qflex_plan_s& p) {
       pi.fuse_out = true;
       X.fused = true;
       p.bufs[size_t(pi.out_buf)].bytes_per = bytes;
+      if (p.tc_kind == 2) p.fp16_fused = true;
     }
   }
 }
@@ -810,7 +829,8 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
   p.total_bytes = p.grid_bytes + align256(p.arena_bytes) + align256(p.opA_bytes) + align256(p.opB_bytes) +
                   align256(p.opcache_bytes) +
                   align256(sizeof(GridQubitMeta) * n) + align256(sizeof(int2) * std::max<size_t>(1, p.gops.size())) +
-                  256 /* status word */ + 768 /* fp16 scale slots: A, B, one per cache */;
+                  256 /* status word */ + 768 /* fp16 scale slots: A, B, one per cache */ +
+                  align256(sizeof(unsigned) * 2 * std::max<size_t>(1, p.bufs.size())) /* fused fp16 words */;
   static_assert((2 + kMaxOpCache) * sizeof(unsigned) <= 768, "fp16 scale slots");
   return QFLEX_OK;
 }
@@ -839,12 +859,22 @@ qflex_status allocate(qflex_plan_s& p) {
   c += align256(sizeof(int2) * std::max<size_t>(1, p.gops.size()));
   p.d_status = reinterpret_cast<int32_t*>(c);
   p.d_smax = reinterpret_cast<unsigned*>(c + 256);
+  c += 256 + 768;
+  p.d_bscale = reinterpret_cast<unsigned*>(c);
+  p.d_bmax = p.d_bscale + std::max<size_t>(1, p.bufs.size());
+  QF_CUDA(cudaMemset(p.d_bscale, 0, sizeof(unsigned) * 2 * std::max<size_t>(1, p.bufs.size())));
   QF_CUDA(cudaMemcpy(p.d_gmeta, p.gmeta.data(), sizeof(GridQubitMeta) * p.n, cudaMemcpyHostToDevice));
   if (!p.gops.empty())
     QF_CUDA(cudaMemcpy(p.d_gops, p.gops.data(), sizeof(int2) * p.gops.size(), cudaMemcpyHostToDevice));
   QF_CUDA(cudaMemset(p.d_status, 0, sizeof(int32_t)));
   for (Step& s : p.steps) {
     if (s.fuse_out) s.po.base = p.d_arena + p.bufs[size_t(s.out_buf)].offset;
+    if (s.fuse_out && p.tc_kind == 2) {
+      s.po.out_scale = p.d_bscale + s.out_buf;
+      s.po.out_max = p.d_bmax + s.out_buf;
+      s.po.max_a = s.A.fused ? p.d_bmax + s.A.ref.id : p.d_smax + op_slot(s.A, true);
+      s.po.max_b = s.B.fused ? p.d_bmax + s.B.ref.id : p.d_smax + op_slot(s.B, false);
+    }
     if (!s.tc) continue;
     if (!encode_step(p, s)) return fail(QFLEX_ERR_CUDA, "tensor map encoding failed (driver entry point missing?)");
   }
@@ -956,8 +986,7 @@ cudaError_t run_step(qflex_plan_s& p, const Step& st, int64_t b, const std::vect
   if (st.tc)
     return timed(p, 3, 8.0 * mnk, mma, gbytes, s, [&] {
       return launch_cgemm_tc(p.tc_kind, p.nsplit, st.bn, fused_mode ? st.maps : st.maps_plain, st.M, st.N, st.K, C,
-                             p.d_status, s, p.tc_kind == 2 ? p.d_smax + op_slot(st.A, true) : nullptr,
-                             p.tc_kind == 2 ? p.d_smax + op_slot(st.B, false) : nullptr,
+                             p.d_status, s, scale_word(p, st.A, true, fused_mode), scale_word(p, st.B, false, fused_mode),
                              st.fuse_out && fused_mode ? &st.po : nullptr);
     });
   const bool thin = st.fp32_kernel == 1 || (st.fp32_kernel == 0 && st.N <= 32);
@@ -1549,6 +1578,7 @@ qflex_status qflex_amplitudes(qflex_plan p, const double* angles, const uint8_t*
     if (ids) key.ids.assign(ids, ids + n_ids);
     return with_graph(*p, key, s, [&]() -> qflex_status {
       QF_CUDA(cudaMemsetAsync(amps, 0, size_t(n_bs) * T * 2 * sizeof(double), s));
+      if (p->fp16_fused) QF_CUDA(cudaMemsetAsync(p->d_bmax, 0, sizeof(unsigned) * p->bufs.size(), s));
       oc_reset(*p, p->oc_b, p->oc_v);
       return walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) -> qflex_status {
         cudaError_t e;
@@ -1702,8 +1732,7 @@ qflex_status qflex_plan_autotune(qflex_plan p, int32_t reps, int32_t* n_shapes, 
         auto launch = [&]() -> cudaError_t {
           if (key.tc)
             return launch_cgemm_tc(p->tc_kind, p->nsplit, cands[c], maps[c], st.M, st.N, st.K, C, p->d_status, s,
-                                   p->tc_kind == 2 ? p->d_smax + op_slot(st.A, true) : nullptr,
-                                   p->tc_kind == 2 ? p->d_smax + op_slot(st.B, false) : nullptr,
+                                   scale_word(*p, st.A, true, true), scale_word(*p, st.B, false, true),
                                    st.fuse_out ? &st.po : nullptr);
           // operands as the step reads them: in place when consumed directly
           // (the scratch is only sized for produced operands), else their buffer

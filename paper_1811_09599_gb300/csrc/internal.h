@@ -175,13 +175,25 @@ __device__ __forceinline__ uint32_t tf32_rna(float x);
 // as the 3M planes of put_entry, one vector store per plane; o is a
 // multiple of V.  Same arithmetic as put_entry, entry by entry.
 template <int FMT, int V>
-__device__ __forceinline__ void put_planes_vec(void* out, int64_t o, const float2* v, int nsplit, int64_t plane) {
+__device__ __forceinline__ void put_planes_vec(void* out, int64_t o, const float2* v, int nsplit, int64_t plane,
+                                               float scale = 1.f) {
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
     float x[V];
 #pragma unroll
     for (int j = 0; j < V; ++j) x[j] = p == 0 ? v[j].x : (p == 1 ? v[j].y : v[j].x + v[j].y);
-    if constexpr (FMT == kFmtTF32) {
+    if constexpr (FMT == kFmtFP16) {
+      __half hi[V], lo[V];
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        const float y = x[j] * scale;   // exact: scale is a power of two
+        hi[j] = __float2half_rn(y);
+        lo[j] = __float2half_rn(y - __half2float(hi[j]));
+      }
+      __half* q = static_cast<__half*>(out);
+      store_bytes<2 * V>(q + int64_t(p * nsplit) * plane + o, hi);
+      if (nsplit == 2) store_bytes<2 * V>(q + int64_t(p * 2 + 1) * plane + o, lo);
+    } else if constexpr (FMT == kFmtTF32) {
       uint32_t hi[V], lo[V];
 #pragma unroll
       for (int j = 0; j < V; ++j) {
@@ -319,6 +331,17 @@ struct TcPlaneOut {
   int32_t vec = 1;           // n_fast: columns per store (wn[b] = 2^b for 2^b < vec)
   int32_t fmt = 0;           // plane format for the CUDA-core producer: kFmtTF32 or kFmtBF16
   int32_t nsplit = 2;        // splits per part, same use
+  // fp16 planes (tensor-core producer only).  The planes hold s x entry with
+  // s = fp16_scale_of(bound), bound = 3 K max_a max_b >= 2 sqrt(2) K max_a max_b,
+  // which no part of any entry can exceed (|C| <= K max|A| max|B|, |A| <=
+  // sqrt(2) times its largest part, |re + im| <= sqrt(2) |C|): block 0 stores
+  // the bound's bits in *out_scale for the consumer, and every warp takes the
+  // atomicMax of the largest |re|, |im|, |re + im| it wrote into *out_max,
+  // which later products read as their max_a / max_b.
+  unsigned* out_scale = nullptr;
+  unsigned* out_max = nullptr;
+  const unsigned* max_a = nullptr;  // bits of upper bounds of the parts of A and of B
+  const unsigned* max_b = nullptr;
 };
 // The pipelined thin product (launch_cgemm_thin's form for this shape) with
 // its result written as operand planes (po) instead of C.

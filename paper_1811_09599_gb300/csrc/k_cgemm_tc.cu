@@ -178,7 +178,7 @@ __device__ __forceinline__ void tile_origin(int64_t tile, int64_t n_mt, int64_t 
 template <int FMT, int NSPLIT, int V>
 __device__ __forceinline__ bool write_sub_columns(const TcPlaneOut& po, const float2* st, int lane, int64_t drow,
                                                   int64_t row0, int64_t M, int64_t gn0, int64_t N, int64_t dn_hi,
-                                                  const int64_t* s_dn, int colb) {
+                                                  const int64_t* s_dn, int colb, float scale) {
   constexpr int LPR = 16 / V, RPI = 32 / LPR;
   const int c = (lane % LPR) * V, rl = lane / LPR;
   bool bad = false;
@@ -192,7 +192,7 @@ __device__ __forceinline__ bool write_sub_columns(const TcPlaneOut& po, const fl
         float2 v[V];
 #pragma unroll
         for (int j = 0; j < V; ++j) v[j] = st[r * 16 + ((c + j) ^ (r & 15))];
-        put_planes_vec<FMT, V>(po.base, d, v, NSPLIT, po.plane);
+        put_planes_vec<FMT, V>(po.base, d, v, NSPLIT, po.plane, scale);
       } else {
         bad = true;
       }
@@ -392,6 +392,15 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
       const float sb = smax_b ? fp16_scale_of(*smax_b) : 1.f;
       unscale = 1.f / (sa * sb);
     }
+    // plane output: raw accumulators x po_factor are the planes' values
+    // (fp16: the entry times the consumer's scale, both powers of two)
+    float po_factor = 1.f;
+    if constexpr (PO && KIND == 2) {
+      const float bound = 3.f * float(K) * __uint_as_float(*po.max_a) * __uint_as_float(*po.max_b);
+      const unsigned bb = __float_as_uint(bound);
+      if (blockIdx.x == 0 && warp == 2 && lane == 0) *po.out_scale = bb;
+      po_factor = fp16_scale_of(bb) * unscale;
+    }
     bool ok = true;
     int cg = 0;
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
@@ -447,6 +456,15 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
         for (int b = BN_LOG; b < po.nbits; ++b)
           if ((n0 >> b) & 1) dn_hi += po.wn[b];
         bool bad = false;
+        if constexpr (KIND == 2) {   // largest part written, for the bounds of later products
+          float mx = 0.f;
+#pragma unroll
+          for (int j = 0; j < G::HALF; ++j)
+            mx = fmaxf(mx, fmaxf(fabsf(re[j]), fmaxf(fabsf(im[j]), fabsf(re[j] + im[j]))));
+          for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+          mx *= unscale;
+          if (lane == 0 && mx > 0.f) atomicMax(po.out_max, __float_as_uint(mx));
+        }
 #pragma unroll
         for (int sub = 0; sub < G::HALF / 16; ++sub) {
 #pragma unroll
@@ -458,13 +476,16 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
             const int64_t row0 = m0 + q * 32, gn0 = n0 + colb;
             if (KIND != 0 && po.vec == 8)
               bad |= write_sub_columns<FMT, NSPLIT, (KIND != 0 ? 8 : 4)>(po, st, lane, drow, row0, M, gn0, N, dn_hi,
-                                                                         s_dn, colb);
+                                                                         s_dn, colb, po_factor);
             else if (po.vec >= 4)
-              bad |= write_sub_columns<FMT, NSPLIT, 4>(po, st, lane, drow, row0, M, gn0, N, dn_hi, s_dn, colb);
+              bad |= write_sub_columns<FMT, NSPLIT, 4>(po, st, lane, drow, row0, M, gn0, N, dn_hi, s_dn, colb,
+                                                       po_factor);
             else if (po.vec == 2)
-              bad |= write_sub_columns<FMT, NSPLIT, 2>(po, st, lane, drow, row0, M, gn0, N, dn_hi, s_dn, colb);
+              bad |= write_sub_columns<FMT, NSPLIT, 2>(po, st, lane, drow, row0, M, gn0, N, dn_hi, s_dn, colb,
+                                                       po_factor);
             else
-              bad |= write_sub_columns<FMT, NSPLIT, 1>(po, st, lane, drow, row0, M, gn0, N, dn_hi, s_dn, colb);
+              bad |= write_sub_columns<FMT, NSPLIT, 1>(po, st, lane, drow, row0, M, gn0, N, dn_hi, s_dn, colb,
+                                                       po_factor);
           } else if (gm_own < M) {
             // each lane its own row, column by column: consecutive lanes are
             // consecutive rows
@@ -474,7 +495,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
               if (n0 + col < N) {
                 const int64_t d = drow + dn_hi + s_dn[col];
                 if (d >= 0 && d < po.plane)
-                  put_entry<FMT>(po.base, d, st[lane * 16 + (c ^ (lane & 15))], NSPLIT, po.plane);
+                  put_entry<FMT>(po.base, d, st[lane * 16 + (c ^ (lane & 15))], NSPLIT, po.plane, po_factor);
                 else
                   bad = true;
               }
@@ -596,21 +617,19 @@ cudaError_t launch_cgemm_tc(int kind, int nsplit, int bn, const TcGemmMaps& maps
   if (3 * nsplit * M > INT32_MAX || 3 * nsplit * N > INT32_MAX) return cudaErrorInvalidValue;
   static const TcPlaneOut none{};
   const TcPlaneOut& po = planes ? *planes : none;
-  if (po.base && (kind == 2 || po.mbits > kMaxOutBits || po.nbits > kMaxOutBits ||
-                  (int64_t(1) << po.mbits) != M || (int64_t(1) << po.nbits) != N))
+  if (po.base && (po.mbits > kMaxOutBits || po.nbits > kMaxOutBits || (int64_t(1) << po.mbits) != M ||
+                  (int64_t(1) << po.nbits) != N))
+    return cudaErrorInvalidValue;
+  if (po.base && kind == 2 && (!po.out_scale || !po.out_max || !po.max_a || !po.max_b || !smax_a || !smax_b))
     return cudaErrorInvalidValue;
 #define QF_TC(KD, B, S)                                                                                  \
   if (kind == KD && bn == B && nsplit == S)                                                              \
     return po.base ? launch_t<KD, B, S, true>(maps, M, N, K, C, status, s, smax_a, smax_b, po)            \
                    : launch_t<KD, B, S, false>(maps, M, N, K, C, status, s, smax_a, smax_b, po);
-#define QF_TC16(B)                                                                                       \
-  if (kind == 2 && bn == B && nsplit == 2)                                                               \
-    return launch_t<2, B, 2, false>(maps, M, N, K, C, status, s, smax_a, smax_b, po);
   QF_TC(0, 64, 1) QF_TC(0, 64, 2) QF_TC(0, 128, 1) QF_TC(0, 128, 2)
   QF_TC(1, 64, 1) QF_TC(1, 64, 2) QF_TC(1, 128, 1) QF_TC(1, 128, 2)
-  QF_TC16(64) QF_TC16(128)
+  QF_TC(2, 64, 2) QF_TC(2, 128, 2)
 #undef QF_TC
-#undef QF_TC16
   return cudaErrorInvalidValue;
 }
 

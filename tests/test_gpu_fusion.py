@@ -57,3 +57,29 @@ def test_fused_plan_counts(api):
     fp32 = api.Plan(c2_problem(0), "fp32", device=-1)
     assert p.cost(1)["permute_bytes"] < fp32.cost(1)["permute_bytes"] / 3
     assert not any(s["out_fused"] or s["a_fused"] for s in fp32.steps(1))
+
+
+def test_fused_fp16_planes_vs_oracle(api):
+    """fp16x3 with fused planes: the producer scales its output by a power of
+    two taken from the bound 3 K max|A| max|B| of its entries (known before
+    the first entry is written), not from their measured maximum, so the
+    planes differ from the unfused path's (gradient calls) in their scale but
+    both sum to the oracle's amplitudes within the split tolerance."""
+    prob = grid_problem(5, 5, 32, 3, r0=2, c0=2, cuts=True, tile_rows=2, tile_cols=2, rotations=True)
+    bits = random_bitstrings(prob.n, 2, 3)
+    bs = torch.from_numpy(bits).cuda()
+    th = torch.from_numpy(prob.circuit.angles).cuda()
+    plan = api.Plan(prob, "fp16x3", device=0)
+    steps = plan.steps(2)
+    assert sum(bool(s["out_fused"]) for s in steps) >= 5
+    fused = plan.amplitudes(bs, th).cpu().numpy()
+    g = torch.ones((2, 16), dtype=torch.complex128, device="cuda")
+    unfused, _ = plan.amplitudes_grad(bs, th, g)
+    plan.sync()
+    assert amp_error(fused, unfused.cpu().numpy(), prob.n) < TOL["fp16x3"]
+    tensors = NW.all_grid_tensors(prob.circuit)
+    for sl in (7, 200):
+        got = plan.amplitudes(bs, th, [sl]).cpu().numpy()
+        plan.sync()
+        ref = np.stack([NW.slice_amplitudes(prob, b, sl, tensors=tensors) for b in bits])
+        assert amp_error(got, ref, prob.n, 1.0 / 256) < TOL["fp16x3"], sl
