@@ -352,9 +352,14 @@ def permute_sweep(api, torch, peaks):
             "peak": "measured hbm_gbs"}
 
 
-def rotation_batch_run(api, torch, precision, local, chunk=32, n_streams=8):
+def rotation_batch_run(api, torch, precision, local, chunk=32, n_streams=8, reps=5):
     """256 uneven rotation circuits (4x4..6x6 grids, depth 1+16..32+1), one
     amplitude and the gradient w.r.t. every angle each.
+    one_call: ONE plan of all 256 problems (one workspace) and ONE
+    qflex_amplitudes_grad call per step, which spreads the circuits over the
+    plan's streams; after a direct and a captured call, `reps` CUDA-graph
+    replays are timed with CUDA events.  Its amplitudes and gradients are
+    compared with those of the sequential run.
     sequential: each circuit's plan is created, run and destroyed in turn;
     GPU time = the sum of CUDA-event intervals around its amplitude+gradient
     call.  concurrent: circuits are taken `chunk` at a time -- their plans
@@ -369,18 +374,55 @@ def rotation_batch_run(api, torch, precision, local, chunk=32, n_streams=8):
                torch.from_numpy(p.circuit.angles).cuda()) for i, p in enumerate(batch)]
     n_params = sum(p.circuit.n_params for p in batch)
     seq_ms = 0.0
+    seq_amps, seq_grads = [], []
     t0 = time.perf_counter()
     for i, prob in enumerate(batch):
         plan = api.Plan(prob, precision, device=local)
         plan.enable_gradients()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        plan.amplitudes_grad(inputs[i][0], inputs[i][1], g)
+        a, gr = plan.amplitudes_grad(inputs[i][0], inputs[i][1], g)
         e1.record()
         torch.cuda.synchronize()
         seq_ms += e0.elapsed_time(e1)
+        seq_amps.append(a.cpu().numpy().reshape(-1))
+        seq_grads.append(gr.cpu().numpy())
         plan.close()
     seq_wall = time.perf_counter() - t0
+    # ---- one plan, one call
+    t0 = time.perf_counter()
+    multi = api.Plan(batch, precision, device=local)
+    multi.enable_gradients()
+    multi.use_graphs(True)
+    plan_s = time.perf_counter() - t0
+    flat_bits = torch.cat([b.reshape(-1) for b, _ in inputs])
+    flat_th = torch.cat([th for _, th in inputs])
+    gflat = torch.zeros((1, len(batch), 2), dtype=torch.float64, device="cuda")
+    gflat[..., 0] = 1.0
+    out = torch.empty((1, len(batch), 2), dtype=torch.float64, device="cuda")
+    gout = torch.empty(n_params, dtype=torch.float64, device="cuda")
+    for _ in range(3):                       # direct, captured, replayed
+        multi.amplitudes_grad(flat_bits, flat_th, gflat, out=out, grad_out=gout)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        amps, grad = multi.amplitudes_grad(flat_bits, flat_th, gflat, out=out, grad_out=gout)
+    e1.record()
+    torch.cuda.synchronize()
+    multi.sync()
+    one_ms = e0.elapsed_time(e1) / reps
+    amps, grad = amps.cpu().numpy(), grad.cpu().numpy()
+    lay = multi.layout(1)
+    same_amps = all(np.array_equal(amps[lay["amps"][k]:lay["amps"][k + 1]], seq_amps[k]) for k in range(len(batch)))
+    gdiff = max(float(np.max(np.abs(grad[lay["params"][k]:lay["params"][k + 1]] - seq_grads[k])) /
+                      max(float(np.max(np.abs(seq_grads[k]))), 1e-300)) for k in range(len(batch)))
+    launches = int(sum(multi.cost(1, None, k)["launches"] for k in range(len(batch))))
+    ws = multi.info()["workspace_bytes"]
+    multi.close()
+    del multi
+    torch.cuda.empty_cache()
+    # ---- one plan per circuit on several streams
     streams = [torch.cuda.Stream() for _ in range(n_streams)]
     conc_ms = 0.0
     t0 = time.perf_counter()
@@ -407,14 +449,21 @@ def rotation_batch_run(api, torch, precision, local, chunk=32, n_streams=8):
             pl.close()
     conc_wall = time.perf_counter() - t0
     return {"circuits": len(batch), "angles": n_params,
+            "one_call": {"gpu_ms": round(one_ms, 2), "replays": reps, "plan_s": round(plan_s, 2),
+                         "workspace_gb": round(ws / 1e9, 2), "forward_launches": launches,
+                         "amplitudes_per_s_gpu": round(len(batch) / (one_ms * 1e-3), 1),
+                         "gradient_entries_per_s_gpu": round(n_params / (one_ms * 1e-3), 1),
+                         "amplitudes_equal_sequential": same_amps,
+                         "gradients_max_rel_diff_vs_sequential": gdiff,
+                         "note": "one plan of 256 problems, one qflex_amplitudes_grad call per step, "
+                                 "CUDA-graph replay over the plan's 8 streams"},
             "sequential": {"gpu_ms": round(seq_ms, 2), "wall_s": round(seq_wall, 3),
                            "amplitudes_per_s_gpu": round(len(batch) / (seq_ms * 1e-3), 1),
                            "gradient_entries_per_s_gpu": round(n_params / (seq_ms * 1e-3), 1)},
             "concurrent": {"chunk": chunk, "streams": n_streams, "gpu_ms": round(conc_ms, 2),
                            "wall_s": round(conc_wall, 3),
                            "amplitudes_per_s_gpu": round(len(batch) / (conc_ms * 1e-3), 1),
-                           "gradient_entries_per_s_gpu": round(n_params / (conc_ms * 1e-3), 1)},
-            "note": "one plan per circuit; concurrent = independent circuits on several streams"}
+                           "gradient_entries_per_s_gpu": round(n_params / (conc_ms * 1e-3), 1)}}
 
 
 def bris70_run(api, torch, precision, local, searched=False):

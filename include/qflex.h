@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define QFLEX_ABI_VERSION 1
+#define QFLEX_ABI_VERSION 2
 
 typedef struct qflex_plan_s* qflex_plan;
 
@@ -64,7 +64,12 @@ typedef enum {
   QFLEX_FP32_SIMT = 0,  /* plain FP32, 4 real FMAs per complex MAC on CUDA cores */
   QFLEX_TF32X3 = 1,     /* tcgen05 kind::tf32, 3-multiply complex trick, operands split
                            hi+lo, products hi*hi + hi*lo + lo*hi, FP32 accumulate */
-  QFLEX_BF16X3 = 2,     /* same with bf16 hi+lo splits (kind::f16, bf16 inputs) */
+  QFLEX_BF16X3 = 2,     /* same with bf16 hi+lo splits (kind::f16, bf16 inputs); a problem
+                           whose schedule has more than 36 tensor-core steps stores its
+                           operands as the scaled fp16 hi+lo of QFLEX_FP16X3 instead (16
+                           significand bits per operand do not hold the amplitude within
+                           1e-4 over longer chains of products); qflex_plan_info's
+                           plane_format tells which */
   QFLEX_BF16_PLAIN = 3, /* one bf16 product per part (reported, not gated) */
   QFLEX_TF32_PLAIN = 4, /* one tf32 product per part (reported, not gated) */
   QFLEX_FP16X3 = 5      /* fp16 hi+lo splits (kind::f16, f16 inputs), 3 products, FP32
@@ -126,6 +131,10 @@ typedef struct {
   int32_t n_tc_steps;        /* steps whose GEMM runs on the tensor cores */
   int32_t n_persistent_buffers;
   int64_t n_nonzero_slices;  /* paths that do not vanish identically (qflex_nonzero_slices) */
+  int32_t n_problems;        /* problems of the plan (qflex_plan_create) */
+  int32_t plane_format;      /* operand planes of the tensor-core steps: 0 none (FP32), 1 tf32,
+                                2 bf16, 3 power-of-two-scaled fp16 (see QFLEX_BF16X3) */
+  size_t problem_workspace_bytes; /* this problem's part of workspace_bytes */
 } qflex_plan_info;
 
 /* Work of one qflex_amplitudes call, counted by replaying the schedule on the
@@ -163,29 +172,41 @@ typedef struct {
 int32_t qflex_abi_version(void);
 const char* qflex_last_error(void);
 
-/* Build a plan: network metadata (grid-tensor layouts, bond dimensions
- * 2^{K_e}), cut/slice indexing, ordering validation, per-step permutation and
- * GEMM descriptors, buffer reuse across paths (SI A: tensors independent of
- * a cut are built once and reused), and one device workspace.
+/* Build a plan for n_problems independent problems (1 <= n_problems <=
+ * 65536; the paper runs independent circuit instances, paths and batches as
+ * separate jobs of one run, Methods "Simulation of RQCs on NASA HPC
+ * clusters"; here they are one plan and one call).  Per problem: network
+ * metadata (grid-tensor layouts, bond dimensions 2^{K_e}), cut/slice
+ * indexing, ordering validation, per-step permutation and GEMM descriptors,
+ * buffer reuse across paths (SI A: tensors independent of a cut are built
+ * once and reused).  All problems share one device workspace (one
+ * allocation, each problem a slice of it) and, when there are several, up to
+ * 8 internal streams on which a call runs them concurrently.
+ * problems: host, [n_problems] (their circuits, orderings, cuts and tiles
+ * are copied; the caller may free them after the call).
  * workspace_bytes_max = 0 means no limit.  device < 0 builds a host-only plan
  * (no device memory, no CUDA calls) whose info/cost calls work and whose
  * amplitude calls return QFLEX_ERR_UNSUPPORTED; used to check plans on hosts
  * without a GPU.  Errors: QFLEX_ERR_ARG, QFLEX_ERR_CIRCUIT, QFLEX_ERR_PLAN,
- * QFLEX_ERR_OOM, QFLEX_ERR_CUDA. */
-qflex_status qflex_plan_create(const qflex_problem* problem, qflex_precision prec,
+ * QFLEX_ERR_OOM, QFLEX_ERR_CUDA (for a failing problem i > 0 of several the
+ * message names i). */
+qflex_status qflex_plan_create(const qflex_problem* problems, int32_t n_problems, qflex_precision prec,
                                size_t workspace_bytes_max, int device, qflex_plan* out);
 void qflex_plan_destroy(qflex_plan plan);
-qflex_status qflex_plan_get_info(qflex_plan plan, qflex_plan_info* info);
+/* Information on problem `problem` (0 <= problem < n_problems) of the plan;
+ * workspace_bytes is the whole plan's. */
+qflex_status qflex_plan_get_info(qflex_plan plan, int32_t problem, qflex_plan_info* info);
 
-/* Cost of qflex_amplitudes(plan, ..., n_bs, slice_ids, n_slice_ids, ...).
- * slice_ids: host, NULL = all slices. */
-qflex_status qflex_plan_cost(qflex_plan plan, int64_t n_bs, const int64_t* slice_ids,
+/* Cost of problem `problem`'s part of qflex_amplitudes(plan, ..., n_bs,
+ * slice_ids, n_slice_ids, ...).  slice_ids: host, NULL = all slices. */
+qflex_status qflex_plan_cost(qflex_plan plan, int32_t problem, int64_t n_bs, const int64_t* slice_ids,
                              int64_t n_slice_ids, qflex_cost* out);
 
-/* The schedule's steps for a call over n_bs bitstrings and `slice_ids` (host,
- * NULL = all): out[i] for i < min(cap, n_steps); *n_steps = number of steps. */
-qflex_status qflex_plan_steps(qflex_plan plan, int64_t n_bs, const int64_t* slice_ids, int64_t n_slice_ids,
-                              qflex_step_info* out, int32_t cap, int32_t* n_steps);
+/* The schedule's steps of problem `problem` for a call over n_bs bitstrings
+ * and `slice_ids` (host, NULL = all): out[i] for i < min(cap, n_steps);
+ * *n_steps = number of steps. */
+qflex_status qflex_plan_steps(qflex_plan plan, int32_t problem, int64_t n_bs, const int64_t* slice_ids,
+                              int64_t n_slice_ids, qflex_step_info* out, int32_t cap, int32_t* n_steps);
 
 /* Automated cut and ordering search (the paper picks both by hand per
  * lattice: Methods "Cutting indexes", "Contraction of the 3D tensor network";
@@ -228,7 +249,7 @@ qflex_status qflex_search_ordering(const qflex_circuit* circuit, const int32_t* 
  * n_f = max(1, floor(f P + 1/2)) capped at P, the first n_f entries of a
  * Fisher-Yates shuffle of 0..P-1 driven by SplitMix64(seed), sorted.
  * slice_ids: host, capacity >= n_f. */
-qflex_status qflex_select_slices(qflex_plan plan, double fidelity, uint64_t seed,
+qflex_status qflex_select_slices(qflex_plan plan, int32_t problem, double fidelity, uint64_t seed,
                                  int64_t* slice_ids, int64_t capacity, int64_t* n_selected);
 
 /* Paths that vanish identically.  A path fixes the cut bonds (Methods,
@@ -243,23 +264,31 @@ qflex_status qflex_select_slices(qflex_plan plan, double fidelity, uint64_t seed
  * slice_ids: host, capacity entries (may be NULL when capacity is 0).
  * *n_nonzero: their number, also set when capacity is too small
  * (QFLEX_ERR_ARG).  QFLEX_ERR_UNSUPPORTED above 2^32 paths. */
-qflex_status qflex_nonzero_slices(qflex_plan plan, int64_t* slice_ids, int64_t capacity, int64_t* n_nonzero);
+qflex_status qflex_nonzero_slices(qflex_plan plan, int32_t problem, int64_t* slice_ids, int64_t capacity,
+                                  int64_t* n_nonzero);
 
 /* Fraction-f path choice among the paths that do not vanish identically:
  * qflex_select_slices' rule over the P' entries of qflex_nonzero_slices'
  * list (n_f = max(1, floor(f P' + 1/2)) capped at P'), mapped to slice ids,
  * ascending.  slice_ids: host, capacity >= n_f. */
-qflex_status qflex_select_nonzero_slices(qflex_plan plan, double fidelity, uint64_t seed,
+qflex_status qflex_select_nonzero_slices(qflex_plan plan, int32_t problem, double fidelity, uint64_t seed,
                                          int64_t* slice_ids, int64_t capacity, int64_t* n_selected);
 
-/* Amplitudes of n_bs bitstrings, each with the open tile enumerated:
+/* Amplitudes of n_bs bitstrings of every problem, each with its open tile
+ * enumerated:
  *   amps_out[b][j] = sum_{s in slice_ids} amp_s(x_b with tile bits j)
+ * For a plan of several problems every array is the problems' arrays back
+ * to back, problem 0 first: angles [sum_i n_params_i], bitstrings
+ * [sum_i n_bs n_qubits_i], amps_out [sum_i n_bs 2^n_open_i]; slice_ids
+ * apply to every problem (NULL: each problem's own P paths).
  * angles:     device, double [n_params] (may be NULL when n_params == 0)
  * bitstrings: device, uint8 [n_bs][n_qubits], one byte (0/1) per qubit; tile bits ignored
  * slice_ids:  host, int64 [n_slice_ids] distinct values in [0, P); NULL = all P slices
  * amps_out:   device, complex128 [n_bs][2^n_open], overwritten
  * Grid tensors and GEMMs run in the plan's precision; the slice sum is FP64.
- * Enqueued on `stream` (a cudaStream_t; NULL = legacy default stream). */
+ * Enqueued on `stream` (a cudaStream_t; NULL = legacy default stream); the
+ * problems of a multi-problem plan run on its internal streams, forked from
+ * `stream` and joined back to it before the call's work completes. */
 qflex_status qflex_amplitudes(qflex_plan plan, const double* angles, const uint8_t* bitstrings,
                               int64_t n_bs, const int64_t* slice_ids, int64_t n_slice_ids,
                               double* amps_out, void* stream);
@@ -277,6 +306,8 @@ qflex_status qflex_plan_enable_gradients(qflex_plan plan);
  * derivative of each grid tensor w.r.t. each rotation angle from prefix/suffix products of
  * its qubit's gate line.  grad_amps: device complex128 [n_bs][2^n_open] (g);
  * grad_angles: device double [n_params], overwritten; amps_out as in qflex_amplitudes.
+ * Several problems: arrays back to back as in qflex_amplitudes (grad_amps as
+ * amps_out, grad_angles as angles).
  * Requires qflex_plan_enable_gradients.  The reverse GEMMs run in the plan's precision;
  * grid-tensor cotangents and the angle gradients are summed in FP64. */
 qflex_status qflex_amplitudes_grad(qflex_plan plan, const double* angles,

@@ -48,7 +48,9 @@ class PlanInfo(C.Structure):
     _fields_ = [("n_slices", C.c_int64), ("n_qubits", C.c_int32), ("n_params", C.c_int32),
                 ("n_open", C.c_int32), ("n_steps", C.c_int32), ("max_tensor_elems", C.c_int64),
                 ("workspace_bytes", C.c_size_t), ("n_tc_steps", C.c_int32),
-                ("n_persistent_buffers", C.c_int32), ("n_nonzero_slices", C.c_int64)]
+                ("n_persistent_buffers", C.c_int32), ("n_nonzero_slices", C.c_int64),
+                ("n_problems", C.c_int32), ("plane_format", C.c_int32),
+                ("problem_workspace_bytes", C.c_size_t)]
 
 
 class Cost(C.Structure):
@@ -82,17 +84,18 @@ PROFILE_CLASSES = ("gridtensor", "permute", "gemm_fp32", "gemm_tc", "slicesum")
 SIGNATURES = [
     ("qflex_abi_version", C.c_int32, []),
     ("qflex_last_error", C.c_char_p, []),
-    ("qflex_plan_create", C.c_int, [C.POINTER(Problem), C.c_int, C.c_size_t, C.c_int,
+    ("qflex_plan_create", C.c_int, [C.POINTER(Problem), C.c_int32, C.c_int, C.c_size_t, C.c_int,
                                     C.POINTER(C.c_void_p)]),
     ("qflex_plan_destroy", None, [C.c_void_p]),
-    ("qflex_plan_get_info", C.c_int, [C.c_void_p, C.POINTER(PlanInfo)]),
-    ("qflex_plan_cost", C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_int64,
+    ("qflex_plan_get_info", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(PlanInfo)]),
+    ("qflex_plan_cost", C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_int64), C.c_int64,
                                   C.POINTER(Cost)]),
-    ("qflex_select_slices", C.c_int, [C.c_void_p, C.c_double, C.c_uint64, C.POINTER(C.c_int64),
+    ("qflex_select_slices", C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_uint64, C.POINTER(C.c_int64),
                                       C.c_int64, C.POINTER(C.c_int64)]),
-    ("qflex_nonzero_slices", C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_int64, C.POINTER(C.c_int64)]),
-    ("qflex_select_nonzero_slices", C.c_int, [C.c_void_p, C.c_double, C.c_uint64, C.POINTER(C.c_int64),
-                                              C.c_int64, C.POINTER(C.c_int64)]),
+    ("qflex_nonzero_slices", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.c_int64,
+                                       C.POINTER(C.c_int64)]),
+    ("qflex_select_nonzero_slices", C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_uint64,
+                                              C.POINTER(C.c_int64), C.c_int64, C.POINTER(C.c_int64)]),
     ("qflex_amplitudes", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                    C.POINTER(C.c_int64), C.c_int64, C.c_void_p, C.c_void_p]),
     ("qflex_amplitudes_grad", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
@@ -116,7 +119,7 @@ SIGNATURES = [
     ("qflex_fidelity_samples", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int32,
                                          C.c_int32, C.c_double, C.c_uint64, C.c_int64, C.c_void_p,
                                          C.c_void_p, C.POINTER(C.c_int64), C.c_void_p]),
-    ("qflex_plan_steps", C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_int64,
+    ("qflex_plan_steps", C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_int64), C.c_int64,
                                    C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
     ("qflex_search_ordering", C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32),
                                         C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.c_uint64,

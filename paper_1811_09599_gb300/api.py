@@ -69,69 +69,98 @@ def search_ordering(problem, max_tensor_elems: int, max_new_cuts: int = 0, trial
 
 
 class Plan:
-    """qflex_plan for one problem (circuit, ordering, cuts, open tile).
+    """qflex_plan for one problem, or for several independent problems that
+    one call contracts together (circuit, ordering, cuts, open tile each).
 
     `problem` is a qflex_inputs.Problem (or any object with .circuit,
-    .cut_edges, .open_tile, .ordering).  device < 0 builds a host-only plan.
+    .cut_edges, .open_tile, .ordering), or a list of them.  device < 0 builds
+    a host-only plan.  With several problems the inputs and outputs of
+    amplitudes / amplitudes_grad are flat tensors holding the problems'
+    arrays back to back (see `layout`).
     """
 
     def __init__(self, problem, precision: str = "bf16x3", device: int = 0,
                  workspace_bytes_max: int = 0):
         self.lib = _lib.load()
-        circ = problem.circuit
-        self.n_qubits = circ.n
-        self.n_params = circ.n_params
+        probs = list(problem) if isinstance(problem, (list, tuple)) else [problem]
+        self.multi = isinstance(problem, (list, tuple))
+        self.n_problems = len(probs)
         self.precision = precision
         self.device = device
         self._keep = []
-        self._circ = _circuit_struct(circ, self._keep)
-        ordering = None
-        if problem.ordering is not None:
-            st = np.ascontiguousarray(np.asarray(problem.ordering, dtype=np.int32).reshape(-1))
-            self._keep.append(st)
-            ordering = _lib.Ordering(st.ctypes.data_as(C.POINTER(C.c_int32)), len(problem.ordering))
-            self._ordering = ordering
-        cuts = np.ascontiguousarray(np.asarray(problem.cut_edges, dtype=np.int32).reshape(-1))
-        tile = np.ascontiguousarray(np.asarray(problem.open_tile, dtype=np.int32).reshape(-1))
-        self._keep += [cuts, tile]
-        self.n_open = int(tile.size)
-        self._prob = _lib.Problem(C.pointer(self._circ),
-                                  C.pointer(ordering) if ordering is not None else None,
+        arr = (_lib.Problem * max(1, len(probs)))()
+        for k, pr in enumerate(probs):
+            circ = _circuit_struct(pr.circuit, self._keep)
+            self._keep.append(circ)
+            ordering = None
+            if pr.ordering is not None:
+                st = np.ascontiguousarray(np.asarray(pr.ordering, dtype=np.int32).reshape(-1))
+                ordering = _lib.Ordering(st.ctypes.data_as(C.POINTER(C.c_int32)), len(pr.ordering))
+                self._keep += [st, ordering]
+            cuts = np.ascontiguousarray(np.asarray(pr.cut_edges, dtype=np.int32).reshape(-1))
+            tile = np.ascontiguousarray(np.asarray(pr.open_tile, dtype=np.int32).reshape(-1))
+            self._keep += [cuts, tile]
+            arr[k] = _lib.Problem(C.pointer(circ), C.pointer(ordering) if ordering is not None else None,
                                   cuts.ctypes.data_as(C.POINTER(C.c_int32)), int(cuts.size),
                                   tile.ctypes.data_as(C.POINTER(C.c_int32)), int(tile.size))
+        self._probs = arr
+        self.qubits = [pr.circuit.n for pr in probs]
+        self.params = [pr.circuit.n_params for pr in probs]
+        self.opens = [len(pr.open_tile) for pr in probs]
+        self.n_qubits, self.n_params, self.n_open = self.qubits[0], self.params[0], self.opens[0]
         handle = C.c_void_p()
-        check(self.lib.qflex_plan_create(C.byref(self._prob), PRECISIONS[precision],
-                                         workspace_bytes_max, device, C.byref(handle)))
+        check(self.lib.qflex_plan_create(arr, len(probs), PRECISIONS[precision], workspace_bytes_max, device,
+                                         C.byref(handle)))
         self.handle = handle
 
+    def layout(self, n_bs: int = 1) -> dict:
+        """Offsets of each problem's part in the flat arrays of a call over
+        n_bs bitstrings: bits (bytes), params (angles), amps (complex entries)."""
+        ob, op, oa = np.cumsum([0] + self.qubits), np.cumsum([0] + self.params), \
+            np.cumsum([0] + [1 << t for t in self.opens])
+        return {"bits": [int(n_bs * v) for v in ob], "params": [int(v) for v in op],
+                "amps": [int(n_bs * v) for v in oa]}
+
     # ------------------------------------------------------------------ info
-    def info(self) -> dict:
+    def info(self, problem: int = 0) -> dict:
         inf = _lib.PlanInfo()
-        check(self.lib.qflex_plan_get_info(self.handle, C.byref(inf)))
+        check(self.lib.qflex_plan_get_info(self.handle, problem, C.byref(inf)))
         return {k: getattr(inf, k) for k, _ in inf._fields_}
 
     @property
     def n_slices(self) -> int:
         return self.info()["n_slices"]
 
-    def cost(self, n_bs: int, slice_ids: Optional[Sequence[int]] = None) -> dict:
+    def cost(self, n_bs: int, slice_ids: Optional[Sequence[int]] = None, problem: Optional[int] = 0) -> dict:
+        """qflex_plan_cost of one problem; problem=None sums over all problems
+        (largest_gemm_cmacs: the largest over them)."""
+        if problem is None:
+            tot = None
+            for k in range(self.n_problems):
+                c = self.cost(n_bs, slice_ids, k)
+                if tot is None:
+                    tot = c
+                else:
+                    for key in c:
+                        tot[key] = max(tot[key], c[key]) if key == "largest_gemm_cmacs" else tot[key] + c[key]
+            return tot
         arr, n = _i64_array(slice_ids)
         c = _lib.Cost()
         ptr = arr.ctypes.data_as(C.POINTER(C.c_int64)) if arr is not None else None
-        check(self.lib.qflex_plan_cost(self.handle, n_bs, ptr, n, C.byref(c)))
+        check(self.lib.qflex_plan_cost(self.handle, problem, n_bs, ptr, n, C.byref(c)))
         return {k: getattr(c, k) for k, _ in c._fields_}
 
     KERNELS = ("fp32_tiled", "fp32_thin16", "fp32_thin32", "fp32_rowwarp", "tensor_cores")
 
-    def steps(self, n_bs: int = 1, slice_ids: Optional[Sequence[int]] = None) -> list:
+    def steps(self, n_bs: int = 1, slice_ids: Optional[Sequence[int]] = None, problem: int = 0) -> list:
         """qflex_plan_steps: per step dst, src, M, N, K, kernel, bn, direct
         operands and executions in one call over n_bs bitstrings."""
         arr, n = _i64_array(slice_ids)
         ptr = arr.ctypes.data_as(C.POINTER(C.c_int64)) if arr is not None else None
         cnt = C.c_int32()
-        check(self.lib.qflex_plan_steps(self.handle, n_bs, ptr, n, None, 0, C.byref(cnt)))
+        check(self.lib.qflex_plan_steps(self.handle, problem, n_bs, ptr, n, None, 0, C.byref(cnt)))
         buf = (_lib.StepInfo * max(1, cnt.value))()
-        check(self.lib.qflex_plan_steps(self.handle, n_bs, ptr, n, buf, cnt.value, C.byref(cnt)))
+        check(self.lib.qflex_plan_steps(self.handle, problem, n_bs, ptr, n, buf, cnt.value, C.byref(cnt)))
         out = []
         for s in buf[: cnt.value]:
             d = {k: getattr(s, k) for k, _ in s._fields_}
@@ -139,36 +168,45 @@ class Plan:
             out.append(d)
         return out
 
-    def select_slices(self, fidelity: float, seed: int, nonzero: bool = False) -> np.ndarray:
+    def select_slices(self, fidelity: float, seed: int, nonzero: bool = False, problem: int = 0) -> np.ndarray:
         """Fraction-f path choice; nonzero=True chooses among the paths that
         do not vanish identically (qflex_select_nonzero_slices)."""
-        P = self.info()["n_nonzero_slices"] if nonzero else self.n_slices
+        inf = self.info(problem)
+        P = inf["n_nonzero_slices"] if nonzero else inf["n_slices"]
         cap = int(min(P, max(1, int(np.floor(float(fidelity) * P + 0.5)))))   # n_f of the rule
         out = np.zeros(max(cap, 1), dtype=np.int64)
         n = C.c_int64()
         fn = self.lib.qflex_select_nonzero_slices if nonzero else self.lib.qflex_select_slices
-        check(fn(self.handle, float(fidelity), C.c_uint64(seed), out.ctypes.data_as(C.POINTER(C.c_int64)),
+        check(fn(self.handle, problem, float(fidelity), C.c_uint64(seed), out.ctypes.data_as(C.POINTER(C.c_int64)),
                  out.size, C.byref(n)))
         return out[: n.value].copy()
 
-    def nonzero_slices(self) -> np.ndarray:
+    def nonzero_slices(self, problem: int = 0) -> np.ndarray:
         """Ascending ids of the paths that do not vanish identically."""
         n = C.c_int64()
-        cnt = self.info()["n_nonzero_slices"]
+        cnt = self.info(problem)["n_nonzero_slices"]
         out = np.zeros(cnt, dtype=np.int64)
-        check(self.lib.qflex_nonzero_slices(self.handle, out.ctypes.data_as(C.POINTER(C.c_int64)), cnt,
+        check(self.lib.qflex_nonzero_slices(self.handle, problem, out.ctypes.data_as(C.POINTER(C.c_int64)), cnt,
                                             C.byref(n)))
         return out[: n.value].copy()
 
     # ------------------------------------------------------------------ compute
+    def _n_bs(self, bitstrings: torch.Tensor) -> int:
+        assert bitstrings.dtype == torch.uint8 and bitstrings.is_cuda and bitstrings.is_contiguous()
+        if not self.multi:
+            return bitstrings.shape[0]
+        total = sum(self.qubits)
+        assert bitstrings.numel() % total == 0, "flat bitstrings of all problems expected"
+        return bitstrings.numel() // total
+
     def amplitudes(self, bitstrings: torch.Tensor, angles: Optional[torch.Tensor] = None,
                    slice_ids: Optional[Sequence[int]] = None, out: Optional[torch.Tensor] = None,
                    stream=None) -> torch.Tensor:
-        """complex128 [n_bs, 2^n_open] on the plan's device (qflex_amplitudes)."""
+        """complex128 [n_bs, 2^n_open] on the plan's device (qflex_amplitudes);
+        several problems: flat bitstrings in, flat amplitudes out (layout)."""
         dev = torch.device("cuda", self.device)
-        assert bitstrings.dtype == torch.uint8 and bitstrings.is_cuda and bitstrings.is_contiguous()
-        n_bs = bitstrings.shape[0]
-        T = 1 << self.n_open
+        n_bs = self._n_bs(bitstrings)
+        T = sum(1 << t for t in self.opens) if self.multi else 1 << self.n_open
         if out is None:
             out = torch.empty((n_bs, T, 2), dtype=torch.float64, device=dev)
         if angles is not None:
@@ -178,6 +216,8 @@ class Plan:
         check(self.lib.qflex_amplitudes(self.handle, C.c_void_p(angles.data_ptr()) if angles is not None else None,
                                         C.c_void_p(bitstrings.data_ptr()), n_bs, ptr, n,
                                         C.c_void_p(out.data_ptr()), _stream_handle(stream)))
+        if self.multi:
+            return torch.view_as_complex(out.view(-1, 2))
         return torch.view_as_complex(out.view(n_bs, T, 2))
 
     def autotune(self, reps: int = 3) -> dict:
@@ -195,21 +235,31 @@ class Plan:
         """qflex_plan_enable_gradients: allocate the reverse-pass workspace once."""
         check(self.lib.qflex_plan_enable_gradients(self.handle))
 
-    def amplitudes_grad(self, bitstrings, angles, grad_amps, slice_ids=None, stream=None):
-        """(amps, grad_angles) for L = Re sum conj(g) amps (qflex_amplitudes_grad)."""
+    def amplitudes_grad(self, bitstrings, angles, grad_amps, slice_ids=None, stream=None, out=None,
+                        grad_out=None):
+        """(amps, grad_angles) for L = Re sum conj(g) amps (qflex_amplitudes_grad);
+        several problems: flat arrays as in amplitudes.  out (float64 [n_bs,
+        T, 2]) and grad_out (float64 [max(1, n_params)]) may be given to keep
+        the output addresses fixed across calls (CUDA-graph replay)."""
         self.enable_gradients()
         dev = torch.device("cuda", self.device)
-        n_bs = bitstrings.shape[0]
-        T = 1 << self.n_open
-        amps = torch.empty((n_bs, T, 2), dtype=torch.float64, device=dev)
-        grad = torch.empty(max(1, self.n_params), dtype=torch.float64, device=dev)
-        g = torch.view_as_real(grad_amps.to(torch.complex128).contiguous()).contiguous()
+        n_bs = self._n_bs(bitstrings)
+        T = sum(1 << t for t in self.opens) if self.multi else 1 << self.n_open
+        n_par = sum(self.params)
+        amps = torch.empty((n_bs, T, 2), dtype=torch.float64, device=dev) if out is None else out
+        grad = torch.empty(max(1, n_par), dtype=torch.float64, device=dev) if grad_out is None else grad_out
+        assert amps.numel() == n_bs * T * 2 and grad.numel() >= max(1, n_par)
+        g = grad_amps if grad_amps.dtype == torch.float64 else \
+            torch.view_as_real(grad_amps.to(torch.complex128).contiguous()).contiguous()
+        assert g.is_contiguous() and g.numel() == n_bs * T * 2
         arr, n = _i64_array(slice_ids)
         ptr = arr.ctypes.data_as(C.POINTER(C.c_int64)) if arr is not None else None
         check(self.lib.qflex_amplitudes_grad(self.handle, C.c_void_p(angles.data_ptr()),
                                              C.c_void_p(bitstrings.data_ptr()), n_bs, ptr, n,
                                              C.c_void_p(g.data_ptr()), C.c_void_p(amps.data_ptr()),
                                              C.c_void_p(grad.data_ptr()), _stream_handle(stream)))
+        if self.multi:
+            return torch.view_as_complex(amps.view(-1, 2)), grad[:n_par]
         return torch.view_as_complex(amps.view(n_bs, T, 2)), grad[: self.n_params]
 
     def profile_start(self, classes=_lib.PROFILE_CLASSES):

@@ -178,10 +178,25 @@ struct Buf {
 
 }  // namespace
 
-struct qflex_plan_s {
+// Profiling state of a plan (qflex_plan_profile), shared by its problems:
+// event pairs around launches of the chosen kernel classes.
+struct Prof {
+  bool on = false;
+  int32_t mask = 0;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  struct Rec { int cls; size_t e0; double flops, mma, bytes; };
+  std::vector<Rec> recs;
+  qflex_profile tot{};
+};
+
+// One problem of a plan: network, schedule, buffers (a slice of the plan's
+// workspace) and the reverse pass's buffers.
+struct Sub {
   int device = -1;
   qflex_precision prec = QFLEX_FP32_SIMT;
   int tc_kind = 0, nsplit = 1;
+  Prof* prof = nullptr;                        // the plan's
   int n = 0, E = 0, n_params = 0;
   std::vector<int> K;                          // per edge
   std::vector<std::vector<int>> inc;           // per qubit: incident edges by neighbour id
@@ -201,7 +216,7 @@ struct qflex_plan_s {
   int64_t max_tensor = 0;
   size_t grid_bytes = 0, arena_bytes = 0, opA_bytes = 0, opB_bytes = 0, total_bytes = 0;
   int n_persistent = 0, n_tc = 0;
-  // device
+  // device (a slice of the plan's one workspace allocation)
   char* d_ws = nullptr;
   float2* d_grid = nullptr;
   char* d_arena = nullptr;
@@ -227,13 +242,10 @@ struct qflex_plan_s {
   unsigned* d_bscale = nullptr;
   unsigned* d_bmax = nullptr;
   bool fp16_fused = false;
-  cudaStream_t last_stream = nullptr;
-  // profiling: event pairs around launches
   // gradients (qflex_plan_enable_gradients)
-  bool grad_ready = false;
   std::vector<StepGrad> sg;
   std::vector<size_t> fwd_off, w_off;          // dedicated forward / cotangent buffers
-  size_t grad_bytes = 0;
+  size_t grad_bytes = 0, garena_bytes = 0, gxa = 0, gyb = 0;
   char* d_gws = nullptr;
   char* d_garena = nullptr;
   char* d_warena = nullptr;
@@ -241,6 +253,30 @@ struct qflex_plan_s {
   void* d_gA = nullptr;
   void* d_gB = nullptr;
   float2* d_gC = nullptr;
+  bool grad_active = false;                    // forward runs on the dedicated buffers
+};
+
+// A plan: one or more problems (qflex_plan_create), one device workspace
+// holding every problem's buffers, the launch state shared by its calls.
+struct qflex_plan_s {
+  int device = -1;
+  qflex_precision prec = QFLEX_FP32_SIMT;
+  std::vector<std::unique_ptr<Sub>> subs;
+  // Inputs and outputs of a call are the problems' arrays back to back:
+  // problem i's bitstrings start at n_bs * off_qubits[i] bytes, its angles
+  // (and angle gradients) at off_params[i], its amplitudes (and upstream
+  // cotangents) at n_bs * off_amps[i] complex entries.
+  std::vector<int64_t> off_qubits, off_params, off_amps;
+  int64_t n_qubits_total = 0, n_params_total = 0, amps_total = 0;
+  size_t total_bytes = 0, grad_bytes = 0;
+  char* d_ws = nullptr;
+  char* d_gws = nullptr;
+  bool grad_ready = false;
+  cudaStream_t last_stream = nullptr;
+  // problems of one call run concurrently on these streams, forked from
+  // and joined to the caller's stream by events
+  std::vector<cudaStream_t> workers;
+  std::vector<cudaEvent_t> fork_ev, join_ev;
   // CUDA-graph replay of qflex_amplitudes / qflex_amplitudes_grad
   bool use_graphs = false;
   struct GraphKey {
@@ -260,19 +296,21 @@ struct qflex_plan_s {
   };
   GraphKey gkey, gseen;
   cudaGraphExec_t gexec = nullptr;
-  bool grad_active = false;                    // forward runs on the dedicated buffers
-  bool profiling = false;
-  int32_t prof_mask = 0;
-  std::vector<cudaEvent_t> ev_pool;
-  size_t ev_used = 0;
-  struct Rec { int cls; size_t e0; double flops, mma, bytes; };
-  std::vector<Rec> recs;
-  qflex_profile prof{};
+  Prof prof;
+  ~qflex_plan_s() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    for (cudaEvent_t e : prof.pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : fork_ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : join_ev) cudaEventDestroy(e);
+    for (cudaStream_t w : workers) cudaStreamDestroy(w);
+    if (d_gws) cudaFree(d_gws);
+    if (d_ws) cudaFree(d_ws);
+  }
 };
 
 namespace {
 
-size_t operand_bytes(const qflex_plan_s& p, bool tc, int64_t elems) {
+size_t operand_bytes(const Sub& p, bool tc, int64_t elems) {
   if (!tc) return size_t(elems) * 8;
   return size_t(elems) * 3 * p.nsplit * (p.tc_kind == 0 ? 4 : 2);
 }
@@ -287,11 +325,14 @@ bool tc_route(int64_t M, int64_t N, int64_t K) {
          !(N <= 32 && K <= 64);
 }
 
-constexpr int kMaxOpCache = 128;                // fp16 scale slots 2..129 of 192
+constexpr int kMaxOpCache = 128;
+constexpr int32_t kMaxProblems = 1 << 16;      // problems of one plan
+constexpr int kBf16MaxTcSteps = 36;             // longest tensor-core chain kept in bf16 planes (QFLEX_BF16X3)
+constexpr int kMaxWorkers = 8;                  // streams a multi-problem call spreads over                // fp16 scale slots 2..129 of 192
 constexpr size_t kOpCacheMinBytes = 0;           // small operands too: each saves a launch per execution
 
 // Buffer an operand is produced into (its cache, else the shared scratch).
-void* op_buf(const qflex_plan_s& p, const Operand& op, bool is_a) {
+void* op_buf(const Sub& p, const Operand& op, bool is_a) {
   if (op.cache >= 0) return p.d_opcache + p.opcache[size_t(op.cache)].off;
   return is_a ? p.d_opA : p.d_opB;
 }
@@ -300,7 +341,7 @@ int op_slot(const Operand& op, bool is_a) { return op.cache >= 0 ? 2 + op.cache 
 // Word whose fp16_scale_of gives the scale of operand X's fp16 planes: the
 // producer's bound for planes written by its epilogue (fusion on), else the
 // measured maximum of the permuted source (launch_absmax).
-const unsigned* scale_word(const qflex_plan_s& p, const Operand& X, bool is_a, bool fused_mode) {
+const unsigned* scale_word(const Sub& p, const Operand& X, bool is_a, bool fused_mode) {
   if (p.tc_kind != 2) return nullptr;
   if (X.fused && fused_mode) return p.d_bscale + X.ref.id;
   return p.d_smax + op_slot(X, is_a);
@@ -308,14 +349,14 @@ const unsigned* scale_word(const qflex_plan_s& p, const Operand& X, bool is_a, b
 
 // Planes a tensor-core step reads for operand X: its producer's fused output
 // (fusion on), else its own buffer.
-void* x_buf(const qflex_plan_s& p, const Operand& X, bool is_a, bool fused_mode) {
+void* x_buf(const Sub& p, const Operand& X, bool is_a, bool fused_mode) {
   if (X.fused && fused_mode) return p.d_arena + p.bufs[size_t(X.ref.id)].offset;
   return op_buf(p, X, is_a);
 }
 
 // Tensor maps of a tensor-core step: fused operands (maps) and, when the step
 // has any, the same on the operand scratch for the unfused gradient forward.
-bool encode_step(qflex_plan_s& p, Step& s) {
+bool encode_step(Sub& p, Step& s) {
   if (!tc_encode_maps(p.tc_kind, p.nsplit, s.bn, x_buf(p, s.A, true, true), s.M, x_buf(p, s.B, false, true), s.N,
                       s.K, &s.maps))
     return false;
@@ -340,7 +381,7 @@ bool oc_hit(std::vector<int64_t>& ob, std::vector<std::vector<int64_t>>& ov, uin
   ov[size_t(c)] = vals;
   return false;
 }
-void oc_reset(const qflex_plan_s& p, std::vector<int64_t>& ob, std::vector<std::vector<int64_t>>& ov) {
+void oc_reset(const Sub& p, std::vector<int64_t>& ob, std::vector<std::vector<int64_t>>& ov) {
   ob.assign(p.opcache.size(), -1);
   ov.assign(p.opcache.size(), {});
 }
@@ -393,7 +434,7 @@ int64_t leg_product(const std::vector<int>& legs, const std::vector<int64_t>& di
 // of its output's entries (3 K max_a max_b, TcPlaneOut) instead of their
 // measured maximum; only tensor-core producers track the maxima these bounds
 // use, so CUDA-core producers do not write fp16 planes.
-void plan_fusion(qflex_plan_s& p) {
+void plan_fusion(Sub& p) {
   if (p.prec == QFLEX_FP32_SIMT) return;
   const int bytes = 3 * p.nsplit * (p.tc_kind == 0 ? 4 : 2);
   for (Step& k : p.steps) {
@@ -471,7 +512,7 @@ void plan_fusion(qflex_plan_s& p) {
   }
 }
 
-qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
+qflex_status build_plan(const qflex_problem* pr, Sub& p) {
   const qflex_circuit* c = pr->circuit;
   if (!c) return fail(QFLEX_ERR_ARG, "problem->circuit is NULL");
   if (c->n_qubits <= 0 || c->n_qubits > 4096) return fail(QFLEX_ERR_CIRCUIT, "n_qubits out of range");
@@ -776,6 +817,19 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
   }
   const uint64_t all_cuts = p.cuts.size() >= 64 ? ~uint64_t(0) : ((uint64_t(1) << p.cuts.size()) - 1);
   if (!p.final_ref.grid) p.bufs[p.final_ref.id].consumer = ns;   // read by the slice sum
+  if (p.prec == QFLEX_BF16X3) {
+    // Long chains of bf16 splits: a bf16 hi + lo split keeps 16 significand
+    // bits per operand, and past 36 split products on the amplitude's path
+    // the accumulated rounding exceeds the 1e-4 amplitude bar (measured
+    // against the FP64 oracle: 5.8e-5 at 36 products on the 7x7 depth-32
+    // region plan, 1.1e-4 to 1.3e-4 at 40 to 45 on the searched 7x7 and the
+    // 70-qubit diamond plans).  Such plans keep the 3-term split products but
+    // store the operands as power-of-two-scaled fp16 hi + lo (22 significand
+    // bits, the same MMA rate and plane bytes): 2.8e-5 to 3.9e-5 there.
+    Sub trial = p;
+    plan_fusion(trial);
+    if (trial.n_tc > kBf16MaxTcSteps) p.tc_kind = 2;
+  }
   plan_fusion(p);
   // buffers: reused across slices -> dedicated; others share by liveness
   for (Buf& b : p.bufs) {
@@ -835,13 +889,10 @@ qflex_status build_plan(const qflex_problem* pr, qflex_plan_s& p) {
   return QFLEX_OK;
 }
 
-qflex_status allocate(qflex_plan_s& p) {
-  QF_CUDA(cudaSetDevice(p.device));
-  if (cudaMalloc(&p.d_ws, p.total_bytes) != cudaSuccess) {
-    cudaGetLastError();
-    p.d_ws = nullptr;
-    return fail(QFLEX_ERR_OOM, "workspace allocation of " + std::to_string(p.total_bytes) + " bytes failed");
-  }
+// Lay out a problem's buffers at `base` (its slice of the plan's workspace,
+// total_bytes long), upload its tables and encode its tensor maps.
+qflex_status allocate(Sub& p, char* base) {
+  p.d_ws = base;
   char* c = p.d_ws;
   p.d_grid = reinterpret_cast<float2*>(c);
   c += p.grid_bytes;
@@ -881,11 +932,11 @@ qflex_status allocate(qflex_plan_s& p) {
   return QFLEX_OK;
 }
 
-char* buf_ptr(const qflex_plan_s& p, int id) {
+char* buf_ptr(const Sub& p, int id) {
   return p.grad_active ? p.d_garena + p.fwd_off[id] : p.d_arena + p.bufs[id].offset;
 }
 
-const float2* ref_ptr(const qflex_plan_s& p, const Ref& r) {
+const float2* ref_ptr(const Sub& p, const Ref& r) {
   if (r.grid) return p.d_grid + p.gmeta[r.id].offset;
   return reinterpret_cast<const float2*>(buf_ptr(p, r.id));
 }
@@ -898,7 +949,7 @@ int64_t ref_base(const Ref& r, const std::vector<int64_t>& vals) {
 
 // Whole tensor behind a view (for the fp16 scale: the largest part of the
 // whole tensor bounds the largest part of any view of it).
-void ref_region(const qflex_plan_s& p, const Ref& r, const float2** ptr, int64_t* n) {
+void ref_region(const Sub& p, const Ref& r, const float2** ptr, int64_t* n) {
   if (r.grid) {
     const GridQubitMeta& m = p.gmeta[r.id];
     *ptr = p.d_grid + m.offset;
@@ -909,7 +960,7 @@ void ref_region(const qflex_plan_s& p, const Ref& r, const float2** ptr, int64_t
   }
 }
 
-cudaError_t produce(const qflex_plan_s& p, const Operand& op, bool tc, int64_t rows, int64_t cols,
+cudaError_t produce(const Sub& p, const Operand& op, bool tc, int64_t rows, int64_t cols,
                     const std::vector<int64_t>& vals, void* out, cudaStream_t s, int slot) {
   const int fmt = tc ? plane_fmt(p.tc_kind) : kFmtC64;
   const float2* in = ref_ptr(p, op.ref);
@@ -929,24 +980,25 @@ cudaError_t produce(const qflex_plan_s& p, const Operand& op, bool tc, int64_t r
 
 // Launch `fn` on `s`, bracketed by an event pair when the plan is profiling.
 template <class F>
-cudaError_t timed(qflex_plan_s& p, int cls, double flops, double mma, double bytes, cudaStream_t s, F&& fn) {
-  if (!p.profiling || !((p.prof_mask >> cls) & 1)) return fn();
-  while (p.ev_pool.size() < p.ev_used + 2) {
+cudaError_t timed(Sub& sp, int cls, double flops, double mma, double bytes, cudaStream_t s, F&& fn) {
+  Prof& p = *sp.prof;
+  if (!p.on || !((p.mask >> cls) & 1)) return fn();
+  while (p.pool.size() < p.used + 2) {
     cudaEvent_t e;
     cudaError_t r = cudaEventCreate(&e);
     if (r != cudaSuccess) return r;
-    p.ev_pool.push_back(e);
+    p.pool.push_back(e);
   }
-  const size_t i = p.ev_used;
-  p.ev_used += 2;
-  cudaError_t r = cudaEventRecord(p.ev_pool[i], s);
+  const size_t i = p.used;
+  p.used += 2;
+  cudaError_t r = cudaEventRecord(p.pool[i], s);
   if (r != cudaSuccess) return r;
   if ((r = fn()) != cudaSuccess) return r;
   p.recs.push_back({cls, i, flops, mma, bytes});
-  return cudaEventRecord(p.ev_pool[i + 1], s);
+  return cudaEventRecord(p.pool[i + 1], s);
 }
 
-cudaError_t run_step(qflex_plan_s& p, const Step& st, int64_t b, const std::vector<int64_t>& vals,
+cudaError_t run_step(Sub& p, const Step& st, int64_t b, const std::vector<int64_t>& vals,
                      cudaStream_t s) {
   cudaError_t e;
   const double out_per = st.tc ? 3.0 * p.nsplit * (p.tc_kind == 0 ? 4 : 2) : 8.0;
@@ -998,7 +1050,7 @@ cudaError_t run_step(qflex_plan_s& p, const Step& st, int64_t b, const std::vect
 
 
 // ------------------------------------------------------------------ reverse pass
-int route_of(const qflex_plan_s& p, int64_t M, int64_t N, int64_t K) {
+int route_of(const Sub& p, int64_t M, int64_t N, int64_t K) {
   const bool tc = p.prec != QFLEX_FP32_SIMT && tc_route(M, N, K);
   return tc ? 2 : (N <= 32 ? 1 : 0);
 }
@@ -1043,7 +1095,7 @@ std::vector<int> cat(const std::vector<int>& a, const std::vector<int>& b) {
 // step output (legs `wlegs`, contiguous) in order xorder = (rows, inner),
 // Y from the forward view `ysrc` in order (cols, inner), and C' (rows, cols)
 // scattered into the view `target`.
-bool make_bwd(const qflex_plan_s& p, const std::vector<int>& wlegs, const std::vector<int>& rows,
+bool make_bwd(const Sub& p, const std::vector<int>& wlegs, const std::vector<int>& rows,
               const std::vector<int>& inner, const std::vector<int>& cols, const Ref& ysrc,
               const Ref& target, BwdGemm* g) {
   const auto& dim = p.leg_dim;
@@ -1064,7 +1116,9 @@ bool make_bwd(const qflex_plan_s& p, const std::vector<int>& wlegs, const std::v
   return true;
 }
 
-qflex_status build_grad(qflex_plan_s& p) {
+// Reverse-pass descriptors and the bytes of a problem's gradient buffers
+// (p.grad_bytes); grad_assign then lays them out at a base address.
+qflex_status build_grad(Sub& p) {
   p.sg.resize(p.steps.size());
   // forward views of each step's operands, as recorded by the planner
   for (size_t i = 0; i < p.steps.size(); ++i) {
@@ -1092,12 +1146,17 @@ qflex_status build_grad(qflex_plan_s& p) {
       yb = std::max(yb, operand_bytes(p, b->route == 2, b->N * b->K));
       cc = std::max(cc, size_t(b->M * b->N) * 8);
     }
-  p.grad_bytes = 2 * arena + align256(size_t(p.grid_elems) * 16) + align256(xa) + align256(yb) + align256(cc);
-  if (cudaMalloc(&p.d_gws, p.grad_bytes) != cudaSuccess) {
-    cudaGetLastError();
-    p.d_gws = nullptr;
-    return fail(QFLEX_ERR_OOM, "gradient workspace allocation of " + std::to_string(p.grad_bytes) + " bytes failed");
-  }
+  p.grad_bytes = align256(2 * arena + align256(size_t(p.grid_elems) * 16) + align256(xa) + align256(yb) +
+                          align256(cc));
+  p.garena_bytes = arena;
+  p.gxa = xa;
+  p.gyb = yb;
+  return QFLEX_OK;
+}
+
+qflex_status grad_assign(Sub& p, char* base) {
+  const size_t arena = p.garena_bytes;
+  p.d_gws = base;
   char* c = p.d_gws;
   p.d_garena = c;
   c += arena;
@@ -1107,19 +1166,18 @@ qflex_status build_grad(qflex_plan_s& p) {
   p.d_wgrid = reinterpret_cast<double2*>(c);
   c += align256(size_t(p.grid_elems) * 16);
   p.d_gA = c;
-  c += align256(xa);
+  c += align256(p.gxa);
   p.d_gB = c;
-  c += align256(yb);
+  c += align256(p.gyb);
   p.d_gC = reinterpret_cast<float2*>(c);
   for (StepGrad& g : p.sg)
     for (BwdGemm* b : {&g.ga, &g.gb})
       if (b->route == 2 && !tc_encode_maps(p.tc_kind, p.nsplit, b->bn, p.d_gA, b->M, p.d_gB, b->N, b->K, &b->maps))
         return fail(QFLEX_ERR_CUDA, "tensor map encoding failed");
-  p.grad_ready = true;
   return QFLEX_OK;
 }
 
-cudaError_t run_bwd(qflex_plan_s& p, const Step& st, const BwdGemm& g, const std::vector<int64_t>& vals,
+cudaError_t run_bwd(Sub& p, const Step& st, const BwdGemm& g, const std::vector<int64_t>& vals,
                     cudaStream_t s) {
   cudaError_t e;
   const float2* W = reinterpret_cast<const float2*>(p.d_warena + p.w_off[st.out_buf]);
@@ -1173,7 +1231,7 @@ cudaError_t run_bwd(qflex_plan_s& p, const Step& st, const BwdGemm& g, const std
   });
 }
 
-void decode_slice(const qflex_plan_s& p, int64_t s, std::vector<int64_t>& vals) {
+void decode_slice(const Sub& p, int64_t s, std::vector<int64_t>& vals) {
   vals.assign(p.cuts.size(), 0);
   for (int i = int(p.cuts.size()) - 1; i >= 0; --i) {
     const int64_t r = int64_t(1) << p.K[p.cuts[i]];
@@ -1184,7 +1242,7 @@ void decode_slice(const qflex_plan_s& p, int64_t s, std::vector<int64_t>& vals) 
 
 // Walk the schedule of one call; `f(step index or -1 for slice sum, vals)`.
 template <class F>
-qflex_status walk(const qflex_plan_s& p, int64_t n_bs, const int64_t* ids, int64_t n_ids, F&& f) {
+qflex_status walk(const Sub& p, int64_t n_bs, const int64_t* ids, int64_t n_ids, F&& f) {
   std::vector<int64_t> vals, prev;
   for (int64_t b = 0; b < n_bs; ++b) {
     if (qflex_status st = f(-2, b, vals)) return st;   // grid tensors for bitstring b
@@ -1208,7 +1266,7 @@ qflex_status walk(const qflex_plan_s& p, int64_t n_bs, const int64_t* ids, int64
   return QFLEX_OK;
 }
 
-qflex_status check_slices(const qflex_plan_s& p, const int64_t* ids, int64_t n_ids) {
+qflex_status check_slices(const Sub& p, const int64_t* ids, int64_t n_ids) {
   if (!ids) return QFLEX_OK;
   if (n_ids < 0) return fail(QFLEX_ERR_ARG, "n_slice_ids < 0");
   for (int64_t k = 0; k < n_ids; ++k)
@@ -1224,7 +1282,7 @@ qflex_status check_slices(const qflex_plan_s& p, const int64_t* ids, int64_t n_i
 // stream) always run directly.
 template <class F>
 qflex_status with_graph(qflex_plan_s& p, const qflex_plan_s::GraphKey& key, cudaStream_t s, F&& enqueue) {
-  if (!p.use_graphs || p.profiling || s == nullptr) return enqueue();
+  if (!p.use_graphs || p.prof.on || s == nullptr) return enqueue();
   if (p.gexec && p.gkey == key) {
     QF_CUDA(cudaGraphLaunch(p.gexec, s));
     return QFLEX_OK;
@@ -1257,6 +1315,103 @@ qflex_status with_graph(qflex_plan_s& p, const qflex_plan_s::GraphKey& key, cuda
   return QFLEX_OK;
 }
 
+// A problem's part of one qflex_amplitudes call, enqueued on stream s:
+// grid tensors per bitstring, the schedule per path (steps rerun when a cut
+// they depend on changes), the FP64 slice sum into amps [n_bs][2^|tile|].
+qflex_status enqueue_amplitudes(Sub& p, const double* angles, const uint8_t* bits, int64_t n_bs, const int64_t* ids,
+                                int64_t n_ids, double* amps, cudaStream_t s) {
+  const int64_t T = int64_t(1) << p.tile.size();
+  QF_CUDA(cudaMemsetAsync(amps, 0, size_t(n_bs) * T * 2 * sizeof(double), s));
+  if (p.fp16_fused) QF_CUDA(cudaMemsetAsync(p.d_bmax, 0, sizeof(unsigned) * p.bufs.size(), s));
+  oc_reset(p, p.oc_b, p.oc_v);
+  return walk(p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) -> qflex_status {
+    cudaError_t e;
+    if (i == -2) {
+      e = timed(p, 0, 0, 0, 8.0 * p.grid_elems, s, [&] {
+        return launch_gridtensor(p.d_gmeta, p.n, p.max_bits, p.d_gops, angles, bits + b * p.n, p.d_grid, s);
+      });
+    } else if (i == -1) {
+      const float2* src = ref_ptr(p, p.final_ref) + ref_base(p.final_ref, vals);
+      e = timed(p, 4, 0, 0, 40.0 * T, s, [&] {
+        return launch_slicesum(src, p.final_strides.data(), int(p.tile.size()), amps + b * T * 2, s);
+      });
+    } else {
+      e = run_step(p, p.steps[size_t(i)], b, vals, s);
+    }
+    if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
+    return QFLEX_OK;
+  });
+}
+
+// A problem's part of one qflex_amplitudes_grad call: the forward pass on
+// the dedicated buffers, then per path the reverse pass (environments of
+// every intermediate and grid tensor, FP64 accumulation over paths), and
+// per bitstring the angle derivatives of the grid tensors.
+qflex_status enqueue_gradients(Sub& p, const double* angles, const uint8_t* bits, int64_t n_bs, const int64_t* ids,
+                               int64_t n_ids, const double* g, double* amps, double* grad, cudaStream_t s) {
+  const int64_t T = int64_t(1) << p.tile.size();
+  const int final_buf = p.final_ref.id;
+  QF_CUDA(cudaMemsetAsync(amps, 0, size_t(n_bs) * T * 2 * sizeof(double), s));
+  if (p.n_params > 0) QF_CUDA(cudaMemsetAsync(grad, 0, size_t(p.n_params) * sizeof(double), s));
+  oc_reset(p, p.oc_b, p.oc_v);
+  qflex_status res = walk(p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) -> qflex_status {
+    cudaError_t e = cudaSuccess;
+    if (i == -2) {
+      if (b > 0 && p.n_params > 0)   // gradient of the previous bitstring
+        e = launch_gridgrad(p.d_gmeta, p.n, p.max_bits, p.d_gops, angles, bits + (b - 1) * p.n, p.d_wgrid, grad, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(p.d_wgrid, 0, size_t(p.grid_elems) * 16, s);
+      if (e == cudaSuccess)
+        e = launch_gridtensor(p.d_gmeta, p.n, p.max_bits, p.d_gops, angles, bits + b * p.n, p.d_grid, s);
+    } else if (i == -1) {
+      const float2* src = ref_ptr(p, p.final_ref);
+      e = launch_slicesum(src, p.final_strides.data(), int(p.tile.size()), amps + b * T * 2, s);
+      // reverse pass of this slice
+      if (e == cudaSuccess)
+        e = launch_init_cotangent(reinterpret_cast<float2*>(p.d_warena + p.w_off[size_t(final_buf)]),
+                                  p.final_strides.data(), int(p.tile.size()), g + b * T * 2, s);
+      for (int k = int(p.steps.size()) - 1; k >= 0 && e == cudaSuccess; --k) {
+        e = run_bwd(p, p.steps[size_t(k)], p.sg[size_t(k)].ga, vals, s);
+        if (e == cudaSuccess) e = run_bwd(p, p.steps[size_t(k)], p.sg[size_t(k)].gb, vals, s);
+      }
+    } else {
+      e = run_step(p, p.steps[size_t(i)], b, vals, s);
+    }
+    if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
+    return QFLEX_OK;
+  });
+  if (res == QFLEX_OK && n_bs > 0 && p.n_params > 0) {
+    cudaError_t e = launch_gridgrad(p.d_gmeta, p.n, p.max_bits, p.d_gops, angles, bits + (n_bs - 1) * p.n,
+                                    p.d_wgrid, grad, s);
+    if (e != cudaSuccess) res = fail(QFLEX_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
+  }
+  return res;
+}
+
+// Run fn(problem, stream) for every problem of a call on stream s: one
+// problem runs on s itself; several are spread round-robin over the plan's
+// worker streams, forked from s by an event and joined back to it, so that
+// independent problems overlap (and a capture of s records the whole
+// fork-join graph).
+template <class F>
+qflex_status for_each_problem(qflex_plan_s& p, cudaStream_t s, F&& fn) {
+  if (p.subs.size() == 1) return fn(0, s);
+  QF_CUDA(cudaEventRecord(p.fork_ev[0], s));
+  for (cudaStream_t w : p.workers) QF_CUDA(cudaStreamWaitEvent(w, p.fork_ev[0], 0));
+  qflex_status res = QFLEX_OK;
+  for (size_t i = 0; i < p.subs.size() && res == QFLEX_OK; ++i) res = fn(i, p.workers[i % p.workers.size()]);
+  // join every worker even after an error, so that no stream is left forked
+  for (size_t k = 0; k < p.workers.size(); ++k) {
+    QF_CUDA(cudaEventRecord(p.join_ev[k], p.workers[k]));
+    QF_CUDA(cudaStreamWaitEvent(s, p.join_ev[k], 0));
+  }
+  return res;
+}
+
+Sub* sub_of(qflex_plan p, int32_t problem) {
+  if (!p || problem < 0 || size_t(problem) >= p->subs.size()) return nullptr;
+  return p->subs[size_t(problem)].get();
+}
+
 }  // namespace
 
 extern "C" {
@@ -1265,78 +1420,117 @@ int32_t qflex_abi_version(void) { return QFLEX_ABI_VERSION; }
 
 const char* qflex_last_error(void) { return g_err.c_str(); }
 
-qflex_status qflex_plan_create(const qflex_problem* problem, qflex_precision prec, size_t ws_max, int device,
-                               qflex_plan* out) {
+qflex_status qflex_plan_create(const qflex_problem* problems, int32_t n_problems, qflex_precision prec,
+                               size_t ws_max, int device, qflex_plan* out) {
   return guarded([&]() -> qflex_status {
-    if (!problem || !out) return fail(QFLEX_ERR_ARG, "null problem or output");
+    if (!problems || !out) return fail(QFLEX_ERR_ARG, "null problems or output");
     *out = nullptr;
+    if (n_problems < 1 || n_problems > kMaxProblems)
+      return fail(QFLEX_ERR_ARG, "n_problems must be in [1, " + std::to_string(kMaxProblems) + "]");
     if (prec < QFLEX_FP32_SIMT || prec > QFLEX_FP16X3) return fail(QFLEX_ERR_ARG, "unknown precision");
-    auto p = std::make_unique<qflex_plan_s>();
-    p->prec = prec;
-    p->device = device;
-    p->tc_kind = tc_kind_of(prec);
-    p->nsplit = nsplit_of(prec);
-    if (qflex_status st = build_plan(problem, *p)) return st;
-    if (ws_max > 0 && p->total_bytes > ws_max)
-      return fail(QFLEX_ERR_PLAN, "plan needs " + std::to_string(p->total_bytes) + " bytes, budget " +
+    auto plan = std::make_unique<qflex_plan_s>();
+    plan->prec = prec;
+    plan->device = device;
+    for (int32_t i = 0; i < n_problems; ++i) {
+      auto sp = std::make_unique<Sub>();
+      sp->prec = prec;
+      sp->device = device;
+      sp->tc_kind = tc_kind_of(prec);
+      sp->nsplit = nsplit_of(prec);
+      sp->prof = &plan->prof;
+      if (qflex_status st = build_plan(&problems[i], *sp)) {
+        if (n_problems > 1) return fail(st, "problem " + std::to_string(i) + ": " + g_err);
+        return st;
+      }
+      plan->off_qubits.push_back(plan->n_qubits_total);
+      plan->off_params.push_back(plan->n_params_total);
+      plan->off_amps.push_back(plan->amps_total);
+      plan->n_qubits_total += sp->n;
+      plan->n_params_total += sp->n_params;
+      plan->amps_total += int64_t(1) << sp->tile.size();
+      plan->total_bytes += align256(sp->total_bytes);
+      plan->subs.push_back(std::move(sp));
+    }
+    if (ws_max > 0 && plan->total_bytes > ws_max)
+      return fail(QFLEX_ERR_PLAN, "plan needs " + std::to_string(plan->total_bytes) + " bytes, budget " +
                                       std::to_string(ws_max));
     if (device >= 0) {
       if (prec != QFLEX_FP32_SIMT && !tc_available())
         return fail(QFLEX_ERR_UNSUPPORTED, "tensor-map encoder unavailable in this driver");
-      if (qflex_status st = allocate(*p)) {
-        if (p->d_ws) cudaFree(p->d_ws);
-        return st;
+      QF_CUDA(cudaSetDevice(device));
+      if (cudaMalloc(&plan->d_ws, plan->total_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        plan->d_ws = nullptr;
+        return fail(QFLEX_ERR_OOM, "workspace allocation of " + std::to_string(plan->total_bytes) + " bytes failed");
+      }
+      char* c = plan->d_ws;
+      for (auto& sp : plan->subs) {
+        if (qflex_status st = allocate(*sp, c)) return st;
+        c += align256(sp->total_bytes);
+      }
+      if (n_problems > 1) {
+        const int w = std::min<int>(kMaxWorkers, n_problems);
+        plan->fork_ev.resize(1);
+        QF_CUDA(cudaEventCreateWithFlags(&plan->fork_ev[0], cudaEventDisableTiming));
+        for (int k = 0; k < w; ++k) {
+          cudaStream_t st = nullptr;
+          QF_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+          plan->workers.push_back(st);
+          cudaEvent_t ev = nullptr;
+          QF_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+          plan->join_ev.push_back(ev);
+        }
       }
     }
-    *out = p.release();
+    *out = plan.release();
     return QFLEX_OK;
   });
 }
 
 void qflex_plan_destroy(qflex_plan plan) {
   if (!plan) return;
-  if (plan->d_ws) {
-    cudaSetDevice(plan->device);
-    cudaFree(plan->d_ws);
-  }
-  if (plan->d_gws) cudaFree(plan->d_gws);
-  if (plan->gexec) cudaGraphExecDestroy(plan->gexec);
-  for (cudaEvent_t e : plan->ev_pool) cudaEventDestroy(e);
-  delete plan;
+  if (plan->device >= 0) cudaSetDevice(plan->device);
+  delete plan;   // ~qflex_plan_s frees the workspaces, graph, streams and events
 }
 
-qflex_status qflex_plan_get_info(qflex_plan p, qflex_plan_info* info) {
+qflex_status qflex_plan_get_info(qflex_plan p, int32_t problem, qflex_plan_info* info) {
   return guarded([&]() -> qflex_status {
-    if (!p || !info) return fail(QFLEX_ERR_ARG, "null argument");
-    info->n_slices = p->P;
-    info->n_qubits = p->n;
-    info->n_params = p->n_params;
-    info->n_open = int(p->tile.size());
-    info->n_steps = int(p->steps.size());
-    info->max_tensor_elems = p->max_tensor;
+    Sub* sp = sub_of(p, problem);
+    if (!sp || !info) return fail(QFLEX_ERR_ARG, "null argument or problem index out of range");
+    info->n_slices = sp->P;
+    info->n_qubits = sp->n;
+    info->n_params = sp->n_params;
+    info->n_open = int(sp->tile.size());
+    info->n_steps = int(sp->steps.size());
+    info->max_tensor_elems = sp->max_tensor;
     info->workspace_bytes = p->total_bytes;
-    info->n_tc_steps = p->n_tc;
-    info->n_persistent_buffers = p->n_persistent;
-    info->n_nonzero_slices = int64_t(p->zeros.n_nonzero());
+    info->n_tc_steps = sp->n_tc;
+    info->n_persistent_buffers = sp->n_persistent;
+    info->n_nonzero_slices = int64_t(sp->zeros.n_nonzero());
+    info->n_problems = int32_t(p->subs.size());
+    info->plane_format = sp->prec == QFLEX_FP32_SIMT ? 0 : (sp->tc_kind == 0 ? 1 : (sp->tc_kind == 1 ? 2 : 3));
+    info->problem_workspace_bytes = sp->total_bytes;
     return QFLEX_OK;
   });
 }
 
-qflex_status qflex_plan_cost(qflex_plan p, int64_t n_bs, const int64_t* ids, int64_t n_ids, qflex_cost* out) {
+qflex_status qflex_plan_cost(qflex_plan p, int32_t problem, int64_t n_bs, const int64_t* ids, int64_t n_ids,
+                             qflex_cost* out) {
   return guarded([&]() -> qflex_status {
-    if (!p || !out || n_bs < 0) return fail(QFLEX_ERR_ARG, "bad argument");
-    if (qflex_status st = check_slices(*p, ids, n_ids)) return st;
+    Sub* sp = sub_of(p, problem);
+    if (!sp || !out || n_bs < 0) return fail(QFLEX_ERR_ARG, "bad argument");
+    if (qflex_status st = check_slices(*sp, ids, n_ids)) return st;
     qflex_cost c{};
-    const double prods = p->nsplit == 2 ? 3.0 : 1.0;
+    const double prods = sp->nsplit == 2 ? 3.0 : 1.0;
     std::vector<int64_t> ob;
     std::vector<std::vector<int64_t>> ov;
-    oc_reset(*p, ob, ov);
-    qflex_status st = walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) {
+    oc_reset(*sp, ob, ov);
+    qflex_status st = walk(*sp, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) {
       if (i < 0) {
         ++c.launches;
         return QFLEX_OK;
       }
-      const Step& s = p->steps[i];
+      const Step& s = sp->steps[i];
       const double mnk = double(s.M) * double(s.N) * double(s.K);
       c.cmacs += mnk;
       c.largest_gemm_cmacs = std::max(c.largest_gemm_cmacs, mnk);
@@ -1347,12 +1541,12 @@ qflex_status qflex_plan_cost(qflex_plan p, int64_t n_bs, const int64_t* ids, int
       // operand producers that run (not in place, not a cache hit): one
       // permutation each, plus the absmax of an fp16 operand
       const bool runA = !s.A.direct && !s.A.fused &&
-                        !(s.A.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.A.cache)].dep, s.A.cache, b, vals));
+                        !(s.A.cache >= 0 && oc_hit(ob, ov, sp->opcache[size_t(s.A.cache)].dep, s.A.cache, b, vals));
       const bool runB = !s.B.direct && !s.B.fused &&
-                        !(s.B.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.B.cache)].dep, s.B.cache, b, vals));
+                        !(s.B.cache >= 0 && oc_hit(ob, ov, sp->opcache[size_t(s.B.cache)].dep, s.B.cache, b, vals));
       if (runA) c.permute_bytes += 16.0 * double(s.M) * double(s.K);
       if (runB) c.permute_bytes += 16.0 * double(s.N) * double(s.K);
-      c.launches += 1 + runA + runB + (s.tc && p->tc_kind == 2 ? int(runA) + int(runB) : 0);
+      c.launches += 1 + runA + runB + (s.tc && sp->tc_kind == 2 ? int(runA) + int(runB) : 0);
       ++c.steps_executed;
       return QFLEX_OK;
     });
@@ -1362,29 +1556,31 @@ qflex_status qflex_plan_cost(qflex_plan p, int64_t n_bs, const int64_t* ids, int
   });
 }
 
-qflex_status qflex_plan_steps(qflex_plan p, int64_t n_bs, const int64_t* ids, int64_t n_ids, qflex_step_info* out,
+qflex_status qflex_plan_steps(qflex_plan p, int32_t problem, int64_t n_bs, const int64_t* ids, int64_t n_ids,
+                              qflex_step_info* out,
                               int32_t cap, int32_t* n_steps) {
   return guarded([&]() -> qflex_status {
-    if (!p || !n_steps || n_bs < 0 || cap < 0 || (cap > 0 && !out)) return fail(QFLEX_ERR_ARG, "bad argument");
-    if (qflex_status st = check_slices(*p, ids, n_ids)) return st;
-    std::vector<int64_t> runs(p->steps.size(), 0), ab(p->steps.size(), 0), bb(p->steps.size(), 0);
+    Sub* sp = sub_of(p, problem);
+    if (!sp || !n_steps || n_bs < 0 || cap < 0 || (cap > 0 && !out)) return fail(QFLEX_ERR_ARG, "bad argument");
+    if (qflex_status st = check_slices(*sp, ids, n_ids)) return st;
+    std::vector<int64_t> runs(sp->steps.size(), 0), ab(sp->steps.size(), 0), bb(sp->steps.size(), 0);
     std::vector<int64_t> ob;
     std::vector<std::vector<int64_t>> ov;
-    oc_reset(*p, ob, ov);
-    qflex_status st = walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) {
+    oc_reset(*sp, ob, ov);
+    qflex_status st = walk(*sp, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) {
       if (i < 0) return QFLEX_OK;
-      const Step& s = p->steps[size_t(i)];
+      const Step& s = sp->steps[size_t(i)];
       ++runs[size_t(i)];
       ab[size_t(i)] += !s.A.direct && !s.A.fused &&
-                       !(s.A.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.A.cache)].dep, s.A.cache, b, vals));
+                       !(s.A.cache >= 0 && oc_hit(ob, ov, sp->opcache[size_t(s.A.cache)].dep, s.A.cache, b, vals));
       bb[size_t(i)] += !s.B.direct && !s.B.fused &&
-                       !(s.B.cache >= 0 && oc_hit(ob, ov, p->opcache[size_t(s.B.cache)].dep, s.B.cache, b, vals));
+                       !(s.B.cache >= 0 && oc_hit(ob, ov, sp->opcache[size_t(s.B.cache)].dep, s.B.cache, b, vals));
       return QFLEX_OK;
     });
     if (st) return st;
-    *n_steps = int32_t(p->steps.size());
-    for (int i = 0; i < int(p->steps.size()) && i < cap; ++i) {
-      const Step& s = p->steps[size_t(i)];
+    *n_steps = int32_t(sp->steps.size());
+    for (int i = 0; i < int(sp->steps.size()) && i < cap; ++i) {
+      const Step& s = sp->steps[size_t(i)];
       qflex_step_info& o = out[i];
       o.dst = s.dst;
       o.src = s.src;
@@ -1517,37 +1713,41 @@ constexpr int64_t kMaxListedSlices = int64_t(1) << 32;
 
 }  // namespace
 
-qflex_status qflex_select_slices(qflex_plan p, double f, uint64_t seed, int64_t* ids, int64_t cap, int64_t* n_sel) {
+qflex_status qflex_select_slices(qflex_plan p, int32_t problem, double f, uint64_t seed, int64_t* ids, int64_t cap,
+                                 int64_t* n_sel) {
   return guarded([&]() -> qflex_status {
-    if (!p || !ids || !n_sel || !(f > 0.0)) return fail(QFLEX_ERR_ARG, "bad argument");
+    Sub* sp = sub_of(p, problem);
+    if (!sp || !ids || !n_sel || !(f > 0.0)) return fail(QFLEX_ERR_ARG, "bad argument");
     std::vector<int64_t> a;
-    if (qflex_status st = shuffle_select(p->P, f, seed, cap, &a)) return st;
+    if (qflex_status st = shuffle_select(sp->P, f, seed, cap, &a)) return st;
     std::copy(a.begin(), a.end(), ids);
     *n_sel = int64_t(a.size());
     return QFLEX_OK;
   });
 }
 
-qflex_status qflex_nonzero_slices(qflex_plan p, int64_t* ids, int64_t cap, int64_t* n_nonzero) {
+qflex_status qflex_nonzero_slices(qflex_plan p, int32_t problem, int64_t* ids, int64_t cap, int64_t* n_nonzero) {
   return guarded([&]() -> qflex_status {
-    if (!p || !n_nonzero || cap < 0 || (cap > 0 && !ids)) return fail(QFLEX_ERR_ARG, "bad argument");
-    const double count = p->zeros.n_nonzero();
+    Sub* sp = sub_of(p, problem);
+    if (!sp || !n_nonzero || cap < 0 || (cap > 0 && !ids)) return fail(QFLEX_ERR_ARG, "bad argument");
+    const double count = sp->zeros.n_nonzero();
     if (count > double(kMaxListedSlices)) return fail(QFLEX_ERR_UNSUPPORTED, "too many paths to list");
     *n_nonzero = int64_t(count);
     if (cap < *n_nonzero) return fail(QFLEX_ERR_ARG, "slice_ids capacity too small");
     std::vector<int64_t> all;
-    if (!p->zeros.list(&all, kMaxListedSlices)) return fail(QFLEX_ERR_UNSUPPORTED, "too many paths to list");
+    if (!sp->zeros.list(&all, kMaxListedSlices)) return fail(QFLEX_ERR_UNSUPPORTED, "too many paths to list");
     std::copy(all.begin(), all.end(), ids);
     return QFLEX_OK;
   });
 }
 
-qflex_status qflex_select_nonzero_slices(qflex_plan p, double f, uint64_t seed, int64_t* ids, int64_t cap,
-                                         int64_t* n_sel) {
+qflex_status qflex_select_nonzero_slices(qflex_plan p, int32_t problem, double f, uint64_t seed, int64_t* ids,
+                                         int64_t cap, int64_t* n_sel) {
   return guarded([&]() -> qflex_status {
-    if (!p || !ids || !n_sel || !(f > 0.0)) return fail(QFLEX_ERR_ARG, "bad argument");
+    Sub* sp = sub_of(p, problem);
+    if (!sp || !ids || !n_sel || !(f > 0.0)) return fail(QFLEX_ERR_ARG, "bad argument");
     std::vector<int64_t> all;
-    if (!p->zeros.list(&all, kMaxListedSlices)) return fail(QFLEX_ERR_UNSUPPORTED, "too many paths to list");
+    if (!sp->zeros.list(&all, kMaxListedSlices)) return fail(QFLEX_ERR_UNSUPPORTED, "too many paths to list");
     std::vector<int64_t> a;
     if (qflex_status st = shuffle_select(int64_t(all.size()), f, seed, cap, &a)) return st;
     for (size_t k = 0; k < a.size(); ++k) ids[k] = all[size_t(a[k])];
@@ -1562,12 +1762,12 @@ qflex_status qflex_amplitudes(qflex_plan p, const double* angles, const uint8_t*
     if (!p) return fail(QFLEX_ERR_ARG, "null plan");
     if (p->device < 0) return fail(QFLEX_ERR_UNSUPPORTED, "host-only plan");
     if (n_bs < 0 || (n_bs > 0 && (!bits || !amps))) return fail(QFLEX_ERR_ARG, "bad bitstrings/output");
-    if (p->n_params > 0 && !angles) return fail(QFLEX_ERR_ARG, "angles required");
-    if (qflex_status st = check_slices(*p, ids, n_ids)) return st;
+    if (p->n_params_total > 0 && !angles) return fail(QFLEX_ERR_ARG, "angles required");
+    for (auto& sp : p->subs)
+      if (qflex_status st = check_slices(*sp, ids, n_ids)) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     QF_CUDA(cudaSetDevice(p->device));
     p->last_stream = s;
-    const int64_t T = int64_t(1) << p->tile.size();
     qflex_plan_s::GraphKey key;
     key.angles = angles;
     key.bits = bits;
@@ -1577,25 +1777,10 @@ qflex_status qflex_amplitudes(qflex_plan p, const double* angles, const uint8_t*
     key.all = ids == nullptr;
     if (ids) key.ids.assign(ids, ids + n_ids);
     return with_graph(*p, key, s, [&]() -> qflex_status {
-      QF_CUDA(cudaMemsetAsync(amps, 0, size_t(n_bs) * T * 2 * sizeof(double), s));
-      if (p->fp16_fused) QF_CUDA(cudaMemsetAsync(p->d_bmax, 0, sizeof(unsigned) * p->bufs.size(), s));
-      oc_reset(*p, p->oc_b, p->oc_v);
-      return walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) -> qflex_status {
-        cudaError_t e;
-        if (i == -2) {
-          e = timed(*p, 0, 0, 0, 8.0 * p->grid_elems, s, [&] {
-            return launch_gridtensor(p->d_gmeta, p->n, p->max_bits, p->d_gops, angles, bits + b * p->n, p->d_grid, s);
-          });
-        } else if (i == -1) {
-          const float2* src = ref_ptr(*p, p->final_ref) + ref_base(p->final_ref, vals);
-          e = timed(*p, 4, 0, 0, 40.0 * T, s, [&] {
-            return launch_slicesum(src, p->final_strides.data(), int(p->tile.size()), amps + b * T * 2, s);
-          });
-        } else {
-          e = run_step(*p, p->steps[i], b, vals, s);
-        }
-        if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
-        return QFLEX_OK;
+      return for_each_problem(*p, s, [&](size_t i, cudaStream_t ws) {
+        return enqueue_amplitudes(*p->subs[i], angles ? angles + p->off_params[i] : nullptr,
+                                  bits + n_bs * p->off_qubits[i], n_bs, ids, n_ids,
+                                  amps + 2 * n_bs * p->off_amps[i], ws);
       });
     });
   });
@@ -1607,11 +1792,23 @@ qflex_status qflex_plan_enable_gradients(qflex_plan p) {
     if (p->device < 0) return fail(QFLEX_ERR_UNSUPPORTED, "host-only plan");
     if (p->grad_ready) return QFLEX_OK;
     QF_CUDA(cudaSetDevice(p->device));
-    if (qflex_status st = build_grad(*p)) {
-      if (p->d_gws) cudaFree(p->d_gws);
-      p->d_gws = nullptr;
-      return st;
+    size_t total = 0;
+    for (auto& sp : p->subs) {
+      if (qflex_status st = build_grad(*sp)) return st;
+      total += sp->grad_bytes;
     }
+    if (cudaMalloc(&p->d_gws, total) != cudaSuccess) {
+      cudaGetLastError();
+      p->d_gws = nullptr;
+      return fail(QFLEX_ERR_OOM, "gradient workspace allocation of " + std::to_string(total) + " bytes failed");
+    }
+    p->grad_bytes = total;
+    char* c = p->d_gws;
+    for (auto& sp : p->subs) {
+      if (qflex_status st = grad_assign(*sp, c)) return st;
+      c += sp->grad_bytes;
+    }
+    p->grad_ready = true;
     return QFLEX_OK;
   });
 }
@@ -1624,13 +1821,14 @@ qflex_status qflex_amplitudes_grad(qflex_plan p, const double* angles, const uin
     if (p->device < 0) return fail(QFLEX_ERR_UNSUPPORTED, "host-only plan");
     if (!p->grad_ready) return fail(QFLEX_ERR_UNSUPPORTED, "call qflex_plan_enable_gradients first");
     if (n_bs < 0 || (n_bs > 0 && (!bits || !amps || !g))) return fail(QFLEX_ERR_ARG, "bad bitstrings/outputs");
-    if (p->n_params > 0 && (!angles || !grad)) return fail(QFLEX_ERR_ARG, "angles and grad_angles required");
-    if (p->steps.empty()) return fail(QFLEX_ERR_UNSUPPORTED, "gradients need at least one contraction step");
-    if (qflex_status st = check_slices(*p, ids, n_ids)) return st;
+    if (p->n_params_total > 0 && (!angles || !grad)) return fail(QFLEX_ERR_ARG, "angles and grad_angles required");
+    for (auto& sp : p->subs) {
+      if (sp->steps.empty()) return fail(QFLEX_ERR_UNSUPPORTED, "gradients need at least one contraction step");
+      if (qflex_status st = check_slices(*sp, ids, n_ids)) return st;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     QF_CUDA(cudaSetDevice(p->device));
     p->last_stream = s;
-    const int64_t T = int64_t(1) << p->tile.size();
     qflex_plan_s::GraphKey key;
     key.angles = angles;
     key.bits = bits;
@@ -1641,46 +1839,15 @@ qflex_status qflex_amplitudes_grad(qflex_plan p, const double* angles, const uin
     key.kind = 1;
     key.all = ids == nullptr;
     if (ids) key.ids.assign(ids, ids + n_ids);
-    p->grad_active = true;
-    const int final_buf = p->final_ref.id;
+    for (auto& sp : p->subs) sp->grad_active = true;
     qflex_status res = with_graph(*p, key, s, [&]() -> qflex_status {
-    QF_CUDA(cudaMemsetAsync(amps, 0, size_t(n_bs) * T * 2 * sizeof(double), s));
-    if (p->n_params > 0) QF_CUDA(cudaMemsetAsync(grad, 0, size_t(p->n_params) * sizeof(double), s));
-    oc_reset(*p, p->oc_b, p->oc_v);
-    qflex_status res = walk(*p, n_bs, ids, n_ids, [&](int i, int64_t b, const std::vector<int64_t>& vals) -> qflex_status {
-      cudaError_t e = cudaSuccess;
-      if (i == -2) {
-        if (b > 0 && p->n_params > 0)   // gradient of the previous bitstring
-          e = launch_gridgrad(p->d_gmeta, p->n, p->max_bits, p->d_gops, angles, bits + (b - 1) * p->n,
-                              p->d_wgrid, grad, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(p->d_wgrid, 0, size_t(p->grid_elems) * 16, s);
-        if (e == cudaSuccess)
-          e = launch_gridtensor(p->d_gmeta, p->n, p->max_bits, p->d_gops, angles, bits + b * p->n, p->d_grid, s);
-      } else if (i == -1) {
-        const float2* src = ref_ptr(*p, p->final_ref);
-        e = launch_slicesum(src, p->final_strides.data(), int(p->tile.size()), amps + b * T * 2, s);
-        // reverse pass of this slice
-        if (e == cudaSuccess)
-          e = launch_init_cotangent(reinterpret_cast<float2*>(p->d_warena + p->w_off[final_buf]),
-                                    p->final_strides.data(), int(p->tile.size()), g + b * T * 2, s);
-        for (int k = int(p->steps.size()) - 1; k >= 0 && e == cudaSuccess; --k) {
-          e = run_bwd(*p, p->steps[k], p->sg[k].ga, vals, s);
-          if (e == cudaSuccess) e = run_bwd(*p, p->steps[k], p->sg[k].gb, vals, s);
-        }
-      } else {
-        e = run_step(*p, p->steps[i], b, vals, s);
-      }
-      if (e != cudaSuccess) return fail(QFLEX_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
-      return QFLEX_OK;
+      return for_each_problem(*p, s, [&](size_t i, cudaStream_t ws) {
+        const int64_t pa = p->off_params[i], pb = n_bs * p->off_qubits[i], pc = 2 * n_bs * p->off_amps[i];
+        return enqueue_gradients(*p->subs[i], angles ? angles + pa : nullptr, bits + pb, n_bs, ids, n_ids, g + pc,
+                                 amps + pc, grad ? grad + pa : nullptr, ws);
+      });
     });
-    if (res == QFLEX_OK && n_bs > 0 && p->n_params > 0) {
-      cudaError_t e = launch_gridgrad(p->d_gmeta, p->n, p->max_bits, p->d_gops, angles, bits + (n_bs - 1) * p->n,
-                                      p->d_wgrid, grad, s);
-      if (e != cudaSuccess) res = fail(QFLEX_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
-    }
-    return res;
-    });
-    p->grad_active = false;
+    for (auto& sp : p->subs) sp->grad_active = false;
     return res;
   });
 }
@@ -1696,95 +1863,101 @@ qflex_status qflex_plan_autotune(qflex_plan p, int32_t reps, int32_t* n_shapes, 
     cudaEvent_t e0, e1;
     QF_CUDA(cudaEventCreate(&e0));
     QF_CUDA(cudaEventCreate(&e1));
-    struct Key {
-      int64_t M, N, K;
-      bool tc;
-      bool operator<(const Key& o) const {
-        return std::tie(M, N, K, tc) < std::tie(o.M, o.N, o.K, o.tc);
-      }
-    };
-    std::map<Key, std::vector<size_t>> groups;
-    for (size_t i = 0; i < p->steps.size(); ++i) {
-      const Step& st = p->steps[i];
-      groups[{st.M, st.N, st.K, st.tc}].push_back(i);
-    }
     int tuned = 0;
     double gain = 0.0;
     qflex_status res = QFLEX_OK;
-    for (auto& [key, idx] : groups) {
-      Step& st = p->steps[idx.front()];
-      float2* C = reinterpret_cast<float2*>(p->d_arena + p->bufs[st.out_buf].offset);
-      std::vector<int> cands;
-      bool fused_fp32 = false;   // CUDA-core producers writing planes keep their form
-      for (size_t i : idx) fused_fp32 = fused_fp32 || (!p->steps[i].tc && p->steps[i].fuse_out);
-      if (key.tc) cands = {128, 64};
-      else if (key.N <= 32 && !fused_fp32) cands = {1, 2};
-      else continue;
-      std::vector<TcGemmMaps> maps(cands.size());
-      float best = 1e30f, first = 0.f;
-      int best_c = -1;
-      for (size_t c = 0; c < cands.size(); ++c) {
-        if (key.tc && !tc_encode_maps(p->tc_kind, p->nsplit, cands[c], x_buf(*p, st.A, true, true), st.M,
-                                      x_buf(*p, st.B, false, true), st.N, st.K, &maps[c])) {
-          res = fail(QFLEX_ERR_CUDA, "tensor map encoding failed");
-          break;
+    for (auto& spu : p->subs) {
+      Sub* sp = spu.get();
+      struct Key {
+        int64_t M, N, K;
+        bool tc;
+        bool operator<(const Key& o) const {
+          return std::tie(M, N, K, tc) < std::tie(o.M, o.N, o.K, o.tc);
         }
-        auto launch = [&]() -> cudaError_t {
-          if (key.tc)
-            return launch_cgemm_tc(p->tc_kind, p->nsplit, cands[c], maps[c], st.M, st.N, st.K, C, p->d_status, s,
-                                   scale_word(*p, st.A, true, true), scale_word(*p, st.B, false, true),
-                                   st.fuse_out ? &st.po : nullptr);
-          // operands as the step reads them: in place when consumed directly
-          // (the scratch is only sized for produced operands), else their buffer
-          const float2* A = st.A.direct ? ref_ptr(*p, st.A.ref) : static_cast<const float2*>(op_buf(*p, st.A, true));
-          const float2* B = st.B.direct ? ref_ptr(*p, st.B.ref) : static_cast<const float2*>(op_buf(*p, st.B, false));
-          return cands[c] == 1 ? launch_cgemm_thin(st.M, st.N, st.K, A, B, C, s)
-                               : launch_cgemm_simt(st.M, st.N, st.K, A, B, C, s);
-        };
-        cudaError_t e = launch();   // warm-up
-        for (int r = 0; r < reps && e == cudaSuccess; ++r) {
-          if (r == 0) e = cudaEventRecord(e0, s);
-          if (e == cudaSuccess) e = launch();
-        }
-        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e != cudaSuccess) {
-          res = fail(QFLEX_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
-          break;
-        }
-        ms /= float(reps);
-        if (c == 0) first = ms;
-        if (ms < best) {
-          best = ms;
-          best_c = int(c);
-        }
+      };
+      std::map<Key, std::vector<size_t>> groups;
+      for (size_t i = 0; i < sp->steps.size(); ++i) {
+        const Step& st = sp->steps[i];
+        groups[{st.M, st.N, st.K, st.tc}].push_back(i);
       }
-      if (res != QFLEX_OK) break;
-      for (size_t i : idx) {
-        Step& t = p->steps[i];
-        if (key.tc) {
-          // steps of one shape may read different operand buffers (caches)
-          t.bn = cands[best_c];
-          if (!encode_step(*p, t)) {
+      for (auto& [key, idx] : groups) {
+        Step& st = sp->steps[idx.front()];
+        float2* C = reinterpret_cast<float2*>(sp->d_arena + sp->bufs[st.out_buf].offset);
+        std::vector<int> cands;
+        bool fused_fp32 = false;   // CUDA-core producers writing planes keep their form
+        for (size_t i : idx) fused_fp32 = fused_fp32 || (!sp->steps[i].tc && sp->steps[i].fuse_out);
+        if (key.tc) cands = {128, 64};
+        else if (key.N <= 32 && !fused_fp32) cands = {1, 2};
+        else continue;
+        std::vector<TcGemmMaps> maps(cands.size());
+        float best = 1e30f, first = 0.f;
+        int best_c = -1;
+        for (size_t c = 0; c < cands.size(); ++c) {
+          if (key.tc && !tc_encode_maps(sp->tc_kind, sp->nsplit, cands[c], x_buf(*sp, st.A, true, true), st.M,
+                                        x_buf(*sp, st.B, false, true), st.N, st.K, &maps[c])) {
             res = fail(QFLEX_ERR_CUDA, "tensor map encoding failed");
             break;
           }
-        } else {
-          t.fp32_kernel = cands[best_c];
+          auto launch = [&]() -> cudaError_t {
+            if (key.tc)
+              return launch_cgemm_tc(sp->tc_kind, sp->nsplit, cands[c], maps[c], st.M, st.N, st.K, C, sp->d_status, s,
+                                     scale_word(*sp, st.A, true, true), scale_word(*sp, st.B, false, true),
+                                     st.fuse_out ? &st.po : nullptr);
+            // operands as the step reads them: in place when consumed directly
+            // (the scratch is only sized for produced operands), else their buffer
+            const float2* A = st.A.direct ? ref_ptr(*sp, st.A.ref) : static_cast<const float2*>(op_buf(*sp, st.A, true));
+            const float2* B = st.B.direct ? ref_ptr(*sp, st.B.ref) : static_cast<const float2*>(op_buf(*sp, st.B, false));
+            return cands[c] == 1 ? launch_cgemm_thin(st.M, st.N, st.K, A, B, C, s)
+                                 : launch_cgemm_simt(st.M, st.N, st.K, A, B, C, s);
+          };
+          cudaError_t e = launch();   // warm-up
+          for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+            if (r == 0) e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess) e = launch();
+          }
+          if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+          if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+          float ms = 0.f;
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+          if (e != cudaSuccess) {
+            res = fail(QFLEX_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+            break;
+          }
+          ms /= float(reps);
+          if (c == 0) first = ms;
+          if (ms < best) {
+            best = ms;
+            best_c = int(c);
+          }
         }
+        if (res != QFLEX_OK) break;
+        for (size_t i : idx) {
+          Step& t = sp->steps[i];
+          if (key.tc) {
+            // steps of one shape may read different operand buffers (caches)
+            t.bn = cands[best_c];
+            if (!encode_step(*sp, t)) {
+              res = fail(QFLEX_ERR_CUDA, "tensor map encoding failed");
+              break;
+            }
+          } else {
+            t.fp32_kernel = cands[best_c];
+          }
+        }
+        ++tuned;
+        gain += double(first - best) * double(idx.size());
       }
-      ++tuned;
-      gain += double(first - best) * double(idx.size());
+      if (res != QFLEX_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(s);
     if (res != QFLEX_OK) return res;
-    int32_t w = 0;
-    QF_CUDA(cudaMemcpy(&w, p->d_status, sizeof(w), cudaMemcpyDeviceToHost));
-    if (w) return fail(QFLEX_ERR_DEVICE_TIMEOUT, "a bounded device-side wait ran out during autotuning");
+    for (auto& spu : p->subs) {
+      int32_t w = 0;
+      QF_CUDA(cudaMemcpy(&w, spu->d_status, sizeof(w), cudaMemcpyDeviceToHost));
+      if (w) return fail(QFLEX_ERR_DEVICE_TIMEOUT, "a bounded device-side wait ran out during autotuning");
+    }
     if (p->gexec) {   // cached graph holds the old configuration
       cudaGraphExecDestroy(p->gexec);
       p->gexec = nullptr;
@@ -1813,34 +1986,34 @@ qflex_status qflex_plan_profile(qflex_plan p, int32_t mode, qflex_profile* out) 
     if (!p) return fail(QFLEX_ERR_ARG, "null plan");
     if (p->device < 0) return fail(QFLEX_ERR_UNSUPPORTED, "host-only plan");
     QF_CUDA(cudaSetDevice(p->device));
+    Prof& pr = p->prof;
     auto drain = [&]() -> qflex_status {
-      if (p->recs.empty()) return QFLEX_OK;
-      QF_CUDA(cudaEventSynchronize(p->ev_pool[p->recs.back().e0 + 1]));
-      for (const auto& r : p->recs) {
+      for (const auto& r : pr.recs) {   // pairs may sit on several streams
+        QF_CUDA(cudaEventSynchronize(pr.pool[r.e0 + 1]));
         float ms = 0.f;
-        QF_CUDA(cudaEventElapsedTime(&ms, p->ev_pool[r.e0], p->ev_pool[r.e0 + 1]));
-        p->prof.launches[r.cls] += 1;
-        p->prof.ms[r.cls] += ms;
-        p->prof.flops[r.cls] += r.flops;
-        p->prof.mma_flops[r.cls] += r.mma;
-        p->prof.bytes[r.cls] += r.bytes;
+        QF_CUDA(cudaEventElapsedTime(&ms, pr.pool[r.e0], pr.pool[r.e0 + 1]));
+        pr.tot.launches[r.cls] += 1;
+        pr.tot.ms[r.cls] += ms;
+        pr.tot.flops[r.cls] += r.flops;
+        pr.tot.mma_flops[r.cls] += r.mma;
+        pr.tot.bytes[r.cls] += r.bytes;
       }
-      p->recs.clear();
-      p->ev_used = 0;
+      pr.recs.clear();
+      pr.used = 0;
       return QFLEX_OK;
     };
     if (mode < 0 || mode > 31) return fail(QFLEX_ERR_ARG, "mode must be a class mask in [0, 31]");
     if (mode != 0) {
       if (qflex_status st = drain()) return st;
-      p->prof = qflex_profile{};
-      p->profiling = true;
-      p->prof_mask = mode;
+      pr.tot = qflex_profile{};
+      pr.on = true;
+      pr.mask = mode;
     } else {
-      p->profiling = false;
+      pr.on = false;
     }
     if (out) {
       if (qflex_status st = drain()) return st;
-      *out = p->prof;
+      *out = pr.tot;
     }
     return QFLEX_OK;
   });
@@ -1853,12 +2026,14 @@ qflex_status qflex_plan_sync(qflex_plan p) {
     QF_CUDA(cudaSetDevice(p->device));
     QF_CUDA(cudaStreamSynchronize(p->last_stream));
     int32_t w = 0;
-    QF_CUDA(cudaMemcpy(&w, p->d_status, sizeof(w), cudaMemcpyDeviceToHost));
-    if (w) {
-      QF_CUDA(cudaMemset(p->d_status, 0, sizeof(int32_t)));
-      if (w & kDevTimeout) return fail(QFLEX_ERR_DEVICE_TIMEOUT, "a bounded device-side wait ran out");
-      return fail(QFLEX_ERR_PLAN, "internal: a fused epilogue destination fell outside its operand planes");
+    for (auto& sp : p->subs) {
+      int32_t v = 0;
+      QF_CUDA(cudaMemcpy(&v, sp->d_status, sizeof(v), cudaMemcpyDeviceToHost));
+      if (v) QF_CUDA(cudaMemset(sp->d_status, 0, sizeof(int32_t)));
+      w |= v;
     }
+    if (w & kDevTimeout) return fail(QFLEX_ERR_DEVICE_TIMEOUT, "a bounded device-side wait ran out");
+    if (w) return fail(QFLEX_ERR_PLAN, "internal: a fused epilogue destination fell outside its operand planes");
     return QFLEX_OK;
   });
 }

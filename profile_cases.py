@@ -1,6 +1,6 @@
 """Small single-purpose workloads for kernel profiling (ncu) of the hot path.
 
-    python -m paper_1811_09599_gb300.profile_cases <case>
+    python profile_cases.py <case>          (from the repository root)
 
 Each case runs its kernel three times on cuda:0 (so `ncu -s 1 -c 1` captures
 a warm launch) and prints "<case> ok".  Cases:
@@ -21,10 +21,13 @@ from __future__ import annotations
 
 import sys
 
+import os
+
 import numpy as np
 import torch
 
-from . import api
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+from paper_1811_09599_gb300 import api  # noqa: E402
 
 
 def main(case: str) -> None:

@@ -29,7 +29,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_abi_version(lib):
-    assert lib.qflex_abi_version() == 1
+    assert lib.qflex_abi_version() == 2
 
 
 @pytest.fixture
@@ -240,11 +240,11 @@ def test_nonzero_slices_match_oracle(Plan):
     import ctypes as C
     p = Plan(_constrained_problems()[1], "fp32", device=-1)
     n = C.c_int64()
-    assert p.lib.qflex_nonzero_slices(p.handle, None, 0, C.byref(n)) != 0   # capacity too small
+    assert p.lib.qflex_nonzero_slices(p.handle, 0, None, 0, C.byref(n)) != 0   # capacity too small
     assert n.value == p.info()["n_nonzero_slices"] < p.n_slices
     with pytest.raises(QFlexError, match="ARG"):
         from paper_1811_09599_gb300._lib import check
-        check(p.lib.qflex_nonzero_slices(p.handle, None, 0, None))
+        check(p.lib.qflex_nonzero_slices(p.handle, 0, None, 0, None))
 
 
 def test_vanishing_paths_are_skipped_in_the_schedule(Plan):
@@ -328,3 +328,55 @@ def test_cost_replay_matches_the_plain_count(Plan, api_mod):
     for prob in (c2_problem(0), rot, searched):
         p = Plan(prob, "bf16x3", device=-1)
         assert p.cost(1)["cmacs"] == _plain_work(prob)
+
+
+def test_multi_problem_plan_matches_single_plans(Plan):
+    """qflex_plan_create over several problems (uneven rotation circuits,
+    two grids with cuts and tiles): each problem's info, cost and schedule
+    equal those of a plan of that problem alone; the flat-array layout of a
+    call follows the problems' sizes; a bad problem index is an argument
+    error and a bad problem is reported by its index."""
+    from paper_1811_09599_gb300._lib import QFlexError
+    from qflex_inputs import grid_problem, rotation_batch
+    probs = rotation_batch(6, 3) + [grid_problem(4, 5, 32, 5, r0=2, c0=2, cuts=True, tile_rows=2, tile_cols=2),
+                                   c2_problem(0)]
+    multi = Plan(probs, "bf16x3", device=-1)
+    assert multi.n_problems == len(probs)
+    tot = 0
+    for k, pr in enumerate(probs):
+        one = Plan(pr, "bf16x3", device=-1)
+        a, b = multi.info(k), one.info()
+        assert a["n_problems"] == len(probs) and b["n_problems"] == 1
+        for key in ("n_slices", "n_qubits", "n_params", "n_open", "n_steps", "max_tensor_elems", "n_tc_steps",
+                    "n_nonzero_slices", "plane_format"):
+            assert a[key] == b[key], (k, key)
+        assert a["problem_workspace_bytes"] == b["workspace_bytes"]
+        tot += b["workspace_bytes"]
+        assert multi.cost(2, None, k) == one.cost(2)
+        assert multi.steps(2, None, k) == one.steps(2)
+    assert multi.info(0)["workspace_bytes"] >= tot
+    lay = multi.layout(3)
+    assert lay["bits"][-1] == 3 * sum(p.n for p in probs)
+    assert lay["params"][-1] == sum(p.circuit.n_params for p in probs)
+    assert lay["amps"][-1] == 3 * sum(1 << len(p.open_tile) for p in probs)
+    with pytest.raises(QFlexError, match="ARG"):
+        multi.info(len(probs))
+    bad = grid_problem(3, 3, 8, 1, cuts=False, tile_rows=0)
+    bad.ordering = bad.ordering[:-1]                       # does not contract to one tensor
+    with pytest.raises(QFlexError, match="problem 2"):
+        Plan(probs[:2] + [bad], "fp32", device=-1)
+
+
+def test_bf16x3_plane_format_by_chain_length(Plan):
+    """QFLEX_BF16X3 keeps bf16 planes up to 36 tensor-core steps (the 7x7
+    depth-32 region plan) and stores longer chains (7x7 depth 40, the
+    70-qubit diamond) as scaled fp16 planes; the other precisions keep theirs."""
+    from qflex_inputs import c4_problem, diamond_problem
+    fmt = lambda pr, prec: Plan(pr, prec, device=-1).info()
+    c2, c4, d = fmt(c2_problem(0), "bf16x3"), fmt(c4_problem(0), "bf16x3"), fmt(diamond_problem(32, 0), "bf16x3")
+    assert (c2["n_tc_steps"], c2["plane_format"]) == (36, 2)
+    assert c4["n_tc_steps"] > 36 and c4["plane_format"] == 3
+    assert d["n_tc_steps"] > 36 and d["plane_format"] == 3
+    assert fmt(diamond_problem(32, 0), "tf32x3")["plane_format"] == 1
+    assert fmt(diamond_problem(32, 0), "fp16x3")["plane_format"] == 3
+    assert fmt(c2_problem(0), "fp32")["plane_format"] == 0
