@@ -78,12 +78,6 @@ def frugal_sample(amps: np.ndarray, n_qubits: int, M: float, seed: int) -> np.nd
     return out
 
 
-def norm_estimate(amps: np.ndarray, n_qubits: int) -> float:
-    """Estimated <psi~|psi~> from a sample of amplitudes: 2^n * mean |a|^2."""
-    a = np.asarray(amps).reshape(-1)
-    return float((2.0 ** n_qubits) * np.mean(np.abs(a) ** 2))
-
-
 def overlap_fidelity(psi_exact: np.ndarray, psi_partial: np.ndarray) -> float:
     """|<psi|psi~>|^2 / <psi~|psi~> (Eq. fidelity_1 / fidelity_2)."""
     a = np.asarray(psi_exact).reshape(-1)

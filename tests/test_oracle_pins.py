@@ -439,6 +439,29 @@ def test_all_slices_give_unit_norm_and_fraction_norm_is_reported():
     assert 0.0 < nrm < 1.0                           # norm ~ f; value is reported, not gated
     f = SEL.overlap_fidelity(full, part)
     assert 0.0 < f <= 1.0 + 1e-12
+    assert abs(SEL.overlap_fidelity(full, full) - 1.0) < 1e-12   # all paths: fidelity 1
+
+
+def test_overlap_fidelity_closed_forms():
+    """Eq. fidelity_1 / fidelity_2 (Methods, "Summing a fraction of the
+    paths"): F = |<psi|psi~>|^2 / <psi~|psi~>.  Hand cases: the uniform
+    2-qubit state and its partial sum over two basis states give F = 1/2
+    (<psi|psi~> = 1/2, <psi~|psi~> = 1/2); a state split into P orthogonal
+    parts of equal weight, summed over k of them, gives F = k / P exactly;
+    a global phase on either side leaves F unchanged."""
+    psi = np.full(4, 0.5, dtype=np.complex128)
+    part = np.array([0.5, 0.5, 0.0, 0.0], dtype=np.complex128)
+    assert abs(SEL.overlap_fidelity(psi, part) - 0.5) < 1e-15
+    assert abs(SEL.overlap_fidelity(psi * 1j, part * np.exp(0.3j)) - 0.5) < 1e-15
+    rng = np.random.default_rng(4)
+    P, n = 8, 64
+    parts = np.zeros((P, n), dtype=np.complex128)
+    for s in range(P):                            # disjoint supports: orthogonal parts
+        v = rng.normal(size=n // P) + 1j * rng.normal(size=n // P)
+        parts[s, s * (n // P):(s + 1) * (n // P)] = v / np.linalg.norm(v) / np.sqrt(P)
+    full = parts.sum(axis=0)
+    for k in (1, 3, 8):
+        assert abs(SEL.overlap_fidelity(full, parts[:k].sum(axis=0)) - k / P) < 1e-12
 
 
 def test_frugal_sampling_acceptance_closed_form():
