@@ -30,7 +30,8 @@ def test_rotation_batch_one_call_equals_separate_plans(api, prec):
     amplitude and every angle gradient each, in one qflex_amplitudes_grad
     call (direct, captured, replayed): amplitudes bit for bit those of one
     plan per circuit, gradients equal up to the order of their FP64 atomic
-    sums, two circuits against the state-vector adjoint."""
+    sums, the first two circuits of at most 20 qubits against the
+    state-vector adjoint."""
     probs = rotation_batch(24, 0)
     bits = [random_bitstrings(p.n, 1, 5000 + i) for i, p in enumerate(probs)]
     flat_bits = torch.from_numpy(np.concatenate([b.reshape(-1) for b in bits])).cuda()
@@ -47,6 +48,8 @@ def test_rotation_batch_one_call_equals_separate_plans(api, prec):
     multi.sync()
     amps, grad = amps.cpu().numpy(), grad.cpu().numpy()
     lay = multi.layout(1)
+    small = [k for k, p in enumerate(probs) if p.n <= 20][:2]   # state vectors of at most 2^20 entries
+    assert len(small) == 2
     for k, p in enumerate(probs):
         one = api.Plan(p, prec, device=0)
         a1, g1 = one.amplitudes_grad(torch.from_numpy(bits[k]).cuda(), torch.from_numpy(p.circuit.angles).cuda(),
@@ -56,7 +59,7 @@ def test_rotation_batch_one_call_equals_separate_plans(api, prec):
         assert np.array_equal(amps[lay["amps"][k]:lay["amps"][k + 1]], a1), k
         gk = grad[lay["params"][k]:lay["params"][k + 1]]
         assert np.max(np.abs(gk - g1)) <= 1e-12 * np.max(np.abs(g1)), k
-        if k < 2:
+        if k in small:
             ref = SV.amplitudes(p.circuit, bits[k], [])
             assert amp_error(a1, ref, p.n) < TOL[prec]
             gref = GR.statevector_adjoint(p.circuit, bits[k], [], np.ones((1, 1), dtype=np.complex128))
