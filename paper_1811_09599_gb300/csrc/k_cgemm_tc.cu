@@ -89,16 +89,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
       : "memory");
 }
-// L2 prefetch of the tile a later pipeline stage will load (no shared-memory
-// destination, no completion to wait for): the loads of a stage then find
-// their data in L2 instead of DRAM, which keeps more bytes in flight per SM
-// than the shared-memory stages alone hold.
-__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
-  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
-                   reinterpret_cast<uint64_t>(map)),
-               "r"(x), "r"(y)
-               : "memory");
-}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -167,7 +157,6 @@ struct Cfg {
   static_assert(SMEM <= 232448, "shared memory per CTA");
 };
 constexpr int KB_CHUNK = 8;      // k-blocks accumulated in TMEM before promotion to registers
-constexpr int PF_AHEAD = 4;      // stages prefetched into L2 beyond the shared-memory stages
 constexpr int EPI_WARPS = 8;
 
 // Tile order of the persistent walk: groups of TILE_GROUP row blocks, each
@@ -316,24 +305,6 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_b)) : "memory");
       int i = 0;
       bool ok = true;
-      // stage j of this CTA's sequence (tile, chunk, part, k-block) -> L2
-      // prefetch of its A and B tiles, PF_AHEAD stages beyond the loads
-      const int64_t per_tile = 3 * int64_t(nkb);
-      const int64_t my_stages = blockIdx.x < n_tiles ? ((n_tiles - 1 - blockIdx.x) / gridDim.x + 1) * per_tile : 0;
-      auto prefetch = [&](int64_t j) {
-        if (j >= my_stages) return;
-        const int64_t t = blockIdx.x + (j / per_tile) * gridDim.x;
-        const int r = int(j % per_tile);
-        const int c = r / (3 * KB_CHUNK), kb0 = c * KB_CHUNK, len = min(nkb, kb0 + KB_CHUNK) - kb0;
-        const int part = (r - 3 * kb0) / len, kb = kb0 + (r - 3 * kb0) % len;
-        int64_t pm0, pn0;
-        tile_origin<BN>(t, n_mt, n_nt, &pm0, &pn0);
-        for (int sp = 0; sp < NSPLIT; ++sp) {
-          tma_prefetch_2d(&map_a, kb * BK, int((part * NSPLIT + sp) * M + pm0));
-          tma_prefetch_2d(&map_b, kb * BK, int((part * NSPLIT + sp) * N + pn0));
-        }
-      };
-      for (int64_t j = 0; j < PF_AHEAD; ++j) prefetch(G::NSTAGE + j);
       for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
       int64_t m0, n0;
       tile_origin<BN>(tile, n_mt, n_nt, &m0, &n0);
@@ -341,7 +312,6 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
         const int kb0 = c * KB_CHUNK, kb1 = min(nkb, kb0 + KB_CHUNK);
         for (int part = 0; part < 3 && ok; ++part) {
           for (int kb = kb0; kb < kb1; ++kb, ++i) {
-            prefetch(int64_t(i) + G::NSTAGE + PF_AHEAD);
             const int s = i % G::NSTAGE;
             const uint32_t ph = (i / G::NSTAGE) & 1;
             if (!mbar_wait(smem_u32(&bars[G::NSTAGE + s]), ph ^ 1, abort_flag, status)) {
