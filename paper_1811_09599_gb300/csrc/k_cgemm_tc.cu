@@ -157,16 +157,6 @@ struct Cfg {
   static_assert(SMEM <= 232448, "shared memory per CTA");
 };
 constexpr int KB_CHUNK = 8;      // k-blocks accumulated in TMEM before promotion to registers
-// Order of the (part, k-block) stages of a chunk, rotated by the tile index:
-// the parts start at part tile % 3 and the k-blocks at (tile / 3) % length,
-// so that CTAs working at the same time on tiles of one column block (all
-// of them when N is one or two tiles wide, as in the region absorbs) read
-// different planes and k-blocks of B instead of the same L2 lines.  The sum
-// of a part's k-blocks and of the parts is the same in any order (up to FP32
-// rounding, fixed per tile).
-constexpr bool kRotate = true;
-__device__ __forceinline__ int part_rot(int64_t tile) { return kRotate ? int(tile % 3) : 0; }
-__device__ __forceinline__ int kb_rot(int64_t tile, int len) { return kRotate ? int((tile / 3) % len) : 0; }
 constexpr int EPI_WARPS = 8;
 
 // Tile order of the persistent walk: groups of TILE_GROUP row blocks, each
@@ -319,12 +309,9 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
       int64_t m0, n0;
       tile_origin<BN>(tile, n_mt, n_nt, &m0, &n0);
       for (int c = 0; c < nchunk && ok; ++c) {
-        const int kb0 = c * KB_CHUNK, len = min(nkb, kb0 + KB_CHUNK) - kb0;
-        const int prot = part_rot(tile), krot = kb_rot(tile, len);
-        for (int pi = 0; pi < 3 && ok; ++pi) {
-          const int part = (pi + prot) % 3;
-          for (int ki = 0; ki < len; ++ki, ++i) {
-            const int kb = kb0 + (ki + krot) % len;
+        const int kb0 = c * KB_CHUNK, kb1 = min(nkb, kb0 + KB_CHUNK);
+        for (int part = 0; part < 3 && ok; ++part) {
+          for (int kb = kb0; kb < kb1; ++kb, ++i) {
             const int s = i % G::NSTAGE;
             const uint32_t ph = (i / G::NSTAGE) & 1;
             if (!mbar_wait(smem_u32(&bars[G::NSTAGE + s]), ph ^ 1, abort_flag, status)) {
@@ -357,17 +344,15 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
       for (int c = 0; c < nchunk && ok; ++c, ++cg) {
-        const int kb0 = c * KB_CHUNK, len = min(nkb, kb0 + KB_CHUNK) - kb0;
-        const int prot = part_rot(tile);
-        for (int pi = 0; pi < 3 && ok; ++pi) {
-          const int part = (pi + prot) % 3;
+        const int kb0 = c * KB_CHUNK, kb1 = min(nkb, kb0 + KB_CHUNK);
+        for (int part = 0; part < 3 && ok; ++part) {
           if (cg > 0 && !mbar_wait(smem_u32(&acc_empty[part]), (cg - 1) & 1, abort_flag, status)) {
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t d = tmem + uint32_t(part * BN);
-          for (int ki = 0; ki < len; ++ki, ++i) {
+          for (int kb = kb0; kb < kb1; ++kb, ++i) {
             const int s = i % G::NSTAGE;
             const uint32_t ph = (i / G::NSTAGE) & 1;
             if (!mbar_wait(smem_u32(&bars[s]), ph, abort_flag, status)) {
@@ -384,7 +369,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
               for (int ks = 0; ks < BK / MMA_K; ++ks) {
                 const uint64_t adesc = smem_desc(sa + ai * G::A_TILE + ks * 32);
                 const uint64_t bdesc = smem_desc(sb + bi * G::B_TILE + ks * 32);
-                mma<KIND>(d, adesc, bdesc, IDESC, (ki | pr | ks) != 0 ? 1u : 0u);
+                mma<KIND>(d, adesc, bdesc, IDESC, ((kb - kb0) | pr | ks) != 0 ? 1u : 0u);
               }
             }
             tc_commit(smem_u32(&bars[G::NSTAGE + s]));
@@ -425,18 +410,12 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
 #pragma unroll
       for (int j = 0; j < G::HALF; ++j) re[j] = im[j] = 0.f;
       for (int c = 0; c < nchunk && ok; ++c, ++cg) {
-        const int prot = part_rot(tile);
-        for (int pi = 0; pi < 3; ++pi) {
-          const int part = (pi + prot) % 3;
+        for (int part = 0; part < 3; ++part) {
           if (!mbar_wait(smem_u32(&acc_full[part]), cg & 1, abort_flag, status)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          // Re += T1 - T2, Im += T3 - T1 - T2: coefficients of this part
-          // (fmaf with +-1 or 0 is the exact add, subtract or no-op)
-          const float cr = part == 0 ? 1.f : (part == 1 ? -1.f : 0.f);
-          const float ci = part == 2 ? 1.f : -1.f;
 #pragma unroll
           for (int sub = 0; sub < G::HALF / 32; ++sub) {
             uint32_t r[32];
@@ -445,8 +424,15 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               const float t = __uint_as_float(r[j]);
-              re[sub * 32 + j] = fmaf(cr, t, re[sub * 32 + j]);
-              im[sub * 32 + j] = fmaf(ci, t, im[sub * 32 + j]);
+              if (part == 0) {
+                re[sub * 32 + j] += t;
+                im[sub * 32 + j] -= t;
+              } else if (part == 1) {
+                re[sub * 32 + j] -= t;
+                im[sub * 32 + j] -= t;
+              } else {
+                im[sub * 32 + j] += t;
+              }
             }
           }
           tc_fence_before();
