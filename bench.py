@@ -511,15 +511,23 @@ def bris70_run(api, torch, precision, local, searched=False):
 
 
 def c4_subset(api, torch, precision, local):
-    """7x7 depth 1+40+1 (bond dimension 32, 2^15-sized GEMMs): the split form
+    """7x7 depth 1+40+1 (bond dimension 32, 2^15-sized GEMMs): the split forms
     against plain FP32 on the first two slices of one bitstring (the paper
-    also times a few paths and extrapolates).  The FP64 oracle cannot contract
-    a slice of this size in reasonable time, so the error is stated against
-    the FP32 result."""
+    also times a few paths and extrapolates), and every precision's error
+    against the FP64 oracle's amplitudes of the same two paths, stored in
+    tests/golden/c4_slices.json by tests/golden/make_c4_golden.py."""
     from qflex_inputs import c4_problem
     prob = c4_problem(0)
-    bits = torch.from_numpy(random_bitstrings(prob.n, 1, 2000)).cuda()
+    bits_np = random_bitstrings(prob.n, 1, 2000)
+    bits = torch.from_numpy(bits_np).cuda()
     subset = [0, 1]
+    gold = None
+    gpath = os.path.join(ROOT, "tests", "golden", "c4_slices.json")
+    if os.path.exists(gpath):
+        g = json.load(open(gpath))
+        if g["bits"] == [int(x) for x in bits_np[0]] and sorted(g["paths"]) == ["0", "1"]:
+            gold = np.concatenate([np.array(g["paths"][k]["re"]) + 1j * np.array(g["paths"][k]["im"])
+                                   for k in ("0", "1")])
     out = {"subset": "1 bitstring x slices 0,1 of 1024 (one AB, two ABD of 2^15 x 2^15 x 2^15)",
            "note": "plain bf16 (one product, 8-bit operands) is reported, not gated"}
     res = {}
@@ -537,6 +545,9 @@ def c4_subset(api, torch, precision, local):
         res[prec] = amp.cpu().numpy()
         out[f"{prec}_ms"] = ms
         out[f"{prec}_tflops_cgemm"] = cost["cmacs"] * 8 / (ms * 1e-3) / 1e12
+        out[f"{prec}_plane_format"] = plan.info()["plane_format"]
+        if gold is not None:   # the sum over the two paths against the oracle's
+            out[f"{prec}_err_vs_oracle"] = amp_error(res[prec], gold[:64] + gold[64:], prob.n, 2.0 / 1024)
         plan.close()
         del plan
         torch.cuda.empty_cache()
