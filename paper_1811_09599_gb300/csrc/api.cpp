@@ -150,6 +150,7 @@ struct Step {
   std::vector<int> out_legs;
   std::vector<int> ml, nl, sh;   // free legs of dst, free legs of src, contracted legs
   TcGemmMaps maps{};
+  unsigned* tmax = nullptr;      // CUDA-core producer of fp16 planes: largest parts of its A and B
 };
 
 // One GEMM of the reverse pass, C'[m][n] = sum_k X[m][k] Y[n][k], followed by
@@ -432,8 +433,9 @@ int64_t leg_product(const std::vector<int>& legs, const std::vector<int64_t>& di
 // the scatter stays coalesced).  fp16 planes need a power-of-two scale
 // before the first entry is written, so the producer takes it from a bound
 // of its output's entries (3 K max_a max_b, TcPlaneOut) instead of their
-// measured maximum; only tensor-core producers track the maxima these bounds
-// use, so CUDA-core producers do not write fp16 planes.
+// measured maximum; tensor-core producers track the maxima of the planes
+// they write, and a CUDA-core producer of fp16 planes measures those of its
+// complex64 operands right before its product.
 void plan_fusion(Sub& p) {
   if (p.prec == QFLEX_FP32_SIMT) return;
   const int bytes = 3 * p.nsplit * (p.tc_kind == 0 ? 4 : 2);
@@ -460,7 +462,7 @@ void plan_fusion(Sub& p) {
       Step& pi = p.steps[size_t(i)];
       // producers: tensor-core steps, and CUDA-core steps that take the
       // pipelined thin form (it has a plane-output variant)
-      const bool thin_prod = !pi.tc && pi.fp32_kernel != 2 && thin_pipelined(pi.M, pi.N, pi.K) && p.tc_kind != 2;
+      const bool thin_prod = !pi.tc && pi.fp32_kernel != 2 && thin_pipelined(pi.M, pi.N, pi.K);
       if ((!pi.tc && !thin_prod) || pi.fuse_out) continue;
       // the operand's layout: target legs row-major
       std::vector<int> target = w == 0 ? k.ml : k.nl;
@@ -884,7 +886,8 @@ qflex_status build_plan(const qflex_problem* pr, Sub& p) {
                   align256(p.opcache_bytes) +
                   align256(sizeof(GridQubitMeta) * n) + align256(sizeof(int2) * std::max<size_t>(1, p.gops.size())) +
                   256 /* status word */ + 768 /* fp16 scale slots: A, B, one per cache */ +
-                  align256(sizeof(unsigned) * 2 * std::max<size_t>(1, p.bufs.size())) /* fused fp16 words */;
+                  align256(sizeof(unsigned) * 2 * std::max<size_t>(1, p.bufs.size())) /* fused fp16 words */ +
+                  align256(sizeof(unsigned) * 2 * std::max<size_t>(1, p.steps.size())) /* thin fp16 producers */;
   static_assert((2 + kMaxOpCache) * sizeof(unsigned) <= 768, "fp16 scale slots");
   return QFLEX_OK;
 }
@@ -914,6 +917,9 @@ qflex_status allocate(Sub& p, char* base) {
   p.d_bscale = reinterpret_cast<unsigned*>(c);
   p.d_bmax = p.d_bscale + std::max<size_t>(1, p.bufs.size());
   QF_CUDA(cudaMemset(p.d_bscale, 0, sizeof(unsigned) * 2 * std::max<size_t>(1, p.bufs.size())));
+  c += align256(sizeof(unsigned) * 2 * std::max<size_t>(1, p.bufs.size()));
+  unsigned* d_tmax = reinterpret_cast<unsigned*>(c);
+  for (size_t i = 0; i < p.steps.size(); ++i) p.steps[i].tmax = d_tmax + 2 * i;
   QF_CUDA(cudaMemcpy(p.d_gmeta, p.gmeta.data(), sizeof(GridQubitMeta) * p.n, cudaMemcpyHostToDevice));
   if (!p.gops.empty())
     QF_CUDA(cudaMemcpy(p.d_gops, p.gops.data(), sizeof(int2) * p.gops.size(), cudaMemcpyHostToDevice));
@@ -923,8 +929,13 @@ qflex_status allocate(Sub& p, char* base) {
     if (s.fuse_out && p.tc_kind == 2) {
       s.po.out_scale = p.d_bscale + s.out_buf;
       s.po.out_max = p.d_bmax + s.out_buf;
-      s.po.max_a = s.A.fused ? p.d_bmax + s.A.ref.id : p.d_smax + op_slot(s.A, true);
-      s.po.max_b = s.B.fused ? p.d_bmax + s.B.ref.id : p.d_smax + op_slot(s.B, false);
+      if (s.tc) {
+        s.po.max_a = s.A.fused ? p.d_bmax + s.A.ref.id : p.d_smax + op_slot(s.A, true);
+        s.po.max_b = s.B.fused ? p.d_bmax + s.B.ref.id : p.d_smax + op_slot(s.B, false);
+      } else {   // complex64 operands: their maxima are taken right before the product
+        s.po.max_a = s.tmax;
+        s.po.max_b = s.tmax + 1;
+      }
     }
     if (!s.tc) continue;
     if (!encode_step(p, s)) return fail(QFLEX_ERR_CUDA, "tensor map encoding failed (driver entry point missing?)");
@@ -1043,7 +1054,14 @@ cudaError_t run_step(Sub& p, const Step& st, int64_t b, const std::vector<int64_
     });
   const bool thin = st.fp32_kernel == 1 || (st.fp32_kernel == 0 && st.N <= 32);
   return timed(p, 2, 8.0 * mnk, 0, gbytes, s, [&] {
-    if (st.fuse_out && fused_mode) return launch_cgemm_thin_planes(st.M, st.N, st.K, A, B, st.po, s);
+    if (st.fuse_out && fused_mode) {
+      if (p.tc_kind == 2) {   // fp16 planes: the bound needs the largest parts of A and B
+        cudaError_t e2 = launch_absmax(A, st.M * st.K, st.tmax, s);
+        if (e2 == cudaSuccess) e2 = launch_absmax(B, st.N * st.K, st.tmax + 1, s);
+        if (e2 != cudaSuccess) return e2;
+      }
+      return launch_cgemm_thin_planes(st.M, st.N, st.K, A, B, st.po, s);
+    }
     return thin ? launch_cgemm_thin(st.M, st.N, st.K, A, B, C, s) : launch_cgemm_simt(st.M, st.N, st.K, A, B, C, s);
   });
 }
@@ -1546,7 +1564,8 @@ qflex_status qflex_plan_cost(qflex_plan p, int32_t problem, int64_t n_bs, const 
                         !(s.B.cache >= 0 && oc_hit(ob, ov, sp->opcache[size_t(s.B.cache)].dep, s.B.cache, b, vals));
       if (runA) c.permute_bytes += 16.0 * double(s.M) * double(s.K);
       if (runB) c.permute_bytes += 16.0 * double(s.N) * double(s.K);
-      c.launches += 1 + runA + runB + (s.tc && sp->tc_kind == 2 ? int(runA) + int(runB) : 0);
+      c.launches += 1 + runA + runB + (s.tc && sp->tc_kind == 2 ? int(runA) + int(runB) : 0) +
+                    (!s.tc && s.fuse_out && sp->tc_kind == 2 ? 2 : 0);
       ++c.steps_executed;
       return QFLEX_OK;
     });

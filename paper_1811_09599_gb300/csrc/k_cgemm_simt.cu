@@ -250,6 +250,16 @@ __global__ void __launch_bounds__(256) k_cgemm_thin2(int64_t M, int N, int K, co
                                                     const float2* __restrict__ B, float2* __restrict__ C,
                                                     const __grid_constant__ TcPlaneOut po) {
   pdl_wait();
+  // fp16 planes: the scale of the bound 3 K max|A| max|B| of the entries
+  // (TcPlaneOut), stored once for the consumer
+  float po_scale = 1.f;
+  if constexpr (PO) {
+    if (po.fmt == kFmtFP16) {
+      const unsigned bb = __float_as_uint(3.f * float(K) * __uint_as_float(*po.max_a) * __uint_as_float(*po.max_b));
+      if (blockIdx.x == 0 && threadIdx.x == 0) *po.out_scale = bb;
+      po_scale = fp16_scale_of(bb);
+    }
+  }
   extern __shared__ __align__(16) float2 sm2[];
   constexpr int LD = KC + 2;                      // padded row (float2), 16-byte multiple
   float2* Bt = sm2;                               // [K][16]
@@ -315,10 +325,14 @@ __global__ void __launch_bounds__(256) k_cgemm_thin2(int64_t M, int N, int K, co
       const int64_t gm = (blockIdx.x + (u / nch) * gridDim.x) * T2_RT + row;
       if constexpr (PO) {
         // the next step's operand planes at the bit-permuted positions
+        float mx = 0.f;   // largest part written (fp16 planes: for later bounds)
         if (gm < M) {
           float2 o[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) o[j] = make_float2(P[j].x - Q[j].y, P[j].y + Q[j].x);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (cq * 4 + j < N) mx = fmaxf(mx, fmaxf(fabsf(o[j].x), fmaxf(fabsf(o[j].y), fabsf(o[j].x + o[j].y))));
           int64_t d0 = 0;
           for (int b = 0; b < po.mbits; ++b)
             if ((gm >> b) & 1) d0 += po.wm[b];
@@ -332,6 +346,8 @@ __global__ void __launch_bounds__(256) k_cgemm_thin2(int64_t M, int N, int K, co
           if (po.n_fast && po.vec >= 4 && cq * 4 + 3 < N && d0 + dn[0] + 4 <= po.plane) {
             if (po.fmt == kFmtTF32)
               put_planes_vec<kFmtTF32, 4>(po.base, d0 + dn[0], o, po.nsplit, po.plane);
+            else if (po.fmt == kFmtFP16)
+              put_planes_vec<kFmtFP16, 4>(po.base, d0 + dn[0], o, po.nsplit, po.plane, po_scale);
             else
               put_planes_vec<kFmtBF16, 4>(po.base, d0 + dn[0], o, po.nsplit, po.plane);
           } else {
@@ -341,11 +357,17 @@ __global__ void __launch_bounds__(256) k_cgemm_thin2(int64_t M, int N, int K, co
               if (cq * 4 + j < N && d >= 0 && d < po.plane) {
                 if (po.fmt == kFmtTF32)
                   put_entry<kFmtTF32>(po.base, d, o[j], po.nsplit, po.plane);
+                else if (po.fmt == kFmtFP16)
+                  put_entry<kFmtFP16>(po.base, d, o[j], po.nsplit, po.plane, po_scale);
                 else
                   put_entry<kFmtBF16>(po.base, d, o[j], po.nsplit, po.plane);
               }
             }
           }
+        }
+        if (po.fmt == kFmtFP16) {
+          for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+          if ((t & 31) == 0 && mx > 0.f) atomicMax(po.out_max, __float_as_uint(mx));
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) P[j] = Q[j] = make_float2(0.f, 0.f);
@@ -413,7 +435,8 @@ cudaError_t launch_cgemm_thin_planes(int64_t M, int64_t N, int64_t K, const floa
                                      const TcPlaneOut& po, cudaStream_t s) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (!thin_pipelined(M, N, K) || (reinterpret_cast<uintptr_t>(A) & 15) != 0 || !po.base ||
-      (po.fmt != kFmtTF32 && po.fmt != kFmtBF16))
+      (po.fmt != kFmtTF32 && po.fmt != kFmtBF16 && po.fmt != kFmtFP16) ||
+      (po.fmt == kFmtFP16 && (!po.out_scale || !po.out_max || !po.max_a || !po.max_b)))
     return cudaErrorInvalidValue;
   return K <= 16 ? launch_thin2<16, true>(M, N, K, A, B, nullptr, po, s)
                  : launch_thin2<32, true>(M, N, K, A, B, nullptr, po, s);
