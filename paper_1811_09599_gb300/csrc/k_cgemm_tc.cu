@@ -218,7 +218,7 @@ __device__ __forceinline__ bool write_sub_columns(const TcPlaneOut& po, const fl
 // accumulators Re += T1 - T2, Im += T3 - T1 - T2, while the tensor core
 // already works on the next part.
 template <int KIND, int BN, int NSPLIT, bool PO>
-__global__ void __maxnreg__(200)
+__global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
     k_cgemm_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                int64_t M, int64_t N, int64_t K, float2* __restrict__ C, int32_t* status,
                const unsigned* smax_a, const unsigned* smax_b, const __grid_constant__ TcPlaneOut po) {
