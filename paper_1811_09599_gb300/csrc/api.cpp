@@ -326,10 +326,10 @@ bool tc_route(int64_t M, int64_t N, int64_t K) {
          !(N <= 32 && K <= 64);
 }
 
-constexpr int kMaxOpCache = 128;
+constexpr int kMaxOpCache = 128;                // fp16 scale slots 2..129 of 192
 constexpr int32_t kMaxProblems = 1 << 16;      // problems of one plan
 constexpr int kBf16MaxTcSteps = 36;             // longest tensor-core chain kept in bf16 planes (QFLEX_BF16X3)
-constexpr int kMaxWorkers = 8;                  // streams a multi-problem call spreads over                // fp16 scale slots 2..129 of 192
+constexpr int kMaxWorkers = 8;                  // streams a multi-problem call spreads over
 constexpr size_t kOpCacheMinBytes = 0;           // small operands too: each saves a launch per execution
 
 // Buffer an operand is produced into (its cache, else the shared scratch).
