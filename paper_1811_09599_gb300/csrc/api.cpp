@@ -159,6 +159,7 @@ struct BwdGemm {
   int64_t M = 0, N = 0, K = 0;
   int route = 0;                 // 0 FP32 tiled, 1 FP32 thin, 2 tensor cores
   int bn = 128;
+  int splits = 1;                // split-K: partial products summed by launch_splitk_reduce
   bool x_direct = false;         // X is the output cotangent itself, already [M][K]
   PermTile xt{}, yt{}, st{};     // producers of X and Y, scatter of C'
   Ref ysrc;                      // forward tensor feeding Y
@@ -246,7 +247,7 @@ struct Sub {
   // gradients (qflex_plan_enable_gradients)
   std::vector<StepGrad> sg;
   std::vector<size_t> fwd_off, w_off;          // dedicated forward / cotangent buffers
-  size_t grad_bytes = 0, garena_bytes = 0, gxa = 0, gyb = 0;
+  size_t grad_bytes = 0, garena_bytes = 0, gxa = 0, gyb = 0, gcc = 0;
   char* d_gws = nullptr;
   char* d_garena = nullptr;
   char* d_warena = nullptr;
@@ -254,6 +255,7 @@ struct Sub {
   void* d_gA = nullptr;
   void* d_gB = nullptr;
   float2* d_gC = nullptr;
+  float2* d_gP = nullptr;                      // split-K partial products of reverse GEMMs
   bool grad_active = false;                    // forward runs on the dedicated buffers
 };
 
@@ -1109,6 +1111,35 @@ std::vector<int> cat(const std::vector<int>& a, const std::vector<int>& b) {
   return r;
 }
 
+// Split-K of a reverse GEMM.  The reverse pass meets products with few
+// outputs and a long K (W_B = W_C^T A for a step whose dst has many free
+// entries: e.g. 256 x 256 outputs over K = 65536), which as one output tile
+// per CTA or one warp per row use a handful of SMs.  Their K range is cut
+// into `splits` parts whose partial products land in the gradient scratch
+// and are summed in split order (deterministic): enough parts to give every
+// SM work, none shorter than 8 k-blocks (tensor cores) or 2048 entries (CUDA
+// cores).  The tiled CUDA-core form keeps its own K tiles inside a part.
+int bwd_splits(const Sub& p, const BwdGemm& g) {
+  constexpr int64_t kSMs = 152;
+  if (g.route == 2) {
+    const int64_t bk = p.tc_kind == 0 ? 32 : 64;
+    const int64_t tiles = ((g.M + 127) / 128) * ((g.N + g.bn - 1) / g.bn);
+    const int64_t nkb = (g.K + bk - 1) / bk;
+    if (tiles * 2 > kSMs || nkb < 16) return 1;
+    return int(std::max<int64_t>(1, std::min<int64_t>((kSMs + tiles - 1) / tiles, nkb / 8)));
+  }
+  const int64_t cgs = (g.N + 15) / 16;
+  if (g.route == 1) {
+    const bool rowwarp = g.K >= 64 && ((g.M + 255) / 256) * cgs < 256;
+    const int64_t warps = g.M * cgs;
+    if (!rowwarp || warps * 4 > kSMs * 32 || g.K < 8192) return 1;
+    return int(std::max<int64_t>(1, std::min<int64_t>((kSMs * 32 + warps - 1) / warps, g.K / 2048)));
+  }
+  const int64_t blocks = ((g.M + 63) / 64) * ((g.N + 63) / 64);
+  if (blocks * 2 > kSMs || g.K < 8192) return 1;
+  return int(std::max<int64_t>(1, std::min<int64_t>((kSMs * 2 + blocks - 1) / blocks, g.K / 2048)));
+}
+
 // Build one reverse GEMM: C' = X Y^T with X taken from the cotangent W of the
 // step output (legs `wlegs`, contiguous) in order xorder = (rows, inner),
 // Y from the forward view `ysrc` in order (cols, inner), and C' (rows, cols)
@@ -1122,6 +1153,7 @@ bool make_bwd(const Sub& p, const std::vector<int>& wlegs, const std::vector<int
   g->N = leg_product(cols, dim);
   g->route = route_of(p, g->M, g->N, g->K);
   g->bn = g->N >= 128 ? 128 : 64;
+  g->splits = bwd_splits(p, *g);
   g->ysrc = ysrc;
   g->target = target;
   const std::vector<int> xorder = cat(rows, inner), yorder = cat(cols, inner), corder = cat(rows, cols);
@@ -1157,18 +1189,20 @@ qflex_status build_grad(Sub& p) {
     off += align256(size_t(p.bufs[b].elems) * 8);
   }
   const size_t arena = off;
-  size_t xa = 0, yb = 0, cc = 0;
+  size_t xa = 0, yb = 0, cc = 0, pp = 0;
   for (const StepGrad& g : p.sg)
     for (const BwdGemm* b : {&g.ga, &g.gb}) {
       xa = std::max(xa, operand_bytes(p, b->route == 2, b->M * b->K));
       yb = std::max(yb, operand_bytes(p, b->route == 2, b->N * b->K));
       cc = std::max(cc, size_t(b->M * b->N) * 8);
+      if (b->splits > 1) pp = std::max(pp, size_t(b->splits) * size_t(b->M * b->N) * 8);
     }
   p.grad_bytes = align256(2 * arena + align256(size_t(p.grid_elems) * 16) + align256(xa) + align256(yb) +
-                          align256(cc));
+                          align256(cc) + align256(pp));
   p.garena_bytes = arena;
   p.gxa = xa;
   p.gyb = yb;
+  p.gcc = cc;
   return QFLEX_OK;
 }
 
@@ -1188,6 +1222,8 @@ qflex_status grad_assign(Sub& p, char* base) {
   p.d_gB = c;
   c += align256(p.gyb);
   p.d_gC = reinterpret_cast<float2*>(c);
+  c += align256(p.gcc);
+  p.d_gP = reinterpret_cast<float2*>(c);
   for (StepGrad& g : p.sg)
     for (BwdGemm* b : {&g.ga, &g.gb})
       if (b->route == 2 && !tc_encode_maps(p.tc_kind, p.nsplit, b->bn, p.d_gA, b->M, p.d_gB, b->N, b->K, &b->maps))
@@ -1225,17 +1261,22 @@ cudaError_t run_bwd(Sub& p, const Step& st, const BwdGemm& g, const std::vector<
     return e;
   const float2* Y = static_cast<const float2*>(p.d_gB);
   const double mnk = double(g.M) * double(g.N) * double(g.K);
+  float2* out = g.splits > 1 ? p.d_gP : p.d_gC;
   if (g.route == 2) {
     e = timed(p, 3, 8.0 * mnk, mnk * 3.0 * (p.nsplit == 2 ? 3.0 : 1.0) * 2.0, 0, s, [&] {
-      return launch_cgemm_tc(p.tc_kind, p.nsplit, g.bn, g.maps, g.M, g.N, g.K, p.d_gC, p.d_status, s,
-                             scaled ? p.d_smax : nullptr, scaled ? p.d_smax + 1 : nullptr);
+      return launch_cgemm_tc(p.tc_kind, p.nsplit, g.bn, g.maps, g.M, g.N, g.K, out, p.d_status, s,
+                             scaled ? p.d_smax : nullptr, scaled ? p.d_smax + 1 : nullptr, nullptr, g.splits);
     });
   } else {
     e = timed(p, 2, 8.0 * mnk, 0, 0, s, [&] {
+      if (g.splits > 1)
+        return g.route == 1 ? launch_cgemm_rowwarp_split(g.M, g.N, g.K, X, Y, out, g.splits, s)
+                            : launch_cgemm_simt_split(g.M, g.N, g.K, X, Y, out, g.splits, s);
       return g.route == 1 ? launch_cgemm_thin(g.M, g.N, g.K, X, Y, p.d_gC, s)
                           : launch_cgemm_simt(g.M, g.N, g.K, X, Y, p.d_gC, s);
     });
   }
+  if (e == cudaSuccess && g.splits > 1) e = launch_splitk_reduce(p.d_gP, g.splits, g.M * g.N, p.d_gC, s);
   if (e != cudaSuccess) return e;
   // scatter C' into the target's cotangent: accumulate (FP64) for grid tensors,
   // plain write for intermediates (each is consumed by exactly one step)

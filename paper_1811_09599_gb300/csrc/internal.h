@@ -306,6 +306,16 @@ cudaError_t launch_cgemm_simt(int64_t M, int64_t N, int64_t K, const float2* A,
 // Same product for thin shapes (N <= 32): one thread per output row.
 cudaError_t launch_cgemm_thin(int64_t M, int64_t N, int64_t K, const float2* A,
                               const float2* B, float2* C, cudaStream_t s);
+// Split-K form of the warp-per-row product (few outputs, long K): warps over
+// (row, 16-column group, split), each summing its K range of `chunk`
+// entries into the partial product P + split M N.
+cudaError_t launch_cgemm_rowwarp_split(int64_t M, int64_t N, int64_t K, const float2* A,
+                                       const float2* B, float2* P, int splits, cudaStream_t s);
+// Split-K form of the tiled product: grid z = split, same partial layout.
+cudaError_t launch_cgemm_simt_split(int64_t M, int64_t N, int64_t K, const float2* A,
+                                    const float2* B, float2* P, int splits, cudaStream_t s);
+// C[i] = sum over s = 0..splits-1, in that order, of P[s * n + i] (FP32).
+cudaError_t launch_splitk_reduce(const float2* P, int splits, int64_t n, float2* C, cudaStream_t s);
 
 // Tensor-core GEMM on split 3M planes (produced by the permutation kernel in
 // kFmtTF32 / kFmtBF16 / kFmtFP16 format).  kind: 0 = tf32, 1 = bf16, 2 = fp16
@@ -350,10 +360,14 @@ cudaError_t launch_cgemm_thin_planes(int64_t M, int64_t N, int64_t K, const floa
                                      const TcPlaneOut& po, cudaStream_t s);
 bool tc_encode_maps(int kind, int nsplit, int bn, const void* a_planes, int64_t M,
                     const void* b_planes, int64_t N, int64_t K, TcGemmMaps* maps);
+// splits > 1 (complex64 output only): split-K, the k-blocks cut into
+// `splits` ranges whose partial products go to C + s M N, s = 0..splits-1
+// (C then holds splits x M x N entries; launch_splitk_reduce sums them).
 cudaError_t launch_cgemm_tc(int kind, int nsplit, int bn, const TcGemmMaps& maps, int64_t M,
                             int64_t N, int64_t K, float2* C, int32_t* d_status,
                             cudaStream_t s, const unsigned* smax_a = nullptr,
-                            const unsigned* smax_b = nullptr, const TcPlaneOut* planes = nullptr);
+                            const unsigned* smax_b = nullptr, const TcPlaneOut* planes = nullptr,
+                            int splits = 1);
 bool tc_available();   // driver entry point for tensor-map encoding found
 
 // ------------------------------------------------------------------ small kernels

@@ -26,6 +26,13 @@ __global__ void __launch_bounds__(256) k_cgemm_simt(int64_t M, int64_t N, int64_
                                                     const float2* __restrict__ B,
                                                     float2* __restrict__ C) {
   pdl_wait();
+  // split-K (gridDim.z > 1): block z sums the K range [z chunk, (z + 1)
+  // chunk) into the partial product C + z M N; the loads below keep their
+  // row stride K and stop at the range's end
+  const int64_t chunk = (K + gridDim.z - 1) / gridDim.z;
+  const int64_t k_begin = min(K, int64_t(blockIdx.z) * chunk);
+  const int64_t k_end = min(K, k_begin + chunk);
+  C += int64_t(blockIdx.z) * M * N;
   __shared__ __align__(16) float2 As[BK][BM + PAD];
   __shared__ __align__(16) float2 Bs[BK][BN + PAD];
   const int tid = threadIdx.x;
@@ -39,15 +46,15 @@ __global__ void __launch_bounds__(256) k_cgemm_simt(int64_t M, int64_t N, int64_
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc_re[i][j] = acc_im[i][j] = 0.f;
 
-  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+  for (int64_t k0 = k_begin; k0 < k_end; k0 += BK) {
 #pragma unroll
     for (int i = 0; i < (BM * BK) / 256; ++i) {
       const int e = tid + i * 256;
       const int r = e / BK, kk = e % BK;
       const int64_t gm = m0 + r, gk = k0 + kk;
-      As[kk][r] = (gm < M && gk < K) ? A[gm * K + gk] : make_float2(0.f, 0.f);
+      As[kk][r] = (gm < M && gk < k_end) ? A[gm * K + gk] : make_float2(0.f, 0.f);
       const int64_t gn = n0 + r;
-      Bs[kk][r] = (gn < N && gk < K) ? B[gn * K + gk] : make_float2(0.f, 0.f);
+      Bs[kk][r] = (gn < N && gk < k_end) ? B[gn * K + gk] : make_float2(0.f, 0.f);
     }
     __syncthreads();
 #pragma unroll
@@ -190,21 +197,30 @@ __global__ void __launch_bounds__(256, 2) k_cgemm_thin(int64_t M, int64_t N, int
 
 // Warp-per-row form for few rows and a long K (too few blocks for the
 // row-per-thread form): the lanes split K, then reduce across the warp.
+// With splits > 1, warp w also takes split w / (M cgs): the K range
+// [split chunk, (split + 1) chunk), chunk = ceil(K / splits), possibly
+// empty, into the partial product C + split M N (every split writes its
+// whole partial, zeros for an empty range).
 __global__ void __launch_bounds__(256) k_cgemm_rowwarp(int64_t M, int64_t N, int64_t K,
                                                       const float2* __restrict__ A,
                                                       const float2* __restrict__ B,
-                                                      float2* __restrict__ C) {
+                                                      float2* __restrict__ C, int splits) {
   pdl_wait();
   const int lane = threadIdx.x & 31;
   const int64_t cgs = (N + 15) / 16;
-  const int64_t w = int64_t(blockIdx.x) * 8 + (threadIdx.x >> 5);
+  const int64_t w_all = int64_t(blockIdx.x) * 8 + (threadIdx.x >> 5);
+  const int64_t split = w_all / (M * cgs), w = w_all % (M * cgs);
+  if (split >= splits) return;
   const int64_t m = w / cgs, n0 = (w % cgs) * 16;
-  if (m >= M) return;
+  const int64_t chunk = (K + splits - 1) / splits;
+  const int64_t k_lo = split * chunk < K ? split * chunk : K;
+  const int64_t k_hi = k_lo + chunk < K ? k_lo + chunk : K;
+  C += split * M * N;
   const int nn = int(N - n0 < 16 ? N - n0 : 16);
   unsigned long long P[16], Q[16];
 #pragma unroll
   for (int n = 0; n < 16; ++n) P[n] = Q[n] = 0ull;
-  for (int64_t k = lane; k < K; k += 32) {
+  for (int64_t k = k_lo + lane; k < k_hi; k += 32) {
     const float2 a = __ldg(A + m * K + k);
     const unsigned long long ax = pk(a.x, a.x), ay = pk(a.y, a.y);
 #pragma unroll
@@ -442,13 +458,51 @@ cudaError_t launch_cgemm_thin_planes(int64_t M, int64_t N, int64_t K, const floa
                  : launch_thin2<32, true>(M, N, K, A, B, nullptr, po, s);
 }
 
+namespace {
+__global__ void __launch_bounds__(256) k_splitk_reduce(const float2* __restrict__ P, int splits, int64_t n,
+                                                      float2* __restrict__ C) {
+  pdl_wait();
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    float2 acc = P[i];
+    for (int sp = 1; sp < splits; ++sp) {
+      const float2 v = P[sp * n + i];
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    C[i] = acc;
+  }
+}
+}  // namespace
+
+cudaError_t launch_cgemm_simt_split(int64_t M, int64_t N, int64_t K, const float2* A, const float2* B,
+                                    float2* P, int splits, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || splits < 1 || splits > 65535 || K <= 0) return cudaErrorInvalidValue;
+  dim3 grid(unsigned((N + BN - 1) / BN), unsigned((M + BM - 1) / BM), unsigned(splits));
+  if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+  return launch_pdl(k_cgemm_simt, grid, dim3(256), 0, s, M, N, K, A, B, P);
+}
+
+cudaError_t launch_cgemm_rowwarp_split(int64_t M, int64_t N, int64_t K, const float2* A, const float2* B,
+                                       float2* P, int splits, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || splits < 1 || K <= 0) return cudaErrorInvalidValue;
+  const int64_t cgs = (N + 15) / 16;
+  const int64_t warps = M * cgs * splits;
+  return launch_pdl(k_cgemm_rowwarp, dim3(unsigned((warps + 7) / 8)), dim3(256), 0, s, M, N, K, A, B, P, splits);
+}
+
+cudaError_t launch_splitk_reduce(const float2* P, int splits, int64_t n, float2* C, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 8);
+  return launch_pdl(k_splitk_reduce, dim3(unsigned(blocks)), dim3(256), 0, s, P, splits, n, C);
+}
+
 cudaError_t launch_cgemm_thin(int64_t M, int64_t N, int64_t K, const float2* A, const float2* B,
                               float2* C, cudaStream_t s) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   const int64_t cgs = (N + 15) / 16;
   if (K >= 64 && ((M + 255) / 256) * cgs < 256) {   // few rows, long K: warp per row
     const int64_t warps = M * cgs;
-    return launch_pdl(k_cgemm_rowwarp, dim3(unsigned((warps + 7) / 8)), dim3(256), 0, s, M, N, K, A, B, C);
+    return launch_pdl(k_cgemm_rowwarp, dim3(unsigned((warps + 7) / 8)), dim3(256), 0, s, M, N, K, A, B, C, 1);
   }
   if (thin_pipelined(M, N, K) && (reinterpret_cast<uintptr_t>(A) & 15) == 0) {
     static const TcPlaneOut none{};

@@ -221,7 +221,8 @@ template <int KIND, int BN, int NSPLIT, bool PO>
 __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
     k_cgemm_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                int64_t M, int64_t N, int64_t K, float2* __restrict__ C, int32_t* status,
-               const unsigned* smax_a, const unsigned* smax_b, const __grid_constant__ TcPlaneOut po) {
+               const unsigned* smax_a, const unsigned* smax_b, const __grid_constant__ TcPlaneOut po,
+               int splits) {
   using G = Cfg<BN, NSPLIT>;
   constexpr int ELEM = KIND == 0 ? 4 : 2;
   constexpr uint32_t FMT_AB = KIND == 0 ? 2u : (KIND == 1 ? 1u : 0u);   // tf32 / bf16 / f16
@@ -270,9 +271,18 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t n_nt = (N + BN - 1) / BN;
   const int64_t n_mt = (M + BM - 1) / BM;
-  const int64_t n_tiles = n_mt * n_nt;
+  // split-K: work item t = output tile t % (n_mt n_nt) over the k-blocks of
+  // split t / (n_mt n_nt), whose partial product goes to C + split M N
+  const int64_t n_out_tiles = n_mt * n_nt;
+  const int64_t n_tiles = n_out_tiles * splits;
   const int nkb = int((K + BK - 1) / BK);
-  const int nchunk = (nkb + KB_CHUNK - 1) / KB_CHUNK;
+  const int kps = (nkb + splits - 1) / splits;    // k-blocks per split
+  // k-block range [kbs, kbe) of work item t and its number of chunks
+  auto krange = [&](int64_t t, int* kbs, int* kbe) {
+    const int sp = int(t / n_out_tiles);
+    *kbs = min(nkb, sp * kps);
+    *kbe = min(nkb, *kbs + kps);
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < G::NSTAGE; ++s) {
@@ -307,9 +317,11 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
       int64_t m0, n0;
-      tile_origin<BN>(tile, n_mt, n_nt, &m0, &n0);
-      for (int c = 0; c < nchunk && ok; ++c) {
-        const int kb0 = c * KB_CHUNK, kb1 = min(nkb, kb0 + KB_CHUNK);
+      tile_origin<BN>(tile % n_out_tiles, n_mt, n_nt, &m0, &n0);
+      int kbs, kbe;
+      krange(tile, &kbs, &kbe);
+      for (int kb0 = kbs; kb0 < kbe && ok; kb0 += KB_CHUNK) {
+        const int kb1 = min(kbe, kb0 + KB_CHUNK);
         for (int part = 0; part < 3 && ok; ++part) {
           for (int kb = kb0; kb < kb1; ++kb, ++i) {
             const int s = i % G::NSTAGE;
@@ -343,8 +355,10 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
       int i = 0, cg = 0;   // stage counter, chunk counter across tiles
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-      for (int c = 0; c < nchunk && ok; ++c, ++cg) {
-        const int kb0 = c * KB_CHUNK, kb1 = min(nkb, kb0 + KB_CHUNK);
+      int kbs, kbe;
+      krange(tile, &kbs, &kbe);
+      for (int kb0 = kbs; kb0 < kbe && ok; kb0 += KB_CHUNK, ++cg) {
+        const int kb1 = min(kbe, kb0 + KB_CHUNK);
         for (int part = 0; part < 3 && ok; ++part) {
           if (cg > 0 && !mbar_wait(smem_u32(&acc_empty[part]), (cg - 1) & 1, abort_flag, status)) {
             ok = false;
@@ -405,11 +419,14 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
     int cg = 0;
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
       int64_t m0, n0;
-      tile_origin<BN>(tile, n_mt, n_nt, &m0, &n0);
+      tile_origin<BN>(tile % n_out_tiles, n_mt, n_nt, &m0, &n0);
+      float2* Ct = C + (tile / n_out_tiles) * M * N;   // this split's partial product
+      int kbs, kbe;
+      krange(tile, &kbs, &kbe);
       float re[G::HALF], im[G::HALF];
 #pragma unroll
       for (int j = 0; j < G::HALF; ++j) re[j] = im[j] = 0.f;
-      for (int c = 0; c < nchunk && ok; ++c, ++cg) {
+      for (int kb0 = kbs; kb0 < kbe && ok; kb0 += KB_CHUNK, ++cg) {
         for (int part = 0; part < 3; ++part) {
           if (!mbar_wait(smem_u32(&acc_full[part]), cg & 1, abort_flag, status)) {
             ok = false;
@@ -521,7 +538,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
         for (int r2 = 0; r2 < 32; r2 += 2) {
           const int r = r2 + (lane >> 4);
           const int64_t gm = m0 + q * 32 + r;
-          if (gm < M && gn < N) C[gm * N + gn] = st[r * 16 + (cj ^ (r & 15))];
+          if (gm < M && gn < N) Ct[gm * N + gn] = st[r * 16 + (cj ^ (r & 15))];
         }
         __syncwarp();
       }
@@ -571,7 +588,7 @@ bool encode(int kind, const void* ptr, int64_t rows, int64_t K, int box_rows, CU
 template <int KIND, int BN, int NSPLIT, bool PO>
 cudaError_t launch_t(const TcGemmMaps& maps, int64_t M, int64_t N, int64_t K, float2* C,
                      int32_t* status, cudaStream_t s, const unsigned* sa, const unsigned* sb,
-                     const TcPlaneOut& po) {
+                     const TcPlaneOut& po, int splits) {
   using G = Cfg<BN, NSPLIT>;
   auto kern = k_cgemm_tc<KIND, BN, NSPLIT, PO>;
   static int configured_dev = -1;
@@ -584,7 +601,7 @@ cudaError_t launch_t(const TcGemmMaps& maps, int64_t M, int64_t N, int64_t K, fl
   }
   static int sms = 0;
   if (sms == 0) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN) * splits;
   const unsigned grid = unsigned(tiles < sms ? tiles : sms);
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(grid);
@@ -596,7 +613,7 @@ cudaError_t launch_t(const TcGemmMaps& maps, int64_t M, int64_t N, int64_t K, fl
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, maps.a, maps.b, M, N, K, C, status, sa, sb, po);
+  return cudaLaunchKernelEx(&cfg, kern, maps.a, maps.b, M, N, K, C, status, sa, sb, po, splits);
 }
 
 }  // namespace
@@ -613,8 +630,10 @@ bool tc_encode_maps(int kind, int nsplit, int bn, const void* a_planes, int64_t 
 
 cudaError_t launch_cgemm_tc(int kind, int nsplit, int bn, const TcGemmMaps& maps, int64_t M,
                             int64_t N, int64_t K, float2* C, int32_t* status, cudaStream_t s,
-                            const unsigned* smax_a, const unsigned* smax_b, const TcPlaneOut* planes) {
+                            const unsigned* smax_a, const unsigned* smax_b, const TcPlaneOut* planes,
+                            int splits) {
   if (3 * nsplit * M > INT32_MAX || 3 * nsplit * N > INT32_MAX) return cudaErrorInvalidValue;
+  if (splits < 1 || splits > 1024 || (splits > 1 && planes && planes->base)) return cudaErrorInvalidValue;
   static const TcPlaneOut none{};
   const TcPlaneOut& po = planes ? *planes : none;
   if (po.base && (po.mbits > kMaxOutBits || po.nbits > kMaxOutBits || (int64_t(1) << po.mbits) != M ||
@@ -624,8 +643,8 @@ cudaError_t launch_cgemm_tc(int kind, int nsplit, int bn, const TcGemmMaps& maps
     return cudaErrorInvalidValue;
 #define QF_TC(KD, B, S)                                                                                  \
   if (kind == KD && bn == B && nsplit == S)                                                              \
-    return po.base ? launch_t<KD, B, S, true>(maps, M, N, K, C, status, s, smax_a, smax_b, po)            \
-                   : launch_t<KD, B, S, false>(maps, M, N, K, C, status, s, smax_a, smax_b, po);
+    return po.base ? launch_t<KD, B, S, true>(maps, M, N, K, C, status, s, smax_a, smax_b, po, splits)    \
+                   : launch_t<KD, B, S, false>(maps, M, N, K, C, status, s, smax_a, smax_b, po, splits);
   QF_TC(0, 64, 1) QF_TC(0, 64, 2) QF_TC(0, 128, 1) QF_TC(0, 128, 2)
   QF_TC(1, 64, 1) QF_TC(1, 64, 2) QF_TC(1, 128, 1) QF_TC(1, 128, 2)
   QF_TC(2, 64, 2) QF_TC(2, 128, 2)

@@ -123,3 +123,31 @@ def test_grad_partial_slices_and_plain_gates(api):
     assert grad_error(grad[used], ref, g, prob.n) < GTOL["fp32"]
     unused = sorted(set(range(prob.circuit.n_params)) - set(used))
     assert np.all(grad[unused] == 0)
+
+
+@pytest.fixture(scope="module")
+def oracle_6x6():
+    """The 6x6 depth 1+32+1 rotation circuit, its bitstring and cotangent, and
+    the oracle's amplitude and shift-rule loss gradient for sampled angles."""
+    prob = grid_problem(6, 6, 32, 99, cuts=False, tile_rows=0, rotations=True)
+    bs = random_bitstrings(prob.n, 1, 6)
+    g = _cotangent((1, 1), 4)
+    n = prob.circuit.n_params
+    params = [0, n // 3, 2 * n // 3, n - 1]
+    amp_fn = lambda th: NW.amplitudes(prob, bs, angles=th)[0]
+    ref_amp = amp_fn(prob.circuit.angles)
+    ref = GR.loss_gradient(GR.shift_rule(amp_fn, prob.circuit.angles, params), g)
+    return prob, bs, g, params, ref_amp, ref
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_grad_6x6_long_reverse_products_vs_shift_rule(api, oracle_6x6, prec):
+    """6x6, 1+32+1 rotations (bonds 16), no cuts, one amplitude: its reverse
+    pass has products with few outputs and a long K (256 x 256 outputs over
+    K = 65536 for the 65536 x 256 x 256 absorbs), which run split-K; sampled
+    angles against the oracle's exact shift rule on its own contraction."""
+    prob, bs, g, params, ref_amp, ref = oracle_6x6
+    amps, grad, plan = _gpu_grad(api, prob, prec, bs, g)
+    assert any((s["M"], s["N"], s["K"]) == (65536, 256, 256) for s in plan.steps(1))
+    assert np.max(np.abs(amps.reshape(-1) - ref_amp)) / np.sqrt(2.0 ** -prob.n) < 1e-3
+    assert grad_error(grad[params], ref, g, prob.n) < GTOL[prec], grad_error(grad[params], ref, g, prob.n)
