@@ -64,7 +64,8 @@ class StepInfo(C.Structure):
                 ("K", C.c_int64), ("kernel", C.c_int32), ("bn", C.c_int32), ("a_direct", C.c_int32),
                 ("b_direct", C.c_int32), ("runs", C.c_int64), ("a_cached", C.c_int32),
                 ("b_cached", C.c_int32), ("a_builds", C.c_int64), ("b_builds", C.c_int64),
-                ("a_fused", C.c_int32), ("b_fused", C.c_int32), ("out_fused", C.c_int32)]
+                ("a_fused", C.c_int32), ("b_fused", C.c_int32), ("out_fused", C.c_int32),
+                ("cta_pair", C.c_int32)]
 
 
 class SearchResult(C.Structure):

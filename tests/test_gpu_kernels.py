@@ -97,6 +97,21 @@ def test_cgemm_tensor_core(K, prec, tol):
     assert K.device_status(0) == 0
 
 
+# products that run on SM pairs (16-bit split operands, N >= 128, M >= 256):
+# one MMA step of K, a K tail with ragged N, ragged M above 2048 (the second
+# SM's rows partly and wholly past M), several tiles per pair, a long K
+PAIR_SHAPES = [(256, 128, 16), (512, 200, 72), (2100, 256, 64), (2176, 136, 200), (8192, 1024, 64),
+               (256, 136, 4096)]
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-4), ("fp16x3", 1e-5)])
+def test_cgemm_cta_pairs(K, prec, tol):
+    for i, (M, N, Kd) in enumerate(PAIR_SHAPES):
+        err = _gemm_case(K, prec, M, N, Kd, 40 + i)
+        assert err < tol, (prec, M, N, Kd, err)
+    assert K.device_status(0) == 0
+
+
 @pytest.mark.parametrize("Kd", [4096, 32768])
 def test_cgemm_long_k_accuracy(K, Kd):
     """Long contractions (K up to 2^15, the 7x7 1+40+1 shape) keep the split
