@@ -167,10 +167,10 @@ typedef struct {
                                 (no permutation; not in gradient calls) */
   int32_t out_fused;         /* this step's epilogue writes its consumer's operand planes:
                                 1 stores along its columns, 2 along its rows; 0 not fused */
-  int32_t cta_pair;          /* kernel 4 on pairs of SMs (cta_group::2): 256 x 128 output
-                                tiles, each SM of the pair loading its 128 rows of A and half
-                                of B; chosen for 16-bit split operands, bn = 128 and
-                                M >= 256 (a multiple of 256, or M >= 2048) */
+  int32_t tc_wide;           /* kernel 4 with split operands: per k-step one MMA of width
+                                2 bn over B hi and B lo ([hi.hi | hi.lo]) and one of width
+                                bn (lo.hi) instead of three of width bn; chosen for bn = 64,
+                                and for bn = 128 when K >= 2048 */
 } qflex_step_info;
 
 int32_t qflex_abi_version(void);

@@ -65,7 +65,7 @@ class StepInfo(C.Structure):
                 ("b_direct", C.c_int32), ("runs", C.c_int64), ("a_cached", C.c_int32),
                 ("b_cached", C.c_int32), ("a_builds", C.c_int64), ("b_builds", C.c_int64),
                 ("a_fused", C.c_int32), ("b_fused", C.c_int32), ("out_fused", C.c_int32),
-                ("cta_pair", C.c_int32)]
+                ("tc_wide", C.c_int32)]
 
 
 class SearchResult(C.Structure):

@@ -1667,7 +1667,7 @@ qflex_status qflex_plan_steps(qflex_plan p, int32_t problem, int64_t n_bs, const
       o.a_fused = s.A.fused;
       o.b_fused = s.B.fused;
       o.out_fused = s.fuse_out ? (s.po.n_fast ? 1 : 2) : 0;
-      o.cta_pair = s.tc && tc_pair_shape(sp->tc_kind, sp->nsplit, s.bn, s.M) ? 1 : 0;
+      o.tc_wide = s.tc && tc_wide_mma(sp->nsplit, s.bn, s.K) ? 1 : 0;
     }
     return QFLEX_OK;
   });

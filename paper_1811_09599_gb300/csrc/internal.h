@@ -323,7 +323,6 @@ cudaError_t launch_splitk_reduce(const float2* P, int splits, int64_t n, float2*
 struct TcGemmMaps {
   CUtensorMap a;
   CUtensorMap b;
-  bool pair = false;   // encoded for the CTA-pair kernel (256-row tiles, B halves)
 };
 // Epilogue output as the next step's 3M operand planes instead of C: entry
 // (m, n) of the product goes to position sum_b bit_b(m) wm[b] + sum_b
@@ -359,11 +358,13 @@ struct TcPlaneOut {
 bool thin_pipelined(int64_t M, int64_t N, int64_t K);
 cudaError_t launch_cgemm_thin_planes(int64_t M, int64_t N, int64_t K, const float2* A, const float2* B,
                                      const TcPlaneOut& po, cudaStream_t s);
-// Tensor-core products with 16-bit split operands, 128-wide tiles and at
-// least 256 rows (a multiple of 256, or 2048 and more) run on CTA pairs
-// (cta_group::2, 256 x 128 tiles); tc_encode_maps records the choice in the
-// maps and launch_cgemm_tc follows it.
-bool tc_pair_shape(int kind, int nsplit, int bn, int64_t M);
+// Form of the split (nsplit = 2) tensor-core product: true = per k-step one
+// MMA of width 2 bn over the adjacent B hi and B lo tiles ([hi.hi | hi.lo])
+// plus one of width bn (lo.hi); false = three MMAs of width bn.  The wide
+// form is taken for bn = 64 and for bn = 128 when K >= 2048 (with bn = 128
+// it leaves room in TMEM for two accumulators instead of three, which costs
+// more than it gains on short K).
+bool tc_wide_mma(int nsplit, int bn, int64_t K);
 bool tc_encode_maps(int kind, int nsplit, int bn, const void* a_planes, int64_t M,
                     const void* b_planes, int64_t N, int64_t K, TcGemmMaps* maps);
 // splits > 1 (complex64 output only): split-K, the k-blocks cut into

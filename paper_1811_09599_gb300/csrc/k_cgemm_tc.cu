@@ -13,9 +13,9 @@
 // Kernel organisation (one 128 x BN output tile per CTA, cta_group::1):
 //   warp 0      one lane issues TMA loads of (A hi, A lo, B hi, B lo) tiles
 //               for one (k-block, part) pair per pipeline stage;
-//   warp 1      allocates TMEM (two accumulators, used in turn) and one lane
-//               issues the tcgen05.mma instructions of each stage, then
-//               tcgen05.commit releases the stage;
+//   warp 1      allocates TMEM (two or three accumulators, used in turn) and
+//               one lane issues the tcgen05.mma instructions of each stage,
+//               then tcgen05.commit releases the stage;
 //   warps 2-9   epilogue: after each part of each K chunk, tcgen05.ld of that
 //               part's accumulator, round-to-nearest FP32 promotion into
 //               Re/Im register accumulators; at the end, staged coalesced
@@ -52,38 +52,24 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
 }
-// CLUSTER: acquire at cluster scope, for barriers that threads of the
-// other CTA of a pair arrive on.
-template <bool CLUSTER = false>
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
-  if constexpr (CLUSTER) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-  }
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
   return ok != 0;
 }
 // Bounded wait: returns false (and flags the CTA / status word) after the
 // limit, or at once when another role of the CTA has already given up.
-template <bool CLUSTER = false>
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
                                           int32_t* status) {
   uint64_t t0 = 0;
   for (uint32_t it = 0;; ++it) {
-    if (mbar_try_wait<CLUSTER>(bar, parity)) return true;
+    if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255u) == 255u) {
       if (*abort_flag) return false;
       const uint64_t now = gtimer();
@@ -96,52 +82,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
   }
 }
-// PAIR: the completion is signalled on `bar`, a shared::cluster address
-// that may lie in the other CTA of the pair.
-template <bool PAIR = false>
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
                                             int x, int y) {
-  if constexpr (PAIR) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
-        : "memory");
-  } else {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
-        : "memory");
-  }
-}
-// ---- CTA pairs (cluster of two, cta_group::2)
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-// shared::cluster address of the same shared-memory offset in CTA `rank`
-__device__ __forceinline__ uint32_t cluster_addr(uint32_t addr, uint32_t rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_bar) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
-}
-__device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t cluster_addr_) {
-  uint32_t v;
-  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(cluster_addr_) : "memory");
-  return v;
-}
-// bounded pause (lets copies already issued land before a CTA gives up)
-__device__ __forceinline__ void pause_ns(uint64_t ns) {
-  const uint64_t t0 = gtimer();
-  while (gtimer() - t0 < ns) __nanosleep(1000);
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -149,20 +96,9 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
-// PAIR: the arrival goes to the barrier at this offset in both CTAs.
-template <bool PAIR = false>
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
-  if constexpr (PAIR) {
-    const uint16_t both = 3;
-    asm volatile(
-        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            bar),
-        "h"(both)
-        : "memory");
-  } else {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-  }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
 }
 // Shared-memory matrix descriptor: K-major tile, 128-byte swizzle, rows of
 // 128 bytes, 8-row groups 1024 bytes apart (SBO), descriptor version 1.
@@ -175,16 +111,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   d |= uint64_t(2) << 61;                         // 128-byte swizzle
   return d;
 }
-template <int KIND, bool PAIR = false>
+template <int KIND>
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                     uint32_t accum) {
-  if constexpr (PAIR) {   // bf16 / fp16 only
-    static_assert(KIND != 0, "pair form instantiated for 16-bit operands only");
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accum));
-  } else if constexpr (KIND == 0) {
+  if constexpr (KIND == 0) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
@@ -209,26 +139,24 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// PAIR: a cluster of two CTAs computes a 256 x BN tile with cta_group::2
-// MMAs; each CTA holds its own 128 rows of A and half (BN / 2 rows) of B.
-template <int BN, int NSPLIT, bool PAIR = false>
+// WIDE (split operands only): B hi and B lo tiles are adjacent in a stage,
+// so one MMA of width 2 BN gives [A_hi B_hi | A_hi B_lo] and a second of
+// width BN adds A_lo B_hi onto the first half: two MMAs per k-step instead of
+// three.  Measured on a GB300: an MMA of width 128 reads its shared-memory
+// operands (8 KB) at ~87 B/cycle, 94 cycles instead of the 64 of its math;
+// width 256 (12 KB) takes 135 cycles for 128 of math.  An accumulator is
+// then DW = 2 BN columns wide (its halves summed when drained).
+template <int BN, int NSPLIT, bool WIDE = false>
 struct Cfg {
-  static constexpr int BN_CTA = PAIR ? BN / 2 : BN;         // B rows held by one CTA
-  static constexpr int BM_TILE = PAIR ? 2 * BM : BM;          // output rows of one tile
   static constexpr int A_TILE = BM * ROW_BYTES;              // bytes of one A plane tile
-  static constexpr int B_TILE = BN_CTA * ROW_BYTES;
+  static constexpr int B_TILE = BN * ROW_BYTES;
   static constexpr int STAGE = NSPLIT * (A_TILE + B_TILE);
   static constexpr int NSTAGE = (196 * 1024) / STAGE > NSTAGE_MAX ? NSTAGE_MAX : (196 * 1024) / STAGE;
   static constexpr int NPROD = NSPLIT == 2 ? 3 : 1;          // hi.hi, hi.lo, lo.hi
-  // Split operands on one SM: B hi and B lo tiles are adjacent in a stage,
-  // so one MMA of width 2 BN gives [A_hi B_hi | A_hi B_lo] and a second of
-  // width BN adds A_lo B_hi onto the first half (two MMAs per k-step instead
-  // of three; the wider MMA reads its shared-memory operands at a better
-  // rate).  An accumulator is then DW = 2 BN columns wide (its halves summed
-  // when drained), otherwise BN.
-  static constexpr bool FUSE_HL = NSPLIT == 2 && !PAIR;
-  static constexpr int DW = FUSE_HL ? 2 * BN : BN;
-  static constexpr int TMEM_COLS = 2 * DW;                    // two accumulators, used in turn
+  static_assert(!WIDE || NSPLIT == 2, "the wide form is for split operands");
+  static constexpr int DW = WIDE ? 2 * BN : BN;              // accumulator width (columns)
+  static constexpr int NBUF = 3 * DW <= 512 ? 3 : 2;         // accumulators, used in turn
+  static constexpr int TMEM_COLS = NBUF * DW <= 256 ? 256 : 512;
   static constexpr int HALF = BN / 2;                        // columns per epilogue warp
   static constexpr int STAGING = 8 * 32 * 16 * 8;            // 8 warps x 32 rows x 16 complex
   static constexpr int DN_TABLE = BN * 8;                     // column offsets of a plane output
@@ -243,12 +171,12 @@ constexpr int EPI_WARPS = 8;
 // group swept column by column, so the tiles in flight at once (one per SM)
 // share a few A row blocks and a part of B instead of all of B.
 constexpr int64_t TILE_GROUP = 8;
-template <int BMT, int BN>
+template <int BN>
 __device__ __forceinline__ void tile_origin(int64_t tile, int64_t n_mt, int64_t n_nt, int64_t* m0, int64_t* n0) {
   const int64_t per_group = TILE_GROUP * n_nt;
   const int64_t g = tile / per_group, r = tile - g * per_group;
   const int64_t rows = min(TILE_GROUP, n_mt - g * TILE_GROUP);
-  *m0 = (g * TILE_GROUP + r % rows) * BMT;
+  *m0 = (g * TILE_GROUP + r % rows) * BM;
   *n0 = (r / rows) * BN;
 }
 
@@ -293,28 +221,18 @@ __device__ __forceinline__ bool write_sub_columns(const TcPlaneOut& po, const fl
 // accumulator with truncation, so a long K accumulation drifts (measured:
 // relative error ~ 7e-9 * K).  The K range is therefore cut into chunks of
 // KB_CHUNK k-blocks; within a chunk the three parts (T1, T2, T3) are
-// accumulated one after another in TMEM, alternating between two
+// accumulated one after another in TMEM, each in the next of NBUF
 // accumulators, and after each part the epilogue warps load it and add it
 // with round-to-nearest FP32 adds into register accumulators
 // Re += T1 - T2, Im += T3 - T1 - T2, while the tensor core already works on
-// the next part in the other accumulator.
-//
-// PAIR (cluster of two CTAs, cta_group::2): the pair walks 256 x BN tiles.
-// Each CTA's producer loads its own 128 rows of A and its half of B into its
-// own shared memory and signals the leader's (rank 0) full barrier, which
-// expects both CTAs' bytes; the leader alone issues the MMAs (M = 256), whose
-// commits arrive on the empty / part-ready barriers of both CTAs; each CTA's
-// epilogue drains its own TMEM lanes (its 128 rows) and arrives on the
-// leader's part-drained barrier. Both CTAs take the leader's reading of the
-// status word, and neither leaves before the other (cluster barrier), so no
-// arrival or copy targets a CTA that has exited.
-template <int KIND, int BN, int NSPLIT, bool PO, bool PAIR>
+// the next part.
+template <int KIND, int BN, int NSPLIT, bool PO, bool WIDE>
 __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
     k_cgemm_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                int64_t M, int64_t N, int64_t K, float2* __restrict__ C, int32_t* status,
                const unsigned* smax_a, const unsigned* smax_b, const __grid_constant__ TcPlaneOut po,
                int splits) {
-  using G = Cfg<BN, NSPLIT, PAIR>;
+  using G = Cfg<BN, NSPLIT, WIDE>;
   constexpr int ELEM = KIND == 0 ? 4 : 2;
   constexpr uint32_t FMT_AB = KIND == 0 ? 2u : (KIND == 1 ? 1u : 0u);   // tf32 / bf16 / f16
   constexpr int BK = ROW_BYTES / ELEM;              // K elements per stage
@@ -323,14 +241,14 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
                              | (FMT_AB << 7)                         // A format
                              | (FMT_AB << 10)                        // B format
                              | (uint32_t(BN >> 3) << 17)             // N
-                             | (uint32_t(G::BM_TILE >> 4) << 24);    // M
+                             | (uint32_t(BM >> 4) << 24);            // M
   constexpr uint32_t IDESC_W = (IDESC & ~(uint32_t(63) << 17)) | (uint32_t((2 * BN) >> 3) << 17);   // N = 2 BN
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
   float2* staging = reinterpret_cast<float2*>(smem + G::NSTAGE * G::STAGE);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G::NSTAGE * G::STAGE + G::STAGING);
-  // [0,NSTAGE) full, [NSTAGE,2NSTAGE) empty, +0..1 accumulator ready, +3..4 accumulator drained
+  // [0,NSTAGE) full, [NSTAGE,2NSTAGE) empty, +0..2 accumulator ready, +3..5 drained
   uint64_t* acc_full = bars + 2 * G::NSTAGE;
   uint64_t* acc_empty = acc_full + 3;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + 3);
@@ -355,20 +273,14 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
 
   // A CTA of an earlier launch gave up on a wait: skip the work (the status
   // word stays set until the host reads and clears it).
-  // (A pair takes the leader's reading after the cluster barrier below.)
   __shared__ int s_skip;
   if (threadIdx.x == 0) s_skip = status ? *reinterpret_cast<volatile int32_t*>(status) : 0;
-  if constexpr (!PAIR) {
-    __syncthreads();
-    if (s_skip) return;
-  }
+  __syncthreads();
+  if (s_skip) return;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t rank = PAIR ? cluster_rank() : 0u;               // CTA within the pair
-  const int64_t unit = PAIR ? blockIdx.x / 2 : blockIdx.x;        // walker index
-  const int64_t n_units = PAIR ? gridDim.x / 2 : gridDim.x;
   const int64_t n_nt = (N + BN - 1) / BN;
-  const int64_t n_mt = (M + G::BM_TILE - 1) / G::BM_TILE;
+  const int64_t n_mt = (M + BM - 1) / BM;
   // split-K: work item t = output tile t % (n_mt n_nt) over the k-blocks of
   // split t / (n_mt n_nt), whose partial product goes to C + split M N
   const int64_t n_out_tiles = n_mt * n_nt;
@@ -389,51 +301,33 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
     }
     for (int p = 0; p < 3; ++p) {
       mbar_init(smem_u32(&acc_full[p]), 1);
-      mbar_init(smem_u32(&acc_empty[p]), PAIR ? 2 * EPI_WARPS : EPI_WARPS);
+      mbar_init(smem_u32(&acc_empty[p]), EPI_WARPS);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  // a pair: both CTAs running and their barriers initialised before any
-  // arrival or copy crosses over, and before the joint TMEM allocation
-  if constexpr (PAIR) cluster_sync_all();
   if (warp == 1) {
-    if constexpr (PAIR) {   // the same columns in both CTAs
-      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                       smem_u32(tmem_holder)),
-                   "r"(G::TMEM_COLS)
-                   : "memory");
-      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
-    } else {
-      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                       smem_u32(tmem_holder)),
-                   "r"(G::TMEM_COLS)
-                   : "memory");
-      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_holder)),
+                 "r"(G::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if constexpr (PAIR) {
-    if (threadIdx.x == 0 && rank != 0) s_skip = int(ld_cluster_u32(cluster_addr(smem_u32(&s_skip), 0)));
-    __syncthreads();
-  }
   const uint32_t tmem = *tmem_holder;
-  const bool run = !PAIR || s_skip == 0;
 
-  if (!run) {
-  } else if (warp == 0) {
+  if (warp == 0) {
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_a)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_b)) : "memory");
       int i = 0;
       bool ok = true;
-      for (int64_t tile = unit; tile < n_tiles && ok; tile += n_units) {
+      for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
       int64_t m0, n0;
-      tile_origin<G::BM_TILE, BN>(tile % n_out_tiles, n_mt, n_nt, &m0, &n0);
-      const int64_t ma = m0 + int64_t(rank) * BM, nb = n0 + int64_t(rank) * G::BN_CTA;   // this CTA's rows
+      tile_origin<BN>(tile % n_out_tiles, n_mt, n_nt, &m0, &n0);
       int kbs, kbe;
       krange(tile, &kbs, &kbe);
       for (int kb0 = kbs; kb0 < kbe && ok; kb0 += KB_CHUNK) {
@@ -442,29 +336,24 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
           for (int kb = kb0; kb < kb1; ++kb, ++i) {
             const int s = i % G::NSTAGE;
             const uint32_t ph = (i / G::NSTAGE) & 1;
-            if (!mbar_wait<PAIR>(smem_u32(&bars[G::NSTAGE + s]), ph ^ 1, abort_flag, status)) {
+            if (!mbar_wait(smem_u32(&bars[G::NSTAGE + s]), ph ^ 1, abort_flag, status)) {
               ok = false;
               break;
             }
             const uint32_t full = smem_u32(&bars[s]);
-            uint32_t sig = full;                          // barrier the copies complete on
-            if constexpr (PAIR) sig = cluster_addr(full, 0);
-            if (rank == 0) mbar_expect_tx(full, (PAIR ? 2 : 1) * G::STAGE);
+            mbar_expect_tx(full, G::STAGE);
             const uint32_t sa = smem_u32(smem + s * G::STAGE);
             for (int sp = 0; sp < NSPLIT; ++sp)
-              tma_load_2d<PAIR>(sa + sp * G::A_TILE, &map_a, sig, kb * BK,
-                                int((part * NSPLIT + sp) * M + ma));
+              tma_load_2d(sa + sp * G::A_TILE, &map_a, full, kb * BK,
+                          int((part * NSPLIT + sp) * M + m0));
             for (int sp = 0; sp < NSPLIT; ++sp)
-              tma_load_2d<PAIR>(sa + NSPLIT * G::A_TILE + sp * G::B_TILE, &map_b, sig, kb * BK,
-                                int((part * NSPLIT + sp) * N + nb));
+              tma_load_2d(sa + NSPLIT * G::A_TILE + sp * G::B_TILE, &map_b, full, kb * BK,
+                          int((part * NSPLIT + sp) * N + n0));
           }
         }
       }
       }
-      if (!ok && PAIR) {
-        // the copies complete on the leader's barriers: give them a bounded
-        // time to land instead (a pair also pauses before its final barrier)
-      } else if (!ok) {   // let the copies this lane started land before the CTA exits
+      if (!ok) {   // let the copies this lane started land before the CTA exits
         for (int j = i > G::NSTAGE ? i - G::NSTAGE : 0; j < i; ++j) {
           volatile int never = 0;
           mbar_wait(smem_u32(&bars[j % G::NSTAGE]), (j / G::NSTAGE) & 1, &never, nullptr);
@@ -472,19 +361,19 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
       }
     }
   } else if (warp == 1) {
-    if (lane == 0 && rank == 0) {   // a pair's leader issues the MMAs of both CTAs
+    if (lane == 0) {
       int i = 0, jb = 0;   // stage counter; (chunk, part) job counter across tiles
       bool ok = true;
-      for (int64_t tile = unit; tile < n_tiles && ok; tile += n_units) {
+      for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
       int kbs, kbe;
       krange(tile, &kbs, &kbe);
       for (int kb0 = kbs; kb0 < kbe && ok; kb0 += KB_CHUNK) {
         const int kb1 = min(kbe, kb0 + KB_CHUNK);
         for (int part = 0; part < 3 && ok; ++part, ++jb) {
-          // job jb accumulates in buffer jb & 1, whose previous job (jb - 2)
-          // must have been drained
-          const int buf = jb & 1, use = jb >> 1;
-          if (use > 0 && !mbar_wait<PAIR>(smem_u32(&acc_empty[buf]), (use - 1) & 1, abort_flag, status)) {
+          // job jb accumulates in buffer jb % NBUF, whose previous job
+          // (jb - NBUF) must have been drained
+          const int buf = jb % G::NBUF, use = jb / G::NBUF;
+          if (use > 0 && !mbar_wait(smem_u32(&acc_empty[buf]), (use - 1) & 1, abort_flag, status)) {
             ok = false;
             break;
           }
@@ -493,20 +382,20 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
           for (int kb = kb0; kb < kb1; ++kb, ++i) {
             const int s = i % G::NSTAGE;
             const uint32_t ph = (i / G::NSTAGE) & 1;
-            if (!mbar_wait<PAIR>(smem_u32(&bars[s]), ph, abort_flag, status)) {
+            if (!mbar_wait(smem_u32(&bars[s]), ph, abort_flag, status)) {
               ok = false;
               break;
             }
             tc_fence_after();
             const uint32_t sa = smem_u32(smem + s * G::STAGE);
             const uint32_t sb = sa + NSPLIT * G::A_TILE;
-            if constexpr (G::FUSE_HL) {
+            if constexpr (WIDE) {
 #pragma unroll
               for (int ks = 0; ks < BK / MMA_K; ++ks) {
                 // [hi.hi | hi.lo] over B hi and B lo as one 2 BN-row operand, then lo.hi
-                mma<KIND, PAIR>(d, smem_desc(sa + ks * 32), smem_desc(sb + ks * 32), IDESC_W,
-                                ((kb - kb0) | ks) != 0 ? 1u : 0u);
-                mma<KIND, PAIR>(d, smem_desc(sa + G::A_TILE + ks * 32), smem_desc(sb + ks * 32), IDESC, 1u);
+                mma<KIND>(d, smem_desc(sa + ks * 32), smem_desc(sb + ks * 32), IDESC_W,
+                          ((kb - kb0) | ks) != 0 ? 1u : 0u);
+                mma<KIND>(d, smem_desc(sa + G::A_TILE + ks * 32), smem_desc(sb + ks * 32), IDESC, 1u);
               }
             } else {
 #pragma unroll
@@ -516,13 +405,13 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
                 for (int ks = 0; ks < BK / MMA_K; ++ks) {
                   const uint64_t adesc = smem_desc(sa + ai * G::A_TILE + ks * 32);
                   const uint64_t bdesc = smem_desc(sb + bi * G::B_TILE + ks * 32);
-                  mma<KIND, PAIR>(d, adesc, bdesc, IDESC, ((kb - kb0) | pr | ks) != 0 ? 1u : 0u);
+                  mma<KIND>(d, adesc, bdesc, IDESC, ((kb - kb0) | pr | ks) != 0 ? 1u : 0u);
                 }
               }
             }
-            tc_commit<PAIR>(smem_u32(&bars[G::NSTAGE + s]));
+            tc_commit(smem_u32(&bars[G::NSTAGE + s]));
           }
-          if (ok) tc_commit<PAIR>(smem_u32(&acc_full[buf]));   // fires when this job's MMAs are done
+          if (ok) tc_commit(smem_u32(&acc_full[buf]));   // fires when this job's MMAs are done
         }
       }
       }
@@ -551,10 +440,9 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
     }
     bool ok = true;
     int jb = 0;   // (chunk, part) job counter, as the MMA issuer's
-    for (int64_t tile = unit; tile < n_tiles && ok; tile += n_units) {
+    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
       int64_t m0, n0;
-      tile_origin<G::BM_TILE, BN>(tile % n_out_tiles, n_mt, n_nt, &m0, &n0);
-      m0 += int64_t(rank) * BM;   // this CTA's 128 rows of the tile
+      tile_origin<BN>(tile % n_out_tiles, n_mt, n_nt, &m0, &n0);
       float2* Ct = C + (tile / n_out_tiles) * M * N;   // this split's partial product
       int kbs, kbe;
       krange(tile, &kbs, &kbe);
@@ -563,8 +451,8 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
       for (int j = 0; j < G::HALF; ++j) re[j] = im[j] = 0.f;
       for (int kb0 = kbs; kb0 < kbe && ok; kb0 += KB_CHUNK) {
         for (int part = 0; part < 3; ++part, ++jb) {
-          const int buf = jb & 1, use = jb >> 1;
-          if (!mbar_wait<PAIR>(smem_u32(&acc_full[buf]), use & 1, abort_flag, status)) {
+          const int buf = jb % G::NBUF, use = jb / G::NBUF;
+          if (!mbar_wait(smem_u32(&acc_full[buf]), use & 1, abort_flag, status)) {
             ok = false;
             break;
           }
@@ -574,12 +462,12 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
           for (int sub = 0; sub < G::HALF / 16; ++sub) {
             uint32_t r[16], r2[16];
             tmem_ld16(acc + uint32_t(sub * 16), r);
-            if constexpr (G::FUSE_HL) tmem_ld16(acc + uint32_t(BN + sub * 16), r2);   // the hi.lo half
+            if constexpr (WIDE) tmem_ld16(acc + uint32_t(BN + sub * 16), r2);   // the hi.lo half
             tmem_wait_ld();
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               float t = __uint_as_float(r[j]);
-              if constexpr (G::FUSE_HL) t += __uint_as_float(r2[j]);
+              if constexpr (WIDE) t += __uint_as_float(r2[j]);
               if (part == 0) {
                 re[sub * 16 + j] += t;
                 im[sub * 16 + j] -= t;
@@ -594,12 +482,8 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
           tc_fence_before();
           __syncwarp();
           if (lane == 0) {
-            if constexpr (PAIR) {   // the leader's barrier counts both CTAs' warps
-              mbar_arrive_cluster(cluster_addr(smem_u32(&acc_empty[buf]), 0));
-            } else {
-              asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[buf]))
-                           : "memory");
-            }
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[buf]))
+                         : "memory");
           }
         }
       }
@@ -688,24 +572,12 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
     }
   }
   tc_fence_before();
-  if constexpr (PAIR) {
-    __syncthreads();
-    if (*abort_flag) pause_ns(2000000);   // 2 ms for copies and MMAs already issued
-    cluster_sync_all();
-  } else {
-    __syncthreads();
-  }
+  __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    if constexpr (PAIR) {
-      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                   "r"(G::TMEM_COLS)
-                   : "memory");
-    } else {
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                   "r"(G::TMEM_COLS)
-                   : "memory");
-    }
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(G::TMEM_COLS)
+                 : "memory");
   }
 }
 
@@ -740,46 +612,34 @@ bool encode(int kind, const void* ptr, int64_t rows, int64_t K, int box_rows, CU
   return r == CUDA_SUCCESS;
 }
 
-template <int KIND, int BN, int NSPLIT, bool PO, bool PAIR>
+template <int KIND, int BN, int NSPLIT, bool PO, bool WIDE>
 cudaError_t launch_t(const TcGemmMaps& maps, int64_t M, int64_t N, int64_t K, float2* C,
                      int32_t* status, cudaStream_t s, const unsigned* sa, const unsigned* sb,
                      const TcPlaneOut& po, int splits) {
-  using G = Cfg<BN, NSPLIT, PAIR>;
-  auto kern = k_cgemm_tc<KIND, BN, NSPLIT, PO, PAIR>;
+  using G = Cfg<BN, NSPLIT, WIDE>;
+  auto kern = k_cgemm_tc<KIND, BN, NSPLIT, PO, WIDE>;
   static int configured_dev = -1;
-  static int sms = 0, max_pairs = 0;   // SMs; clusters of two that fit at once
   int dev = 0;
   cudaGetDevice(&dev);
-  cudaLaunchConfig_t cfg{};
-  cfg.blockDim = dim3(64 + 32 * EPI_WARPS);
-  cfg.dynamicSmemBytes = G::SMEM;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[2];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  attr[1].id = cudaLaunchAttributeClusterDimension;
-  attr[1].val.clusterDim.x = 2;
-  attr[1].val.clusterDim.y = 1;
-  attr[1].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = PAIR ? 2 : 1;
   if (configured_dev != dev) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
     if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    if (PAIR) {
-      cudaLaunchConfig_t q = cfg;
-      q.gridDim = dim3(unsigned(sms & ~1));
-      e = cudaOccupancyMaxActiveClusters(&max_pairs, reinterpret_cast<const void*>(kern), &q);
-      if (e != cudaSuccess) return e;
-      if (max_pairs < 1) return cudaErrorInvalidConfiguration;
-    }
     configured_dev = dev;
   }
-  const int64_t tiles = ((M + G::BM_TILE - 1) / G::BM_TILE) * ((N + BN - 1) / BN) * splits;
-  const int64_t units = PAIR ? max_pairs : sms;
-  cfg.gridDim = dim3(unsigned((tiles < units ? tiles : units) * (PAIR ? 2 : 1)));
+  static int sms = 0;
+  if (sms == 0) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN) * splits;
+  const unsigned grid = unsigned(tiles < sms ? tiles : sms);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(64 + 32 * EPI_WARPS);
+  cfg.dynamicSmemBytes = G::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kern, maps.a, maps.b, M, N, K, C, status, sa, sb, po, splits);
 }
 
@@ -787,17 +647,14 @@ cudaError_t launch_t(const TcGemmMaps& maps, int64_t M, int64_t N, int64_t K, fl
 
 bool tc_available() { return get_encode() != nullptr; }
 
-bool tc_pair_shape(int kind, int nsplit, int bn, int64_t M) {
-  return kind != 0 && nsplit == 2 && bn == 128 && M >= 2 * BM && (M % (2 * BM) == 0 || M >= 16 * BM);
-}
+bool tc_wide_mma(int nsplit, int bn, int64_t K) { return nsplit == 2 && (bn == 64 || K >= 2048); }
 
 bool tc_encode_maps(int kind, int nsplit, int bn, const void* a_planes, int64_t M,
                     const void* b_planes, int64_t N, int64_t K, TcGemmMaps* maps) {
   if (K % 8 != 0 || M <= 0 || N <= 0) return false;
   const int64_t planes = 3 * nsplit;
-  maps->pair = tc_pair_shape(kind, nsplit, bn, M);
   return encode(kind, a_planes, planes * M, K, BM, &maps->a) &&
-         encode(kind, b_planes, planes * N, K, maps->pair ? bn / 2 : bn, &maps->b);
+         encode(kind, b_planes, planes * N, K, bn, &maps->b);
 }
 
 cudaError_t launch_cgemm_tc(int kind, int nsplit, int bn, const TcGemmMaps& maps, int64_t M,
@@ -813,22 +670,15 @@ cudaError_t launch_cgemm_tc(int kind, int nsplit, int bn, const TcGemmMaps& maps
     return cudaErrorInvalidValue;
   if (po.base && kind == 2 && (!po.out_scale || !po.out_max || !po.max_a || !po.max_b || !smax_a || !smax_b))
     return cudaErrorInvalidValue;
-  // maps encoded for a pair (B boxes of bn / 2 rows) go to the pair kernel only
-  if (maps.pair != tc_pair_shape(kind, nsplit, bn, M)) return cudaErrorInvalidValue;
-#define QF_TC(KD, B, S)                                                                                  \
-  if (kind == KD && bn == B && nsplit == S && !maps.pair)                                                \
-    return po.base ? launch_t<KD, B, S, true, false>(maps, M, N, K, C, status, s, smax_a, smax_b, po, splits) \
-                   : launch_t<KD, B, S, false, false>(maps, M, N, K, C, status, s, smax_a, smax_b, po, splits);
-#define QF_TC_PAIR(KD)                                                                                   \
-  if (kind == KD && bn == 128 && nsplit == 2 && maps.pair)                                               \
-    return po.base ? launch_t<KD, 128, 2, true, true>(maps, M, N, K, C, status, s, smax_a, smax_b, po, splits) \
-                   : launch_t<KD, 128, 2, false, true>(maps, M, N, K, C, status, s, smax_a, smax_b, po, splits);
-  QF_TC(0, 64, 1) QF_TC(0, 64, 2) QF_TC(0, 128, 1) QF_TC(0, 128, 2)
-  QF_TC(1, 64, 1) QF_TC(1, 64, 2) QF_TC(1, 128, 1) QF_TC(1, 128, 2)
-  QF_TC(2, 64, 2) QF_TC(2, 128, 2)
-  QF_TC_PAIR(1) QF_TC_PAIR(2)
+  const bool wide = tc_wide_mma(nsplit, bn, K);
+#define QF_TC(KD, B, S, W)                                                                               \
+  if (kind == KD && bn == B && nsplit == S && wide == W)                                                 \
+    return po.base ? launch_t<KD, B, S, true, W>(maps, M, N, K, C, status, s, smax_a, smax_b, po, splits) \
+                   : launch_t<KD, B, S, false, W>(maps, M, N, K, C, status, s, smax_a, smax_b, po, splits);
+  QF_TC(0, 64, 1, false) QF_TC(0, 64, 2, true) QF_TC(0, 128, 1, false) QF_TC(0, 128, 2, false) QF_TC(0, 128, 2, true)
+  QF_TC(1, 64, 1, false) QF_TC(1, 64, 2, true) QF_TC(1, 128, 1, false) QF_TC(1, 128, 2, false) QF_TC(1, 128, 2, true)
+  QF_TC(2, 64, 2, true) QF_TC(2, 128, 2, false) QF_TC(2, 128, 2, true)
 #undef QF_TC
-#undef QF_TC_PAIR
   return cudaErrorInvalidValue;
 }
 

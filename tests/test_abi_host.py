@@ -382,20 +382,20 @@ def test_bf16x3_plane_format_by_chain_length(Plan):
     assert fmt(c2_problem(0), "fp32")["plane_format"] == 0
 
 
-def test_cta_pair_choice(Plan):
-    """Tensor-core steps with 16-bit split operands, 128-wide tiles and at
-    least 256 rows (a multiple of 256, or 2048 and more) run on SM pairs
-    (256 x 128 tiles); tf32 operands, 64-wide tiles and short products stay on
-    single SMs.  The 7x7 1+32+1 plan's 4096^3 products and 65536-row absorbs
-    are pair steps."""
-    def rule(s):
-        return s["bn"] == 128 and s["M"] >= 256 and (s["M"] % 256 == 0 or s["M"] >= 2048)
-    for prec in ("bf16x3", "fp16x3", "tf32x3", "fp32"):
+def test_wide_mma_choice(Plan):
+    """Split tensor-core products take one MMA of width 2 bn ([hi.hi | hi.lo])
+    plus one of width bn per k-step for 64-wide tiles and, with 128-wide
+    tiles, for K >= 2048; otherwise three of width bn.  In the 7x7 1+32+1
+    plan that puts the 4096^3 products on the wide form and the K = 256
+    region absorbs on the three-MMA form; unsplit precisions never use it."""
+    for prec in ("bf16x3", "fp16x3", "tf32x3", "bf16", "fp32"):
         steps = Plan(c2_problem(0), prec, device=-1).steps(1)
         for s in steps:
-            want = s["kernel"] == "tensor_cores" and prec != "tf32x3" and rule(s)
-            assert s["cta_pair"] == int(want), (prec, s["M"], s["N"], s["K"], s["bn"])
-        if prec in ("bf16x3", "fp16x3"):
+            split = prec in ("bf16x3", "fp16x3", "tf32x3")
+            want = s["kernel"] == "tensor_cores" and split and (s["bn"] == 64 or s["K"] >= 2048)
+            assert s["tc_wide"] == int(want), (prec, s["M"], s["N"], s["K"], s["bn"])
+        if prec == "bf16x3":
             big = [s for s in steps if (s["M"], s["N"], s["K"]) == (4096, 4096, 4096)]
             absorb = [s for s in steps if (s["M"], s["N"], s["K"]) == (65536, 256, 256)]
-            assert big and absorb and all(s["cta_pair"] for s in big + absorb)
+            assert big and absorb
+            assert all(s["tc_wide"] for s in big) and not any(s["tc_wide"] for s in absorb)

@@ -97,16 +97,16 @@ def test_cgemm_tensor_core(K, prec, tol):
     assert K.device_status(0) == 0
 
 
-# products that run on SM pairs (16-bit split operands, N >= 128, M >= 256):
-# one MMA step of K, a K tail with ragged N, ragged M above 2048 (the second
-# SM's rows partly and wholly past M), several tiles per pair, a long K
-PAIR_SHAPES = [(256, 128, 16), (512, 200, 72), (2100, 256, 64), (2176, 136, 200), (8192, 1024, 64),
-               (256, 136, 4096)]
+# split products in both MMA forms: the wide form (64-wide tiles, and
+# 128-wide tiles with K >= 2048: two accumulators in turn) with ragged M and
+# N, a K tail, several tiles per SM; the three-MMA form just below K = 2048
+WIDE_SHAPES = [(256, 48, 16), (1000, 100, 200), (300, 128, 2048), (2100, 200, 2056), (8192, 1024, 2048),
+               (4096, 256, 2040), (640, 130, 4096)]
 
 
-@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-4), ("fp16x3", 1e-5)])
-def test_cgemm_cta_pairs(K, prec, tol):
-    for i, (M, N, Kd) in enumerate(PAIR_SHAPES):
+@pytest.mark.parametrize("prec,tol", [("tf32x3", 1e-5), ("bf16x3", 1e-4), ("fp16x3", 1e-5)])
+def test_cgemm_wide_mma_form(K, prec, tol):
+    for i, (M, N, Kd) in enumerate(WIDE_SHAPES):
         err = _gemm_case(K, prec, M, N, Kd, 40 + i)
         assert err < tol, (prec, M, N, Kd, err)
     assert K.device_status(0) == 0
