@@ -16,7 +16,8 @@
 //   warp 1      allocates TMEM (two or three accumulators, used in turn) and
 //               one lane issues the tcgen05.mma instructions of each stage,
 //               then tcgen05.commit releases the stage;
-//   warps 2-9   epilogue: after each part of each K chunk, tcgen05.ld of that
+//   warps 2-3   idle (they complete warpgroup 0 for the register split)
+//   warps 4-11  epilogue: after each part of each K chunk, tcgen05.ld of that
 //               part's accumulator, round-to-nearest FP32 promotion into
 //               Re/Im register accumulators; at the end, staged coalesced
 //               complex64 stores (or the next product's operand planes).
@@ -166,6 +167,18 @@ struct Cfg {
 };
 constexpr int KB_CHUNK = 8;      // k-blocks accumulated in TMEM before promotion to registers
 constexpr int EPI_WARPS = 8;
+// Block of three warpgroups: warpgroup 0 = warp 0 (TMA producer), warp 1
+// (TMEM owner, MMA issuer) and two idle warps; warpgroups 1 and 2 = the
+// epilogue warps.  Launched at REG_LAUNCH registers per thread, warpgroup 0
+// gives registers back (REG_LOW) and the epilogue warpgroups take them
+// (REG_HIGH), so that the epilogue's register accumulators (two per column
+// of its half tile) do not spill: 128 REG_LOW + 256 REG_HIGH must not exceed
+// 384 REG_LAUNCH, or the increase would wait forever (checked on the host
+// against the compiled kernel's register count before the first launch).
+constexpr int EPI_WARP0 = 4;
+constexpr int THREADS = 32 * (EPI_WARP0 + EPI_WARPS);
+constexpr int REG_LAUNCH = 168, REG_LOW = 56, REG_HIGH = 224;
+static_assert(128 * REG_LOW + 32 * EPI_WARPS * REG_HIGH <= THREADS * REG_LAUNCH, "register split");
 
 // Tile order of the persistent walk: groups of TILE_GROUP row blocks, each
 // group swept column by column, so the tiles in flight at once (one per SM)
@@ -211,7 +224,7 @@ __device__ __forceinline__ bool write_sub_columns(const TcPlaneOut& po, const fl
 
 // Persistent: one CTA per SM walks the output tiles (tile += gridDim.x, N
 // fastest).  Block: warp 0 = TMA producer, warp 1 = TMEM owner + MMA issuer,
-// warps 2..9 = epilogue (two warps per TMEM lane quarter, each owning half of
+// warps 4..11 = epilogue (two warps per TMEM lane quarter, each owning half of
 // the BN columns).  Barrier set-up and TMEM allocation happen once per CTA,
 // the producer runs ahead into the next tile, and the final store of a tile
 // (from registers, through a dedicated staging area) overlaps the next tile's
@@ -227,7 +240,7 @@ __device__ __forceinline__ bool write_sub_columns(const TcPlaneOut& po, const fl
 // Re += T1 - T2, Im += T3 - T1 - T2, while the tensor core already works on
 // the next part.
 template <int KIND, int BN, int NSPLIT, bool PO, bool WIDE>
-__global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
+__global__ void __launch_bounds__(THREADS, 1)
     k_cgemm_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                int64_t M, int64_t N, int64_t K, float2* __restrict__ C, int32_t* status,
                const unsigned* smax_a, const unsigned* smax_b, const __grid_constant__ TcPlaneOut po,
@@ -319,6 +332,8 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
 
+  if (warp < EPI_WARP0) {
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_LOW));
   if (warp == 0) {
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_a)) : "memory");
@@ -416,12 +431,14 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
       }
       }
     }
+  }
   } else {
-    // epilogue warps 2..9: TMEM lane quarter q = warp % 4, column half h
-    const int q = warp & 3, h = (warp - 2) >> 2;
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_HIGH));
+    // epilogue warps 4..11: TMEM lane quarter q = warp % 4, column half h
+    const int q = warp & 3, h = (warp - EPI_WARP0) >> 2;
     const int col0 = h * G::HALF;
     const uint32_t lane_base = tmem + (uint32_t(q * 32) << 16) + uint32_t(col0);
-    float2* st = staging + (warp - 2) * (32 * 16);
+    float2* st = staging + (warp - EPI_WARP0) * (32 * 16);
     // fp16 operands were scaled by exact powers of two: undo both here
     float unscale = 1.f;
     if constexpr (KIND == 2) {
@@ -435,7 +452,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
     if constexpr (PO && KIND == 2) {
       const float bound = 3.f * float(K) * __uint_as_float(*po.max_a) * __uint_as_float(*po.max_b);
       const unsigned bb = __float_as_uint(bound);
-      if (blockIdx.x == 0 && warp == 2 && lane == 0) *po.out_scale = bb;
+      if (blockIdx.x == 0 && warp == EPI_WARP0 && lane == 0) *po.out_scale = bb;
       po_factor = fp16_scale_of(bb) * unscale;
     }
     bool ok = true;
@@ -622,7 +639,13 @@ cudaError_t launch_t(const TcGemmMaps& maps, int64_t M, int64_t N, int64_t K, fl
   int dev = 0;
   cudaGetDevice(&dev);
   if (configured_dev != dev) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+    // the register split assumes the block is launched with REG_LAUNCH
+    // registers per thread
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    if (fa.numRegs < REG_LAUNCH) return cudaErrorInvalidConfiguration;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
     if (e != cudaSuccess) return e;
     configured_dev = dev;
   }
@@ -632,7 +655,7 @@ cudaError_t launch_t(const TcGemmMaps& maps, int64_t M, int64_t N, int64_t K, fl
   const unsigned grid = unsigned(tiles < sms ? tiles : sms);
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(64 + 32 * EPI_WARPS);
+  cfg.blockDim = dim3(THREADS);
   cfg.dynamicSmemBytes = G::SMEM;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
