@@ -294,6 +294,34 @@ def per_step_roofline(plan, n_bs, precision, peak_tflops, peak_gbs, measured_ms_
             "peaks": "measured bf16 sustained (tensor), measured copy (HBM)"}
 
 
+def per_shape_roofline(shapes, precision, peak_tflops, peak_gbs, top=8):
+    """The tensor-core launches of the profiled pass by product shape: per
+    shape its launches, mean CUDA-event time, the bound that limits it (MMA
+    flops / tensor peak or algorithmic bytes / HBM peak, bytes as in
+    per_step_roofline) and the achieved fraction of that bound; the `top`
+    shapes by summed time."""
+    nsplit = 1 if precision in ("bf16", "tf32") else 2
+    plane_b = 3 * nsplit * (4 if precision.startswith("tf32") else 2)
+    rows = []
+    for r in shapes:
+        if r["cls"] != "gemm_tc" or r["launches"] == 0 or r["ms"] <= 0:
+            continue
+        M, N, K = r["M"], r["N"], r["K"]
+        flops = r["mma_flops"] / r["launches"]
+        byts = (M * K + N * K) * plane_b + M * N * (plane_b if r["out_planes"] else 8)
+        t = r["ms"] * 1e-3 / r["launches"]
+        tf, tb = flops / (peak_tflops * 1e12), byts / (peak_gbs * 1e9)
+        hbm = tb > tf
+        rows.append({"M": M, "N": N, "K": K, "out_planes": r["out_planes"], "launches": r["launches"],
+                     "share_ms": round(r["ms"], 3), "us": round(t * 1e6, 2),
+                     "bound": "hbm" if hbm else "tensor",
+                     "achieved": round(byts / t / 1e9, 1) if hbm else round(flops / t / 1e12, 1),
+                     "unit": "GB/s" if hbm else "TFLOP/s",
+                     "frac": round((tb if hbm else tf) / t, 4)})
+    rows.sort(key=lambda x: -x["share_ms"])
+    return rows[:top]
+
+
 def permute_sweep(api, torch, peaks):
     """Complex64 tensors of 2^m entries, m = 20..30: (i) m binary axes, 8
     seeded random permutations each; (ii) axes of dimension 16 (plus one of
@@ -777,7 +805,8 @@ def run_ours(args):
                                + (" x 1.1/2.25 (nominal tf32/bf16 ratio)" if tf_scale != 1.0 else ""),
                 "flops_convention": "executed tensor-core flops: 3M x (hi.hi+hi.lo+lo.hi) = 18 per complex MAC",
                 "per_step": per_step_roofline(plan, N_BS, args.precision, peak, peaks["hbm_gbs"],
-                                              tc["ms"] / prof_steps)}
+                                              tc["ms"] / prof_steps),
+                "per_shape": per_shape_roofline(plan.profile_shapes(), args.precision, peak, peaks["hbm_gbs"])}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,

@@ -359,6 +359,26 @@ typedef struct {
 } qflex_profile;
 qflex_status qflex_plan_profile(qflex_plan plan, int32_t mode, qflex_profile* out);
 
+/* The GEMM launches of the profiled totals by product shape, for a roofline
+ * per step kind (e.g. the region absorbs apart from the square products):
+ * one record per (class, M, N, K, out_planes) of the class-2 and class-3
+ * launches recorded since profiling was last started.  out_planes = 1 when
+ * the epilogue wrote the next product's operand planes instead of complex64.
+ * Call after qflex_plan_profile(plan, ., out != NULL) has read the recorded
+ * events (else QFLEX_ERR_ARG).  Writes min(cap, count) records to the host
+ * array out (caller-owned) in ascending (class, M, N, K) order and the count
+ * to *n; cap = 0 with out = NULL queries the count.  Host-only plans:
+ * QFLEX_ERR_UNSUPPORTED. */
+typedef struct {
+  int32_t cls;
+  int32_t out_planes;
+  int64_t M, N, K;
+  int64_t launches;
+  double ms;          /* summed event-to-event milliseconds */
+  double mma_flops;   /* real tensor-core flops executed (class 3) */
+} qflex_profile_shape;
+qflex_status qflex_plan_profile_shapes(qflex_plan plan, qflex_profile_shape* out, int64_t cap, int64_t* n);
+
 /* Synchronize the plan's last stream and report its device status word
  * (QFLEX_ERR_DEVICE_TIMEOUT if a bounded wait ran out; QFLEX_ERR_PLAN if a
  * fused epilogue computed a destination outside its operand planes, which

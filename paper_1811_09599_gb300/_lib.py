@@ -79,6 +79,11 @@ class Profile(C.Structure):
                 ("mma_flops", C.c_double * 5), ("bytes", C.c_double * 5)]
 
 
+class ProfileShape(C.Structure):
+    _fields_ = [("cls", C.c_int32), ("out_planes", C.c_int32), ("M", C.c_int64), ("N", C.c_int64),
+                ("K", C.c_int64), ("launches", C.c_int64), ("ms", C.c_double), ("mma_flops", C.c_double)]
+
+
 PROFILE_CLASSES = ("gridtensor", "permute", "gemm_fp32", "gemm_tc", "slicesum")
 
 # (name, restype, argtypes) for every exported symbol of include/qflex.h
@@ -108,6 +113,7 @@ SIGNATURES = [
     ("qflex_plan_autotune", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32),
                                       C.POINTER(C.c_double)]),
     ("qflex_plan_profile", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Profile)]),
+    ("qflex_plan_profile_shapes", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     ("qflex_permute", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int64),
                                 C.POINTER(C.c_int32), C.c_void_p]),
     ("qflex_cgemm_workspace_size", C.c_int, [C.c_int32, C.c_int64, C.c_int64, C.c_int64,

@@ -276,6 +276,16 @@ class Plan:
                       "mma_flops": pr.mma_flops[i], "bytes": pr.bytes[i]}
                 for i, cls in enumerate(_lib.PROFILE_CLASSES)}
 
+    def profile_shapes(self) -> list:
+        """The GEMM launches of the last profile_stop() by product shape:
+        dicts with cls, M, N, K, out_planes, launches, ms, mma_flops."""
+        n = C.c_int64()
+        check(self.lib.qflex_plan_profile_shapes(self.handle, None, 0, C.byref(n)))
+        arr = (_lib.ProfileShape * max(1, n.value))()
+        check(self.lib.qflex_plan_profile_shapes(self.handle, arr, n.value, C.byref(n)))
+        return [{"cls": _lib.PROFILE_CLASSES[r.cls], "M": r.M, "N": r.N, "K": r.K, "out_planes": r.out_planes,
+                 "launches": r.launches, "ms": r.ms, "mma_flops": r.mma_flops} for r in arr[:n.value]]
+
     def sync(self):
         check(self.lib.qflex_plan_sync(self.handle))
 

@@ -187,9 +187,17 @@ struct Prof {
   int32_t mask = 0;
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
-  struct Rec { int cls; size_t e0; double flops, mma, bytes; };
+  struct Rec { int cls; size_t e0; double flops, mma, bytes; int64_t M, N, K; int planes; };
   std::vector<Rec> recs;
   qflex_profile tot{};
+  // GEMM launches by (class, M, N, K, output as operand planes)
+  std::map<std::tuple<int, int64_t, int64_t, int64_t, int>, qflex_profile_shape> shapes;
+};
+
+// The product shape a GEMM launch records with its event pair.
+struct ProfShape {
+  int64_t M = 0, N = 0, K = 0;
+  int planes = 0;
 };
 
 // One problem of a plan: network, schedule, buffers (a slice of the plan's
@@ -993,7 +1001,8 @@ cudaError_t produce(const Sub& p, const Operand& op, bool tc, int64_t rows, int6
 
 // Launch `fn` on `s`, bracketed by an event pair when the plan is profiling.
 template <class F>
-cudaError_t timed(Sub& sp, int cls, double flops, double mma, double bytes, cudaStream_t s, F&& fn) {
+cudaError_t timed_shape(Sub& sp, int cls, double flops, double mma, double bytes, const ProfShape& sh,
+                        cudaStream_t s, F&& fn) {
   Prof& p = *sp.prof;
   if (!p.on || !((p.mask >> cls) & 1)) return fn();
   while (p.pool.size() < p.used + 2) {
@@ -1007,8 +1016,12 @@ cudaError_t timed(Sub& sp, int cls, double flops, double mma, double bytes, cuda
   cudaError_t r = cudaEventRecord(p.pool[i], s);
   if (r != cudaSuccess) return r;
   if ((r = fn()) != cudaSuccess) return r;
-  p.recs.push_back({cls, i, flops, mma, bytes});
+  p.recs.push_back({cls, i, flops, mma, bytes, sh.M, sh.N, sh.K, sh.planes});
   return cudaEventRecord(p.pool[i + 1], s);
+}
+template <class F>
+cudaError_t timed(Sub& sp, int cls, double flops, double mma, double bytes, cudaStream_t s, F&& fn) {
+  return timed_shape(sp, cls, flops, mma, bytes, ProfShape{}, s, std::forward<F>(fn));
 }
 
 cudaError_t run_step(Sub& p, const Step& st, int64_t b, const std::vector<int64_t>& vals,
@@ -1048,14 +1061,15 @@ cudaError_t run_step(Sub& p, const Step& st, int64_t b, const std::vector<int64_
   const double mnk = double(st.M) * double(st.N) * double(st.K);
   const double mma = st.tc ? mnk * 3.0 * (p.nsplit == 2 ? 3.0 : 1.0) * 2.0 : 0.0;
   const double gbytes = 8.0 * (double(st.M) * st.K + double(st.N) * st.K + double(st.M) * st.N);
+  const ProfShape shape{st.M, st.N, st.K, st.fuse_out && fused_mode ? 1 : 0};
   if (st.tc)
-    return timed(p, 3, 8.0 * mnk, mma, gbytes, s, [&] {
+    return timed_shape(p, 3, 8.0 * mnk, mma, gbytes, shape, s, [&] {
       return launch_cgemm_tc(p.tc_kind, p.nsplit, st.bn, fused_mode ? st.maps : st.maps_plain, st.M, st.N, st.K, C,
                              p.d_status, s, scale_word(p, st.A, true, fused_mode), scale_word(p, st.B, false, fused_mode),
                              st.fuse_out && fused_mode ? &st.po : nullptr);
     });
   const bool thin = st.fp32_kernel == 1 || (st.fp32_kernel == 0 && st.N <= 32);
-  return timed(p, 2, 8.0 * mnk, 0, gbytes, s, [&] {
+  return timed_shape(p, 2, 8.0 * mnk, 0, gbytes, shape, s, [&] {
     if (st.fuse_out && fused_mode) {
       if (p.tc_kind == 2) {   // fp16 planes: the bound needs the largest parts of A and B
         cudaError_t e2 = launch_absmax(A, st.M * st.K, st.tmax, s);
@@ -2058,6 +2072,17 @@ qflex_status qflex_plan_profile(qflex_plan p, int32_t mode, qflex_profile* out) 
         pr.tot.flops[r.cls] += r.flops;
         pr.tot.mma_flops[r.cls] += r.mma;
         pr.tot.bytes[r.cls] += r.bytes;
+        if (r.M > 0) {
+          qflex_profile_shape& q = pr.shapes[std::make_tuple(r.cls, r.M, r.N, r.K, r.planes)];
+          q.cls = r.cls;
+          q.out_planes = r.planes;
+          q.M = r.M;
+          q.N = r.N;
+          q.K = r.K;
+          q.launches += 1;
+          q.ms += ms;
+          q.mma_flops += r.mma;
+        }
       }
       pr.recs.clear();
       pr.used = 0;
@@ -2067,6 +2092,7 @@ qflex_status qflex_plan_profile(qflex_plan p, int32_t mode, qflex_profile* out) 
     if (mode != 0) {
       if (qflex_status st = drain()) return st;
       pr.tot = qflex_profile{};
+      pr.shapes.clear();
       pr.on = true;
       pr.mask = mode;
     } else {
@@ -2075,6 +2101,23 @@ qflex_status qflex_plan_profile(qflex_plan p, int32_t mode, qflex_profile* out) 
     if (out) {
       if (qflex_status st = drain()) return st;
       *out = pr.tot;
+    }
+    return QFLEX_OK;
+  });
+}
+
+qflex_status qflex_plan_profile_shapes(qflex_plan p, qflex_profile_shape* out, int64_t cap, int64_t* n) {
+  return guarded([&]() -> qflex_status {
+    if (!p || !n) return fail(QFLEX_ERR_ARG, "null plan or count");
+    if (cap < 0 || (cap > 0 && !out)) return fail(QFLEX_ERR_ARG, "bad output array");
+    if (p->device < 0) return fail(QFLEX_ERR_UNSUPPORTED, "host-only plan");
+    Prof& pr = p->prof;
+    if (!pr.recs.empty()) return fail(QFLEX_ERR_ARG, "launches not yet read: call qflex_plan_profile with out first");
+    *n = int64_t(pr.shapes.size());
+    int64_t i = 0;
+    for (const auto& kv : pr.shapes) {
+      if (i >= cap) break;
+      out[i++] = kv.second;
     }
     return QFLEX_OK;
   });

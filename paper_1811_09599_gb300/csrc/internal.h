@@ -171,6 +171,39 @@ __device__ __forceinline__ void store_bytes(void* dst, const void* src) {
   }
 }
 __device__ __forceinline__ uint32_t tf32_rna(float x);
+// Two values rounded to nearest even into one packed pair of 16-bit values
+// (the first at the lower address) by one paired conversion, and the pair
+// widened back to fp32 (exact).  The rounding is the same as two single
+// conversions'; one paired instruction per two values halves the conversion
+// work of the plane writers below.
+template <int FMT>
+__device__ __forceinline__ uint32_t pack2_rn(float a, float b) {
+  if constexpr (FMT == kFmtFP16) {
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  } else {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+}
+template <int FMT>
+__device__ __forceinline__ float2 unpack2(uint32_t w) {
+  if constexpr (FMT == kFmtFP16) {
+    return __half22float2(*reinterpret_cast<const __half2*>(&w));
+  } else {
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+  }
+}
+template <int NW>
+__device__ __forceinline__ void store_words(void* dst, const uint32_t* w) {
+  if constexpr (NW == 4) {
+    *static_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+  } else if constexpr (NW == 2) {
+    *static_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
+  } else {
+    *static_cast<uint32_t*>(dst) = w[0];
+  }
+}
 // V consecutive entries (positions o .. o + V - 1 of every plane) written
 // as the 3M planes of put_entry, one vector store per plane; o is a
 // multiple of V.  Same arithmetic as put_entry, entry by entry.
@@ -182,7 +215,21 @@ __device__ __forceinline__ void put_planes_vec(void* out, int64_t o, const float
     float x[V];
 #pragma unroll
     for (int j = 0; j < V; ++j) x[j] = p == 0 ? v[j].x : (p == 1 ? v[j].y : v[j].x + v[j].y);
-    if constexpr (FMT == kFmtFP16) {
+    if constexpr ((FMT == kFmtFP16 || FMT == kFmtBF16) && V >= 2) {
+      // paired conversions: hi = rn(x), lo = rn(x - hi) (x - hi is exact)
+      uint32_t hi[V / 2], lo[V / 2];
+#pragma unroll
+      for (int j = 0; j < V / 2; ++j) {
+        const float y0 = FMT == kFmtFP16 ? x[2 * j] * scale : x[2 * j];   // exact: a power of two
+        const float y1 = FMT == kFmtFP16 ? x[2 * j + 1] * scale : x[2 * j + 1];
+        hi[j] = pack2_rn<FMT>(y0, y1);
+        const float2 h = unpack2<FMT>(hi[j]);
+        lo[j] = pack2_rn<FMT>(y0 - h.x, y1 - h.y);
+      }
+      uint16_t* q = static_cast<uint16_t*>(out);
+      store_words<V / 2>(q + int64_t(p * nsplit) * plane + o, hi);
+      if (nsplit == 2) store_words<V / 2>(q + int64_t(p * 2 + 1) * plane + o, lo);
+    } else if constexpr (FMT == kFmtFP16) {
       __half hi[V], lo[V];
 #pragma unroll
       for (int j = 0; j < V; ++j) {

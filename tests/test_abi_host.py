@@ -84,6 +84,9 @@ def test_host_plan_refuses_compute(Plan):
     with pytest.raises(QFlexError) as e:
         check(p.lib.qflex_amplitudes(p.handle, None, None, 0, None, 0, None, None))
     assert "UNSUPPORTED" in str(e.value)
+    with pytest.raises(QFlexError) as e:
+        p.profile_shapes()
+    assert "UNSUPPORTED" in str(e.value)
 
 
 def test_validation_errors(Plan):

@@ -83,3 +83,28 @@ def test_fused_fp16_planes_vs_oracle(api):
         plan.sync()
         ref = np.stack([NW.slice_amplitudes(prob, b, sl, tensors=tensors) for b in bits])
         assert amp_error(got, ref, prob.n, 1.0 / 256) < TOL["fp16x3"], sl
+
+
+def test_profile_by_shape(api):
+    """Profiled launches by product shape add up to the per-class totals, and
+    every recorded shape is a product of the plan's schedule (the records the
+    bench's per-shape roofline is computed from)."""
+    prob = grid_problem(5, 5, 32, 3, r0=2, c0=2, cuts=True, tile_rows=2, tile_cols=2, rotations=True)
+    bs = torch.from_numpy(random_bitstrings(prob.n, 2, 3)).cuda()
+    th = torch.from_numpy(prob.circuit.angles).cuda()
+    plan = api.Plan(prob, "bf16x3", device=0)
+    plan.amplitudes(bs, th)
+    plan.profile_start(["gemm_fp32", "gemm_tc"])
+    plan.amplitudes(bs, th)
+    tot = plan.profile_stop()
+    shapes = plan.profile_shapes()
+    plan.sync()
+    sched = {(s["M"], s["N"], s["K"], s["kernel"] == "tensor_cores") for s in plan.steps(2)}
+    for cls in ("gemm_fp32", "gemm_tc"):
+        rows = [r for r in shapes if r["cls"] == cls]
+        assert sum(r["launches"] for r in rows) == tot[cls]["launches"]
+        assert np.isclose(sum(r["ms"] for r in rows), tot[cls]["ms"], rtol=1e-9, atol=1e-9)
+        assert np.isclose(sum(r["mma_flops"] for r in rows), tot[cls]["mma_flops"], rtol=1e-12)
+        for r in rows:
+            assert (r["M"], r["N"], r["K"], cls == "gemm_tc") in sched, r
+    assert tot["gemm_tc"]["launches"] > 0 and any(r["out_planes"] for r in shapes)
