@@ -170,7 +170,7 @@ typedef struct {
   int32_t tc_wide;           /* kernel 4 with split operands: per k-step one MMA of width
                                 2 bn over B hi and B lo ([hi.hi | hi.lo]) and one of width
                                 bn (lo.hi) instead of three of width bn; chosen for bn = 64,
-                                and for bn = 128 when K >= 2048 */
+                                and for bn = 128 when K >= 256 */
 } qflex_step_info;
 
 int32_t qflex_abi_version(void);

@@ -408,9 +408,9 @@ cudaError_t launch_cgemm_thin_planes(int64_t M, int64_t N, int64_t K, const floa
 // Form of the split (nsplit = 2) tensor-core product: true = per k-step one
 // MMA of width 2 bn over the adjacent B hi and B lo tiles ([hi.hi | hi.lo])
 // plus one of width bn (lo.hi); false = three MMAs of width bn.  The wide
-// form is taken for bn = 64 and for bn = 128 when K >= 2048 (with bn = 128
+// form is taken for bn = 64 and for bn = 128 when K >= 256 (with bn = 128
 // it leaves room in TMEM for two accumulators instead of three, which costs
-// more than it gains on short K).
+// more than it gains when K is a single k-block).
 bool tc_wide_mma(int nsplit, int bn, int64_t K);
 bool tc_encode_maps(int kind, int nsplit, int bn, const void* a_planes, int64_t M,
                     const void* b_planes, int64_t N, int64_t K, TcGemmMaps* maps);

@@ -311,6 +311,28 @@ __global__ void __launch_bounds__(256) k_cgemm_thin2(int64_t M, int N, int K, co
   };
   for (int u = 0; u < T2_NST - 1; ++u) issue(u);
   const int row = t >> 2, cq = t & 3;
+  // plane output: the destination of (row gm, column n) is the sum of the
+  // weights of the set bits of gm and n.  Per thread, the weights of its
+  // row within a tile (bits 0-5 of gm) and of its four columns are summed
+  // once; the weights of the tile index (bits 6-19 of gm) come from two
+  // 128-entry tables built once per block.
+  int64_t d_low = 0, dn[4] = {0, 0, 0, 0};
+  int64_t* dtab = reinterpret_cast<int64_t*>(As + size_t(T2_NST) * T2_RT * LD);   // [2][128]
+  if constexpr (PO) {
+    for (int b = 0; b < 6 && b < po.mbits; ++b)
+      if ((row >> b) & 1) d_low += po.wm[b];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      for (int b = 0; b < po.nbits; ++b)
+        if (((cq * 4 + j) >> b) & 1) dn[j] += po.wn[b];
+    const int half = t >> 7, v = t & 127;
+    int64_t d = 0;
+    for (int i = 0; i < 7; ++i) {
+      const int b = 6 + 7 * half + i;
+      if (b < po.mbits && ((v >> i) & 1)) d += po.wm[b];
+    }
+    dtab[t] = d;   // visible after the first unit's barrier
+  }
   float2 P[4], Q[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) P[j] = Q[j] = make_float2(0.f, 0.f);
@@ -349,16 +371,10 @@ __global__ void __launch_bounds__(256) k_cgemm_thin2(int64_t M, int N, int K, co
 #pragma unroll
           for (int j = 0; j < 4; ++j)
             if (cq * 4 + j < N) mx = fmaxf(mx, fmaxf(fabsf(o[j].x), fmaxf(fabsf(o[j].y), fabsf(o[j].x + o[j].y))));
-          int64_t d0 = 0;
-          for (int b = 0; b < po.mbits; ++b)
+          const int64_t tile = gm / T2_RT;
+          int64_t d0 = d_low + dtab[tile & 127] + dtab[128 + ((tile >> 7) & 127)];
+          for (int b = 20; b < po.mbits; ++b)
             if ((gm >> b) & 1) d0 += po.wm[b];
-          int64_t dn[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            dn[j] = 0;
-            for (int b = 0; b < po.nbits; ++b)
-              if (((cq * 4 + j) >> b) & 1) dn[j] += po.wn[b];
-          }
           if (po.n_fast && po.vec >= 4 && cq * 4 + 3 < N && d0 + dn[0] + 4 <= po.plane) {
             if (po.fmt == kFmtTF32)
               put_planes_vec<kFmtTF32, 4>(po.base, d0 + dn[0], o, po.nsplit, po.plane);
@@ -413,8 +429,9 @@ __global__ void __launch_bounds__(256) k_cgemm_thin2(int64_t M, int N, int K, co
 template <int KC, bool PO>
 cudaError_t launch_thin2(int64_t M, int64_t N, int64_t K, const float2* A, const float2* B, float2* C,
                          const TcPlaneOut& po, cudaStream_t s) {
-  const size_t smem = size_t(K) * 16 * sizeof(float2) + size_t(T2_NST) * T2_RT * (KC + 2) * sizeof(float2);
-  // at most 512 x 16 x 8 + 4 x 64 x 34 x 8 bytes (K <= 512): opt in once per device
+  const size_t smem = size_t(K) * 16 * sizeof(float2) + size_t(T2_NST) * T2_RT * (KC + 2) * sizeof(float2) +
+                      (PO ? 256 * sizeof(int64_t) : 0);
+  // at most 512 x 16 x 8 + 4 x 64 x 34 x 8 + 2048 bytes (K <= 512): opt in once per device
   int dev = 0, sms = 148, occ = 0;
   cudaGetDevice(&dev);
   static std::mutex mu;

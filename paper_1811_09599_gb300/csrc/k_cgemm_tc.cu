@@ -670,7 +670,7 @@ cudaError_t launch_t(const TcGemmMaps& maps, int64_t M, int64_t N, int64_t K, fl
 
 bool tc_available() { return get_encode() != nullptr; }
 
-bool tc_wide_mma(int nsplit, int bn, int64_t K) { return nsplit == 2 && (bn == 64 || K >= 2048); }
+bool tc_wide_mma(int nsplit, int bn, int64_t K) { return nsplit == 2 && (bn == 64 || K >= 256); }
 
 bool tc_encode_maps(int kind, int nsplit, int bn, const void* a_planes, int64_t M,
                     const void* b_planes, int64_t N, int64_t K, TcGemmMaps* maps) {

@@ -388,17 +388,19 @@ def test_bf16x3_plane_format_by_chain_length(Plan):
 def test_wide_mma_choice(Plan):
     """Split tensor-core products take one MMA of width 2 bn ([hi.hi | hi.lo])
     plus one of width bn per k-step for 64-wide tiles and, with 128-wide
-    tiles, for K >= 2048; otherwise three of width bn.  In the 7x7 1+32+1
-    plan that puts the 4096^3 products on the wide form and the K = 256
-    region absorbs on the three-MMA form; unsplit precisions never use it."""
+    tiles, for K >= 256; otherwise three of width bn.  In the 7x7 1+32+1
+    plan that puts the 4096^3 products and the K = 256 region absorbs on the
+    wide form and the K = 16 products on the three-MMA form; unsplit
+    precisions never use it."""
     for prec in ("bf16x3", "fp16x3", "tf32x3", "bf16", "fp32"):
         steps = Plan(c2_problem(0), prec, device=-1).steps(1)
         for s in steps:
             split = prec in ("bf16x3", "fp16x3", "tf32x3")
-            want = s["kernel"] == "tensor_cores" and split and (s["bn"] == 64 or s["K"] >= 2048)
+            want = s["kernel"] == "tensor_cores" and split and (s["bn"] == 64 or s["K"] >= 256)
             assert s["tc_wide"] == int(want), (prec, s["M"], s["N"], s["K"], s["bn"])
         if prec == "bf16x3":
             big = [s for s in steps if (s["M"], s["N"], s["K"]) == (4096, 4096, 4096)]
             absorb = [s for s in steps if (s["M"], s["N"], s["K"]) == (65536, 256, 256)]
             assert big and absorb
-            assert all(s["tc_wide"] for s in big) and not any(s["tc_wide"] for s in absorb)
+            k16 = [s for s in steps if s["kernel"] == "tensor_cores" and s["K"] == 16 and s["bn"] == 128]
+            assert k16 and all(s["tc_wide"] for s in big + absorb) and not any(s["tc_wide"] for s in k16)

@@ -98,10 +98,10 @@ def test_cgemm_tensor_core(K, prec, tol):
 
 
 # split products in both MMA forms: the wide form (64-wide tiles, and
-# 128-wide tiles with K >= 2048: two accumulators in turn) with ragged M and
-# N, a K tail, several tiles per SM; the three-MMA form just below K = 2048
+# 128-wide tiles with K >= 256: two accumulators in turn) with ragged M and
+# N, a K tail, several tiles per SM; the three-MMA form just below K = 256
 WIDE_SHAPES = [(256, 48, 16), (1000, 100, 200), (300, 128, 2048), (2100, 200, 2056), (8192, 1024, 2048),
-               (4096, 256, 2040), (640, 130, 4096)]
+               (4096, 256, 248), (65536, 256, 256), (640, 130, 4096)]
 
 
 @pytest.mark.parametrize("prec,tol", [("tf32x3", 1e-5), ("bf16x3", 1e-4), ("fp16x3", 1e-5)])
