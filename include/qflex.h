@@ -156,7 +156,7 @@ typedef struct {
   int32_t dst, src;          /* tensor ids of the ordering step (result keeps dst) */
   int64_t M, N, K;           /* C[M][N] = sum_k A[M][k] B[N][k] */
   int32_t kernel;            /* 0 FP32 tiled, 1 FP32 thin (N <= 16), 2 FP32 thin (N <= 32),
-                                3 FP32 warp per row, 4 tensor cores */
+                                3 FP32 block per row (few rows, long K), 4 tensor cores */
   int32_t bn;                /* tensor-core tile width (kernel 4) */
   int32_t a_direct, b_direct;/* operand read in place, without a permutation */
   int64_t runs;              /* executions in one call over n_bs bitstrings and the slices */

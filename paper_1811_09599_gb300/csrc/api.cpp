@@ -1128,7 +1128,7 @@ std::vector<int> cat(const std::vector<int>& a, const std::vector<int>& b) {
 // Split-K of a reverse GEMM.  The reverse pass meets products with few
 // outputs and a long K (W_B = W_C^T A for a step whose dst has many free
 // entries: e.g. 256 x 256 outputs over K = 65536), which as one output tile
-// per CTA or one warp per row use a handful of SMs.  Their K range is cut
+// per CTA or one block per row use a handful of SMs.  Their K range is cut
 // into `splits` parts whose partial products land in the gradient scratch
 // and are summed in split order (deterministic): enough parts to give every
 // SM work, none shorter than 8 k-blocks (tensor cores) or 2048 entries (CUDA
@@ -1145,7 +1145,7 @@ int bwd_splits(const Sub& p, const BwdGemm& g) {
   const int64_t cgs = (g.N + 15) / 16;
   if (g.route == 1) {
     const bool rowwarp = g.K >= 64 && ((g.M + 255) / 256) * cgs < 256;
-    const int64_t warps = g.M * cgs;
+    const int64_t warps = g.M * cgs * 8;   // a block of 8 warps per (row, 16 columns)
     if (!rowwarp || warps * 4 > kSMs * 32 || g.K < 8192) return 1;
     return int(std::max<int64_t>(1, std::min<int64_t>((kSMs * 32 + warps - 1) / warps, g.K / 2048)));
   }

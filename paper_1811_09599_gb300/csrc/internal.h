@@ -353,8 +353,8 @@ cudaError_t launch_cgemm_simt(int64_t M, int64_t N, int64_t K, const float2* A,
 // Same product for thin shapes (N <= 32): one thread per output row.
 cudaError_t launch_cgemm_thin(int64_t M, int64_t N, int64_t K, const float2* A,
                               const float2* B, float2* C, cudaStream_t s);
-// Split-K form of the warp-per-row product (few outputs, long K): warps over
-// (row, 16-column group, split), each summing its K range of `chunk`
+// Split-K form of the block-per-row product (few outputs, long K): blocks
+// over (row, 16-column group, split), each summing its K range of `chunk`
 // entries into the partial product P + split M N.
 cudaError_t launch_cgemm_rowwarp_split(int64_t M, int64_t N, int64_t K, const float2* A,
                                        const float2* B, float2* P, int splits, cudaStream_t s);

@@ -195,21 +195,25 @@ __global__ void __launch_bounds__(256, 2) k_cgemm_thin(int64_t M, int64_t N, int
   }
 }
 
-// Warp-per-row form for few rows and a long K (too few blocks for the
-// row-per-thread form): the lanes split K, then reduce across the warp.
-// With splits > 1, warp w also takes split w / (M cgs): the K range
-// [split chunk, (split + 1) chunk), chunk = ceil(K / splits), possibly
-// empty, into the partial product C + split M N (every split writes its
-// whole partial, zeros for an empty range).
+// Block-per-row form for few rows and a long K (the row-per-thread forms
+// would leave most SMs idle): block b computes row m and 16 output columns
+// n0 .. n0 + 15 of split `split` ((split, m, column group) = b); its 8 warps
+// take interleaved 32-entry runs of the K range, every lane accumulating in
+// k order, then each warp sums its lanes with shuffles and the 8 warp sums
+// are added in warp order (deterministic).  With splits > 1 the K range of
+// split s is [s chunk, (s + 1) chunk), chunk = ceil(K / splits), possibly
+// empty, written as the partial product C + s M N (zeros for an empty
+// range).
 __global__ void __launch_bounds__(256) k_cgemm_rowwarp(int64_t M, int64_t N, int64_t K,
                                                       const float2* __restrict__ A,
                                                       const float2* __restrict__ B,
                                                       float2* __restrict__ C, int splits) {
   pdl_wait();
-  const int lane = threadIdx.x & 31;
+  __shared__ float2 part[8][16];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t cgs = (N + 15) / 16;
-  const int64_t w_all = int64_t(blockIdx.x) * 8 + (threadIdx.x >> 5);
-  const int64_t split = w_all / (M * cgs), w = w_all % (M * cgs);
+  const int64_t item = blockIdx.x;
+  const int64_t split = item / (M * cgs), w = item % (M * cgs);
   if (split >= splits) return;
   const int64_t m = w / cgs, n0 = (w % cgs) * 16;
   const int64_t chunk = (K + splits - 1) / splits;
@@ -220,7 +224,7 @@ __global__ void __launch_bounds__(256) k_cgemm_rowwarp(int64_t M, int64_t N, int
   unsigned long long P[16], Q[16];
 #pragma unroll
   for (int n = 0; n < 16; ++n) P[n] = Q[n] = 0ull;
-  for (int64_t k = k_lo + lane; k < k_hi; k += 32) {
+  for (int64_t k = k_lo + warp * 32 + lane; k < k_hi; k += 256) {
     const float2 a = __ldg(A + m * K + k);
     const unsigned long long ax = pk(a.x, a.x), ay = pk(a.y, a.y);
 #pragma unroll
@@ -241,7 +245,17 @@ __global__ void __launch_bounds__(256) k_cgemm_rowwarp(int64_t M, int64_t N, int
       re += __shfl_xor_sync(0xffffffffu, re, o);
       im += __shfl_xor_sync(0xffffffffu, im, o);
     }
-    if (lane == n && n < nn) C[m * N + n0 + n] = make_float2(re, im);
+    if (lane == n) part[warp][n] = make_float2(re, im);
+  }
+  __syncthreads();
+  if (threadIdx.x < nn) {
+    float2 acc = part[0][threadIdx.x];
+#pragma unroll
+    for (int v = 1; v < 8; ++v) {
+      acc.x += part[v][threadIdx.x].x;
+      acc.y += part[v][threadIdx.x].y;
+    }
+    C[m * N + n0 + threadIdx.x] = acc;
   }
 }
 
@@ -503,8 +517,9 @@ cudaError_t launch_cgemm_rowwarp_split(int64_t M, int64_t N, int64_t K, const fl
                                        float2* P, int splits, cudaStream_t s) {
   if (M <= 0 || N <= 0 || splits < 1 || K <= 0) return cudaErrorInvalidValue;
   const int64_t cgs = (N + 15) / 16;
-  const int64_t warps = M * cgs * splits;
-  return launch_pdl(k_cgemm_rowwarp, dim3(unsigned((warps + 7) / 8)), dim3(256), 0, s, M, N, K, A, B, P, splits);
+  const int64_t blocks = M * cgs * splits;
+  if (blocks > INT32_MAX) return cudaErrorInvalidValue;
+  return launch_pdl(k_cgemm_rowwarp, dim3(unsigned(blocks)), dim3(256), 0, s, M, N, K, A, B, P, splits);
 }
 
 cudaError_t launch_splitk_reduce(const float2* P, int splits, int64_t n, float2* C, cudaStream_t s) {
@@ -518,8 +533,7 @@ cudaError_t launch_cgemm_thin(int64_t M, int64_t N, int64_t K, const float2* A, 
   if (M <= 0 || N <= 0) return cudaSuccess;
   const int64_t cgs = (N + 15) / 16;
   if (K >= 64 && ((M + 255) / 256) * cgs < 256) {   // few rows, long K: warp per row
-    const int64_t warps = M * cgs;
-    return launch_pdl(k_cgemm_rowwarp, dim3(unsigned((warps + 7) / 8)), dim3(256), 0, s, M, N, K, A, B, C, 1);
+    return launch_pdl(k_cgemm_rowwarp, dim3(unsigned(M * cgs)), dim3(256), 0, s, M, N, K, A, B, C, 1);
   }
   if (thin_pipelined(M, N, K) && (reinterpret_cast<uintptr_t>(A) & 15) == 0) {
     static const TcPlaneOut none{};

@@ -80,7 +80,11 @@ SHAPES = [(128, 128, 64), (256, 128, 128), (300, 200, 72), (128, 64, 8), (1024, 
           (4096, 17, 16), (2048, 256, 16),
           # pipelined thin form (N <= 16, even K <= 512): ragged rows, a K
           # tail chunk, K = 2, odd N, the largest K, and K = 514 (older form)
-          (1000, 5, 6), (777, 16, 40), (3000, 13, 512), (129, 16, 2), (65, 1, 200), (300, 16, 514)]
+          (1000, 5, 6), (777, 16, 40), (3000, 13, 512), (129, 16, 2), (65, 1, 200), (300, 16, 514),
+          # block-per-row form (few rows, K >= 64): the 7x7 plan's 256 x 32 x 256 and
+          # 32 x 2 x 256, a ragged second column group, one output, K not a
+          # multiple of the block's 256-entry stride
+          (256, 32, 256), (32, 2, 256), (5, 20, 1000), (1, 1, 64), (3, 17, 4099)]
 
 
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-5)])
