@@ -768,7 +768,10 @@ qflex_status build_plan(const qflex_problem* pr, Sub& p) {
     if (s.M * s.N > (int64_t(1) << 34) || s.M * s.K > (int64_t(1) << 34) || s.N * s.K > (int64_t(1) << 34))
       return fail(QFLEX_ERR_PLAN, "intermediate tensor larger than 2^34 entries at step " + std::to_string(i));
     s.tc = tc_prec && tc_route(s.M, s.N, s.K);
-    s.bn = s.N >= 128 ? 128 : 64;
+    // 128-wide tiles when they fill the SMs; 64-wide for products of fewer
+    // than 152 such tiles (twice the CTAs, half the per-tile latency: what
+    // the autotuner picks for every such shape of the 7x7 plan)
+    s.bn = (s.N >= 128 && ((s.M + 127) / 128) * ((s.N + 127) / 128) >= 152) ? 128 : 64;
     s.ml = ml;
     s.nl = nl;
     s.sh = shared;
