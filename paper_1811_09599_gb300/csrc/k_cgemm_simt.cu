@@ -48,12 +48,12 @@ __global__ void __launch_bounds__(256) k_cgemm_simt(int64_t M, int64_t N, int64_
   const int tid = threadIdx.x;
   const int tx = tid % (BN / TN), ty = tid / (BN / TN);
   const int64_t m0 = int64_t(blockIdx.y) * BM, n0 = int64_t(blockIdx.x) * BN;
-  // p_* / q_*: the current K tile's partial sums over its even and odd k
-  // (two chains of BK / 2 k each), added once per tile to the running sums
-  // acc_* with Kahan's compensated summation (c_*: the compensation), so the
-  // FP32 rounding error of an output does not grow with the number of tiles.
+  // p_*: the current K tile's partial sums, added once per tile to the
+  // running sums acc_* with Kahan's compensated summation (c_*: the
+  // compensation), so the FP32 rounding error of an output does not grow
+  // with the number of tiles.
   float acc_re[TM][TN], acc_im[TM][TN], c_re[TM][TN], c_im[TM][TN];
-  float p_re[TM][TN], p_im[TM][TN], q_re[TM][TN], q_im[TM][TN];
+  float p_re[TM][TN], p_im[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256) k_cgemm_simt(int64_t M, int64_t N, int64_
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int j = 0; j < TN; ++j) p_re[i][j] = p_im[i][j] = q_re[i][j] = q_im[i][j] = 0.f;
+      for (int j = 0; j < TN; ++j) p_re[i][j] = p_im[i][j] = 0.f;
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       float2 a[TM], b[TN];
@@ -87,24 +87,22 @@ __global__ void __launch_bounds__(256) k_cgemm_simt(int64_t M, int64_t N, int64_
         b[2 * i] = make_float2(vb.x, vb.y);
         b[2 * i + 1] = make_float2(vb.z, vb.w);
       }
-      float(&pr)[TM][TN] = (kk & 1) ? q_re : p_re;
-      float(&pi)[TM][TN] = (kk & 1) ? q_im : p_im;
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
-          pr[i][j] = fmaf(a[i].x, b[j].x, pr[i][j]);
-          pr[i][j] = fmaf(-a[i].y, b[j].y, pr[i][j]);
-          pi[i][j] = fmaf(a[i].x, b[j].y, pi[i][j]);
-          pi[i][j] = fmaf(a[i].y, b[j].x, pi[i][j]);
+          p_re[i][j] = fmaf(a[i].x, b[j].x, p_re[i][j]);
+          p_re[i][j] = fmaf(-a[i].y, b[j].y, p_re[i][j]);
+          p_im[i][j] = fmaf(a[i].x, b[j].y, p_im[i][j]);
+          p_im[i][j] = fmaf(a[i].y, b[j].x, p_im[i][j]);
         }
     }
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
       for (int j = 0; j < TN; ++j) {
-        kahan_add(acc_re[i][j], c_re[i][j], __fadd_rn(p_re[i][j], q_re[i][j]));
-        kahan_add(acc_im[i][j], c_im[i][j], __fadd_rn(p_im[i][j], q_im[i][j]));
+        kahan_add(acc_re[i][j], c_re[i][j], p_re[i][j]);
+        kahan_add(acc_im[i][j], c_im[i][j], p_im[i][j]);
       }
     __syncthreads();
   }
