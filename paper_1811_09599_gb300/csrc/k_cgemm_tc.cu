@@ -222,6 +222,56 @@ __device__ __forceinline__ bool write_sub_columns(const TcPlaneOut& po, const fl
   return bad;
 }
 
+// Plane output of this warp's HALF columns of a tile, 16 at a time through
+// its staging area: column mode (V consecutive columns per vector store).
+template <int FMT, int NSPLIT, int V, int HALF>
+__device__ __forceinline__ bool store_tile_columns(const TcPlaneOut& po, float2* st, const float (&re)[HALF],
+                                                   const float (&im)[HALF], int lane, int64_t drow, int64_t row0,
+                                                   int64_t M, int64_t n0, int64_t N, int64_t dn_hi,
+                                                   const int64_t* s_dn, int col0, float scale) {
+  bool bad = false;
+#pragma unroll
+  for (int sub = 0; sub < HALF / 16; ++sub) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) st[lane * 16 + (j ^ (lane & 15))] = make_float2(re[sub * 16 + j], im[sub * 16 + j]);
+    __syncwarp();
+    const int colb = col0 + sub * 16;
+    bad |= write_sub_columns<FMT, NSPLIT, V>(po, st, lane, drow, row0, M, n0 + colb, N, dn_hi, s_dn, colb, scale);
+    __syncwarp();
+  }
+  return bad;
+}
+// Row mode: each lane its own row (`own`: inside M), column by column from
+// the staging area, so that consecutive lanes write consecutive
+// destinations.
+template <int FMT, int NSPLIT, int HALF>
+__device__ __forceinline__ bool store_tile_rows(const TcPlaneOut& po, float2* st, const float (&re)[HALF],
+                                                const float (&im)[HALF], int lane, int64_t drow, bool own, int64_t n0,
+                                                int64_t N, int64_t dn_hi, const int64_t* s_dn, int col0, float scale) {
+  bool bad = false;
+#pragma unroll
+  for (int sub = 0; sub < HALF / 16; ++sub) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) st[lane * 16 + (j ^ (lane & 15))] = make_float2(re[sub * 16 + j], im[sub * 16 + j]);
+    __syncwarp();
+    if (own) {
+#pragma unroll 4
+      for (int c = 0; c < 16; ++c) {
+        const int col = col0 + sub * 16 + c;
+        if (n0 + col < N) {
+          const int64_t d = drow + dn_hi + s_dn[col];
+          if (d >= 0 && d < po.plane)
+            put_entry<FMT>(po.base, d, st[lane * 16 + (c ^ (lane & 15))], NSPLIT, po.plane, scale);
+          else
+            bad = true;
+        }
+      }
+    }
+    __syncwarp();
+  }
+  return bad;
+}
+
 // Persistent: one CTA per SM walks the output tiles (tile += gridDim.x, N
 // fastest).  Block: warp 0 = TMA producer, warp 1 = TMEM owner + MMA issuer,
 // warps 4..11 = epilogue (two warps per TMEM lane quarter, each owning half of
@@ -526,44 +576,24 @@ __global__ void __launch_bounds__(THREADS, 1)
           mx *= unscale;
           if (lane == 0 && mx > 0.f) atomicMax(po.out_max, __float_as_uint(mx));
         }
-#pragma unroll
-        for (int sub = 0; sub < G::HALF / 16; ++sub) {
-#pragma unroll
-          for (int j = 0; j < 16; ++j)
-            st[lane * 16 + (j ^ (lane & 15))] = make_float2(re[sub * 16 + j], im[sub * 16 + j]);
-          __syncwarp();
-          if (po.n_fast) {
-            const int colb = col0 + sub * 16;
-            const int64_t row0 = m0 + q * 32, gn0 = n0 + colb;
-            if (KIND != 0 && po.vec == 8)
-              bad |= write_sub_columns<FMT, NSPLIT, (KIND != 0 ? 8 : 4)>(po, st, lane, drow, row0, M, gn0, N, dn_hi,
-                                                                         s_dn, colb, po_factor);
-            else if (po.vec >= 4)
-              bad |= write_sub_columns<FMT, NSPLIT, 4>(po, st, lane, drow, row0, M, gn0, N, dn_hi, s_dn, colb,
-                                                       po_factor);
-            else if (po.vec == 2)
-              bad |= write_sub_columns<FMT, NSPLIT, 2>(po, st, lane, drow, row0, M, gn0, N, dn_hi, s_dn, colb,
-                                                       po_factor);
-            else
-              bad |= write_sub_columns<FMT, NSPLIT, 1>(po, st, lane, drow, row0, M, gn0, N, dn_hi, s_dn, colb,
-                                                       po_factor);
-          } else if (gm_own < M) {
-            // each lane its own row, column by column: consecutive lanes are
-            // consecutive rows
-#pragma unroll 4
-            for (int c = 0; c < 16; ++c) {
-              const int col = col0 + sub * 16 + c;
-              if (n0 + col < N) {
-                const int64_t d = drow + dn_hi + s_dn[col];
-                if (d >= 0 && d < po.plane)
-                  put_entry<FMT>(po.base, d, st[lane * 16 + (c ^ (lane & 15))], NSPLIT, po.plane, po_factor);
-                else
-                  bad = true;
-              }
-            }
-          }
-          __syncwarp();
-        }
+        // the store form is chosen once per tile, so that the code of the
+        // form in use lies in one piece (instruction-cache locality)
+        const int64_t row0 = m0 + q * 32;
+        if (po.n_fast && KIND != 0 && po.vec == 8)
+          bad |= store_tile_columns<FMT, NSPLIT, (KIND != 0 ? 8 : 4), G::HALF>(po, st, re, im, lane, drow, row0, M,
+                                                                                 n0, N, dn_hi, s_dn, col0, po_factor);
+        else if (po.n_fast && po.vec >= 4)
+          bad |= store_tile_columns<FMT, NSPLIT, 4, G::HALF>(po, st, re, im, lane, drow, row0, M, n0, N, dn_hi, s_dn,
+                                                             col0, po_factor);
+        else if (po.n_fast && po.vec == 2)
+          bad |= store_tile_columns<FMT, NSPLIT, 2, G::HALF>(po, st, re, im, lane, drow, row0, M, n0, N, dn_hi, s_dn,
+                                                             col0, po_factor);
+        else if (po.n_fast)
+          bad |= store_tile_columns<FMT, NSPLIT, 1, G::HALF>(po, st, re, im, lane, drow, row0, M, n0, N, dn_hi, s_dn,
+                                                             col0, po_factor);
+        else
+          bad |= store_tile_rows<FMT, NSPLIT, G::HALF>(po, st, re, im, lane, drow, gm_own < M, n0, N, dn_hi, s_dn,
+                                                       col0, po_factor);
         if (bad && status) atomicOr(status, kDevBadIndex);
         continue;
       }
