@@ -327,20 +327,6 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   }
 
-  // Launched with programmatic stream serialization: the launch itself can
-  // be staged while the previous kernel on the stream runs; wait here for
-  // its completion (and the visibility of its writes) before anything else,
-  // then let the next such launch stage itself.
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-
-  // A CTA of an earlier launch gave up on a wait: skip the work (the status
-  // word stays set until the host reads and clears it).
-  __shared__ int s_skip;
-  if (threadIdx.x == 0) s_skip = status ? *reinterpret_cast<volatile int32_t*>(status) : 0;
-  __syncthreads();
-  if (s_skip) return;
-
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t n_nt = (N + BN - 1) / BN;
   const int64_t n_mt = (M + BM - 1) / BM;
@@ -357,6 +343,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     *kbe = min(nkb, *kbs + kps);
   };
 
+  // Set-up that reads nothing the previous kernel writes (barriers, TMEM,
+  // tensor-map prefetch) runs before the wait below, so that it overlaps the
+  // tail of the previous kernel on the stream.  (TMEM is free: a CTA of this
+  // kernel needs more shared memory than two CTAs can share an SM with, and
+  // no other kernel here uses TMEM.)
   if (threadIdx.x == 0) {
     for (int s = 0; s < G::NSTAGE; ++s) {
       mbar_init(smem_u32(&bars[s]), 1);
@@ -370,6 +361,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
+  if (warp == 0 && lane == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_a)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_b)) : "memory");
+  }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_holder)),
@@ -378,16 +373,27 @@ __global__ void __launch_bounds__(THREADS, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
+
+  // Launched with programmatic stream serialization: the launch itself can
+  // be staged while the previous kernel on the stream runs; wait here for
+  // its completion (and the visibility of its writes) before reading any
+  // input, then let the next such launch stage itself.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+
+  // A CTA of an earlier launch gave up on a wait: skip the work (the status
+  // word stays set until the host reads and clears it).
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = status ? *reinterpret_cast<volatile int32_t*>(status) : 0;
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
 
+  if (!s_skip) {
   if (warp < EPI_WARP0) {
   asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_LOW));
   if (warp == 0) {
     if (lane == 0) {
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_a)) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_b)) : "memory");
       int i = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
@@ -618,6 +624,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
   }
+  }   // !s_skip
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
