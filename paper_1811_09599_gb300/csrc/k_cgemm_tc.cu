@@ -193,7 +193,9 @@ __device__ __forceinline__ void tile_origin(int64_t tile, int64_t n_mt, int64_t 
   *n0 = (r / rows) * BN;
 }
 
-// Column-mode plane output of one staged 32 x 16 sub-block: V consecutive
+// Column-mode plane output of one staged 32 x 16 sub-block (row r's column
+// j in slot j ^ 2 (r % 8): both the 16-byte pair stores and the 16-byte
+// pair loads are free of bank conflicts): V consecutive
 // columns per lane (their destinations are consecutive), 16 / V lanes per
 // row; returns whether a destination fell outside the planes.
 template <int FMT, int NSPLIT, int V>
@@ -210,9 +212,20 @@ __device__ __forceinline__ bool write_sub_columns(const TcPlaneOut& po, const fl
     if (row0 + r < M && gn0 + c < N) {
       const int64_t d = dr + dn_hi + s_dn[colb + c];
       if (d >= 0 && d + V <= po.plane) {
+        // staged with column pairs kept adjacent (slot = column ^ 2 (row % 8)):
+        // V >= 2 columns are read as 16-byte pairs
         float2 v[V];
+        const int swz = (r & 7) << 1;
+        if constexpr (V >= 2) {
 #pragma unroll
-        for (int j = 0; j < V; ++j) v[j] = st[r * 16 + ((c + j) ^ (r & 15))];
+          for (int j = 0; j < V; j += 2) {
+            const float4 w = *reinterpret_cast<const float4*>(&st[r * 16 + ((c + j) ^ swz)]);
+            v[j] = make_float2(w.x, w.y);
+            v[j + 1] = make_float2(w.z, w.w);
+          }
+        } else {
+          v[0] = st[r * 16 + (c ^ swz)];
+        }
         put_planes_vec<FMT, V>(po.base, d, v, NSPLIT, po.plane, scale);
       } else {
         bad = true;
@@ -233,7 +246,9 @@ __device__ __forceinline__ bool store_tile_columns(const TcPlaneOut& po, float2*
 #pragma unroll
   for (int sub = 0; sub < HALF / 16; ++sub) {
 #pragma unroll
-    for (int j = 0; j < 16; ++j) st[lane * 16 + (j ^ (lane & 15))] = make_float2(re[sub * 16 + j], im[sub * 16 + j]);
+    for (int j = 0; j < 16; j += 2)   // column pairs stay adjacent: 16-byte stores
+      *reinterpret_cast<float4*>(&st[lane * 16 + (j ^ ((lane & 7) << 1))]) =
+          make_float4(re[sub * 16 + j], im[sub * 16 + j], re[sub * 16 + j + 1], im[sub * 16 + j + 1]);
     __syncwarp();
     const int colb = col0 + sub * 16;
     bad |= write_sub_columns<FMT, NSPLIT, V>(po, st, lane, drow, row0, M, n0 + colb, N, dn_hi, s_dn, colb, scale);
