@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define QFLEX_ABI_VERSION 3
+#define QFLEX_ABI_VERSION 4
 
 typedef struct qflex_plan_s* qflex_plan;
 

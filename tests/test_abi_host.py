@@ -29,7 +29,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_abi_version(lib):
-    assert lib.qflex_abi_version() == 3
+    assert lib.qflex_abi_version() == 4
 
 
 @pytest.fixture
