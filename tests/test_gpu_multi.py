@@ -91,3 +91,35 @@ def test_mixed_problems_one_call_vs_statevector(api):
         got = amps[lay["amps"][k]:lay["amps"][k + 1]].reshape(n_bs, -1)
         ref = SV.amplitudes(p.circuit, bits[k], p.open_tile)
         assert amp_error(got, ref, p.n) < TOL["bf16x3"], k
+
+
+def test_full_rotation_batch_small_members_vs_statevector(api):
+    """The whole 256-circuit rotation batch of the benchmark (seed 0) in one
+    bf16x3 qflex_amplitudes_grad call: the amplitude of every member of at
+    most 20 qubits (85 of the 256) against the state vector, and every angle
+    gradient of the 17 members of 16 qubits against the state-vector adjoint."""
+    probs = rotation_batch(256, 0)
+    bits = [random_bitstrings(p.n, 1, 5000 + i) for i, p in enumerate(probs)]
+    flat_bits = torch.from_numpy(np.concatenate([b.reshape(-1) for b in bits])).cuda()
+    flat_th = torch.from_numpy(np.concatenate([p.circuit.angles for p in probs])).cuda()
+    multi = api.Plan(probs, "bf16x3", device=0)
+    g = torch.zeros((1, len(probs), 2), dtype=torch.float64, device="cuda")
+    g[..., 0] = 1.0
+    amps, grad = multi.amplitudes_grad(flat_bits, flat_th, g)
+    multi.sync()
+    amps, grad = amps.cpu().numpy(), grad.cpu().numpy()
+    lay = multi.layout(1)
+    multi.close()
+    small = [k for k, p in enumerate(probs) if p.n <= 20]
+    assert len(small) == 85
+    n_grad = 0
+    for k in small:
+        p = probs[k]
+        ref = SV.amplitudes(p.circuit, bits[k], [])
+        assert amp_error(amps[lay["amps"][k]:lay["amps"][k + 1]], ref, p.n) < TOL["bf16x3"], k
+        if p.n == 16:
+            gref = GR.statevector_adjoint(p.circuit, bits[k], [], np.ones((1, 1), dtype=np.complex128))
+            gk = grad[lay["params"][k]:lay["params"][k + 1]]
+            assert np.max(np.abs(gk - gref)) / (0.5 * np.sqrt(2.0 ** -p.n)) < 2e-4, k
+            n_grad += 1
+    assert n_grad == 17
