@@ -7,10 +7,12 @@
 // Each real operand is split x = hi + lo (tf32, bf16, or fp16 after an exact
 // power-of-two scaling) and each real product is taken as hi.hi + hi.lo +
 // lo.hi with FP32 accumulation in TMEM.
-// The operand planes (re, im, re+im; hi, lo) are written by the permutation
-// kernel (fused operand producer) in [plane][rows][K] layout.
+// The operand planes (re, im, re+im; hi, lo) are in [plane][rows][K]
+// layout, written by the permutation kernel, by the pipelined thin CUDA-core
+// product, or by this kernel's own epilogue for the next product.
 //
-// Kernel organisation (one 128 x BN output tile per CTA, cta_group::1):
+// Kernel organisation (128 x BN output tiles, walked persistently, one CTA
+// per SM, cta_group::1):
 //   warp 0      one lane issues TMA loads of (A hi, A lo, B hi, B lo) tiles
 //               for one (k-block, part) pair per pipeline stage;
 //   warp 1      allocates TMEM (two or three accumulators, used in turn) and
